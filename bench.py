@@ -1,0 +1,304 @@
+"""Benchmark: HFX force+stress evaluations per second on the 64-atom Si-like
+supercell (2x2x2 diamond, n_ao 13, n_abf 50, r_c 3.7 A, thresholds 1e-10).
+
+One step = one full evaluation of the hot path (block generation, two-step
+screening, Y build, both exchange products, force/stress/energy reduction)
+on a warm plan, at a new geometry (small seeded jitter within the pair-list
+skin, so every block, norm and screening decision is recomputed).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+`--impl reference` times the CPU oracle (the only reference that exists:
+the paper has no code) on a bounded sample of the same workload.
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "HFX force+stress evals/s & %tensor roofline, mixed vs FP64 at 1e-5 rel; p99 latency"
+UNIT = "evals/s"
+WORKLOAD = "si64: 2x2x2 diamond supercell, 64 atoms, n_ao 13, n_abf 50, r_c 3.7 A, theta 1e-10"
+
+
+def _env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.hw_slowdown",
+              "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
+              "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) != len(self.FIELDS):
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def fp64_gemm_peak(torch, dev):
+    """FP64 reference peak on this GPU: cuBLAS DGEMM 4096^3, best of 3
+    (the FP64 counterpart of the bf16 cuBLAS figure in MEASURED_PEAKS)."""
+    n = 4096
+    a = torch.randn(n, n, dtype=torch.float64, device=dev)
+    b = torch.randn(n, n, dtype=torch.float64, device=dev)
+    torch.matmul(a, b)
+    torch.cuda.synchronize()
+    best = 1e30
+    for _ in range(3):
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        torch.matmul(a, b)
+        e.record()
+        torch.cuda.synchronize()
+        best = min(best, s.elapsed_time(e) / 1e3)
+    del a, b
+    return 2.0 * n ** 3 / best / 1e12
+
+
+def geometry_sequence(w, n, seed=17, amp=0.01):
+    """Seeded small displacements (a relaxation-like sequence within the skin)."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    return [w.positions + rng.normal(0.0, amp, w.positions.shape) for _ in range(n)]
+
+
+def cpu_baseline(w, homes, reps=1):
+    """Time the oracle, as it stands, on `homes` home atoms of the workload.
+    Its work is a sum over home atoms, so evals/s = 1 / (t * N / k)."""
+    from oracle import OraclePlan
+    plan = OraclePlan(w)
+    t = time.time()
+    for _ in range(reps):
+        plan.evaluate(homes=list(range(homes)))
+    dt = (time.time() - t) / reps
+    per_eval = dt * w.n_atoms / homes
+    return {"value": 1.0 / per_eval, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{homes} of {w.n_atoms} home atoms of {w.name} ({dt:.1f} s), scaled by N/k; "
+                      f"numpy/OpenBLAS threads = cores"}
+
+
+def run_reference(args):
+    rank, world, _ = _env_rank()
+    if rank != 0:
+        return 0
+    from paper_2412_11081_gb300 import inputs
+    w = inputs.si_supercell(2)
+    from oracle import OraclePlan
+    plan = OraclePlan(w)
+    homes = 1
+    for _ in range(args.warmup):
+        plan.evaluate(homes=[0])
+    times = []
+    for k in range(args.steps):
+        t = time.time()
+        plan.evaluate(homes=[k % w.n_atoms])
+        times.append(time.time() - t)
+    per_eval = statistics.mean(times) * w.n_atoms / homes
+    value = 1.0 / per_eval
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": per_eval * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD, "sample": "one home atom per step, scaled by 64"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"{homes} of 64 home atoms per step ({statistics.mean(times):.1f} s)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = _env_rank()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2412_11081_gb300 import hfx, inputs
+    w = inputs.si_supercell(2)
+    stream = torch.cuda.current_stream(dev)
+    plan = hfx.Plan(w, stream=stream.cuda_stream, device=local)
+    geoms = geometry_sequence(w, args.warmup + args.steps + 8)
+    n = w.n_atoms
+    d_pos = [torch.tensor(g, dtype=torch.float64, device=dev) for g in geoms]
+    d_out = torch.zeros(1 + 3 * n + 9, dtype=torch.float64, device=dev)
+
+    # warm-up (also the stats of one step)
+    for k in range(args.warmup):
+        plan.evaluate_device(w.lattice, d_pos[k].data_ptr(), d_out.data_ptr(), stats=True)
+    st = plan.stats.as_dict()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    # ---- device-resident timing (value)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for k in range(args.steps):
+        plan.evaluate_device(w.lattice, d_pos[args.warmup + k].data_ptr(), d_out.data_ptr())
+    ev1.record(stream)
+    barrier()
+    ck = clocks.stop()
+    t_dev = ev0.elapsed_time(ev1) / 1e3
+    launches = st["kernel_launches"] * args.steps
+
+    # ---- end-to-end through the host entry point (H2D positions, D2H results)
+    pin_pos = [torch.tensor(g, dtype=torch.float64).pin_memory().numpy() for g in geoms]
+    barrier()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        plan.evaluate(w.lattice, pin_pos[args.warmup + k])
+    barrier()
+    t_e2e = time.perf_counter() - t0
+
+    # ---- per-stage times of the dominant kernel (CUDA events on the plan's stream)
+    plan.set_timing(True)
+    stage = {"ms_blocks": [], "ms_screen": [], "ms_y": [], "ms_term1": [], "ms_term2": [], "ms_reduce": []}
+    flops = None
+    for k in range(min(3, args.steps)):
+        plan.evaluate_device(w.lattice, d_pos[k].data_ptr(), d_out.data_ptr(), stats=True)
+        s2 = plan.stats.as_dict()
+        flops = s2
+        for key in stage:
+            stage[key].append(s2[key])
+    plan.set_timing(False)
+    stage_ms = {k: statistics.mean(v) for k, v in stage.items()}
+
+    t_max = t_dev
+    t_e2e_max = t_e2e
+    if dist is not None:
+        tt = torch.tensor([t_dev, t_e2e], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max, t_e2e_max = float(tt[0]), float(tt[1])
+    value = world * args.steps / t_max
+    e2e_value = world * args.steps / t_e2e_max
+
+    if rank == 0:
+        peaks = measured_peaks()
+        fp64_peak = fp64_gemm_peak(torch, dev)
+        # dominant kernel: the larger of the two exchange products
+        dom = "term1" if stage_ms["ms_term1"] >= stage_ms["ms_term2"] else "term2"
+        dom_flops = flops["flops_term1"] if dom == "term1" else flops["flops_term2"]
+        dom_ms = stage_ms["ms_" + dom]
+        achieved = dom_flops / (dom_ms / 1e3) / 1e12
+        roofline = {"kernel": "k_" + dom, "bound": "alu", "achieved": achieved, "peak": fp64_peak,
+                    "unit": "TFLOP/s", "frac": achieved / fp64_peak, "traffic": None,
+                    "peak_source": "FP64 cuBLAS DGEMM 4096^3 measured in this run (FP64 pipe; "
+                                   "MEASURED_PEAKS has no FP64 figure)"}
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            cpu = cpu_baseline(w, homes=1)
+        h2d = 3 * n * 8 + 9 * 8
+        d2h = (1 + 3 * n + 9) * 8
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "precision": "fp64",
+                           "parallelism": f"replicas{world}" if world > 1 else "single",
+                           "l2": "working set > L2 (C+gradC, V, Y stores of several GB per step)"},
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "gpu_launches": launches,
+                "roofline": roofline,
+                "cpu_baseline": cpu,
+                "clocks": ck,
+                "stages_ms": stage_ms,
+                "gflop_per_eval": flops["flops_total"] / 1e9,
+                "achieved_tflops_total": flops["flops_total"] / (t_max / args.steps) / 1e12,
+                "counts": {k: flops[k] for k in ("c_pairs", "v_pairs", "triplets", "term1_pairs",
+                                                 "term2_pairs", "y_blocks", "device_bytes")},
+                "peaks": {"hbm_gbs": peaks.get("hbm_gbs"), "bf16_tflops": peaks.get("bf16_tflops"),
+                          "fp64_dgemm_tflops": fp64_peak}}
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

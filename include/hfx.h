@@ -1,0 +1,170 @@
+/*
+ * hfx.h -- C ABI of the GB300 exact-exchange (HFX) force and stress library.
+ *
+ * The library evaluates, for a periodic structure, the LRI exchange energy
+ * of Eq. exx_expand (paper Sec. 2)
+ *
+ *   E = - sum_{A in cell} sum_{F,B,G} C^A_{AF} V_{AB} C^B_{BG}
+ *                                     (D_AB D_FG + D_AG D_FB)
+ *
+ * with real, fixed D, together with the force part that comes from the
+ * variation of C and V (F^X1, Eq. Fexx1) and the matching stress
+ * (sigma^X1, Eq. stress).  The problem statement is the paper's: given C, V,
+ * their nuclear gradients and a fixed D, return F^X1 and sigma^X1 (Sec. 2,
+ * after Eq. HD_ES, and Sec. 3.1).  The blocks C, V and their gradients come
+ * from the built-in block model evaluated at the caller's positions:
+ *
+ *   C_{I,(J,R)} = G_{s(I)s(J)} f(r) [+ G'_{s(I)s(J)} f(r) (d.e)/R_C]
+ *   V_{I,(J,R)} = M_{s(I)s(J)} h(r)
+ *   f(r) = (1 - (r/R_C)^2)^3 exp(-r^2/2) for r < R_C = 2 r_c, else 0
+ *   h(r) = erfc(omega r) / (r + 1)
+ *
+ * where d = tau_J + R.L - tau_I, r = |d|, and on-site blocks (I = J, R = 0)
+ * do not move (their gradients vanish, Sec. 3.1).  Items are screened in two
+ * steps (Sec. 3.2, Algorithm 1): per-tensor Frobenius-norm filters, then a
+ * Cauchy-Schwarz bound per item.
+ *
+ * Conventions for every entry point:
+ *  - Every call returns an hfx_status; no C++ exception crosses the ABI.
+ *  - Outputs are written only when the call returns HFX_OK.
+ *  - A plan is bound to one CUDA stream and one device and is not thread
+ *    safe; calls on one plan must be serialised by the caller.
+ *  - Units: positions and lattice in Angstrom; E in model units; F in E/A;
+ *    sigma in E/A^3, row-major 3x3, symmetric within rounding for the
+ *    isotropic model.
+ *  - Failing CUDA calls give HFX_ERR_CUDA; allocation failures HFX_ERR_OOM;
+ *    bad arguments (null pointers, non-finite numbers, out-of-range species
+ *    or indices, singular lattice) HFX_ERR_INVALID.  hfx_last_error()
+ *    returns a message for the last failing call on a plan.
+ */
+#ifndef HFX_H_
+#define HFX_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HFX_OK = 0,
+  HFX_ERR_INVALID = 1,
+  HFX_ERR_OOM = 2,
+  HFX_ERR_CUDA = 3,
+  HFX_ERR_TIMEOUT = 4,
+  HFX_ERR_PAIRLIST_STALE = 5,
+  HFX_ERR_UNSUPPORTED = 6
+} hfx_status;
+
+/* Arithmetic of the contraction.  HFX_FP64 runs every step in FP64.  The
+ * other values select split-precision tensor-core contractions with FP32
+ * accumulation and FP64 screening, force, stress and energy reduction. */
+enum { HFX_FP64 = 0, HFX_TF32X3 = 1, HFX_BF16X3 = 2, HFX_BF16X6 = 3 };
+
+/* Exchange products of Eq. exx_expand: bit 0 = D_AB D_FG, bit 1 = D_AG D_FB. */
+enum { HFX_TERM_AB_FG = 1, HFX_TERM_AG_FB = 2, HFX_TERMS_ALL = 3 };
+
+typedef struct hfx_plan hfx_plan; /* opaque, owned by the library */
+
+/* The structure (Eqs. 1-2: atom I of the cell plus lattice vector R). */
+typedef struct {
+  int n_atoms;            /* > 0 */
+  const int* species;     /* [n_atoms], each in 0..n_species-1; host memory */
+  double lattice[9];      /* rows a1, a2, a3 (Angstrom); det != 0 */
+  const double* positions;/* [n_atoms*3] Cartesian (Angstrom); host memory */
+} hfx_system;
+
+/* The block model and the fixed density matrix (host memory; copied by
+ * hfx_plan_create, so the caller may free it afterwards). */
+typedef struct {
+  int n_species;                  /* 1..16 */
+  const int* n_ao;                /* [n_species], 1..32 orbitals per atom */
+  const int* n_abf;               /* [n_species], 1..128 auxiliary functions */
+  double r_c;                     /* > 0; C range R_C = 2 r_c (Angstrom) */
+  double omega;                   /* > 0; screening of h(r) (1/Angstrom) */
+  const double* const* G;         /* [s*n_species+t] -> n_abf(s)*n_ao(s)*n_ao(t), row-major */
+  const double* const* M;         /* [s*n_species+t] -> n_abf(s)*n_abf(t); M_ts = M_st^T,
+                                     M_ss symmetric (gives V_BA = V_AB^T, Sec. 3.1) */
+  const double* const* G_aniso;   /* NULL, or like G: anisotropic C term */
+  double aniso_dir[3];            /* unit vector e of the anisotropic term */
+  long long n_d;                  /* number of D blocks */
+  const int* d_index;             /* [n_d*5] rows (I, J, R1, R2, R3), any order, no duplicates */
+  const long long* d_offset;      /* [n_d+1] element offsets into d_values */
+  const double* d_values;         /* block k is n_ao(I)*n_ao(J) row-major; both orientations
+                                     must be present with D_JI(-R) = D_IJ(R)^T */
+} hfx_model;
+
+typedef struct {
+  /* Screening thresholds (Sec. 3.2): step 1 drops a C pair only if
+   * ||C|| <= theta_C and ||grad C|| <= theta_dC (likewise V), and a D
+   * block if ||D|| <= theta_D (Frobenius norms).  Step 2 drops an item
+   * whose Cauchy-Schwarz bound is <= theta_CS.  0 disables a filter. */
+  double theta_C, theta_dC, theta_V, theta_dV, theta_D, theta_CS;
+  int precision;      /* HFX_FP64 (default) or a split-precision mode */
+  int terms;          /* HFX_TERMS_ALL by default */
+  double skin;        /* Verlet skin of the pair lists (Angstrom), default 0.5 */
+  int freeze_lists;   /* 1: keep pair lists and the first call's screening
+                         decisions; a move beyond skin/2 gives
+                         HFX_ERR_PAIRLIST_STALE.  0: lists are rebuilt when
+                         stale and screening is redone on every call. */
+  int deterministic;  /* reserved; must be 0 */
+  void* stream;       /* cudaStream_t for every launch and copy; NULL = legacy default */
+  int device;         /* CUDA device ordinal */
+} hfx_options;
+
+/* Counters of the last call (FLOPs are the algorithmic count of the
+ * factorised contraction; times are CUDA-event times per stage in ms when
+ * timing was requested via hfx_set_timing). */
+typedef struct {
+  long long c_pairs, v_pairs, d_blocks;        /* kept after step 1 */
+  long long triplets, term1_pairs, term2_pairs; /* kept after step 2 */
+  long long y_blocks;                           /* Y^{XZ} = sum_W C_XW D_WZ built */
+  double flops_y, flops_term1, flops_term2, flops_total;
+  double ms_blocks, ms_screen, ms_y, ms_term1, ms_term2, ms_reduce, ms_total;
+  long long device_bytes;                       /* device memory held by the plan */
+  long long kernel_launches;                    /* CUDA kernels this library launched in the call */
+} hfx_stats;
+
+/* Fill *opt with the defaults (all thresholds 1e-10, FP64, both terms,
+ * skin 0.5, no freeze, default stream, device 0).  HFX_ERR_INVALID if
+ * opt is NULL. */
+hfx_status hfx_default_options(hfx_options* opt);
+
+/* Validate the inputs, copy the model and D to the device, build the pair
+ * lists (Eqs. 1-2 labels) and lookup tables.  On HFX_OK *out owns a plan
+ * that hfx_plan_destroy frees.  All pointers are host pointers. */
+hfx_status hfx_plan_create(const hfx_system* sys, const hfx_model* model,
+                           const hfx_options* opt, hfx_plan** out);
+
+/* Evaluate E, F^X1 (Eq. Fexx1) and sigma^X1 (Eq. stress) at the given
+ * geometry (host pointers).  lattice: 9 doubles (rows); positions:
+ * n_atoms*3 doubles.  E: 1 double, F: n_atoms*3 doubles, sigma: 9 doubles,
+ * all written only on HFX_OK; stats may be NULL.  The call is synchronous
+ * (it returns after the results are on the host). */
+hfx_status hfx_energy_force_stress(hfx_plan* plan, const double* lattice, const double* positions,
+                                   double* E, double* F, double* sigma, hfx_stats* stats);
+
+/* Same as hfx_energy_force_stress with positions and results in device
+ * memory of the plan's device: d_positions [n_atoms*3], d_out
+ * [1 + 3*n_atoms + 9] receives E, F, sigma in that order.  lattice is a
+ * host pointer.  The call returns after the work is enqueued and the
+ * results are complete on the plan's stream. */
+hfx_status hfx_energy_force_stress_device(hfx_plan* plan, const double* lattice,
+                                          const double* d_positions, double* d_out,
+                                          hfx_stats* stats);
+
+/* Per-stage CUDA-event timing on (1) or off (0, default). */
+hfx_status hfx_set_timing(hfx_plan* plan, int on);
+
+/* Free every resource of the plan.  NULL is accepted. */
+hfx_status hfx_plan_destroy(hfx_plan* plan);
+
+/* Static strings; never NULL. */
+const char* hfx_status_string(hfx_status s);
+const char* hfx_last_error(const hfx_plan* plan);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HFX_H_ */

@@ -1,0 +1,963 @@
+// Host side of libhfx: the C ABI, input validation, the periodic pair lists
+// (atom I plus lattice vector R as one label, paper Eqs. 1-2), the dense
+// lookup tables for D and Y blocks, device memory, and the order of the
+// stages of one evaluation.  Every stage of the arithmetic runs in the CUDA
+// kernels of hfx_kernels.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <functional>
+#include <limits>
+#include <new>
+#include <stdexcept>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/hfx.h"
+#include "hfx_internal.h"
+
+using hfx::DevPlan;
+
+namespace {
+
+struct Failure {
+  hfx_status status;
+  std::string msg;
+};
+
+[[noreturn]] void fail(hfx_status s, const std::string& m) { throw Failure{s, m}; }
+
+void ck(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return;
+  if (e == cudaErrorMemoryAllocation) fail(HFX_ERR_OOM, std::string(what) + ": " + cudaGetErrorString(e));
+  fail(HFX_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// Device allocation tracked by the plan.
+struct DevMem {
+  std::vector<std::pair<void*, size_t>> ptrs;
+  long long bytes = 0;
+  template <class T>
+  T* alloc(size_t n) {
+    if (n == 0) n = 1;
+    void* p = nullptr;
+    ck(cudaMalloc(&p, n * sizeof(T)), "cudaMalloc");
+    ptrs.emplace_back(p, n * sizeof(T));
+    bytes += (long long)(n * sizeof(T));
+    return static_cast<T*>(p);
+  }
+  void release(void* p) {
+    for (auto it = ptrs.begin(); it != ptrs.end(); ++it)
+      if (it->first == p) {
+        cudaFree(p);
+        bytes -= (long long)it->second;
+        ptrs.erase(it);
+        return;
+      }
+  }
+  void free_all() {
+    for (auto& q : ptrs) cudaFree(q.first);
+    ptrs.clear();
+    bytes = 0;
+  }
+};
+
+template <class T>
+void upload(T* dst, const std::vector<T>& src, cudaStream_t s) {
+  if (!src.empty()) ck(cudaMemcpyAsync(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, s), "H2D");
+}
+
+double det3(const double* L) {
+  return L[0] * (L[4] * L[8] - L[5] * L[7]) - L[1] * (L[3] * L[8] - L[5] * L[6]) + L[2] * (L[3] * L[7] - L[4] * L[6]);
+}
+
+bool finite_all(const double* p, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(p[i])) return false;
+  return true;
+}
+
+// Model radial function of V and its derivative (host copy for the radius).
+void h_host(double r, double om, double& h, double& hp) {
+  const double ec = std::erfc(om * r);
+  h = ec / (r + 1.0);
+  hp = (-2.0 * om / std::sqrt(M_PI)) * std::exp(-(om * r) * (om * r)) / (r + 1.0) - ec / ((r + 1.0) * (r + 1.0));
+}
+
+}  // namespace
+
+struct hfx_plan {
+  int dev = 0;
+  cudaStream_t stream = nullptr;
+  hfx_options opt{};
+  int N = 0, S = 0;
+  std::vector<int> species, n_ao, n_abf;
+  double RC = 0, omega = 0, mmax = 0;
+  bool aniso = false;
+  double e[3] = {0, 0, 0};
+  std::string err;
+  DevMem mem;
+
+  // host copies of D (for the lookup table and the D reach)
+  std::vector<int> d_index;
+  long long n_d = 0;
+
+  // device model
+  int *d_species = nullptr, *d_n_ao = nullptr, *d_n_abf = nullptr;
+  long long *d_G_off = nullptr, *d_M_off = nullptr;
+  double *d_G = nullptr, *d_Gp = nullptr, *d_M = nullptr;
+  double* d_Dval = nullptr;
+  long long* d_Doff = nullptr;
+  int* d_Didx = nullptr;
+  double* d_Dkept = nullptr;
+  int* d_dlut = nullptr;
+  int HD[3] = {0, 0, 0};
+
+  // lists (host side, at the reference geometry)
+  std::vector<double> pos_ref, lat_ref;
+  double list_Rabs = 0;    // largest |R_k| sum over listed pairs, for the staleness bound
+  int nC = 0, nV = 0, nY = 0;
+  int maxC = 0;
+  int HY[3] = {0, 0, 0};
+  bool lists_ready = false;
+  bool frozen_ready = false;
+
+  // device lists and per-call buffers
+  std::vector<void*> list_bufs;   // freed on rebuild
+  int *c_ptr = nullptr, *c_home = nullptr, *c_j = nullptr, *c_R = nullptr;
+  long long* c_off = nullptr;
+  double *Cst = nullptr, *dCst = nullptr, *c_norm = nullptr;
+  unsigned char* c_keep = nullptr;
+  int *v_ptr = nullptr, *v_home = nullptr, *v_j = nullptr, *v_R = nullptr, *v_didx = nullptr;
+  double* v_norm = nullptr;
+  unsigned char *v_keep = nullptr, *v_t2 = nullptr;
+  unsigned* v_mask = nullptr;
+  int* v_flag = nullptr;
+  long long *v_off = nullptr, *v_size = nullptr, *v_idx = nullptr, *t1_idx = nullptr, *t2_idx = nullptr;
+  int *v_list = nullptr, *t1_list = nullptr, *t2_list = nullptr;
+  int *y_ptr = nullptr, *y_home = nullptr, *y_j = nullptr, *y_R = nullptr, *ylut = nullptr;
+  double* yhat = nullptr;
+  int* y_flag = nullptr;
+  long long *y_off = nullptr, *y_size = nullptr, *y_idx = nullptr;
+  int* y_list = nullptr;
+  double *gC = nullptr, *gV = nullptr;
+  long long c_elems = 0;
+
+  // per-call state
+  double* d_pos = nullptr;
+  double* d_out = nullptr;     // [1 + 3N + 9]
+  double* d_acc = nullptr;     // hfx::ACC_N
+  long long* d_tot = nullptr;  // [8] totals of the scans, then hfx::CNT_N counters
+  double* Yst = nullptr;
+  long long Ycap = 0;
+  double* Vst = nullptr;
+  long long Vcap = 0;
+  hfx::ScanTmp scan_tmp;
+  long long tot[8] = {0};      // y elems, y count, v elems, v count, t1, t2
+  unsigned long long cnt[hfx::CNT_N] = {0};
+
+  // kernel shapes
+  int beta_chunk = 1, alpha_chunk = 1;
+  size_t smem_t1 = 0, smem_t2 = 0;
+
+  bool timing = false;
+  std::vector<double> pos_host_buf;
+  hfx_stats last{};
+
+  template <class T>
+  T* lalloc(size_t n) {
+    T* p = mem.alloc<T>(n);
+    list_bufs.push_back(p);
+    return p;
+  }
+  void free_lists() {
+    for (void* p : list_bufs) mem.release(p);
+    list_bufs.clear();
+  }
+};
+
+namespace {
+
+void validate_options(const hfx_options* o) {
+  if (!o) fail(HFX_ERR_INVALID, "options is NULL");
+  const double th[6] = {o->theta_C, o->theta_dC, o->theta_V, o->theta_dV, o->theta_D, o->theta_CS};
+  for (double t : th)
+    if (!std::isfinite(t) || t < 0) fail(HFX_ERR_INVALID, "thresholds must be finite and >= 0");
+  if (o->precision != HFX_FP64) fail(HFX_ERR_UNSUPPORTED, "only HFX_FP64 is available in this build");
+  if (o->terms < 1 || o->terms > 3) fail(HFX_ERR_INVALID, "terms must be 1, 2 or 3");
+  if (!std::isfinite(o->skin) || o->skin < 0) fail(HFX_ERR_INVALID, "skin must be finite and >= 0");
+  if (o->deterministic != 0) fail(HFX_ERR_UNSUPPORTED, "deterministic mode is not available");
+}
+
+void validate_geometry(int N, const double* lattice, const double* positions) {
+  if (!lattice || !positions) fail(HFX_ERR_INVALID, "lattice or positions is NULL");
+  if (!finite_all(lattice, 9) || !finite_all(positions, (size_t)N * 3))
+    fail(HFX_ERR_INVALID, "non-finite lattice or positions");
+  if (std::fabs(det3(lattice)) < 1e-9) fail(HFX_ERR_INVALID, "singular lattice");
+}
+
+void upload_model(hfx_plan* P, const hfx_system* sys, const hfx_model* m) {
+  const int S = m->n_species, N = sys->n_atoms;
+  cudaStream_t s = P->stream;
+  P->species.assign(sys->species, sys->species + N);
+  P->n_ao.assign(m->n_ao, m->n_ao + S);
+  P->n_abf.assign(m->n_abf, m->n_abf + S);
+  for (int i = 0; i < N; ++i)
+    if (P->species[i] < 0 || P->species[i] >= S) fail(HFX_ERR_INVALID, "species out of range");
+  for (int t = 0; t < S; ++t) {
+    if (P->n_ao[t] < 1 || P->n_ao[t] > hfx::kMaxAO) fail(HFX_ERR_INVALID, "n_ao out of range 1..32");
+    if (P->n_abf[t] < 1 || P->n_abf[t] > hfx::kMaxABF) fail(HFX_ERR_INVALID, "n_abf out of range 1..128");
+  }
+  std::vector<long long> goff(S * S), moff(S * S);
+  long long gsz = 0, msz = 0;
+  for (int a = 0; a < S; ++a)
+    for (int b = 0; b < S; ++b) {
+      goff[a * S + b] = gsz;
+      moff[a * S + b] = msz;
+      gsz += (long long)P->n_abf[a] * P->n_ao[a] * P->n_ao[b];
+      msz += (long long)P->n_abf[a] * P->n_abf[b];
+    }
+  std::vector<double> G(gsz), M(msz), Gp;
+  if (m->G_aniso) Gp.resize(gsz);
+  double mmax = 0;
+  for (int a = 0; a < S; ++a)
+    for (int b = 0; b < S; ++b) {
+      const long long ng = (long long)P->n_abf[a] * P->n_ao[a] * P->n_ao[b];
+      const long long nm = (long long)P->n_abf[a] * P->n_abf[b];
+      if (!m->G[a * S + b] || !m->M[a * S + b]) fail(HFX_ERR_INVALID, "NULL template");
+      std::memcpy(&G[goff[a * S + b]], m->G[a * S + b], ng * sizeof(double));
+      std::memcpy(&M[moff[a * S + b]], m->M[a * S + b], nm * sizeof(double));
+      if (m->G_aniso) {
+        if (!m->G_aniso[a * S + b]) fail(HFX_ERR_INVALID, "NULL anisotropic template");
+        std::memcpy(&Gp[goff[a * S + b]], m->G_aniso[a * S + b], ng * sizeof(double));
+      }
+      double s2 = 0;
+      for (long long k = 0; k < nm; ++k) s2 += M[moff[a * S + b] + k] * M[moff[a * S + b] + k];
+      mmax = std::max(mmax, std::sqrt(s2));
+    }
+  if (!finite_all(G.data(), G.size()) || !finite_all(M.data(), M.size()) || !finite_all(Gp.data(), Gp.size()))
+    fail(HFX_ERR_INVALID, "non-finite template");
+  // V_BA = V_AB^T needs M_ts = M_st^T (Sec. 3.1)
+  for (int a = 0; a < S; ++a)
+    for (int b = 0; b < S; ++b)
+      for (int x = 0; x < P->n_abf[a]; ++x)
+        for (int y = 0; y < P->n_abf[b]; ++y) {
+          const double u = M[moff[a * S + b] + (long long)x * P->n_abf[b] + y];
+          const double v = M[moff[b * S + a] + (long long)y * P->n_abf[a] + x];
+          if (std::fabs(u - v) > 1e-12 * (1.0 + std::fabs(u))) fail(HFX_ERR_INVALID, "M_ts != M_st^T");
+        }
+  P->mmax = mmax;
+  P->d_species = P->mem.alloc<int>(N);
+  P->d_n_ao = P->mem.alloc<int>(S);
+  P->d_n_abf = P->mem.alloc<int>(S);
+  P->d_G_off = P->mem.alloc<long long>(S * S);
+  P->d_M_off = P->mem.alloc<long long>(S * S);
+  P->d_G = P->mem.alloc<double>(gsz);
+  P->d_M = P->mem.alloc<double>(msz);
+  upload(P->d_species, P->species, s);
+  upload(P->d_n_ao, P->n_ao, s);
+  upload(P->d_n_abf, P->n_abf, s);
+  upload(P->d_G_off, goff, s);
+  upload(P->d_M_off, moff, s);
+  upload(P->d_G, G, s);
+  upload(P->d_M, M, s);
+  if (m->G_aniso) {
+    P->d_Gp = P->mem.alloc<double>(gsz);
+    upload(P->d_Gp, Gp, s);
+    P->aniso = true;
+    for (int k = 0; k < 3; ++k) P->e[k] = m->aniso_dir[k];
+    if (!finite_all(P->e, 3)) fail(HFX_ERR_INVALID, "non-finite anisotropy direction");
+  }
+  ck(cudaStreamSynchronize(s), "upload model");
+}
+
+// D blocks: validation, the dense (i, j, R) lookup table, device copies.
+void upload_density(hfx_plan* P, const hfx_model* m) {
+  const int N = P->N;
+  const long long nd = m->n_d;
+  if (nd < 0) fail(HFX_ERR_INVALID, "n_d < 0");
+  if (nd > 0 && (!m->d_index || !m->d_offset || !m->d_values)) fail(HFX_ERR_INVALID, "NULL D arrays");
+  P->n_d = nd;
+  P->d_index.assign(m->d_index, m->d_index + 5 * nd);
+  std::vector<long long> off(m->d_offset, m->d_offset + nd + 1);
+  if (off[0] != 0) fail(HFX_ERR_INVALID, "d_offset[0] != 0");
+  int H[3] = {0, 0, 0};
+  for (long long k = 0; k < nd; ++k) {
+    const int* r = &P->d_index[5 * k];
+    if (r[0] < 0 || r[0] >= N || r[1] < 0 || r[1] >= N) fail(HFX_ERR_INVALID, "D atom index out of range");
+    const long long want = (long long)P->n_ao[P->species[r[0]]] * P->n_ao[P->species[r[1]]];
+    if (off[k + 1] - off[k] != want) fail(HFX_ERR_INVALID, "D block size != n_ao(I)*n_ao(J)");
+    for (int c = 0; c < 3; ++c) {
+      if (std::abs(r[2 + c]) > 1000) fail(HFX_ERR_INVALID, "D image index too large");
+      H[c] = std::max(H[c], std::abs(r[2 + c]));
+    }
+  }
+  const long long nvals = off[nd];
+  if (!finite_all(m->d_values, (size_t)nvals)) fail(HFX_ERR_INVALID, "non-finite D values");
+  for (int c = 0; c < 3; ++c) P->HD[c] = H[c];
+  const long long n0 = 2 * H[0] + 1, n1 = 2 * H[1] + 1, n2 = 2 * H[2] + 1;
+  const long long lut_n = (long long)N * N * n0 * n1 * n2;
+  if (lut_n > (1ll << 31)) fail(HFX_ERR_UNSUPPORTED, "D lookup table too large");
+  std::vector<int> lut(lut_n, -1);
+  auto lidx = [&](int i, int j, int a, int b, int c) {
+    return ((((long long)i * N + j) * n0 + (a + H[0])) * n1 + (b + H[1])) * n2 + (c + H[2]);
+  };
+  for (long long k = 0; k < nd; ++k) {
+    const int* r = &P->d_index[5 * k];
+    int& slot = lut[lidx(r[0], r[1], r[2], r[3], r[4])];
+    if (slot != -1) fail(HFX_ERR_INVALID, "duplicate D block");
+    slot = (int)k;
+  }
+  // both orientations, D_JI(-R) = D_IJ(R)^T (needed by the symmetric exchange products)
+  for (long long k = 0; k < nd; ++k) {
+    const int* r = &P->d_index[5 * k];
+    const int t = lut[lidx(r[1], r[0], -r[2], -r[3], -r[4])];
+    if (t < 0) fail(HFX_ERR_INVALID, "D_JI(-R) missing for a given D_IJ(R)");
+    const int na = P->n_ao[P->species[r[0]]], nb = P->n_ao[P->species[r[1]]];
+    for (int x = 0; x < na; ++x)
+      for (int y = 0; y < nb; ++y) {
+        const double u = m->d_values[off[k] + (long long)x * nb + y];
+        const double v = m->d_values[off[t] + (long long)y * na + x];
+        if (std::fabs(u - v) > 1e-12 * (1.0 + std::fabs(u))) fail(HFX_ERR_INVALID, "D_JI(-R) != D_IJ(R)^T");
+      }
+  }
+  cudaStream_t s = P->stream;
+  P->d_Dval = P->mem.alloc<double>(nvals);
+  P->d_Doff = P->mem.alloc<long long>(nd + 1);
+  P->d_Didx = P->mem.alloc<int>(5 * nd);
+  P->d_Dkept = P->mem.alloc<double>(nd);
+  P->d_dlut = P->mem.alloc<int>(lut_n);
+  if (nvals) ck(cudaMemcpyAsync(P->d_Dval, m->d_values, nvals * sizeof(double), cudaMemcpyHostToDevice, s), "H2D D");
+  upload(P->d_Doff, off, s);
+  upload(P->d_Didx, P->d_index, s);
+  upload(P->d_dlut, lut, s);
+  ck(cudaStreamSynchronize(s), "upload D");
+}
+
+double v_radius(const hfx_plan* P) {
+  const double tv = P->opt.theta_V, tdv = P->opt.theta_dV;
+  if (tv <= 0 && tdv <= 0) return std::numeric_limits<double>::infinity();
+  auto above = [&](double r) {
+    double h, hp;
+    h_host(r, P->omega, h, hp);
+    return P->mmax * h > tv || P->mmax * std::fabs(hp) > tdv;
+  };
+  double lo = 0, hi = 1;
+  while (above(hi) && hi < 1e6) hi *= 2;
+  for (int it = 0; it < 80; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (above(mid)) lo = mid;
+    else hi = mid;
+  }
+  return hi + 1.0;
+}
+
+DevPlan make_devplan(hfx_plan* P, const double* lattice) {
+  DevPlan D{};
+  D.N = P->N;
+  D.S = P->S;
+  D.species = P->d_species;
+  D.n_ao = P->d_n_ao;
+  D.n_abf = P->d_n_abf;
+  D.G_off = P->d_G_off;
+  D.G = P->d_G;
+  D.Gp = P->aniso ? P->d_Gp : nullptr;
+  D.M_off = P->d_M_off;
+  D.M = P->d_M;
+  for (int k = 0; k < 3; ++k) D.e[k] = P->e[k];
+  D.RC = P->RC;
+  D.omega = P->omega;
+  D.thC = P->opt.theta_C;
+  D.thdC = P->opt.theta_dC;
+  D.thV = P->opt.theta_V;
+  D.thdV = P->opt.theta_dV;
+  D.thD = P->opt.theta_D;
+  D.thCS = P->opt.theta_CS;
+  D.terms = P->opt.terms;
+  D.pos = P->d_pos;
+  for (int k = 0; k < 9; ++k) D.L[k] = lattice[k];
+  D.n_d = P->n_d;
+  D.Dval = P->d_Dval;
+  D.Doff = P->d_Doff;
+  D.Didx = P->d_Didx;
+  D.Dkept = P->d_Dkept;
+  D.dlut = P->d_dlut;
+  D.HD0 = P->HD[0];
+  D.HD1 = P->HD[1];
+  D.HD2 = P->HD[2];
+  D.nC = P->nC;
+  D.c_ptr = P->c_ptr;
+  D.c_home = P->c_home;
+  D.c_j = P->c_j;
+  D.c_R = P->c_R;
+  D.c_off = P->c_off;
+  D.Cst = P->Cst;
+  D.dCst = P->dCst;
+  D.c_norm = P->c_norm;
+  D.c_keep = P->c_keep;
+  D.nV = P->nV;
+  D.v_ptr = P->v_ptr;
+  D.v_home = P->v_home;
+  D.v_j = P->v_j;
+  D.v_R = P->v_R;
+  D.v_didx = P->v_didx;
+  D.v_norm = P->v_norm;
+  D.v_keep = P->v_keep;
+  D.v_mask = P->v_mask;
+  D.v_t2 = P->v_t2;
+  D.v_flag = P->v_flag;
+  D.v_off = P->v_off;
+  D.Vst = P->Vst;
+  D.nY = P->nY;
+  D.y_ptr = P->y_ptr;
+  D.y_home = P->y_home;
+  D.y_j = P->y_j;
+  D.y_R = P->y_R;
+  D.yhat = P->yhat;
+  D.y_flag = P->y_flag;
+  D.y_off = P->y_off;
+  D.Yst = P->Yst;
+  D.ylut = P->ylut;
+  D.HY0 = P->HY[0];
+  D.HY1 = P->HY[1];
+  D.HY2 = P->HY[2];
+  D.gC = P->gC;
+  D.gV = P->gV;
+  D.acc = P->d_acc;
+  D.cnt = reinterpret_cast<unsigned long long*>(P->d_tot + 8);
+  return D;
+}
+
+// Pair lists (K0): C pairs within R_C + skin, V pairs within the V radius
+// (capped at R_C + D reach + 1) + skin, Y keys within R_C + D reach + skin.
+void build_lists(hfx_plan* P, const double* L, const double* pos) {
+  const int N = P->N;
+  // D reach at this geometry
+  double rd = 0;
+  for (long long k = 0; k < P->n_d; ++k) {
+    const int* r = &P->d_index[5 * k];
+    double d2 = 0;
+    for (int c = 0; c < 3; ++c) {
+      const double dv = pos[3 * r[1] + c] + r[2] * L[c] + r[3] * L[3 + c] + r[4] * L[6 + c] - pos[3 * r[0] + c];
+      d2 += dv * dv;
+    }
+    rd = std::max(rd, std::sqrt(d2));
+  }
+  const double skin = P->opt.skin;
+  const double rC = P->RC + skin;
+  const double rV = std::min(v_radius(P), P->RC + rd + 1.0) + skin;
+  const double rY = P->RC + rd + skin;
+  const double rmax = std::max(rC, std::max(rV, rY));
+  // reciprocal vectors: rows of inv(L)^T
+  const double det = det3(L);
+  double B[9];
+  B[0] = (L[4] * L[8] - L[5] * L[7]) / det;
+  B[1] = (L[5] * L[6] - L[3] * L[8]) / det;
+  B[2] = (L[3] * L[7] - L[4] * L[6]) / det;
+  B[3] = (L[2] * L[7] - L[1] * L[8]) / det;
+  B[4] = (L[0] * L[8] - L[2] * L[6]) / det;
+  B[5] = (L[1] * L[6] - L[0] * L[7]) / det;
+  B[6] = (L[1] * L[5] - L[2] * L[4]) / det;
+  B[7] = (L[2] * L[3] - L[0] * L[5]) / det;
+  B[8] = (L[0] * L[4] - L[1] * L[3]) / det;
+  int nm[3];
+  for (int k = 0; k < 3; ++k) {
+    const double bn = std::sqrt(B[3 * k] * B[3 * k] + B[3 * k + 1] * B[3 * k + 1] + B[3 * k + 2] * B[3 * k + 2]);
+    nm[k] = (int)std::ceil(rmax * bn) + 1;
+    if (nm[k] > 200) fail(HFX_ERR_UNSUPPORTED, "pair range spans too many images");
+  }
+  std::vector<int> c_ptr(N + 1, 0), v_ptr(N + 1, 0), y_ptr(N + 1, 0);
+  std::vector<int> c_home, c_j, c_R, v_home, v_j, v_R, y_home, y_j, y_R;
+  int HY[3] = {0, 0, 0};
+  double Rabs = 0;
+  for (int A = 0; A < N; ++A) {
+    c_ptr[A] = (int)c_j.size();
+    v_ptr[A] = (int)v_j.size();
+    y_ptr[A] = (int)y_j.size();
+    for (int j = 0; j < N; ++j)
+      for (int a = -nm[0]; a <= nm[0]; ++a)
+        for (int b = -nm[1]; b <= nm[1]; ++b)
+          for (int c = -nm[2]; c <= nm[2]; ++c) {
+            double d2 = 0;
+            for (int k = 0; k < 3; ++k) {
+              const double dv = (pos[3 * j + k] + (a * L[k] + b * L[3 + k] + c * L[6 + k])) - pos[3 * A + k];
+              d2 += dv * dv;
+            }
+            const double r = std::sqrt(d2);
+            const bool inC = r < rC, inV = r < rV, inY = r < rY;
+            if (!(inC || inV || inY)) continue;
+            Rabs = std::max(Rabs, (double)(std::abs(a) + std::abs(b) + std::abs(c)));
+            if (inC) {
+              c_home.push_back(A);
+              c_j.push_back(j);
+              c_R.insert(c_R.end(), {a, b, c});
+            }
+            if (inV) {
+              v_home.push_back(A);
+              v_j.push_back(j);
+              v_R.insert(v_R.end(), {a, b, c});
+            }
+            if (inY) {
+              y_home.push_back(A);
+              y_j.push_back(j);
+              y_R.insert(y_R.end(), {a, b, c});
+              HY[0] = std::max(HY[0], std::abs(a));
+              HY[1] = std::max(HY[1], std::abs(b));
+              HY[2] = std::max(HY[2], std::abs(c));
+            }
+          }
+    if ((int)c_j.size() - c_ptr[A] > hfx::kMaxCPerAtom)
+      fail(HFX_ERR_UNSUPPORTED, "more than 256 C-pair candidates on one atom");
+  }
+  c_ptr[N] = (int)c_j.size();
+  v_ptr[N] = (int)v_j.size();
+  y_ptr[N] = (int)y_j.size();
+  const int nC = c_ptr[N], nV = v_ptr[N], nY = y_ptr[N];
+  int maxC = 0;
+  for (int A = 0; A < N; ++A) maxC = std::max(maxC, c_ptr[A + 1] - c_ptr[A]);
+  // D block of each V pair, Y-key lookup table
+  const long long n0 = 2 * P->HD[0] + 1, n1 = 2 * P->HD[1] + 1, n2 = 2 * P->HD[2] + 1;
+  std::vector<int> v_didx(nV, -1);
+  {
+    std::vector<int> dl((size_t)N * N * n0 * n1 * n2);
+    ck(cudaMemcpy(dl.data(), P->d_dlut, dl.size() * sizeof(int), cudaMemcpyDeviceToHost), "D2H dlut");
+    for (int p = 0; p < nV; ++p) {
+      const int a = v_R[3 * p], b = v_R[3 * p + 1], c = v_R[3 * p + 2];
+      if (std::abs(a) > P->HD[0] || std::abs(b) > P->HD[1] || std::abs(c) > P->HD[2]) continue;
+      v_didx[p] = dl[((((long long)v_home[p] * N + v_j[p]) * n0 + (a + P->HD[0])) * n1 + (b + P->HD[1])) * n2 +
+                     (c + P->HD[2])];
+    }
+  }
+  const long long m0 = 2 * HY[0] + 1, m1 = 2 * HY[1] + 1, m2 = 2 * HY[2] + 1;
+  const long long ylut_n = (long long)N * N * m0 * m1 * m2;
+  if (ylut_n > (1ll << 31)) fail(HFX_ERR_UNSUPPORTED, "Y lookup table too large");
+  std::vector<int> ylut(ylut_n, -1);
+  for (int y = 0; y < nY; ++y) {
+    const long long idx = ((((long long)y_home[y] * N + y_j[y]) * m0 + (y_R[3 * y] + HY[0])) * m1 +
+                           (y_R[3 * y + 1] + HY[1])) * m2 + (y_R[3 * y + 2] + HY[2]);
+    ylut[idx] = y;
+  }
+  std::vector<long long> c_off(nC + 1, 0), v_size(nV), y_size(nY);
+  for (int p = 0; p < nC; ++p) {
+    const int sA = P->species[c_home[p]], sj = P->species[c_j[p]];
+    c_off[p + 1] = c_off[p] + (long long)P->n_abf[sA] * P->n_ao[sA] * P->n_ao[sj];
+  }
+  for (int p = 0; p < nV; ++p)
+    v_size[p] = 4ll * P->n_abf[P->species[v_home[p]]] * P->n_abf[P->species[v_j[p]]];
+  for (int y = 0; y < nY; ++y) {
+    const int sX = P->species[y_home[y]], sz = P->species[y_j[y]];
+    y_size[y] = (long long)P->n_abf[sX] * P->n_ao[sX] * P->n_ao[sz];
+  }
+
+  // (re)allocate list buffers
+  P->free_lists();
+  P->nC = nC;
+  P->nV = nV;
+  P->nY = nY;
+  P->maxC = maxC;
+  for (int k = 0; k < 3; ++k) P->HY[k] = HY[k];
+  P->c_elems = c_off[nC];
+  cudaStream_t s = P->stream;
+  P->c_ptr = P->lalloc<int>(N + 1);
+  P->c_home = P->lalloc<int>(nC);
+  P->c_j = P->lalloc<int>(nC);
+  P->c_R = P->lalloc<int>(3 * (size_t)nC);
+  P->c_off = P->lalloc<long long>(nC + 1);
+  P->Cst = P->lalloc<double>(P->c_elems);
+  P->dCst = P->lalloc<double>(3 * P->c_elems);
+  P->c_norm = P->lalloc<double>(nC);
+  P->c_keep = P->lalloc<unsigned char>(nC);
+  P->v_ptr = P->lalloc<int>(N + 1);
+  P->v_home = P->lalloc<int>(nV);
+  P->v_j = P->lalloc<int>(nV);
+  P->v_R = P->lalloc<int>(3 * (size_t)nV);
+  P->v_didx = P->lalloc<int>(nV);
+  P->v_norm = P->lalloc<double>(nV);
+  P->v_keep = P->lalloc<unsigned char>(nV);
+  P->v_t2 = P->lalloc<unsigned char>(nV);
+  P->v_mask = P->lalloc<unsigned>((size_t)nV * hfx::kMaskWords);
+  P->v_flag = P->lalloc<int>(nV);
+  P->v_off = P->lalloc<long long>(nV);
+  P->v_size = P->lalloc<long long>(nV);
+  P->v_idx = P->lalloc<long long>(nV);
+  P->t1_idx = P->lalloc<long long>(nV);
+  P->t2_idx = P->lalloc<long long>(nV);
+  P->v_list = P->lalloc<int>(nV);
+  P->t1_list = P->lalloc<int>(nV);
+  P->t2_list = P->lalloc<int>(nV);
+  P->y_ptr = P->lalloc<int>(N + 1);
+  P->y_home = P->lalloc<int>(nY);
+  P->y_j = P->lalloc<int>(nY);
+  P->y_R = P->lalloc<int>(3 * (size_t)nY);
+  P->ylut = P->lalloc<int>(ylut_n);
+  P->yhat = P->lalloc<double>(nY);
+  P->y_flag = P->lalloc<int>(nY);
+  P->y_off = P->lalloc<long long>(nY);
+  P->y_size = P->lalloc<long long>(nY);
+  P->y_idx = P->lalloc<long long>(nY);
+  P->y_list = P->lalloc<int>(nY);
+  P->gC = P->lalloc<double>(3 * (size_t)nC);
+  P->gV = P->lalloc<double>(3 * (size_t)nV);
+  upload(P->c_ptr, c_ptr, s);
+  upload(P->c_home, c_home, s);
+  upload(P->c_j, c_j, s);
+  upload(P->c_R, c_R, s);
+  upload(P->c_off, c_off, s);
+  upload(P->v_ptr, v_ptr, s);
+  upload(P->v_home, v_home, s);
+  upload(P->v_j, v_j, s);
+  upload(P->v_R, v_R, s);
+  upload(P->v_didx, v_didx, s);
+  upload(P->v_size, v_size, s);
+  upload(P->y_ptr, y_ptr, s);
+  upload(P->y_home, y_home, s);
+  upload(P->y_j, y_j, s);
+  upload(P->y_R, y_R, s);
+  upload(P->ylut, ylut, s);
+  upload(P->y_size, y_size, s);
+  ck(cudaMemsetAsync(P->c_keep, 0, nC, s), "memset");
+  ck(cudaMemsetAsync(P->v_keep, 0, nV, s), "memset");
+  ck(cudaStreamSynchronize(s), "upload lists");
+  P->pos_ref.assign(pos, pos + 3 * N);
+  P->lat_ref.assign(L, L + 9);
+  P->list_Rabs = Rabs;
+  P->lists_ready = true;
+  P->frozen_ready = false;
+}
+
+// Largest change of any listed pair distance since the lists were built.
+double list_drift(const hfx_plan* P, const double* L, const double* pos) {
+  double disp = 0;
+  for (int i = 0; i < P->N; ++i) {
+    double d2 = 0;
+    for (int k = 0; k < 3; ++k) {
+      const double dv = pos[3 * i + k] - P->pos_ref[3 * i + k];
+      d2 += dv * dv;
+    }
+    disp = std::max(disp, std::sqrt(d2));
+  }
+  double dl = 0;
+  for (int a = 0; a < 3; ++a) {
+    double d2 = 0;
+    for (int k = 0; k < 3; ++k) {
+      const double dv = L[3 * a + k] - P->lat_ref[3 * a + k];
+      d2 += dv * dv;
+    }
+    dl = std::max(dl, std::sqrt(d2));
+  }
+  return 2.0 * disp + P->list_Rabs * dl;
+}
+
+void setup_shapes(hfx_plan* P) {
+  int dev_smem = 0;
+  ck(cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->dev), "attr");
+  const size_t limit = (size_t)dev_smem - 2048;  // static shared memory of the kernels
+  int maxAO = 0, maxABF = 0;
+  for (int t = 0; t < P->S; ++t) {
+    maxAO = std::max(maxAO, P->n_ao[t]);
+    maxABF = std::max(maxABF, P->n_abf[t]);
+  }
+  const size_t base1 = (size_t)(hfx::kMaxAO * hfx::kMaxAO + maxABF * maxABF) * sizeof(double);
+  const size_t per1 = (size_t)maxAO * maxAO * sizeof(double);
+  if (base1 + per1 > limit) fail(HFX_ERR_UNSUPPORTED, "block shapes exceed shared memory");
+  P->beta_chunk = (int)std::min<size_t>(maxABF, (limit - base1) / per1);
+  P->smem_t1 = base1 + per1 * P->beta_chunk;
+  const size_t base2 = (size_t)(3 * hfx::kMaxCPerAtom + hfx::kMaxAO * hfx::kMaxAO) * sizeof(double);
+  P->alpha_chunk = (int)std::min<size_t>(maxABF, (limit - base2) / per1);
+  P->smem_t2 = base2 + per1 * P->alpha_chunk;
+  ck(hfx::set_kernel_smem_limits(P->smem_t1, P->smem_t2), "smem attributes");
+}
+
+void ensure_store(hfx_plan* P, double*& buf, long long& cap, long long need) {
+  if (need <= cap) return;
+  if (buf) P->mem.release(buf);
+  buf = nullptr;
+  cap = 0;
+  const long long n = need + need / 8 + 1024;
+  buf = P->mem.alloc<double>((size_t)n);
+  cap = n;
+}
+
+struct Timer {
+  bool on;
+  cudaStream_t s;
+  std::vector<cudaEvent_t> ev;
+  explicit Timer(bool o, cudaStream_t st) : on(o), s(st) {}
+  void mark() {
+    if (!on) return;
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    cudaEventRecord(e, s);
+    ev.push_back(e);
+  }
+  double ms(int a, int b) {
+    if (!on || b >= (int)ev.size()) return 0;
+    float t = 0;
+    cudaEventElapsedTime(&t, ev[a], ev[b]);
+    return t;
+  }
+  ~Timer() {
+    for (auto e : ev) cudaEventDestroy(e);
+  }
+};
+
+// One evaluation.  positions are in P->d_pos already; writes d_out.
+void evaluate(hfx_plan* P, const double* L, hfx_stats* st) {
+  cudaStream_t s = P->stream;
+  DevPlan D = make_devplan(P, L);
+  const long long launches0 = hfx::launch_count();
+  const bool reuse = P->opt.freeze_lists && P->frozen_ready;
+  Timer tm(P->timing, s);
+  tm.mark();  // 0
+  ck(cudaMemsetAsync(P->d_acc, 0, hfx::ACC_N * sizeof(double), s), "memset");
+  ck(cudaMemsetAsync(P->d_tot + 8, 0, hfx::CNT_N * sizeof(long long), s), "memset");
+  ck(cudaMemsetAsync(P->gC, 0, 3 * (size_t)P->nC * sizeof(double), s), "memset");
+  ck(cudaMemsetAsync(P->gV, 0, 3 * (size_t)P->nV * sizeof(double), s), "memset");
+  ck(hfx::launch_dnorm(D, s), "dnorm");
+  ck(hfx::launch_cblocks(D, reuse ? 1 : 0, s), "cblocks");
+  ck(hfx::launch_vnorm(D, reuse ? 1 : 0, s), "vnorm");
+  tm.mark();  // 1
+  if (!reuse) {
+    ck(cudaMemsetAsync(P->y_flag, 0, (size_t)P->nY * sizeof(int), s), "memset");
+    ck(hfx::launch_yhat(D, s), "yhat");
+    ck(hfx::launch_screen(D, s), "screen");
+    long long* T = P->d_tot;
+    ck(hfx::scan_flags(P->y_flag, P->y_size, nullptr, nullptr, 1, P->nY, P->y_off, T + 0, P->scan_tmp, s), "scan");
+    ck(hfx::scan_flags(P->y_flag, nullptr, nullptr, nullptr, 0, P->nY, P->y_idx, T + 1, P->scan_tmp, s), "scan");
+    ck(hfx::scatter_list(P->y_flag, nullptr, nullptr, 0, P->nY, P->y_idx, P->y_list, s), "scatter");
+    ck(hfx::scan_flags(P->v_flag, P->v_size, nullptr, nullptr, 1, P->nV, P->v_off, T + 2, P->scan_tmp, s), "scan");
+    ck(hfx::scan_flags(P->v_flag, nullptr, nullptr, nullptr, 0, P->nV, P->v_idx, T + 3, P->scan_tmp, s), "scan");
+    ck(hfx::scatter_list(P->v_flag, nullptr, nullptr, 0, P->nV, P->v_idx, P->v_list, s), "scatter");
+    ck(hfx::scan_flags(nullptr, nullptr, P->v_mask, nullptr, 2, P->nV, P->t1_idx, T + 4, P->scan_tmp, s), "scan");
+    ck(hfx::scatter_list(nullptr, P->v_mask, nullptr, 2, P->nV, P->t1_idx, P->t1_list, s), "scatter");
+    ck(hfx::scan_flags(nullptr, nullptr, nullptr, P->v_t2, 3, P->nV, P->t2_idx, T + 5, P->scan_tmp, s), "scan");
+    ck(hfx::scatter_list(nullptr, nullptr, P->v_t2, 3, P->nV, P->t2_idx, P->t2_list, s), "scatter");
+  }
+  ck(cudaMemcpyAsync(P->tot, P->d_tot, 8 * sizeof(long long), cudaMemcpyDeviceToHost, s), "D2H totals");
+  ck(cudaMemcpyAsync(P->cnt, P->d_tot + 8, hfx::CNT_N * sizeof(long long), cudaMemcpyDeviceToHost, s), "D2H counts");
+  ck(cudaStreamSynchronize(s), "screening");
+  if (P->opt.freeze_lists) P->frozen_ready = true;
+  tm.mark();  // 2
+  ensure_store(P, P->Yst, P->Ycap, P->tot[0]);
+  ensure_store(P, P->Vst, P->Vcap, P->tot[2]);
+  D.Yst = P->Yst;
+  D.Vst = P->Vst;
+  ck(hfx::launch_vblocks(D, P->v_list, (int)P->tot[3], s), "vblocks");
+  ck(hfx::launch_ybuild(D, P->y_list, (int)P->tot[1], s), "ybuild");
+  tm.mark();  // 3
+  ck(hfx::launch_term1(D, P->t1_list, (int)P->tot[4], P->beta_chunk, P->smem_t1, s), "term1");
+  tm.mark();  // 4
+  ck(hfx::launch_term2(D, P->t2_list, (int)P->tot[5], P->alpha_chunk, P->smem_t2, s), "term2");
+  tm.mark();  // 5
+  ck(cudaMemsetAsync(P->d_out, 0, (1 + 3 * (size_t)P->N + 9) * sizeof(double), s), "memset");
+  ck(hfx::launch_reduce(D, P->d_out, s), "reduce");
+  tm.mark();  // 6
+  if (st) {
+    double acc[hfx::ACC_N];
+    ck(cudaMemcpyAsync(acc, P->d_acc, sizeof(acc), cudaMemcpyDeviceToHost, s), "D2H acc");
+    ck(cudaStreamSynchronize(s), "stats");
+    hfx_stats S{};
+    S.c_pairs = (long long)P->cnt[hfx::CNT_C];
+    S.v_pairs = (long long)P->cnt[hfx::CNT_V];
+    S.d_blocks = (long long)P->cnt[hfx::CNT_D];
+    S.triplets = (long long)P->cnt[hfx::CNT_TRIP];
+    S.term1_pairs = P->tot[4];
+    S.term2_pairs = P->tot[5];
+    S.y_blocks = P->tot[1];
+    S.flops_y = acc[hfx::ACC_FY];
+    S.flops_term1 = acc[hfx::ACC_F1];
+    S.flops_term2 = acc[hfx::ACC_F2];
+    S.flops_total = S.flops_y + S.flops_term1 + S.flops_term2;
+    S.ms_blocks = tm.ms(0, 1);
+    S.ms_screen = tm.ms(1, 2);
+    S.ms_y = tm.ms(2, 3);
+    S.ms_term1 = tm.ms(3, 4);
+    S.ms_term2 = tm.ms(4, 5);
+    S.ms_reduce = tm.ms(5, 6);
+    S.ms_total = tm.ms(0, 6);
+    S.device_bytes = P->mem.bytes;
+    S.kernel_launches = hfx::launch_count() - launches0;
+    *st = S;
+  }
+}
+
+}  // namespace
+
+namespace {
+hfx_status run_guarded(hfx_plan* P, const std::function<void()>& fn) {
+  try {
+    fn();
+    if (P) P->err.clear();
+    return HFX_OK;
+  } catch (const Failure& f) {
+    if (P) P->err = f.msg;
+    return f.status;
+  } catch (const std::bad_alloc&) {
+    if (P) P->err = "host allocation failed";
+    return HFX_ERR_OOM;
+  } catch (const std::exception& e) {
+    if (P) P->err = e.what();
+    return HFX_ERR_INVALID;
+  } catch (...) {
+    if (P) P->err = "unknown error";
+    return HFX_ERR_INVALID;
+  }
+}
+
+thread_local std::string g_create_error;
+
+void prepare_call(hfx_plan* P, const double* lattice, const double* positions_host) {
+  validate_geometry(P->N, lattice, positions_host);
+  const double drift = list_drift(P, lattice, positions_host);
+  if (2.0 * drift >= P->opt.skin) {
+    if (P->opt.freeze_lists) fail(HFX_ERR_PAIRLIST_STALE, "atoms moved beyond skin/2 on a frozen plan");
+    build_lists(P, lattice, positions_host);
+  }
+}
+}  // namespace
+
+extern "C" {
+
+hfx_status hfx_default_options(hfx_options* o) {
+  if (!o) return HFX_ERR_INVALID;
+  std::memset(o, 0, sizeof(*o));
+  o->theta_C = o->theta_dC = o->theta_V = o->theta_dV = o->theta_D = o->theta_CS = 1e-10;
+  o->precision = HFX_FP64;
+  o->terms = HFX_TERMS_ALL;
+  o->skin = 0.5;
+  o->freeze_lists = 0;
+  o->deterministic = 0;
+  o->stream = nullptr;
+  o->device = 0;
+  return HFX_OK;
+}
+
+hfx_status hfx_plan_create(const hfx_system* sys, const hfx_model* model, const hfx_options* opt, hfx_plan** out) {
+  if (!out) return HFX_ERR_INVALID;
+  *out = nullptr;
+  hfx_plan* P = nullptr;
+  try {
+    P = new hfx_plan();
+  } catch (...) {
+    return HFX_ERR_OOM;
+  }
+  hfx_status st = run_guarded(P, [&]() {
+    validate_options(opt);
+    if (!sys || !model) fail(HFX_ERR_INVALID, "system or model is NULL");
+    if (sys->n_atoms <= 0 || !sys->species) fail(HFX_ERR_INVALID, "bad n_atoms or species");
+    if (model->n_species < 1 || model->n_species > hfx::kMaxSpecies) fail(HFX_ERR_INVALID, "n_species out of range");
+    if (!model->n_ao || !model->n_abf || !model->G || !model->M) fail(HFX_ERR_INVALID, "NULL model arrays");
+    if (!(model->r_c > 0) || !std::isfinite(model->r_c) || !(model->omega > 0) || !std::isfinite(model->omega))
+      fail(HFX_ERR_INVALID, "r_c and omega must be finite and > 0");
+    validate_geometry(sys->n_atoms, sys->lattice, sys->positions);
+    P->opt = *opt;
+    P->dev = opt->device;
+    P->stream = static_cast<cudaStream_t>(opt->stream);
+    ck(cudaSetDevice(P->dev), "cudaSetDevice");
+    P->N = sys->n_atoms;
+    P->S = model->n_species;
+    P->RC = 2.0 * model->r_c;
+    P->omega = model->omega;
+    upload_model(P, sys, model);
+    upload_density(P, model);
+    P->d_pos = P->mem.alloc<double>(3 * (size_t)P->N);
+    P->d_out = P->mem.alloc<double>(1 + 3 * (size_t)P->N + 9);
+    P->d_acc = P->mem.alloc<double>(hfx::ACC_N);
+    P->d_tot = P->mem.alloc<long long>(8 + hfx::CNT_N);
+    ck(cudaMemset(P->d_tot, 0, (8 + hfx::CNT_N) * sizeof(long long)), "memset");
+    setup_shapes(P);
+    build_lists(P, sys->lattice, sys->positions);
+  });
+  if (st != HFX_OK) {
+    g_create_error = P->err;
+    if (P->scan_tmp.buf) cudaFree(P->scan_tmp.buf);
+    P->mem.free_all();
+    delete P;
+    return st;
+  }
+  *out = P;
+  return HFX_OK;
+}
+
+hfx_status hfx_energy_force_stress(hfx_plan* P, const double* lattice, const double* positions, double* E,
+                                   double* F, double* sigma, hfx_stats* stats) {
+  if (!P) return HFX_ERR_INVALID;
+  return run_guarded(P, [&]() {
+    if (!E || !F || !sigma) fail(HFX_ERR_INVALID, "NULL output");
+    ck(cudaSetDevice(P->dev), "cudaSetDevice");
+    prepare_call(P, lattice, positions);
+    ck(cudaMemcpyAsync(P->d_pos, positions, 3 * (size_t)P->N * sizeof(double), cudaMemcpyHostToDevice, P->stream),
+       "H2D positions");
+    evaluate(P, lattice, stats);
+    const size_t n = 1 + 3 * (size_t)P->N + 9;
+    P->pos_host_buf.resize(n);
+    ck(cudaMemcpyAsync(P->pos_host_buf.data(), P->d_out, n * sizeof(double), cudaMemcpyDeviceToHost, P->stream),
+       "D2H results");
+    ck(cudaStreamSynchronize(P->stream), "results");
+    *E = P->pos_host_buf[0];
+    std::memcpy(F, P->pos_host_buf.data() + 1, 3 * (size_t)P->N * sizeof(double));
+    std::memcpy(sigma, P->pos_host_buf.data() + 1 + 3 * P->N, 9 * sizeof(double));
+  });
+}
+
+hfx_status hfx_energy_force_stress_device(hfx_plan* P, const double* lattice, const double* d_positions,
+                                          double* d_out, hfx_stats* stats) {
+  if (!P) return HFX_ERR_INVALID;
+  return run_guarded(P, [&]() {
+    if (!d_positions || !d_out) fail(HFX_ERR_INVALID, "NULL device pointer");
+    ck(cudaSetDevice(P->dev), "cudaSetDevice");
+    std::vector<double> ph(3 * (size_t)P->N);
+    ck(cudaMemcpyAsync(ph.data(), d_positions, ph.size() * sizeof(double), cudaMemcpyDeviceToHost, P->stream),
+       "D2H positions");
+    ck(cudaStreamSynchronize(P->stream), "positions");
+    prepare_call(P, lattice, ph.data());
+    ck(cudaMemcpyAsync(P->d_pos, d_positions, ph.size() * sizeof(double), cudaMemcpyDeviceToDevice, P->stream),
+       "D2D positions");
+    evaluate(P, lattice, stats);
+    ck(cudaMemcpyAsync(d_out, P->d_out, (1 + 3 * (size_t)P->N + 9) * sizeof(double), cudaMemcpyDeviceToDevice,
+                       P->stream),
+       "D2D results");
+    ck(cudaStreamSynchronize(P->stream), "results");
+  });
+}
+
+hfx_status hfx_set_timing(hfx_plan* P, int on) {
+  if (!P) return HFX_ERR_INVALID;
+  P->timing = on != 0;
+  return HFX_OK;
+}
+
+hfx_status hfx_plan_destroy(hfx_plan* P) {
+  if (!P) return HFX_OK;
+  cudaSetDevice(P->dev);
+  cudaStreamSynchronize(P->stream);
+  if (P->scan_tmp.buf) cudaFree(P->scan_tmp.buf);
+  P->mem.free_all();
+  delete P;
+  return HFX_OK;
+}
+
+const char* hfx_status_string(hfx_status s) {
+  switch (s) {
+    case HFX_OK: return "ok";
+    case HFX_ERR_INVALID: return "invalid argument";
+    case HFX_ERR_OOM: return "out of memory";
+    case HFX_ERR_CUDA: return "CUDA error";
+    case HFX_ERR_TIMEOUT: return "timeout";
+    case HFX_ERR_PAIRLIST_STALE: return "pair list stale";
+    case HFX_ERR_UNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+const char* hfx_last_error(const hfx_plan* P) {
+  if (!P) return g_create_error.c_str();
+  return P->err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,133 @@
+// Internal declarations shared by the host planner (hfx_host.cpp) and the
+// CUDA kernels (hfx_kernels.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace hfx {
+
+constexpr int kMaxSpecies = 16;
+constexpr int kMaxAO = 32;
+constexpr int kMaxABF = 128;
+constexpr int kMaxCPerAtom = 256;     // C-pair candidates per home atom (mask width)
+constexpr int kMaskWords = kMaxCPerAtom / 32;
+
+// Everything a kernel needs, passed by value.  All pointers are device
+// pointers.  Pair p of a list is (home atom *_home[p] -> atom *_j[p], image
+// *_R[3p..3p+2]); its vector is d = tau_j + R.L - tau_home.
+struct DevPlan {
+  int N, S;
+  const int* species;
+  const int* n_ao;
+  const int* n_abf;
+  const long long* G_off;      // [S*S] element offsets of G_st (and G'_st)
+  const double* G;
+  const double* Gp;            // anisotropic templates or nullptr
+  const long long* M_off;
+  const double* M;
+  double e[3];
+  double RC, omega;
+  double thC, thdC, thV, thdV, thD, thCS;
+  int terms;
+
+  const double* pos;           // [N*3] current positions
+  double L[9];                 // current lattice (rows)
+
+  // density matrix
+  long long n_d;
+  const double* Dval;
+  const long long* Doff;
+  const int* Didx;             // [n_d*5]
+  double* Dkept;               // [n_d] ||D|| if kept by step 1, else 0
+  const int* dlut;             // dense (i, j, R) -> block index or -1
+  int HD0, HD1, HD2;
+
+  // C-pair candidates
+  int nC;
+  const int* c_ptr;            // [N+1]
+  const int* c_home;
+  const int* c_j;
+  const int* c_R;
+  const long long* c_off;      // element offset of C_p in Cst (grad C_p at 3*c_off in dCst)
+  double* Cst;
+  double* dCst;
+  double* c_norm;              // max(||C||, ||grad C||) if kept, else 0
+  unsigned char* c_keep;
+
+  // V-pair candidates
+  int nV;
+  const int* v_ptr;
+  const int* v_home;
+  const int* v_j;
+  const int* v_R;
+  const int* v_didx;           // D block of (home, j, R) or -1
+  double* v_norm;              // max(||V||, ||grad V||) if kept, else 0
+  unsigned char* v_keep;
+  unsigned int* v_mask;        // [nV*kMaskWords] kept F (C-pair slots of home)
+  unsigned char* v_t2;         // kept for the second exchange product
+  int* v_flag;                 // V block needed this call
+  long long* v_off;            // offset of (V, grad V) in Vst
+  double* Vst;
+
+  // Y^{XZ} candidates (X home, Z = (j, R))
+  int nY;
+  const int* y_ptr;
+  const int* y_home;
+  const int* y_j;
+  const int* y_R;
+  double* yhat;
+  int* y_flag;
+  long long* y_off;
+  double* Yst;
+  const int* ylut;
+  int HY0, HY1, HY2;
+
+  // accumulators
+  double* gC;                  // [nC*3] dE/dd for C pairs
+  double* gV;                  // [nV*3]
+  double* acc;                 // [0] E, [1..9] virial sum g (x) d, [10] flops y, [11] t1, [12] t2
+  unsigned long long* cnt;     // [0] c kept, [1] v kept, [2] d kept, [3] triplets
+};
+
+enum AccSlot { ACC_E = 0, ACC_W = 1, ACC_FY = 10, ACC_F1 = 11, ACC_F2 = 12, ACC_N = 16 };
+enum CntSlot { CNT_C = 0, CNT_V = 1, CNT_D = 2, CNT_TRIP = 3, CNT_N = 8 };
+
+// Kernels launched by this library since load (every launcher adds its
+// launches); the host reads it before and after a call.
+long long launch_count();
+
+// Kernel launchers (hfx_kernels.cu).  Each returns the launch's cudaError_t.
+cudaError_t launch_dnorm(const DevPlan& P, cudaStream_t s);
+cudaError_t launch_cblocks(const DevPlan& P, int frozen, cudaStream_t s);
+cudaError_t launch_vnorm(const DevPlan& P, int frozen, cudaStream_t s);
+cudaError_t launch_yhat(const DevPlan& P, cudaStream_t s);
+cudaError_t launch_screen(const DevPlan& P, cudaStream_t s);
+cudaError_t launch_vblocks(const DevPlan& P, const int* v_list, int n, cudaStream_t s);
+cudaError_t launch_ybuild(const DevPlan& P, const int* y_list, int n, cudaStream_t s);
+cudaError_t launch_term1(const DevPlan& P, const int* list, int n, int beta_chunk, size_t smem,
+                         cudaStream_t s);
+cudaError_t launch_term2(const DevPlan& P, const int* list, int n, int alpha_chunk, size_t smem,
+                         cudaStream_t s);
+cudaError_t launch_reduce(const DevPlan& P, double* out, cudaStream_t s);
+cudaError_t set_kernel_smem_limits(size_t t1, size_t t2);
+
+// Exclusive scan helpers.  `mode` selects what is summed per element i:
+//   0: flag[i] != 0 (int32 flags)
+//   1: flag[i] != 0 ? size[i] : 0
+//   2: popcount-free "mask nonzero" over kMaskWords words (v_mask)
+// The scan writes out[i] (exclusive prefix, int64) and *total (device).
+struct ScanTmp {
+  long long* buf = nullptr;
+  size_t cap = 0;
+};
+cudaError_t scan_flags(const int* flag, const long long* size, const unsigned* mask,
+                       const unsigned char* bytes, int mode, int n, long long* out,
+                       long long* total, ScanTmp& tmp, cudaStream_t s);
+// list[out[i]] = i for every i selected by the same `mode` rule.
+cudaError_t scatter_list(const int* flag, const unsigned* mask, const unsigned char* bytes, int mode,
+                         int n, const long long* off, int* list, cudaStream_t s);
+
+}  // namespace hfx
