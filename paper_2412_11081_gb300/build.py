@@ -32,6 +32,8 @@ def build(verbose: bool = False) -> str:
     units = {
         "hfx_kernels.o": [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", *inc,
                           "-c", os.path.join(CSRC, "hfx_kernels.cu")],
+        "hfx_mixed.o": [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", *inc,
+                        "-c", os.path.join(CSRC, "hfx_mixed.cu")],
         "hfx_host.o": [nvcc, *ARCH, "-O2", "-std=c++17", "-Xcompiler", "-fPIC", *inc,
                        "-x", "cu", "-c", os.path.join(CSRC, "hfx_host.cpp")],
     }

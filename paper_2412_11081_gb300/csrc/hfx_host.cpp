@@ -22,6 +22,7 @@
 #include "hfx_internal.h"
 
 using hfx::DevPlan;
+constexpr int kTot = 16;
 
 namespace {
 
@@ -152,18 +153,37 @@ struct hfx_plan {
   double* d_pos = nullptr;
   double* d_out = nullptr;     // [1 + 3N + 9]
   double* d_acc = nullptr;     // hfx::ACC_N
-  long long* d_tot = nullptr;  // [8] totals of the scans, then hfx::CNT_N counters
+  long long* d_tot = nullptr;  // [kTot] totals of the scans, then hfx::CNT_N counters
   double* Yst = nullptr;
   long long Ycap = 0;
   double* Vst = nullptr;
   long long Vcap = 0;
   hfx::ScanTmp scan_tmp;
-  long long tot[8] = {0};      // y elems, y count, v elems, v count, t1, t2
+  long long tot[16] = {0};     // y elems, y count, v elems, v count, t1, t2, triplets, t1q, vm elems
   unsigned long long cnt[hfx::CNT_N] = {0};
 
   // kernel shapes
   int beta_chunk = 1, alpha_chunk = 1;
   size_t smem_t1 = 0, smem_t2 = 0;
+
+  // split-precision path (np = bf16 pieces per operand; 0 = FP64 path)
+  int np = 0;
+  uint16_t* Dsp = nullptr;
+  long long* dsp_off = nullptr;
+  uint16_t* Ysp = nullptr;
+  long long Yspcap = 0;
+  uint16_t* Cm = nullptr;
+  long long* cm_off = nullptr;
+  uint16_t* Vm = nullptr;
+  long long Vmcap = 0;
+  long long *vm_off = nullptr, *vm_size = nullptr;
+  int* qcnt = nullptr;
+  long long *qoff = nullptr, *q_idx = nullptr;
+  int* t1q_list = nullptr;
+  int* blist = nullptr;
+  long long blist_cap = 0;
+  int MAmax = 0, MBmax = 0, KSmax = 0, ZROWS = 0, ZSmax = 0;
+  size_t smem_m1 = 0, smem_m2 = 0;
 
   bool timing = false;
   std::vector<double> pos_host_buf;
@@ -188,7 +208,8 @@ void validate_options(const hfx_options* o) {
   const double th[6] = {o->theta_C, o->theta_dC, o->theta_V, o->theta_dV, o->theta_D, o->theta_CS};
   for (double t : th)
     if (!std::isfinite(t) || t < 0) fail(HFX_ERR_INVALID, "thresholds must be finite and >= 0");
-  if (o->precision != HFX_FP64) fail(HFX_ERR_UNSUPPORTED, "only HFX_FP64 is available in this build");
+  if (o->precision != HFX_FP64 && o->precision != HFX_BF16X3 && o->precision != HFX_BF16X6)
+    fail(HFX_ERR_UNSUPPORTED, "precision must be HFX_FP64, HFX_BF16X3 or HFX_BF16X6");
   if (o->terms < 1 || o->terms > 3) fail(HFX_ERR_INVALID, "terms must be 1, 2 or 3");
   if (!std::isfinite(o->skin) || o->skin < 0) fail(HFX_ERR_INVALID, "skin must be finite and >= 0");
   if (o->deterministic != 0) fail(HFX_ERR_UNSUPPORTED, "deterministic mode is not available");
@@ -429,7 +450,7 @@ DevPlan make_devplan(hfx_plan* P, const double* lattice) {
   D.gC = P->gC;
   D.gV = P->gV;
   D.acc = P->d_acc;
-  D.cnt = reinterpret_cast<unsigned long long*>(P->d_tot + 8);
+  D.cnt = reinterpret_cast<unsigned long long*>(P->d_tot + kTot);
   return D;
 }
 
@@ -551,7 +572,10 @@ void build_lists(hfx_plan* P, const double* L, const double* pos) {
     v_size[p] = 4ll * P->n_abf[P->species[v_home[p]]] * P->n_abf[P->species[v_j[p]]];
   for (int y = 0; y < nY; ++y) {
     const int sX = P->species[y_home[y]], sz = P->species[y_j[y]];
-    y_size[y] = (long long)P->n_abf[sX] * P->n_ao[sX] * P->n_ao[sz];
+    if (P->np)  // bf16 pieces of [alpha][z][rup16(n_ao(X))]
+      y_size[y] = (long long)P->np * P->n_abf[sX] * P->n_ao[sz] * ((P->n_ao[sX] + 15) / 16 * 16);
+    else
+      y_size[y] = (long long)P->n_abf[sX] * P->n_ao[sX] * P->n_ao[sz];
   }
 
   // (re)allocate list buffers
@@ -603,6 +627,29 @@ void build_lists(hfx_plan* P, const double* L, const double* pos) {
   P->y_list = P->lalloc<int>(nY);
   P->gC = P->lalloc<double>(3 * (size_t)nC);
   P->gV = P->lalloc<double>(3 * (size_t)nV);
+  if (P->np) {
+    std::vector<long long> cm_off(nC + 1, 0), vm_size(nV);
+    for (int p = 0; p < nC; ++p) {
+      const int sA = P->species[c_home[p]], sj = P->species[c_j[p]];
+      const long long rows = (long long)P->n_abf[sA] * P->n_ao[sA];
+      const long long pF = (P->n_ao[sj] + 15) / 16 * 16;
+      cm_off[p + 1] = cm_off[p] + P->np * rows * pF + 2 * 3 * rows * P->n_ao[sj];
+    }
+    for (int p = 0; p < nV; ++p) {
+      const long long mA = P->n_abf[P->species[v_home[p]]], mB = P->n_abf[P->species[v_j[p]]];
+      vm_size[p] = P->np * mA * ((mB + 15) / 16 * 16) + 2 * 4 * mA * mB;
+    }
+    P->cm_off = P->lalloc<long long>(nC + 1);
+    P->Cm = P->lalloc<uint16_t>(cm_off[nC]);
+    P->vm_off = P->lalloc<long long>(nV);
+    P->vm_size = P->lalloc<long long>(nV);
+    upload(P->cm_off, cm_off, s);
+    upload(P->vm_size, vm_size, s);
+    P->qcnt = P->lalloc<int>(nC);
+    P->qoff = P->lalloc<long long>(nC);
+    P->q_idx = P->lalloc<long long>(nC);
+    P->t1q_list = P->lalloc<int>(nC);
+  }
   upload(P->c_ptr, c_ptr, s);
   upload(P->c_home, c_home, s);
   upload(P->c_j, c_j, s);
@@ -671,6 +718,43 @@ void setup_shapes(hfx_plan* P) {
   P->alpha_chunk = (int)std::min<size_t>(maxABF, (limit - base2) / per1);
   P->smem_t2 = base2 + per1 * P->alpha_chunk;
   ck(hfx::set_kernel_smem_limits(P->smem_t1, P->smem_t2), "smem attributes");
+  if (P->np) {
+    auto r16 = [](int x) { return (x + 15) / 16 * 16; };
+    int maxKAF = 0, zrows = 0;
+    for (int a = 0; a < P->S; ++a) {
+      zrows = std::max(zrows, r16(P->n_abf[a] * P->n_ao[a]));
+      for (int b = 0; b < P->S; ++b) maxKAF = std::max(maxKAF, P->n_ao[a] * P->n_ao[b]);
+    }
+    P->MAmax = r16(maxABF);
+    P->MBmax = r16(maxABF);
+    P->KSmax = r16(maxKAF) + 8;
+    P->ZROWS = zrows;
+    P->ZSmax = r16(maxAO) + 8;
+    P->smem_m1 = hfx::term1_mma_smem(P->np, P->MAmax, P->MBmax, P->KSmax);
+    P->smem_m2 = hfx::term2_mma_smem(P->np, P->ZROWS, P->ZSmax);
+    const int qtiles = (P->MAmax / 16) * ((maxKAF + 7) / 8);
+    if (P->smem_m1 > limit || P->smem_m2 > limit || qtiles > 256)
+      fail(HFX_ERR_UNSUPPORTED, "block shapes too large for the split-precision kernels");
+    ck(hfx::set_mixed_smem_limits(P->np, P->smem_m1, P->smem_m2), "smem attributes");
+  }
+}
+
+// bf16 pieces of every D block (fixed for the plan)
+void split_density(hfx_plan* P) {
+  if (!P->np || P->n_d == 0) return;
+  std::vector<long long> off(P->n_d + 1, 0);
+  for (long long k = 0; k < P->n_d; ++k) {
+    const int* r = &P->d_index[5 * k];
+    const long long a = (P->n_ao[P->species[r[0]]] + 15) / 16 * 16, b = (P->n_ao[P->species[r[1]]] + 15) / 16 * 16;
+    off[k + 1] = off[k] + (long long)P->np * a * b;
+  }
+  P->dsp_off = P->mem.alloc<long long>(P->n_d + 1);
+  P->Dsp = P->mem.alloc<uint16_t>(off[P->n_d]);
+  upload(P->dsp_off, off, P->stream);
+  DevPlan D = make_devplan(P, P->lat_ref.data());
+  hfx::MixPlan X{P->Dsp, P->dsp_off, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  ck(hfx::launch_dsplit(D, X, P->np, P->stream), "dsplit");
+  ck(cudaStreamSynchronize(P->stream), "dsplit");
 }
 
 void ensure_store(hfx_plan* P, double*& buf, long long& cap, long long need) {
@@ -680,6 +764,17 @@ void ensure_store(hfx_plan* P, double*& buf, long long& cap, long long need) {
   cap = 0;
   const long long n = need + need / 8 + 1024;
   buf = P->mem.alloc<double>((size_t)n);
+  cap = n;
+}
+
+template <class T>
+void ensure_buf(hfx_plan* P, T*& buf, long long& cap, long long need) {
+  if (need <= cap) return;
+  if (buf) P->mem.release(buf);
+  buf = nullptr;
+  cap = 0;
+  const long long n = need + need / 8 + 1024;
+  buf = P->mem.alloc<T>((size_t)n);
   cap = n;
 }
 
@@ -710,12 +805,13 @@ struct Timer {
 void evaluate(hfx_plan* P, const double* L, hfx_stats* st) {
   cudaStream_t s = P->stream;
   DevPlan D = make_devplan(P, L);
-  const long long launches0 = hfx::launch_count();
+  const long long launches0 = hfx::launch_count() + hfx::mixed_launch_count();
+  hfx::MixPlan X{P->Dsp, P->dsp_off, P->Ysp, P->Cm, P->cm_off, P->Vm, P->vm_off, P->qcnt, P->qoff, P->blist};
   const bool reuse = P->opt.freeze_lists && P->frozen_ready;
   Timer tm(P->timing, s);
   tm.mark();  // 0
   ck(cudaMemsetAsync(P->d_acc, 0, hfx::ACC_N * sizeof(double), s), "memset");
-  ck(cudaMemsetAsync(P->d_tot + 8, 0, hfx::CNT_N * sizeof(long long), s), "memset");
+  ck(cudaMemsetAsync(P->d_tot + kTot, 0, hfx::CNT_N * sizeof(long long), s), "memset");
   ck(cudaMemsetAsync(P->gC, 0, 3 * (size_t)P->nC * sizeof(double), s), "memset");
   ck(cudaMemsetAsync(P->gV, 0, 3 * (size_t)P->nV * sizeof(double), s), "memset");
   ck(hfx::launch_dnorm(D, s), "dnorm");
@@ -737,23 +833,56 @@ void evaluate(hfx_plan* P, const double* L, hfx_stats* st) {
     ck(hfx::scatter_list(nullptr, P->v_mask, nullptr, 2, P->nV, P->t1_idx, P->t1_list, s), "scatter");
     ck(hfx::scan_flags(nullptr, nullptr, nullptr, P->v_t2, 3, P->nV, P->t2_idx, T + 5, P->scan_tmp, s), "scan");
     ck(hfx::scatter_list(nullptr, nullptr, P->v_t2, 3, P->nV, P->t2_idx, P->t2_list, s), "scatter");
+    if (P->np) {
+      // (A,F) view of the kept triplets: per C pair, its kept B in V-pair order
+      ck(hfx::scan_flags(P->v_flag, P->vm_size, nullptr, nullptr, 1, P->nV, P->vm_off, T + 8, P->scan_tmp, s), "scan");
+      ck(hfx::launch_t1_lists(D, X, 0, s), "t1 count");
+      ck(hfx::scan_flags(P->qcnt, nullptr, nullptr, nullptr, 4, P->nC, P->qoff, T + 6, P->scan_tmp, s), "scan");
+      ck(hfx::scan_flags(P->qcnt, nullptr, nullptr, nullptr, 0, P->nC, P->q_idx, T + 7, P->scan_tmp, s), "scan");
+      ck(hfx::scatter_list(P->qcnt, nullptr, nullptr, 0, P->nC, P->q_idx, P->t1q_list, s), "scatter");
+    }
   }
-  ck(cudaMemcpyAsync(P->tot, P->d_tot, 8 * sizeof(long long), cudaMemcpyDeviceToHost, s), "D2H totals");
-  ck(cudaMemcpyAsync(P->cnt, P->d_tot + 8, hfx::CNT_N * sizeof(long long), cudaMemcpyDeviceToHost, s), "D2H counts");
+  ck(cudaMemcpyAsync(P->tot, P->d_tot, kTot * sizeof(long long), cudaMemcpyDeviceToHost, s), "D2H totals");
+  ck(cudaMemcpyAsync(P->cnt, P->d_tot + kTot, hfx::CNT_N * sizeof(long long), cudaMemcpyDeviceToHost, s), "D2H counts");
   ck(cudaStreamSynchronize(s), "screening");
   if (P->opt.freeze_lists) P->frozen_ready = true;
   tm.mark();  // 2
-  ensure_store(P, P->Yst, P->Ycap, P->tot[0]);
   ensure_store(P, P->Vst, P->Vcap, P->tot[2]);
-  D.Yst = P->Yst;
   D.Vst = P->Vst;
-  ck(hfx::launch_vblocks(D, P->v_list, (int)P->tot[3], s), "vblocks");
-  ck(hfx::launch_ybuild(D, P->y_list, (int)P->tot[1], s), "ybuild");
-  tm.mark();  // 3
-  ck(hfx::launch_term1(D, P->t1_list, (int)P->tot[4], P->beta_chunk, P->smem_t1, s), "term1");
-  tm.mark();  // 4
-  ck(hfx::launch_term2(D, P->t2_list, (int)P->tot[5], P->alpha_chunk, P->smem_t2, s), "term2");
-  tm.mark();  // 5
+  if (!P->np) {
+    ensure_store(P, P->Yst, P->Ycap, P->tot[0]);
+    D.Yst = P->Yst;
+    ck(hfx::launch_vblocks(D, P->v_list, (int)P->tot[3], s), "vblocks");
+    ck(hfx::launch_ybuild(D, P->y_list, (int)P->tot[1], s), "ybuild");
+    tm.mark();  // 3
+    ck(hfx::launch_term1(D, P->t1_list, (int)P->tot[4], P->beta_chunk, P->smem_t1, s), "term1");
+    tm.mark();  // 4
+    ck(hfx::launch_term2(D, P->t2_list, (int)P->tot[5], P->alpha_chunk, P->smem_t2, s), "term2");
+    tm.mark();  // 5
+  } else {
+    ensure_buf(P, P->Ysp, P->Yspcap, P->tot[0]);
+    X.Ysp = P->Ysp;
+    if (!reuse) {
+      ensure_buf(P, P->blist, P->blist_cap, P->tot[6]);
+      X.blist = P->blist;
+      ck(hfx::launch_t1_lists(D, X, 1, s), "t1 fill");
+    }
+    X.blist = P->blist;
+    ensure_buf(P, P->Vm, P->Vmcap, P->tot[8]);
+    X.Vm = P->Vm;
+    ck(hfx::launch_vblocks(D, P->v_list, (int)P->tot[3], s), "vblocks");
+    ck(hfx::launch_vpieces(D, X, P->np, P->v_list, (int)P->tot[3], s), "vpieces");
+    ck(hfx::launch_cpieces(D, X, P->np, s), "cpieces");
+    int wide = 0;
+    for (int t = 0; t < P->S; ++t) wide |= P->n_ao[t] > 16;
+    ck(hfx::launch_ybuild_mma(D, X, P->np, P->y_list, (int)P->tot[1], wide, s), "ybuild");
+    tm.mark();  // 3
+    ck(hfx::launch_term1_mma(D, X, P->np, P->t1q_list, (int)P->tot[7], P->MAmax, P->MBmax, P->KSmax, P->smem_m1, s),
+       "term1");
+    tm.mark();  // 4
+    ck(hfx::launch_term2_mma(D, X, P->np, P->t2_list, (int)P->tot[5], P->ZROWS, P->smem_m2, s), "term2");
+    tm.mark();  // 5
+  }
   ck(cudaMemsetAsync(P->d_out, 0, (1 + 3 * (size_t)P->N + 9) * sizeof(double), s), "memset");
   ck(hfx::launch_reduce(D, P->d_out, s), "reduce");
   tm.mark();  // 6
@@ -781,7 +910,7 @@ void evaluate(hfx_plan* P, const double* L, hfx_stats* st) {
     S.ms_reduce = tm.ms(5, 6);
     S.ms_total = tm.ms(0, 6);
     S.device_bytes = P->mem.bytes;
-    S.kernel_launches = hfx::launch_count() - launches0;
+    S.kernel_launches = hfx::launch_count() + hfx::mixed_launch_count() - launches0;
     *st = S;
   }
 }
@@ -863,15 +992,17 @@ hfx_status hfx_plan_create(const hfx_system* sys, const hfx_model* model, const 
     P->S = model->n_species;
     P->RC = 2.0 * model->r_c;
     P->omega = model->omega;
+    P->np = opt->precision == HFX_BF16X3 ? 2 : opt->precision == HFX_BF16X6 ? 3 : 0;
     upload_model(P, sys, model);
     upload_density(P, model);
     P->d_pos = P->mem.alloc<double>(3 * (size_t)P->N);
     P->d_out = P->mem.alloc<double>(1 + 3 * (size_t)P->N + 9);
     P->d_acc = P->mem.alloc<double>(hfx::ACC_N);
-    P->d_tot = P->mem.alloc<long long>(8 + hfx::CNT_N);
-    ck(cudaMemset(P->d_tot, 0, (8 + hfx::CNT_N) * sizeof(long long)), "memset");
+    P->d_tot = P->mem.alloc<long long>(kTot + hfx::CNT_N);
+    ck(cudaMemset(P->d_tot, 0, (kTot + hfx::CNT_N) * sizeof(long long)), "memset");
     setup_shapes(P);
     build_lists(P, sys->lattice, sys->positions);
+    split_density(P);
   });
   if (st != HFX_OK) {
     g_create_error = P->err;

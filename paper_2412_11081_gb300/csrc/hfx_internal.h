@@ -92,6 +92,20 @@ struct DevPlan {
   unsigned long long* cnt;     // [0] c kept, [1] v kept, [2] d kept, [3] triplets
 };
 
+// Extra state of the split-precision path.
+struct MixPlan {
+  uint16_t* Dsp;               // D blocks as bf16 pieces, rup16(n_ao(I)) x rup16(n_ao(J)) per piece
+  const long long* dsp_off;    // [n_d]
+  uint16_t* Ysp;               // Y^{XZ} as bf16 pieces, [alpha][z][rup16(n_ao(X))] per piece
+  uint16_t* Cm;                // per C pair: bf16 pieces of C, then grad C in FP32
+  const long long* cm_off;     // [nC] offsets (uint16 units)
+  uint16_t* Vm;                // per needed V pair: bf16 pieces of V, then V and grad V in FP32
+  const long long* vm_off;     // [nV] offsets (uint16 units), from the per-call scan
+  int* qcnt;                   // [nC] kept B per (A,F)
+  long long* qoff;             // [nC] offsets into blist
+  int* blist;                  // V pairs (A,B) per (A,F), in V-pair order
+};
+
 enum AccSlot { ACC_E = 0, ACC_W = 1, ACC_FY = 10, ACC_F1 = 11, ACC_F2 = 12, ACC_N = 16 };
 enum CntSlot { CNT_C = 0, CNT_V = 1, CNT_D = 2, CNT_TRIP = 3, CNT_N = 8 };
 
@@ -114,10 +128,28 @@ cudaError_t launch_term2(const DevPlan& P, const int* list, int n, int alpha_chu
 cudaError_t launch_reduce(const DevPlan& P, double* out, cudaStream_t s);
 cudaError_t set_kernel_smem_limits(size_t t1, size_t t2);
 
+// Split-precision kernels (hfx_mixed.cu); np = bf16 pieces per operand (2 or 3).
+long long mixed_launch_count();
+cudaError_t launch_dsplit(const DevPlan& P, const MixPlan& X, int np, cudaStream_t s);
+cudaError_t launch_cpieces(const DevPlan& P, const MixPlan& X, int np, cudaStream_t s);
+cudaError_t launch_vpieces(const DevPlan& P, const MixPlan& X, int np, const int* list, int n, cudaStream_t s);
+cudaError_t launch_ybuild_mma(const DevPlan& P, const MixPlan& X, int np, const int* list, int n, int wide,
+                              cudaStream_t s);
+cudaError_t launch_t1_lists(const DevPlan& P, const MixPlan& X, int phase, cudaStream_t s);
+size_t term1_mma_smem(int np, int MAmax, int MBmax, int KSmax);
+size_t term2_mma_smem(int np, int zrows, int zs);
+cudaError_t set_mixed_smem_limits(int np, size_t t1, size_t t2);
+cudaError_t launch_term1_mma(const DevPlan& P, const MixPlan& X, int np, const int* qlist, int n, int MAmax,
+                             int MBmax, int KSmax, size_t smem, cudaStream_t s);
+cudaError_t launch_term2_mma(const DevPlan& P, const MixPlan& X, int np, const int* list, int n, int zrows,
+                             size_t smem, cudaStream_t s);
+
 // Exclusive scan helpers.  `mode` selects what is summed per element i:
 //   0: flag[i] != 0 (int32 flags)
 //   1: flag[i] != 0 ? size[i] : 0
 //   2: popcount-free "mask nonzero" over kMaskWords words (v_mask)
+//   3: bytes[i] != 0
+//   4: flag[i] itself (a count)
 // The scan writes out[i] (exclusive prefix, int64) and *total (device).
 struct ScanTmp {
   long long* buf = nullptr;

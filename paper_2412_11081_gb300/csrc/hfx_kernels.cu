@@ -681,7 +681,8 @@ __device__ __forceinline__ long long scan_value(const int* flag, const long long
       for (int w = 0; w < kMaskWords; ++w) any |= mask[(size_t)i * kMaskWords + w];
       return any ? 1 : 0;
     }
-    default: return bytes[i] != 0 ? 1 : 0;
+    case 3: return bytes[i] != 0 ? 1 : 0;
+    default: return flag[i];
   }
 }
 
