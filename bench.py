@@ -4,7 +4,11 @@ supercell (2x2x2 diamond, n_ao 13, n_abf 50, r_c 3.7 A, thresholds 1e-10).
 One step = one full evaluation of the hot path (block generation, two-step
 screening, Y build, both exchange products, force/stress/energy reduction)
 on a warm plan, at a new geometry (small seeded jitter within the pair-list
-skin, so every block, norm and screening decision is recomputed).
+skin, so every block, norm and screening decision is recomputed).  The
+headline precision is HFX_BF16X6 (split bf16 on the tensor cores, within
+1e-5 relative force/stress error of FP64); FP64 and BF16X3 are reported
+beside it, with the error of each split measured against the FP64 GPU
+result of the same geometry.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -169,6 +173,21 @@ def run_reference(args):
     return 0
 
 
+def _time_device(plan, w, d_pos, d_out, first, steps, stream, torch):
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for k in range(steps):
+        plan.evaluate_device(w.lattice, d_pos[first + k].data_ptr(), d_out.data_ptr())
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1) / 1e3
+
+
+def _rel(a, b):
+    a, b = np.asarray(a, float), np.asarray(b, float)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
 def run_ours(args):
     import torch
     rank, world, local = _env_rank()
@@ -183,34 +202,46 @@ def run_ours(args):
     from paper_2412_11081_gb300 import hfx, inputs
     w = inputs.si_supercell(2)
     stream = torch.cuda.current_stream(dev)
-    plan = hfx.Plan(w, stream=stream.cuda_stream, device=local)
-    geoms = geometry_sequence(w, args.warmup + args.steps + 8)
     n = w.n_atoms
+    geoms = geometry_sequence(w, args.warmup + args.steps + 8)
     d_pos = [torch.tensor(g, dtype=torch.float64, device=dev) for g in geoms]
     d_out = torch.zeros(1 + 3 * n + 9, dtype=torch.float64, device=dev)
-
-    # warm-up (also the stats of one step)
-    for k in range(args.warmup):
-        plan.evaluate_device(w.lattice, d_pos[k].data_ptr(), d_out.data_ptr(), stats=True)
-    st = plan.stats.as_dict()
+    head_prec = {"bf16x6": hfx.HFX_BF16X6, "bf16x3": hfx.HFX_BF16X3, "fp64": hfx.HFX_FP64}[args.precision]
 
     def barrier():
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    # ---- device-resident timing (value)
+    # ---- reference result of the same geometry on the FP64 GPU path (parity-tested
+    #      against the CPU oracle to 1e-10): the error of the mixed path is taken here
+    fp64 = hfx.Plan(w, precision=hfx.HFX_FP64, stream=stream.cuda_stream, device=local)
+    ref = fp64.evaluate(w.lattice, geoms[0])
+    fp64_steps = max(1, min(2, args.steps))
+    fp64.evaluate_device(w.lattice, d_pos[1].data_ptr(), d_out.data_ptr())
+    barrier()
+    t_fp64 = _time_device(fp64, w, d_pos, d_out, 2, fp64_steps, stream, torch) / fp64_steps
+    fp64.close()
+
+    variants = {}
+    for name, prec in (("bf16x6", hfx.HFX_BF16X6), ("bf16x3", hfx.HFX_BF16X3)):
+        pl = hfx.Plan(w, precision=prec, stream=stream.cuda_stream, device=local)
+        E, F, S = pl.evaluate(w.lattice, geoms[0])
+        variants[name] = dict(plan=pl, errE=abs(E - ref[0]) / abs(ref[0]), errF=_rel(F, ref[1]), errS=_rel(S, ref[2]))
+    plan = variants[args.precision]["plan"] if args.precision != "fp64" else \
+        hfx.Plan(w, precision=hfx.HFX_FP64, stream=stream.cuda_stream, device=local)
+
+    for k in range(args.warmup):
+        plan.evaluate_device(w.lattice, d_pos[k].data_ptr(), d_out.data_ptr(), stats=True)
+    st = plan.stats.as_dict()
+
+    # ---- device-resident timing of the headline precision (value)
     clocks = ClockSampler(local)
     clocks.start()
     barrier()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for k in range(args.steps):
-        plan.evaluate_device(w.lattice, d_pos[args.warmup + k].data_ptr(), d_out.data_ptr())
-    ev1.record(stream)
+    t_dev = _time_device(plan, w, d_pos, d_out, args.warmup, args.steps, stream, torch)
     barrier()
     ck = clocks.stop()
-    t_dev = ev0.elapsed_time(ev1) / 1e3
     launches = st["kernel_launches"] * args.steps
 
     # ---- end-to-end through the host entry point (H2D positions, D2H results)
@@ -222,21 +253,29 @@ def run_ours(args):
     barrier()
     t_e2e = time.perf_counter() - t0
 
-    # ---- per-stage times of the dominant kernel (CUDA events on the plan's stream)
+    # ---- the other split precision (secondary line items)
+    other = {}
+    for name, v in variants.items():
+        if name == args.precision:
+            continue
+        pl = v["plan"]
+        pl.evaluate_device(w.lattice, d_pos[0].data_ptr(), d_out.data_ptr())
+        tt = _time_device(pl, w, d_pos, d_out, args.warmup, min(args.steps, 5), stream, torch) / min(args.steps, 5)
+        other[name] = {"evals_per_s": 1.0 / tt, "errE": v["errE"], "errF": v["errF"], "errS": v["errS"]}
+
+    # ---- per-stage times (CUDA events on the plan's stream)
     plan.set_timing(True)
-    stage = {"ms_blocks": [], "ms_screen": [], "ms_y": [], "ms_term1": [], "ms_term2": [], "ms_reduce": []}
+    stage = {k: [] for k in ("ms_blocks", "ms_screen", "ms_y", "ms_term1", "ms_term2", "ms_reduce")}
     flops = None
     for k in range(min(3, args.steps)):
         plan.evaluate_device(w.lattice, d_pos[k].data_ptr(), d_out.data_ptr(), stats=True)
-        s2 = plan.stats.as_dict()
-        flops = s2
+        flops = plan.stats.as_dict()
         for key in stage:
-            stage[key].append(s2[key])
+            stage[key].append(flops[key])
     plan.set_timing(False)
     stage_ms = {k: statistics.mean(v) for k, v in stage.items()}
 
-    t_max = t_dev
-    t_e2e_max = t_e2e
+    t_max, t_e2e_max = t_dev, t_e2e
     if dist is not None:
         tt = torch.tensor([t_dev, t_e2e], dtype=torch.float64, device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -247,40 +286,61 @@ def run_ours(args):
     if rank == 0:
         peaks = measured_peaks()
         fp64_peak = fp64_gemm_peak(torch, dev)
-        # dominant kernel: the larger of the two exchange products
-        dom = "term1" if stage_ms["ms_term1"] >= stage_ms["ms_term2"] else "term2"
-        dom_flops = flops["flops_term1"] if dom == "term1" else flops["flops_term2"]
+        dom = max(("y", "term1", "term2"), key=lambda k: stage_ms["ms_" + k])
+        dom_flops = flops["flops_" + dom]
         dom_ms = stage_ms["ms_" + dom]
         achieved = dom_flops / (dom_ms / 1e3) / 1e12
-        roofline = {"kernel": "k_" + dom, "bound": "alu", "achieved": achieved, "peak": fp64_peak,
-                    "unit": "TFLOP/s", "frac": achieved / fp64_peak, "traffic": None,
-                    "peak_source": "FP64 cuBLAS DGEMM 4096^3 measured in this run (FP64 pipe; "
-                                   "MEASURED_PEAKS has no FP64 figure)"}
+        kname = {"y": "k_ybuild", "term1": "k_term1", "term2": "k_term2"}[dom]
+        if args.precision == "fp64":
+            roofline = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                        "frac": achieved / fp64_peak, "traffic": None,
+                        "peak_source": "FP64 cuBLAS DGEMM 4096^3 measured in this run (FP64 pipe)"}
+        else:
+            pk = peaks.get("bf16_tflops_sustained") or 1717.3
+            pieces = 6 if args.precision == "bf16x6" else 3
+            roofline = {"kernel": kname + "_mma", "bound": "tensor", "achieved": achieved, "peak": pk,
+                        "unit": "TFLOP/s", "frac": achieved / pk, "traffic": None,
+                        "peak_source": "bf16 dense, sustained, of measured (MEASURED_PEAKS.json)",
+                        "note": f"achieved counts algorithmic FLOPs only; the {pieces} bf16 piece products per "
+                                f"multiply and the 13->16 / 50->64 tile padding are not counted",
+                        "tensor_issue_tflops": achieved * pieces}
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
             cpu = cpu_baseline(w, homes=1)
         h2d = 3 * n * 8 + 9 * 8
         d2h = (1 + 3 * n + 9) * 8
+        head = variants.get(args.precision, {})
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "precision": "fp64",
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "bf16" if args.precision != "fp64" else "f64",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD, "precision": args.precision,
+                           "arithmetic": "bf16 pieces on tensor cores, fp32 accumulate, fp64 screening/reduction"
+                           if args.precision != "fp64" else "fp64",
                            "parallelism": f"replicas{world}" if world > 1 else "single",
-                           "l2": "working set > L2 (C+gradC, V, Y stores of several GB per step)"},
+                           "l2": "working set > L2 (block, Y and Z stores of several GB per step)"},
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches,
                 "roofline": roofline,
                 "cpu_baseline": cpu,
                 "clocks": ck,
+                "error_vs_fp64": {k: head.get(k) for k in ("errE", "errF", "errS")} if head else None,
+                "fp64": {"evals_per_s": 1.0 / t_fp64, "speedup_of_headline": value / world * t_fp64},
+                "other_precisions": other,
                 "stages_ms": stage_ms,
                 "gflop_per_eval": flops["flops_total"] / 1e9,
                 "achieved_tflops_total": flops["flops_total"] / (t_max / args.steps) / 1e12,
                 "counts": {k: flops[k] for k in ("c_pairs", "v_pairs", "triplets", "term1_pairs",
                                                  "term2_pairs", "y_blocks", "device_bytes")},
                 "peaks": {"hbm_gbs": peaks.get("hbm_gbs"), "bf16_tflops": peaks.get("bf16_tflops"),
+                          "bf16_tflops_sustained": peaks.get("bf16_tflops_sustained"),
                           "fp64_dgemm_tflops": fp64_peak}}
         print(json.dumps(line), flush=True)
-    plan.close()
+    for v in variants.values():
+        v["plan"].close()
+    if args.precision == "fp64":
+        plan.close()
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
@@ -290,10 +350,11 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="bf16x6", choices=["bf16x6", "bf16x3", "fp64"])
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -182,7 +182,10 @@ struct hfx_plan {
   int* t1q_list = nullptr;
   int* blist = nullptr;
   long long blist_cap = 0;
-  int MAmax = 0, MBmax = 0, KSmax = 0, ZROWS = 0, ZSmax = 0;
+  int MAmax = 0, MBmax = 0, KSmax = 0, YRmax = 0, ZROWS = 0, KZmax = 0, FC = 0, MC = 0;
+  long long zblk = 0;
+  uint16_t* Zst = nullptr;
+  long long Zcap = 0;
   size_t smem_m1 = 0, smem_m2 = 0;
 
   bool timing = false;
@@ -728,10 +731,15 @@ void setup_shapes(hfx_plan* P) {
     P->MAmax = r16(maxABF);
     P->MBmax = r16(maxABF);
     P->KSmax = r16(maxKAF) + 8;
-    P->ZROWS = zrows;
-    P->ZSmax = r16(maxAO) + 8;
-    P->smem_m1 = hfx::term1_mma_smem(P->np, P->MAmax, P->MBmax, P->KSmax);
-    P->smem_m2 = hfx::term2_mma_smem(P->np, P->ZROWS, P->ZSmax);
+    int maxrows = 0;
+    for (int a = 0; a < P->S; ++a) maxrows = std::max(maxrows, P->n_abf[a] * P->n_ao[a]);
+    P->ZROWS = maxrows;
+    P->KZmax = maxAO * r16(maxAO) + 8;
+    P->zblk = (long long)P->np * maxrows * r16(maxAO);
+    P->MC = (maxrows + 127) / 128;
+    P->YRmax = r16(maxABF * maxAO);
+    P->smem_m1 = hfx::term1_mma_smem(P->np, P->MAmax, P->MBmax, P->KSmax, P->YRmax);
+    P->smem_m2 = hfx::term2_mma_smem(P->np, P->MAmax, P->KZmax);
     const int qtiles = (P->MAmax / 16) * ((maxKAF + 7) / 8);
     if (P->smem_m1 > limit || P->smem_m2 > limit || qtiles > 256)
       fail(HFX_ERR_UNSUPPORTED, "block shapes too large for the split-precision kernels");
@@ -752,7 +760,7 @@ void split_density(hfx_plan* P) {
   P->Dsp = P->mem.alloc<uint16_t>(off[P->n_d]);
   upload(P->dsp_off, off, P->stream);
   DevPlan D = make_devplan(P, P->lat_ref.data());
-  hfx::MixPlan X{P->Dsp, P->dsp_off, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  hfx::MixPlan X{P->Dsp, P->dsp_off, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   ck(hfx::launch_dsplit(D, X, P->np, P->stream), "dsplit");
   ck(cudaStreamSynchronize(P->stream), "dsplit");
 }
@@ -806,7 +814,7 @@ void evaluate(hfx_plan* P, const double* L, hfx_stats* st) {
   cudaStream_t s = P->stream;
   DevPlan D = make_devplan(P, L);
   const long long launches0 = hfx::launch_count() + hfx::mixed_launch_count();
-  hfx::MixPlan X{P->Dsp, P->dsp_off, P->Ysp, P->Cm, P->cm_off, P->Vm, P->vm_off, P->qcnt, P->qoff, P->blist};
+  hfx::MixPlan X{P->Dsp, P->dsp_off, P->Ysp, P->Cm, P->cm_off, P->Vm, P->vm_off, P->Zst, P->qcnt, P->qoff, P->blist};
   const bool reuse = P->opt.freeze_lists && P->frozen_ready;
   Timer tm(P->timing, s);
   tm.mark();  // 0
@@ -877,10 +885,16 @@ void evaluate(hfx_plan* P, const double* L, hfx_stats* st) {
     for (int t = 0; t < P->S; ++t) wide |= P->n_ao[t] > 16;
     ck(hfx::launch_ybuild_mma(D, X, P->np, P->y_list, (int)P->tot[1], wide, s), "ybuild");
     tm.mark();  // 3
-    ck(hfx::launch_term1_mma(D, X, P->np, P->t1q_list, (int)P->tot[7], P->MAmax, P->MBmax, P->KSmax, P->smem_m1, s),
+    ck(hfx::launch_term1_mma(D, X, P->np, P->t1q_list, (int)P->tot[7], P->MAmax, P->MBmax, P->KSmax, P->YRmax,
+                             P->smem_m1, s),
        "term1");
     tm.mark();  // 4
-    ck(hfx::launch_term2_mma(D, X, P->np, P->t2_list, (int)P->tot[5], P->ZROWS, P->smem_m2, s), "term2");
+    ensure_buf(P, P->Zst, P->Zcap, P->tot[5] * P->zblk);
+    X.Zst = P->Zst;
+    const int FC = (P->maxC + 3) / 4;
+    ck(hfx::launch_term2_mma(D, X, P->np, P->t2_list, P->t2_idx, (int)P->tot[5], P->MAmax, P->KZmax, P->zblk, P->ZROWS,
+                             FC, P->MC, P->smem_m2, s),
+       "term2");
     tm.mark();  // 5
   }
   ck(cudaMemsetAsync(P->d_out, 0, (1 + 3 * (size_t)P->N + 9) * sizeof(double), s), "memset");

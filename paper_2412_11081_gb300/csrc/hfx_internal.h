@@ -101,6 +101,7 @@ struct MixPlan {
   const long long* cm_off;     // [nC] offsets (uint16 units)
   uint16_t* Vm;                // per needed V pair: bf16 pieces of V, then V and grad V in FP32
   const long long* vm_off;     // [nV] offsets (uint16 units), from the per-call scan
+  uint16_t* Zst;               // per pair of the second product: bf16 pieces of Z = V_AB . Y^{BA}
   int* qcnt;                   // [nC] kept B per (A,F)
   long long* qoff;             // [nC] offsets into blist
   int* blist;                  // V pairs (A,B) per (A,F), in V-pair order
@@ -136,13 +137,14 @@ cudaError_t launch_vpieces(const DevPlan& P, const MixPlan& X, int np, const int
 cudaError_t launch_ybuild_mma(const DevPlan& P, const MixPlan& X, int np, const int* list, int n, int wide,
                               cudaStream_t s);
 cudaError_t launch_t1_lists(const DevPlan& P, const MixPlan& X, int phase, cudaStream_t s);
-size_t term1_mma_smem(int np, int MAmax, int MBmax, int KSmax);
-size_t term2_mma_smem(int np, int zrows, int zs);
+size_t term1_mma_smem(int np, int MAmax, int MBmax, int KSmax, int YRmax);
+size_t term2_mma_smem(int np, int MAmax, int KZmax);
 cudaError_t set_mixed_smem_limits(int np, size_t t1, size_t t2);
 cudaError_t launch_term1_mma(const DevPlan& P, const MixPlan& X, int np, const int* qlist, int n, int MAmax,
-                             int MBmax, int KSmax, size_t smem, cudaStream_t s);
-cudaError_t launch_term2_mma(const DevPlan& P, const MixPlan& X, int np, const int* list, int n, int zrows,
-                             size_t smem, cudaStream_t s);
+                             int MBmax, int KSmax, int YRmax, size_t smem, cudaStream_t s);
+cudaError_t launch_term2_mma(const DevPlan& P, const MixPlan& X, int np, const int* list, const long long* slot0,
+                             int n, int MAmax, int KZmax, long long zblk, int zrows, int FC, int MC, size_t smem,
+                             cudaStream_t s);
 
 // Exclusive scan helpers.  `mode` selects what is summed per element i:
 //   0: flag[i] != 0 (int32 flags)
