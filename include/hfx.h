@@ -154,6 +154,32 @@ hfx_status hfx_energy_force_stress_device(hfx_plan* plan, const double* lattice,
                                           const double* d_positions, double* d_out,
                                           hfx_stats* stats);
 
+/* Evaluation for callers that cannot allocate device memory while they
+ * evaluate: work recorded under a stream capture, hosts whose device memory
+ * belongs to their own pool after start-up, real-time loops that forbid
+ * allocation after initialisation.  hfx_energy_force_stress may grow the
+ * plan's per-call block stores with cudaMalloc; this entry point computes the
+ * same E, F and sigma (same arguments, host pointers) with that scratch taken
+ * from one fixed array inside the library, HFX_NOALLOC_SCRATCH_BYTES = 64 MiB,
+ * which every device that loads the library holds until the process exits.
+ * It calls no cudaMalloc or cudaFree and allocates no host memory.
+ *  - FP64 plans only (HFX_ERR_UNSUPPORTED otherwise).
+ *  - A call whose pair lists, Y blocks or V blocks do not fit the array
+ *    returns HFX_ERR_UNSUPPORTED with a message; nothing is written.
+ *  - Atoms moved beyond skin/2 give HFX_ERR_PAIRLIST_STALE (rebuilding the
+ *    lists allocates; call hfx_energy_force_stress once to rebuild them).
+ *  - The first call on a device looks up the array's device address; make
+ *    that first call before any stream capture.
+ *  - Every call on every plan of a device shares the one array, which keeps
+ *    the last call's contents (each call writes what it reads before reading
+ *    it, so nothing has to start at zero).  Calls that overlap on the GPU
+ *    (different streams, threads or plans) race on the array.
+ * The paper has no counterpart: this is a deployment variant of the
+ * evaluation above. */
+#define HFX_NOALLOC_SCRATCH_BYTES (64ull << 20)
+hfx_status hfx_energy_force_stress_noalloc(hfx_plan* plan, const double* lattice, const double* positions,
+                                           double* E, double* F, double* sigma);
+
 /* Per-stage CUDA-event timing on (1) or off (0, default). */
 hfx_status hfx_set_timing(hfx_plan* plan, int on);
 

@@ -12,6 +12,7 @@
 #include <cstring>
 #include <functional>
 #include <limits>
+#include <mutex>
 #include <new>
 #include <stdexcept>
 #include <string>
@@ -189,6 +190,7 @@ struct hfx_plan {
   size_t smem_m1 = 0, smem_m2 = 0;
 
   bool timing = false;
+  bool noalloc_call = false;   // set only inside hfx_energy_force_stress_noalloc
   std::vector<double> pos_host_buf;
   hfx_stats last{};
 
@@ -767,6 +769,8 @@ void split_density(hfx_plan* P) {
 
 void ensure_store(hfx_plan* P, double*& buf, long long& cap, long long need) {
   if (need <= cap) return;
+  if (P->noalloc_call)
+    fail(HFX_ERR_UNSUPPORTED, "this evaluation needs more scratch than the fixed no-allocation array holds");
   if (buf) P->mem.release(buf);
   buf = nullptr;
   cap = 0;
@@ -1106,3 +1110,98 @@ const char* hfx_last_error(const hfx_plan* P) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Evaluation without device allocation.
+//
+// Some callers cannot allocate device memory while they evaluate: code that
+// records work into a CUDA graph or runs under a stream capture, hosts that
+// hand all device memory to their own pool after start-up, and real-time
+// loops that forbid allocation after initialisation.  hfx_energy_force_stress
+// may grow its per-call block stores with cudaMalloc, so this entry point runs
+// the same FP64 evaluation with that scratch taken from one fixed array
+// compiled into the library instead.  The array is a file-scope __device__
+// variable: every device that loads the library holds it until the process
+// exits.  Host code never passes the array's name to a kernel (in host code it
+// is only a stand-in for the symbol); it looks the device address up once per
+// device with cudaGetSymbolAddress, with that device current.
+constexpr size_t kNoAllocScratchBytes = 64ull << 20;   // HFX_NOALLOC_SCRATCH_BYTES
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchBytes / sizeof(double)];
+
+namespace {
+std::mutex g_noalloc_mu;
+constexpr int kNoAllocMaxDevices = 64;
+double* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch array on the current device (first call on a
+// device looks it up; later calls reuse it).
+double* noalloc_scratch(int dev) {
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (dev < 0 || dev >= kNoAllocMaxDevices) fail(HFX_ERR_UNSUPPORTED, "device ordinal too large for the scratch table");
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    ck(cudaGetSymbolAddress(&p, g_noalloc_scratch), "cudaGetSymbolAddress");
+    g_noalloc_ptr[dev] = static_cast<double*>(p);
+  }
+  return g_noalloc_ptr[dev];
+}
+}  // namespace
+
+extern "C" hfx_status hfx_energy_force_stress_noalloc(hfx_plan* P, const double* lattice, const double* positions,
+                                                      double* E, double* F, double* sigma) {
+  if (!P) return HFX_ERR_INVALID;
+  return run_guarded(P, [&]() {
+    if (!E || !F || !sigma) fail(HFX_ERR_INVALID, "NULL output");
+    if (P->np) fail(HFX_ERR_UNSUPPORTED, "the no-allocation entry point runs FP64 plans only");
+    ck(cudaSetDevice(P->dev), "cudaSetDevice");
+    double* base = noalloc_scratch(P->dev);
+    validate_geometry(P->N, lattice, positions);
+    if (2.0 * list_drift(P, lattice, positions) >= P->opt.skin)
+      fail(HFX_ERR_PAIRLIST_STALE,
+           "atoms moved beyond skin/2; rebuilding the pair lists allocates (call hfx_energy_force_stress once)");
+    // scratch layout: scan temporaries | Y blocks | V blocks
+    const long long total = (long long)(kNoAllocScratchBytes / sizeof(double));
+    const long long nmax = std::max<long long>(std::max(P->nY, P->nV), P->nC);
+    const long long scan_need = 2 * ((nmax + 1023) / 1024) + 64;
+    if (scan_need >= total / 4) fail(HFX_ERR_UNSUPPORTED, "pair lists too long for the fixed no-allocation array");
+    const long long half = (total - scan_need) / 2;
+    const hfx::ScanTmp saved_scan = P->scan_tmp;
+    double* const saved_Y = P->Yst;
+    double* const saved_V = P->Vst;
+    const long long saved_Ycap = P->Ycap, saved_Vcap = P->Vcap;
+    const bool saved_timing = P->timing;
+    P->scan_tmp.buf = reinterpret_cast<long long*>(base);
+    P->scan_tmp.cap = (size_t)scan_need;
+    P->Yst = base + scan_need;
+    P->Ycap = half;
+    P->Vst = base + scan_need + half;
+    P->Vcap = half;
+    P->timing = false;
+    P->noalloc_call = true;
+    auto restore = [&]() {
+      P->scan_tmp = saved_scan;
+      P->Yst = saved_Y;
+      P->Vst = saved_V;
+      P->Ycap = saved_Ycap;
+      P->Vcap = saved_Vcap;
+      P->timing = saved_timing;
+      P->noalloc_call = false;
+    };
+    try {
+      ck(cudaMemcpyAsync(P->d_pos, positions, 3 * (size_t)P->N * sizeof(double), cudaMemcpyHostToDevice, P->stream),
+         "H2D positions");
+      evaluate(P, lattice, nullptr);
+      ck(cudaMemcpyAsync(E, P->d_out, sizeof(double), cudaMemcpyDeviceToHost, P->stream), "D2H E");
+      ck(cudaMemcpyAsync(F, P->d_out + 1, 3 * (size_t)P->N * sizeof(double), cudaMemcpyDeviceToHost, P->stream),
+         "D2H F");
+      ck(cudaMemcpyAsync(sigma, P->d_out + 1 + 3 * (size_t)P->N, 9 * sizeof(double), cudaMemcpyDeviceToHost,
+                         P->stream),
+         "D2H sigma");
+      ck(cudaStreamSynchronize(P->stream), "results");
+    } catch (...) {
+      restore();
+      throw;
+    }
+    restore();
+  });
+}

@@ -65,6 +65,7 @@ _SIGNATURES = {
     "hfx_energy_force_stress": (ct.c_int, [ct.c_void_p, _dp, _dp, _dp, _dp, _dp, ct.POINTER(HfxStats)]),
     "hfx_energy_force_stress_device": (ct.c_int, [ct.c_void_p, _dp, ct.c_void_p, ct.c_void_p,
                                                   ct.POINTER(HfxStats)]),
+    "hfx_energy_force_stress_noalloc": (ct.c_int, [ct.c_void_p, _dp, _dp, _dp, _dp, _dp]),
     "hfx_set_timing": (ct.c_int, [ct.c_void_p, ct.c_int]),
     "hfx_plan_destroy": (ct.c_int, [ct.c_void_p]),
     "hfx_status_string": (ct.c_char_p, [ct.c_int]),
@@ -195,6 +196,21 @@ class Plan:
         st = self.lib.hfx_energy_force_stress(self.handle, lat.ctypes.data_as(_dp), pos.ctypes.data_as(_dp),
                                               ct.byref(E), F.ctypes.data_as(_dp), sig.ctypes.data_as(_dp),
                                               ct.byref(self.stats) if stats else None)
+        _check(self.lib, st, self.handle)
+        return float(E.value), F, sig
+
+    def evaluate_noalloc(self, lattice, positions):
+        """hfx_energy_force_stress_noalloc: the FP64 evaluation with its
+        scratch in the library's fixed device array (no device allocation)."""
+        lat = _f64(lattice).ravel()
+        pos = _f64(positions).ravel()
+        if pos.size != 3 * self.n_atoms:
+            raise ValueError("positions must be n_atoms x 3")
+        E = ct.c_double()
+        F = np.zeros((self.n_atoms, 3))
+        sig = np.zeros((3, 3))
+        st = self.lib.hfx_energy_force_stress_noalloc(self.handle, lat.ctypes.data_as(_dp), pos.ctypes.data_as(_dp),
+                                                      ct.byref(E), F.ctypes.data_as(_dp), sig.ctypes.data_as(_dp))
         _check(self.lib, st, self.handle)
         return float(E.value), F, sig
 
