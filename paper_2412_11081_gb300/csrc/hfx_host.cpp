@@ -155,6 +155,7 @@ struct hfx_plan {
   double* d_out = nullptr;     // [1 + 3N + 9]
   double* d_acc = nullptr;     // hfx::ACC_N
   long long* d_tot = nullptr;  // [kTot] totals of the scans, then hfx::CNT_N counters
+  int* d_err = nullptr;        // set by a kernel whose bounded wait ran out
   double* Yst = nullptr;
   long long Ycap = 0;
   double* Vst = nullptr;
@@ -187,6 +188,8 @@ struct hfx_plan {
   long long zblk = 0;
   uint16_t* Zst = nullptr;
   long long Zcap = 0;
+  uint16_t* zero512 = nullptr;   // 512 zero bf16 (absent D blocks in tensor-core tiles)
+  int maxV = 0;                  // most V-pair candidates of one home atom
   size_t smem_m1 = 0, smem_m2 = 0;
 
   bool timing = false;
@@ -544,8 +547,11 @@ void build_lists(hfx_plan* P, const double* L, const double* pos) {
   v_ptr[N] = (int)v_j.size();
   y_ptr[N] = (int)y_j.size();
   const int nC = c_ptr[N], nV = v_ptr[N], nY = y_ptr[N];
-  int maxC = 0;
-  for (int A = 0; A < N; ++A) maxC = std::max(maxC, c_ptr[A + 1] - c_ptr[A]);
+  int maxC = 0, maxV = 0;
+  for (int A = 0; A < N; ++A) {
+    maxC = std::max(maxC, c_ptr[A + 1] - c_ptr[A]);
+    maxV = std::max(maxV, v_ptr[A + 1] - v_ptr[A]);
+  }
   // D block of each V pair, Y-key lookup table
   const long long n0 = 2 * P->HD[0] + 1, n1 = 2 * P->HD[1] + 1, n2 = 2 * P->HD[2] + 1;
   std::vector<int> v_didx(nV, -1);
@@ -589,6 +595,7 @@ void build_lists(hfx_plan* P, const double* L, const double* pos) {
   P->nV = nV;
   P->nY = nY;
   P->maxC = maxC;
+  P->maxV = maxV;
   for (int k = 0; k < 3; ++k) P->HY[k] = HY[k];
   P->c_elems = c_off[nC];
   cudaStream_t s = P->stream;
@@ -737,13 +744,16 @@ void setup_shapes(hfx_plan* P) {
     for (int a = 0; a < P->S; ++a) maxrows = std::max(maxrows, P->n_abf[a] * P->n_ao[a]);
     P->ZROWS = maxrows;
     P->KZmax = maxAO * r16(maxAO) + 8;
-    P->zblk = (long long)P->np * maxrows * r16(maxAO);
     P->MC = (maxrows + 127) / 128;
+    P->zblk = (long long)P->np * P->MC * 128 * 16;   // 128-row tiles of 16 columns, per piece
     P->YRmax = r16(maxABF * maxAO);
     P->smem_m1 = hfx::term1_mma_smem(P->np, P->MAmax, P->MBmax, P->KSmax, P->YRmax);
     P->smem_m2 = hfx::term2_mma_smem(P->np, P->MAmax, P->KZmax);
-    const int qtiles = (P->MAmax / 16) * ((maxKAF + 7) / 8);
-    if (P->smem_m1 > limit || P->smem_m2 > limit || qtiles > 256)
+    // term 1: each warp owns one alpha tile and ceil(NTq / (16 / MT)) Q tiles (at most 16);
+    // the second product's GEMM holds two column tiles per F (n_ao <= 16)
+    const int MT = P->MAmax / 16, wpm = MT > 0 ? 16 / MT : 0;
+    const int qtiles = wpm > 0 ? ((maxKAF + 7) / 8 + wpm - 1) / wpm : 1 << 20;
+    if (P->smem_m1 > limit || P->smem_m2 > limit || qtiles > 16 || maxAO > 16)
       fail(HFX_ERR_UNSUPPORTED, "block shapes too large for the split-precision kernels");
     ck(hfx::set_mixed_smem_limits(P->np, P->smem_m1, P->smem_m2), "smem attributes");
   }
@@ -893,17 +903,33 @@ void evaluate(hfx_plan* P, const double* L, hfx_stats* st) {
                              P->smem_m1, s),
        "term1");
     tm.mark();  // 4
-    ensure_buf(P, P->Zst, P->Zcap, P->tot[5] * P->zblk);
+    if (P->tot[5] * P->zblk > P->Zcap) {
+      ensure_buf(P, P->Zst, P->Zcap, P->tot[5] * P->zblk);
+      ck(cudaMemsetAsync(P->Zst, 0, (size_t)P->Zcap * sizeof(uint16_t), s), "memset");   // tile padding rows stay zero
+    }
+    if (!P->zero512) {
+      P->zero512 = P->mem.alloc<uint16_t>(512);
+      ck(cudaMemsetAsync(P->zero512, 0, 512 * sizeof(uint16_t), s), "memset");
+    }
     X.Zst = P->Zst;
     const int FC = (P->maxC + 3) / 4;
     ck(hfx::launch_term2_mma(D, X, P->np, P->t2_list, P->t2_idx, (int)P->tot[5], P->MAmax, P->KZmax, P->zblk, P->ZROWS,
-                             FC, P->MC, P->smem_m2, s),
+                             FC, P->MC, hfx::q2_umma_segments(P->maxV), P->zero512, P->smem_m2, P->d_err, s),
        "term2");
     tm.mark();  // 5
   }
   ck(cudaMemsetAsync(P->d_out, 0, (1 + 3 * (size_t)P->N + 9) * sizeof(double), s), "memset");
   ck(hfx::launch_reduce(D, P->d_out, s), "reduce");
   tm.mark();  // 6
+  if (P->np) {
+    int errflag = 0;
+    ck(cudaMemcpyAsync(&errflag, P->d_err, sizeof(int), cudaMemcpyDeviceToHost, s), "D2H error flag");
+    ck(cudaStreamSynchronize(s), "error flag");
+    if (errflag) {
+      ck(cudaMemsetAsync(P->d_err, 0, sizeof(int), s), "memset");
+      fail(HFX_ERR_TIMEOUT, "a tensor-core pipeline wait ran out (results discarded)");
+    }
+  }
   if (st) {
     double acc[hfx::ACC_N];
     ck(cudaMemcpyAsync(acc, P->d_acc, sizeof(acc), cudaMemcpyDeviceToHost, s), "D2H acc");
@@ -1017,6 +1043,8 @@ hfx_status hfx_plan_create(const hfx_system* sys, const hfx_model* model, const 
     P->d_out = P->mem.alloc<double>(1 + 3 * (size_t)P->N + 9);
     P->d_acc = P->mem.alloc<double>(hfx::ACC_N);
     P->d_tot = P->mem.alloc<long long>(kTot + hfx::CNT_N);
+    P->d_err = P->mem.alloc<int>(1);
+    ck(cudaMemset(P->d_err, 0, sizeof(int)), "memset");
     ck(cudaMemset(P->d_tot, 0, (kTot + hfx::CNT_N) * sizeof(long long)), "memset");
     setup_shapes(P);
     build_lists(P, sys->lattice, sys->positions);

@@ -143,8 +143,9 @@ cudaError_t set_mixed_smem_limits(int np, size_t t1, size_t t2);
 cudaError_t launch_term1_mma(const DevPlan& P, const MixPlan& X, int np, const int* qlist, int n, int MAmax,
                              int MBmax, int KSmax, int YRmax, size_t smem, cudaStream_t s);
 cudaError_t launch_term2_mma(const DevPlan& P, const MixPlan& X, int np, const int* list, const long long* slot0,
-                             int n, int MAmax, int KZmax, long long zblk, int zrows, int FC, int MC, size_t smem,
-                             cudaStream_t s);
+                             int n, int MAmax, int KZmax, long long zblk, int zrows, int FC, int MC, int nseg,
+                             const uint16_t* zero512, size_t smem, int* err, cudaStream_t s);
+int q2_umma_segments(int max_pairs_per_atom);
 
 // Exclusive scan helpers.  `mode` selects what is summed per element i:
 //   0: flag[i] != 0 (int32 flags)

@@ -42,6 +42,13 @@ long long g_mix_launches = 0;
 
 __device__ __forceinline__ int rup16(int x) { return (x + 15) & ~15; }
 
+// Element offset of (row r, column c < 16) inside a tile stored in the
+// K-major core-matrix order of the tensor cores: 8-row x 8-column core
+// matrices (16 bytes per row), the two column halves 64 elements apart and
+// 8-row groups 128 elements apart.  D piece blocks (16 x 16) and the Z store
+// (128-row tiles) use it, so a tile is copied to shared memory as one block.
+__device__ __forceinline__ int tix(int r, int c) { return ((r >> 3) << 7) + ((c >> 3) << 6) + ((r & 7) << 3) + (c & 7); }
+
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -88,7 +95,7 @@ __device__ __forceinline__ void split_f(float x, uint16_t (&p)[NP]) {
 __device__ __forceinline__ uint32_t pack2(uint16_t lo, uint16_t hi) { return (uint32_t)lo | ((uint32_t)hi << 16); }
 
 __device__ __forceinline__ void mma16816(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-  asm volatile(
+  asm(
       "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
       "{%0,%1,%2,%3};\n"
       : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
@@ -108,6 +115,29 @@ __device__ __forceinline__ void mma_split(float (&c)[4], const uint32_t (&a)[NP]
     mma16816(c, a[1], b[0]);
   }
   mma16816(c, a[0], b[0]);
+}
+
+// Two independent accumulators with their product chains interleaved, so the
+// dependent MMAs of one tile overlap the other's.
+template <int NP>
+__device__ __forceinline__ void mma_split2(float (&c0)[4], const uint32_t (&a0)[NP][4], const uint32_t (&b0)[NP][2],
+                                           float (&c1)[4], const uint32_t (&a1)[NP][4], const uint32_t (&b1)[NP][2]) {
+  if (NP == 3) {
+    mma16816(c0, a0[1], b0[1]);
+    mma16816(c1, a1[1], b1[1]);
+    mma16816(c0, a0[0], b0[2]);
+    mma16816(c1, a1[0], b1[2]);
+    mma16816(c0, a0[2], b0[0]);
+    mma16816(c1, a1[2], b1[0]);
+  }
+  if (NP >= 2) {
+    mma16816(c0, a0[0], b0[1]);
+    mma16816(c1, a1[0], b1[1]);
+    mma16816(c0, a0[1], b0[0]);
+    mma16816(c1, a1[1], b1[0]);
+  }
+  mma16816(c0, a0[0], b0[0]);
+  mma16816(c1, a1[0], b1[0]);
 }
 
 __device__ __forceinline__ void ldm_x4(uint32_t (&r)[4], const void* p) {
@@ -156,7 +186,7 @@ __global__ void k_dsplit(DevPlan P, MixPlan X) {
       uint16_t pc[NP];
       split_f<NP>((a < na && b < nb) ? (float)src[a * nb + b] : 0.f, pc);
 #pragma unroll
-      for (int p = 0; p < NP; ++p) out[p * pa * pb + e] = pc[p];
+      for (int p = 0; p < NP; ++p) out[p * pa * pb + tix(a, b)] = pc[p];
     }
   }
 }
@@ -265,9 +295,9 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_ybuild_mma(DevPlan P, MixPla
           if (nt < NT) {
 #pragma unroll
             for (int p = 0; p < NP; ++p) {
-              const uint16_t* Db = Dm + p * pZ * pW + (nt * 8 + gid) * pW + k0 + 2 * tig;
+              const uint16_t* Db = Dm + p * 256 + tix(nt * 8 + gid, 2 * tig);
               bf[nt][p][0] = *reinterpret_cast<const uint32_t*>(Db);
-              bf[nt][p][1] = *reinterpret_cast<const uint32_t*>(Db + 8);
+              bf[nt][p][1] = *reinterpret_cast<const uint32_t*>(Db + 64);
             }
           }
         }
@@ -285,8 +315,8 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_ybuild_mma(DevPlan P, MixPla
               af[p][h] = r < rows ? *reinterpret_cast<const uint32_t*>(Cq + p * cplane + (long long)r * pW + kc) : 0u;
           }
 #pragma unroll
-          for (int nt = 0; nt < NTM; ++nt)
-            if (nt < NT) mma_split<NP>(acc[i][nt], af, bf[nt]);
+          for (int nt = 0; nt < NTM; nt += 2)
+            if (nt < NT) mma_split2<NP>(acc[i][nt], af, bf[nt], acc[i][nt + 1], af, bf[nt + 1]);
         }
       }
     }
@@ -532,16 +562,18 @@ __global__ void __launch_bounds__(kWarps1 * 32) k_term1_mma(DevPlan P, MixPlan X
                 }
               }
 #pragma unroll
-              for (int nt = 0; nt < 4; ++nt) {
+              for (int nt = 0; nt < 4; nt += 2) {
                 if (nt >= NTU) break;
-                uint32_t bf[NP][2];
+                uint32_t bf0[NP][2], bf1[NP][2];
 #pragma unroll
                 for (int pp = 0; pp < NP; ++pp) {
-                  const uint16_t* Db = Dab + pp * pA * pB + (nt * 8 + gid) * pB + k0 + 2 * tig;
-                  bf[pp][0] = *reinterpret_cast<const uint32_t*>(Db);
-                  bf[pp][1] = *reinterpret_cast<const uint32_t*>(Db + 8);
+                  const uint16_t* Db = Dab + pp * 256 + tix(nt * 8 + gid, 2 * tig);
+                  bf0[pp][0] = *reinterpret_cast<const uint32_t*>(Db);
+                  bf0[pp][1] = *reinterpret_cast<const uint32_t*>(Db + 64);
+                  bf1[pp][0] = *reinterpret_cast<const uint32_t*>(Db + 128);
+                  bf1[pp][1] = *reinterpret_cast<const uint32_t*>(Db + 192);
                 }
-                mma_split<NP>(acc[nt], af, bf);
+                mma_split2<NP>(acc[nt], af, bf0, acc[nt + 1], af, bf1);
               }
             }
 #pragma unroll
@@ -564,34 +596,48 @@ __global__ void __launch_bounds__(kWarps1 * 32) k_term1_mma(DevPlan P, MixPlan X
         }
         __syncthreads();   // Us ready; Ys and the other V buffer free
         if (t + 1 < nb) prefetch(t + 1, (t + 1) & 1);
-        // R_t = C_AF . U^T (M = alpha, N = beta, K = (a,f)); dotted with V and grad V
+        // R_t = C_AF . U^T (M = alpha, N = beta, K = (a,f)); dotted with V and grad V.
+        // Warp -> one alpha tile (A fragments reused) and up to two beta tiles
+        // (their product chains interleaved).
         float evf[4] = {0.f, 0.f, 0.f, 0.f};
         {
           const int NTR = MB >> 3;
-          const int nt_tiles = MT * NTR;
-          for (int tt = warp; tt < nt_tiles; tt += kWarps1) {
-            const int mt = tt / NTR, nt = tt - mt * NTR;
-            float acc[4] = {0.f, 0.f, 0.f, 0.f};
-            for (int k0 = 0; k0 < KP; k0 += 16) {
-              uint32_t af[NP][4], bf[NP][2];
+          const int wpm = kWarps1 / MT;              // warps per alpha tile
+          const int mt = warp % MT, w0 = warp / MT;
+          if (w0 < wpm) {
+            for (int nt0 = w0; nt0 < NTR; nt0 += 2 * wpm) {
+              const int nt1 = nt0 + wpm;
+              const bool two = nt1 < NTR;
+              float acc0[4] = {0.f, 0.f, 0.f, 0.f}, acc1[4] = {0.f, 0.f, 0.f, 0.f};
+              for (int k0 = 0; k0 < KP; k0 += 16) {
+                uint32_t af[NP][4], bf0[NP][2], bf1[NP][2];
 #pragma unroll
-              for (int pp = 0; pp < NP; ++pp) {
-                ldm_x4(af[pp], Cs + (size_t)pp * MA * KS + (size_t)(mt * 16 + (lane & 15)) * KS + k0 + ((lane >> 4) << 3));
-                ldm_x2(bf[pp], Us + (size_t)pp * MB * KS + (size_t)(nt * 8 + (lane & 7)) * KS + k0 + (((lane >> 3) & 1) << 3));
+                for (int pp = 0; pp < NP; ++pp) {
+                  ldm_x4(af[pp], Cs + (size_t)pp * MA * KS + (size_t)(mt * 16 + (lane & 15)) * KS + k0 + ((lane >> 4) << 3));
+                  ldm_x2(bf0[pp], Us + (size_t)pp * MB * KS + (size_t)(nt0 * 8 + (lane & 7)) * KS + k0 + (((lane >> 3) & 1) << 3));
+                  ldm_x2(bf1[pp], Us + (size_t)pp * MB * KS + (size_t)((two ? nt1 : nt0) * 8 + (lane & 7)) * KS + k0 +
+                                      (((lane >> 3) & 1) << 3));
+                }
+                mma_split2<NP>(acc0, af, bf0, acc1, af, bf1);
               }
-              mma_split<NP>(acc, af, bf);
-            }
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-              const int al = mt * 16 + gid + ((c & 2) ? 8 : 0);
-              const int be = nt * 8 + 2 * tig + (c & 1);
-              if (al < mA && be < mB) {
-                const int o = al * mB + be;
-                const float r = acc[c];
-                evf[0] = fmaf(V[o], r, evf[0]);
-                evf[1] = fmaf(V[nvb + o], r, evf[1]);
-                evf[2] = fmaf(V[2 * nvb + o], r, evf[2]);
-                evf[3] = fmaf(V[3 * nvb + o], r, evf[3]);
+              for (int h = 0; h < 2; ++h) {
+                if (h == 1 && !two) break;
+                const int nt = h ? nt1 : nt0;
+                const float* acc = h ? acc1 : acc0;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                  const int al = mt * 16 + gid + ((c & 2) ? 8 : 0);
+                  const int be = nt * 8 + 2 * tig + (c & 1);
+                  if (al < mA && be < mB) {
+                    const int o = al * mB + be;
+                    const float r = acc[c];
+                    evf[0] = fmaf(V[o], r, evf[0]);
+                    evf[1] = fmaf(V[nvb + o], r, evf[1]);
+                    evf[2] = fmaf(V[2 * nvb + o], r, evf[2]);
+                    evf[3] = fmaf(V[3 * nvb + o], r, evf[3]);
+                  }
+                }
               }
             }
           }
@@ -601,31 +647,44 @@ __global__ void __launch_bounds__(kWarps1 * 32) k_term1_mma(DevPlan P, MixPlan X
           const float w = warp_sum_f(evf[c]);
           if (lane == 0) atomicAdd(&sacc[c], (double)w);
         }
-        // Q += V_AB . U (M = alpha, N = (a,f), K = beta)
+        // Q += V_AB . U (M = alpha, N = (a,f), K = beta).  Warp -> one alpha tile
+        // and the (a,f) tiles nt = w0 + i * wpm; tiles i, i + 1 interleaved.
+        {
+          const int wpm = kWarps1 / MT;
+          const int mt = warp % MT, w0 = warp / MT;
+          if (w0 < wpm) {
+            for (int k0 = 0; k0 < MB; k0 += 16) {
+              uint32_t af[NP][4];
 #pragma unroll
-        for (int i = 0; i < kQT; ++i) {
-          const int tt = warp + i * kWarps1;
-          if (tt >= MT * NTq) continue;
-          const int mt = tt / NTq, nt = tt - mt * NTq;
-          for (int k0 = 0; k0 < MB; k0 += 16) {
-            uint32_t af[NP][4], bf[NP][2];
+              for (int pp = 0; pp < NP; ++pp)
+                ldm_x4(af[pp], Vs + (size_t)pp * MA * VS + (size_t)(mt * 16 + (lane & 15)) * VS + k0 + ((lane >> 4) << 3));
 #pragma unroll
-            for (int pp = 0; pp < NP; ++pp) {
-              ldm_x4(af[pp], Vs + (size_t)pp * MA * VS + (size_t)(mt * 16 + (lane & 15)) * VS + k0 + ((lane >> 4) << 3));
-              ldm_x2_trans(bf[pp], Us + (size_t)pp * MB * KS + (size_t)(k0 + (lane & 15)) * KS + nt * 8);
+              for (int i = 0; i < kQT; i += 2) {
+                const int nt0 = w0 + i * wpm, nt1 = w0 + (i + 1) * wpm;
+                if (nt0 >= NTq) continue;
+                const bool two = nt1 < NTq;
+                uint32_t bf0[NP][2], bf1[NP][2];
+#pragma unroll
+                for (int pp = 0; pp < NP; ++pp) {
+                  ldm_x2_trans(bf0[pp], Us + (size_t)pp * MB * KS + (size_t)(k0 + (lane & 15)) * KS + nt0 * 8);
+                  ldm_x2_trans(bf1[pp], Us + (size_t)pp * MB * KS + (size_t)(k0 + (lane & 15)) * KS + (two ? nt1 : nt0) * 8);
+                }
+                if (two) mma_split2<NP>(qacc[i], af, bf0, qacc[i + 1], af, bf1);
+                else mma_split<NP>(qacc[i], af, bf0);
+              }
             }
-            mma_split<NP>(qacc[i], af, bf);
           }
         }
         // flush the FP32 run of Q into the FP64 gradient dot
         const long long bi = c0 + t;
         if ((bi % kFlush) == kFlush - 1 || bi + 1 == nbt) {
           float gf[3] = {0.f, 0.f, 0.f};
+          const int wpm = kWarps1 / MT;
+          const int mt = warp % MT, w0 = warp / MT;
 #pragma unroll
           for (int i = 0; i < kQT; ++i) {
-            const int tt = warp + i * kWarps1;
-            if (tt >= MT * NTq) continue;
-            const int mt = tt / NTq, nt = tt - mt * NTq;
+            const int nt = w0 + i * wpm;
+            if (w0 >= wpm || nt >= NTq) continue;
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
               const int al = mt * 16 + gid + ((c & 2) ? 8 : 0);
@@ -743,10 +802,9 @@ __global__ void __launch_bounds__(kWarps * 32) k_term2_pairs(DevPlan P, MixPlan 
         }
       }
     }
-    // Z (M = alpha, N = (a,b), K = beta) -> Z store
+    // Z (M = alpha, N = (a,b), K = beta) -> Z store, 128-row tiles of rows (alpha,a)
     {
       uint16_t* Zo = X.Zst + (long long)kk * zblk;
-      const long long zpl = (long long)zrows * pB;
       const int MT = MA >> 4, NT = NAB >> 3;
       for (int t = warp; t < MT * NT; t += kWarps) {
         const int mt = t / NT, nt = t - mt * NT;
@@ -776,8 +834,10 @@ __global__ void __launch_bounds__(kWarps * 32) k_term2_pairs(DevPlan P, MixPlan 
             split_f<NP>(acc[2 * h], p0);
             split_f<NP>(acc[2 * h + 1], p1);
 #pragma unroll
+            const int r = al * nA + a;
             for (int pp = 0; pp < NP; ++pp)
-              *reinterpret_cast<uint32_t*>(Zo + pp * zpl + (long long)(al * nA + a) * pB + bb) = pack2(p0[pp], p1[pp]);
+              *reinterpret_cast<uint32_t*>(Zo + ((long long)(r >> 7) * NP + pp) * 2048 + tix(r & 127, bb)) =
+                  pack2(p0[pp], p1[pp]);
           }
         }
       }
@@ -799,156 +859,307 @@ __global__ void __launch_bounds__(kWarps * 32) k_term2_pairs(DevPlan P, MixPlan 
   }
 }
 
-// Phase 2: Q2^{AF}[(alpha,a)][f] = sum_{B} sum_b Z^{AB}[(alpha,a)][b] D_FB[f][b]
-// as one GEMM per home atom A (K = (B, b) over its pairs of the second
-// product), dotted with grad C_AF.  CTA = (A, 4 C slots F, 128 rows); each
-// warp owns one 16-row tile and the 4 x 2 column tiles of the 4 F.  The D
-// blocks of each chunk of pairs are resolved into shared memory first.
-constexpr int kQ2Meta = 64;
+// ------------------------------------------------------------ tcgen05 Q2 GEMM
+// Same product as k_q2_gemm on the 5th-generation tensor cores: per CTA
+// (home atom A, 8 C slots F, 128 rows (alpha,a)), D[row][(F,f)] +=
+// Z^{AB}[row][b] D_FB[f][b] over the pairs (A,B) of the second product, one
+// k16 step per pair and all bf16 piece products into one FP32 accumulator in
+// tensor memory (128 lanes x 128 columns).  Operands are staged by cp.async in
+// the K-major no-swizzle core-matrix layout (8 rows x 16 bytes per core
+// matrix; LBO = 128 B between the two K halves, SBO = 256 B between 8-row
+// groups) through a 4-stage ring; thread 0 issues the MMAs and commits each
+// stage to an mbarrier.  Every 32 pairs the accumulator is read back
+// (tcgen05.ld) and dotted with grad C_AF into FP64.  Every wait is bounded;
+// on timeout the CTA sets *err and stops.
+namespace umma {
+
+constexpr int kStages = 4;
+constexpr int kTileElems = 128 * 16;     // bf16 elements of one 128 x 16 operand tile (one piece)
+constexpr int kMetaPairs = 1024;         // pairs per CTA segment (metadata in shared memory)
+constexpr int kFlushPairs = 32;
+constexpr long long kSpin = 1ll << 26;   // bounded mbarrier wait
+
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)(128 >> 4) << 16;       // LBO: K-adjacent core matrices
+  d |= (uint64_t)(256 >> 4) << 32;       // SBO: 8-row groups
+  d |= (uint64_t)1 << 46;                // descriptor version of the sm_100 family
+  return d;
+}
+
+// element offset (uint16 units) of (row r, k) inside one 128 x 16 tile
+__device__ __forceinline__ int toff(int r, int kh) { return (r >> 3) * 128 + kh * 64 + (r & 7) * 8; }
+
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+  for (long long it = 0; it < kSpin; ++it) {
+    uint32_t done;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(done)
+                 : "r"(mbar), "r"(parity)
+                 : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
+
+}  // namespace umma
+
 template <int NP>
-__global__ void __launch_bounds__(kWarps * 32, 2) k_q2_gemm(DevPlan P, MixPlan X, const int* list,
-                                                            const long long* slot0, int n_slots, int FC, int MC,
-                                                            long long zblk, int zrows) {
-  __shared__ long long m_d[kQ2Meta][4];
-  __shared__ int m_pB[kQ2Meta], m_nB[kQ2Meta];
-  __shared__ double sg[4][3];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gid = lane >> 2, tig = lane & 3;
-  const int A = blockIdx.x / (FC * MC);
-  const int rem = blockIdx.x - A * FC * MC;
-  const int fc = rem / MC, mc = rem - fc * MC;
+__global__ void __launch_bounds__(192) k_q2_umma(DevPlan P, MixPlan X, const int* list, const long long* slot0,
+                                                 int n_slots, int FC8, int MC, int NSEG, long long zblk,
+                                                 const uint16_t* zero512, int* err) {
+  // Warp roles: warp 0 lane 0 produces (bulk async copies into a 4-stage
+  // ring, completion counted in bytes on full[s]); warp 1 lane 0 issues the
+  // MMAs (all piece products of a pair into one of two TMEM accumulators,
+  // commits free the stage / hand the accumulator to the epilogue); warps 2..5
+  // read the accumulator (each its 32-lane quarter of tensor memory) and dot
+  // it with grad C_AF.  No block barrier inside the pipeline.
+  using namespace umma;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  uint16_t* stA = reinterpret_cast<uint16_t*>(smem_raw);                  // [kStages][NP][kTileElems]
+  uint16_t* stB = stA + (size_t)kStages * NP * kTileElems;                // [kStages][NP][kTileElems]
+  int* m_dblk = reinterpret_cast<int*>(stB + (size_t)kStages * NP * kTileElems);   // [kMetaPairs][8]
+  __shared__ __align__(8) uint64_t bar_full[kStages], bar_empty[kStages], bar_accf[2], bar_acce[2];
+  __shared__ uint32_t tmem_base;
+  __shared__ double sg[8][3];
+  __shared__ int s_abort;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  int rem = blockIdx.x;
+  const int seg = rem % NSEG;
+  rem /= NSEG;
+  const int mc = rem % MC;
+  rem /= MC;
+  const int fc = rem % FC8;
+  const int A = rem / FC8;
   const int sA = P.species[A];
   const int nA = P.n_ao[sA], mA = P.n_abf[sA];
   const int rows = mA * nA;
   const int q0 = P.c_ptr[A], nq = P.c_ptr[A + 1] - q0;
-  if (fc * 4 >= nq || mc * 128 >= rows) return;
-  const int mt = mc * 8 + warp;
-  const bool active = mt * 16 < rows;
-  int qf[4], nF[4];
+  if (fc * 8 >= nq || mc * 128 >= rows) return;
+  const long long s0 = slot0[P.v_ptr[A]];
+  const long long s1 = A + 1 < P.N ? slot0[P.v_ptr[A + 1]] : (long long)n_slots;
+  const long long p0 = s0 + (long long)seg * kMetaPairs;
+  const int np = (int)max(0ll, min((long long)kMetaPairs, s1 - p0));
+  if (np <= 0) return;
+  const int row0 = mc * 128;
+  int qf[8], nF[8];
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int j = fc * 4 + i;
+  for (int i = 0; i < 8; ++i) {
+    const int j = fc * 8 + i;
     qf[i] = (j < nq && P.c_keep[q0 + j]) ? q0 + j : -1;
     nF[i] = qf[i] >= 0 ? P.n_ao[P.species[P.c_j[qf[i]]]] : 0;
   }
-  if (threadIdx.x < 12) sg[threadIdx.x / 3][threadIdx.x % 3] = 0.0;
-  const long long s0 = slot0[P.v_ptr[A]];
-  const long long s1 = A + 1 < P.N ? slot0[P.v_ptr[A + 1]] : (long long)n_slots;
-  float acc[4][2][4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int n = 0; n < 2; ++n)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) acc[i][n][c] = 0.f;
-  unsigned long long fl = 0ull;
-  int run = 0;
-  for (long long c0 = s0; c0 < s1; c0 += kQ2Meta) {
-    const int nb = (int)min((long long)kQ2Meta, s1 - c0);
-    __syncthreads();
-    for (int e = threadIdx.x; e < nb * 4; e += blockDim.x) {
-      const int t = e >> 2, i = e & 3;
-      const int p = list[c0 + t];
+  // D block (units of 256 elements) of every (pair, F), or -1
+  for (int e = tid; e < np * 8; e += blockDim.x) {
+    const int t = e >> 3, i = e & 7;
+    int db = -1;
+    if (qf[i] >= 0) {
+      const int p = list[p0 + t];
       const int b = P.v_j[p];
       const int* Rb = P.v_R + 3 * p;
-      long long doff = -1;
-      if (qf[i] >= 0) {
-        const int* Rf = P.c_R + 3 * qf[i];
-        const int d = dlut_get(P, P.c_j[qf[i]], b, Rb[0] - Rf[0], Rb[1] - Rf[1], Rb[2] - Rf[2]);
-        if (d >= 0 && P.Dkept[d] != 0.0) doff = X.dsp_off[d];
-      }
-      m_d[t][i] = doff;
-      if (i == 0) {
-        m_nB[t] = P.n_ao[P.species[b]];
-        m_pB[t] = rup16(m_nB[t]);
+      const int* Rf = P.c_R + 3 * qf[i];
+      const int d = dlut_get(P, P.c_j[qf[i]], b, Rb[0] - Rf[0], Rb[1] - Rf[1], Rb[2] - Rf[2]);
+      if (d >= 0 && P.Dkept[d] != 0.0) db = (int)(X.dsp_off[d] >> 8);
+    }
+    m_dblk[e] = db;
+  }
+  const uint32_t mfull = (uint32_t)__cvta_generic_to_shared(&bar_full[0]);
+  const uint32_t mempty = (uint32_t)__cvta_generic_to_shared(&bar_empty[0]);
+  const uint32_t maccf = (uint32_t)__cvta_generic_to_shared(&bar_accf[0]);
+  const uint32_t macce = (uint32_t)__cvta_generic_to_shared(&bar_acce[0]);
+  if (tid < 24) sg[tid / 3][tid % 3] = 0.0;
+  if (tid == 0) {
+    s_abort = 0;
+    for (int s = 0; s < kStages; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mfull + 8 * s));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mempty + 8 * s));
+    }
+    for (int b = 0; b < 2; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(maccf + 8 * b));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;\n" ::"r"(macce + 8 * b));
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
+  }
+  if (warp == 1) {
+    const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&tmem_base);
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(dst), "r"(256));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t taddr = tmem_base;
+  const int nruns = (np + kFlushPairs - 1) / kFlushPairs;
+  unsigned long long fl = 0ull;
+
+  if (warp == 0) {
+    // producer warp: every lane waits for the stage, then lanes issue the
+    // copies of one stage in parallel (lane 0 also posts the byte count)
+    const uint32_t bytes = (uint32_t)NP * 2 * kTileElems * 2;
+    for (int k = 0; k < np; ++k) {
+      const int s = k % kStages;
+      if (k >= kStages && !mbar_wait(mempty + 8 * s, (uint32_t)((k / kStages - 1) & 1))) s_abort = 1;
+      __syncwarp();
+      if (s_abort) break;
+      if (lane == 0)
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mfull + 8 * s), "r"(bytes)
+                     : "memory");
+      // copy c < NP: Z piece tile (4 KB); c = NP + pp * 8 + i: D block i of piece pp (512 B)
+      for (int c = lane; c < NP * 9; c += 32) {
+        uint32_t dst;
+        const uint16_t* src;
+        uint32_t nb;
+        if (c < NP) {
+          dst = (uint32_t)__cvta_generic_to_shared(stA + ((size_t)s * NP + c) * kTileElems);
+          src = X.Zst + (p0 + k) * zblk + ((long long)mc * NP + c) * kTileElems;
+          nb = kTileElems * 2;
+        } else {
+          const int pp = (c - NP) >> 3, i = (c - NP) & 7;
+          const int db = m_dblk[k * 8 + i];
+          dst = (uint32_t)__cvta_generic_to_shared(stB + ((size_t)s * NP + pp) * kTileElems + i * 256);
+          src = db >= 0 ? X.Dsp + (long long)db * 256 + pp * 256 : zero512;
+          nb = 512;
+        }
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+                     "l"(src), "r"(nb), "r"(mfull + 8 * s)
+                     : "memory");
       }
     }
-    __syncthreads();
-    if (mc == 0 && threadIdx.x == 0)
-      for (int t = 0; t < nb; ++t)
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-          if (m_d[t][i] >= 0) fl += 2ull * mA * nA * m_nB[t] * nF[i];
-    for (int t = 0; t < nb; ++t) {
-      const int pB = m_pB[t];
-      if (active) {
-        const uint16_t* Zp = X.Zst + (c0 + t) * zblk;
-        const long long zpl = (long long)zrows * pB;
-        for (int k0 = 0; k0 < pB; k0 += 16) {
-          uint32_t af[NP][4];
-#pragma unroll
-          for (int h = 0; h < 4; ++h) {
-            const int r = mt * 16 + gid + ((h & 1) ? 8 : 0);
-            const int kc = k0 + 2 * tig + ((h & 2) ? 8 : 0);
-#pragma unroll
-            for (int pp = 0; pp < NP; ++pp)
-              af[pp][h] = r < rows ? *reinterpret_cast<const uint32_t*>(Zp + pp * zpl + (long long)r * pB + kc) : 0u;
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // MMA issuer: D f32, A/B bf16, both K-major, N = 128, M = 128
+      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+      for (int r = 0; r < nruns && !s_abort; ++r) {
+        const int b = r & 1;
+        if (r >= 2 && !mbar_wait(macce + 8 * b, (uint32_t)((r / 2 - 1) & 1))) {
+          s_abort = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        const uint32_t dacc = taddr + 128u * b;
+        const int k1 = min(np, (r + 1) * kFlushPairs);
+        bool first = true;
+        for (int k = r * kFlushPairs; k < k1; ++k) {
+          const int s = k % kStages;
+          if (!mbar_wait(mfull + 8 * s, (uint32_t)((k / kStages) & 1))) {
+            s_abort = 1;
+            break;
           }
+          asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+          const uint32_t a0 = (uint32_t)__cvta_generic_to_shared(stA + (size_t)s * NP * kTileElems);
+          const uint32_t b0 = (uint32_t)__cvta_generic_to_shared(stB + (size_t)s * NP * kTileElems);
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const long long doff = m_d[t][i];
-            if (doff < 0) continue;
-            const int pF = rup16(nF[i]);
-            const uint16_t* Dfb = X.Dsp + doff;
+          for (int sum = NP - 1; sum >= 0; --sum)
 #pragma unroll
-            for (int nt = 0; nt < 2; ++nt) {
-              if (nt * 8 >= pF) continue;
-              uint32_t bf[NP][2];
-#pragma unroll
-              for (int pp = 0; pp < NP; ++pp) {
-                const uint16_t* Db = Dfb + pp * pF * pB + (nt * 8 + gid) * pB + k0 + 2 * tig;
-                bf[pp][0] = *reinterpret_cast<const uint32_t*>(Db);
-                bf[pp][1] = *reinterpret_cast<const uint32_t*>(Db + 8);
-              }
-              mma_split<NP>(acc[i][nt], af, bf);
+            for (int ia = 0; ia <= sum; ++ia) {
+              const int ib = sum - ia;
+              const uint64_t ad = sdesc(a0 + ia * kTileElems * 2);
+              const uint64_t bd = sdesc(b0 + ib * kTileElems * 2);
+              const uint32_t acc = first ? 0u : 1u;
+              asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                           " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dacc),
+                           "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+              first = false;
             }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mempty + 8 * s)
+                       : "memory");
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(maccf + 8 * b)
+                     : "memory");
+      }
+    }
+  } else {
+    // epilogue: warps 2..5, tensor-memory lane quarter q = warp % 4
+    const int q = warp & 3;
+    const int r = row0 + q * 32 + lane;
+    const bool rv = r < rows;
+    const int al = rv ? r / nA : 0, a = rv ? r - al * nA : 0;
+    double gd[8][3];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) gd[i][0] = gd[i][1] = gd[i][2] = 0.0;
+    for (int run = 0; run < nruns; ++run) {
+      const int b = run & 1;
+      if (!mbar_wait(maccf + 8 * b, (uint32_t)((run / 2) & 1))) {
+        s_abort = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+#pragma unroll
+      for (int c0 = 0; c0 < 128; c0 += 32) {
+        uint32_t v[32];
+        tmem_ld32(taddr + ((uint32_t)(q * 32) << 16) + 128u * b + c0, v);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int i = (c0 >> 4) + h;
+          if (!rv || qf[i] < 0) continue;
+          const int KAF = nA * nF[i];
+          const long long ncq = (long long)mA * KAF;
+          const int pF = rup16(nF[i]);
+          const float* dC = reinterpret_cast<const float*>(X.Cm + X.cm_off[qf[i]] + (long long)NP * rows * pF);
+          const long long o = (long long)al * KAF + a * nF[i];
+          float g0 = 0.f, g1 = 0.f, g2 = 0.f;
+#pragma unroll
+          for (int ff = 0; ff < 16; ++ff) {
+            if (ff >= nF[i]) break;
+            const float x = __uint_as_float(v[h * 16 + ff]);
+            g0 = fmaf(dC[o + ff], x, g0);
+            g1 = fmaf(dC[ncq + o + ff], x, g1);
+            g2 = fmaf(dC[2 * ncq + o + ff], x, g2);
           }
+          gd[i][0] += (double)g0;
+          gd[i][1] += (double)g1;
+          gd[i][2] += (double)g2;
         }
       }
-      // flush the FP32 run into the FP64 gradient dots (shared accumulators)
-      if (++run == 32 || c0 + t + 1 == s1) {
-        run = 0;
-        if (active) {
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(macce + 8 * b) : "memory");
+    }
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            float gf[3] = {0.f, 0.f, 0.f};
-            if (qf[i] >= 0) {
-              const int pF = rup16(nF[i]);
-              const int KAF = nA * nF[i];
-              const long long ncq = (long long)mA * KAF;
-              const float* dC = reinterpret_cast<const float*>(X.Cm + X.cm_off[qf[i]] + (long long)NP * rows * pF);
+    for (int i = 0; i < 8; ++i)
 #pragma unroll
-              for (int nt = 0; nt < 2; ++nt)
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                  const int r = mt * 16 + gid + ((c & 2) ? 8 : 0);
-                  const int ff = nt * 8 + 2 * tig + (c & 1);
-                  if (r < rows && ff < nF[i]) {
-                    const int al = r / nA, a = r - al * nA;
-                    const long long o = (long long)al * KAF + a * nF[i] + ff;
-                    const float v = acc[i][nt][c];
-                    gf[0] = fmaf(dC[o], v, gf[0]);
-                    gf[1] = fmaf(dC[ncq + o], v, gf[1]);
-                    gf[2] = fmaf(dC[2 * ncq + o], v, gf[2]);
-                  }
-                  acc[i][nt][c] = 0.f;
-                }
-            }
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-              const float w = warp_sum_f(gf[c]);
-              if (lane == 0 && w != 0.f) atomicAdd(&sg[i][c], (double)w);
-            }
-          }
-        }
+      for (int c = 0; c < 3; ++c) {
+        const double w = warp_sum_d(gd[i][c]);
+        if (lane == 0 && w != 0.0) atomicAdd(&sg[i][c], w);
       }
+  }
+  if (tid == 0 && mc == 0) {
+    for (int t = 0; t < np; ++t) {
+      const int nB = P.n_ao[P.species[P.v_j[list[p0 + t]]]];
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        if (m_dblk[t * 8 + i] >= 0) fl += 2ull * mA * nA * nB * nF[i];
     }
   }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
-  if (threadIdx.x < 12) {
-    const int i = threadIdx.x / 3, c = threadIdx.x % 3;
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(256));
+  if (tid < 24) {
+    const int i = tid / 3, c = tid % 3;
     if (qf[i] >= 0 && sg[i][c] != 0.0) atomicAdd(&P.gC[3 * qf[i] + c], -2.0 * sg[i][c]);
   }
-  if (threadIdx.x == 0 && fl) atomicAdd(&P.acc[ACC_F2], (double)fl);
+  if (tid == 0) {
+    if (s_abort) atomicExch(err, 1);
+    if (fl) atomicAdd(&P.acc[ACC_F2], (double)fl);
+  }
+}
+
+size_t q2_umma_smem(int np) {
+  return (size_t)2 * umma::kStages * np * umma::kTileElems * sizeof(uint16_t) + (size_t)umma::kMetaPairs * 8 * sizeof(int);
 }
 
 int grid_for(long long n, int cap) {
@@ -959,6 +1170,8 @@ int grid_for(long long n, int cap) {
 }  // namespace
 
 long long mixed_launch_count() { return g_mix_launches; }
+
+int q2_umma_segments(int max_pairs_per_atom) { return (max_pairs_per_atom + umma::kMetaPairs - 1) / umma::kMetaPairs; }
 
 cudaError_t launch_dsplit(const DevPlan& P, const MixPlan& X, int np, cudaStream_t s) {
   if (P.n_d == 0) return cudaSuccess;
@@ -1015,6 +1228,9 @@ size_t term2_mma_smem(int np, int MAmax, int KZmax) {
 
 cudaError_t set_mixed_smem_limits(int np, size_t t1, size_t t2) {
   cudaError_t e;
+  e = cudaFuncSetAttribute(np == 2 ? (const void*)k_q2_umma<2> : (const void*)k_q2_umma<3>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)q2_umma_smem(np));
+  if (e != cudaSuccess) return e;
   if (np == 2) {
     e = cudaFuncSetAttribute(k_term1_mma<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t1);
     if (e != cudaSuccess) return e;
@@ -1037,16 +1253,19 @@ cudaError_t launch_term1_mma(const DevPlan& P, const MixPlan& X, int np, const i
 }
 
 cudaError_t launch_term2_mma(const DevPlan& P, const MixPlan& X, int np, const int* list, const long long* slot0,
-                             int n, int MAmax, int KZmax, long long zblk, int zrows, int FC, int MC, size_t smem,
-                             cudaStream_t s) {
+                             int n, int MAmax, int KZmax, long long zblk, int zrows, int FC, int MC, int nseg,
+                             const uint16_t* zero512, size_t smem, int* err, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   g_mix_launches += 2;
+  const int FC8 = (FC * 4 + 7) / 8;     // groups of 8 C slots for the tcgen05 kernel
+  const size_t sq = q2_umma_smem(np);
+  const long long grid = (long long)P.N * FC8 * MC * nseg;
   if (np == 2) {
     k_term2_pairs<2><<<grid_for(n, 152 * 32), kWarps * 32, smem, s>>>(P, X, list, n, MAmax, KZmax, zblk, zrows);
-    k_q2_gemm<2><<<P.N * FC * MC, kWarps * 32, 0, s>>>(P, X, list, slot0, n, FC, MC, zblk, zrows);
+    k_q2_umma<2><<<(unsigned)grid, 192, sq, s>>>(P, X, list, slot0, n, FC8, MC, nseg, zblk, zero512, err);
   } else {
     k_term2_pairs<3><<<grid_for(n, 152 * 32), kWarps * 32, smem, s>>>(P, X, list, n, MAmax, KZmax, zblk, zrows);
-    k_q2_gemm<3><<<P.N * FC * MC, kWarps * 32, 0, s>>>(P, X, list, slot0, n, FC, MC, zblk, zrows);
+    k_q2_umma<3><<<(unsigned)grid, 192, sq, s>>>(P, X, list, slot0, n, FC8, MC, nseg, zblk, zero512, err);
   }
   return cudaGetLastError();
 }
