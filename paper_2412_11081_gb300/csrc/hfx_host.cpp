@@ -176,6 +176,8 @@ struct hfx_plan {
   long long Yspcap = 0;
   uint16_t* Cm = nullptr;
   long long* cm_off = nullptr;
+  int *gcnt = nullptr, *gX = nullptr, *gS = nullptr, *gN = nullptr;   // groups of needed Y keys
+  long long* goff = nullptr;
   uint16_t* Vm = nullptr;
   long long Vmcap = 0;
   long long *vm_off = nullptr, *vm_size = nullptr;
@@ -644,8 +646,9 @@ void build_lists(hfx_plan* P, const double* L, const double* pos) {
     for (int p = 0; p < nC; ++p) {
       const int sA = P->species[c_home[p]], sj = P->species[c_j[p]];
       const long long rows = (long long)P->n_abf[sA] * P->n_ao[sA];
-      const long long pF = (P->n_ao[sj] + 15) / 16 * 16;
-      cm_off[p + 1] = cm_off[p] + P->np * rows * pF + 2 * 3 * rows * P->n_ao[sj];
+      // bf16 tiles then FP32 grad C; each block rounded to 128 bytes (bulk copies need 16-byte alignment)
+      const long long sz = P->np * ((rows + 127) / 128) * 2048 + 2 * 3 * rows * P->n_ao[sj];
+      cm_off[p + 1] = cm_off[p] + (sz + 63) / 64 * 64;
     }
     for (int p = 0; p < nV; ++p) {
       const long long mA = P->n_abf[P->species[v_home[p]]], mB = P->n_abf[P->species[v_j[p]]];
@@ -657,6 +660,11 @@ void build_lists(hfx_plan* P, const double* L, const double* pos) {
     P->vm_size = P->lalloc<long long>(nV);
     upload(P->cm_off, cm_off, s);
     upload(P->vm_size, vm_size, s);
+    P->gcnt = P->lalloc<int>(N);
+    P->goff = P->lalloc<long long>(N);
+    P->gX = P->lalloc<int>(nY);
+    P->gS = P->lalloc<int>(nY);
+    P->gN = P->lalloc<int>(nY);
     P->qcnt = P->lalloc<int>(nC);
     P->qoff = P->lalloc<long long>(nC);
     P->q_idx = P->lalloc<long long>(nC);
@@ -858,6 +866,9 @@ void evaluate(hfx_plan* P, const double* L, hfx_stats* st) {
     if (P->np) {
       // (A,F) view of the kept triplets: per C pair, its kept B in V-pair order
       ck(hfx::scan_flags(P->v_flag, P->vm_size, nullptr, nullptr, 1, P->nV, P->vm_off, T + 8, P->scan_tmp, s), "scan");
+      ck(hfx::launch_ygroups(D, P->y_idx, T + 1, P->gcnt, nullptr, nullptr, nullptr, nullptr, 0, s), "ygroups");
+      ck(hfx::scan_flags(P->gcnt, nullptr, nullptr, nullptr, 4, P->N, P->goff, T + 9, P->scan_tmp, s), "scan");
+      ck(hfx::launch_ygroups(D, P->y_idx, T + 1, P->gcnt, P->goff, P->gX, P->gS, P->gN, 1, s), "ygroups");
       ck(hfx::launch_t1_lists(D, X, 0, s), "t1 count");
       ck(hfx::scan_flags(P->qcnt, nullptr, nullptr, nullptr, 4, P->nC, P->qoff, T + 6, P->scan_tmp, s), "scan");
       ck(hfx::scan_flags(P->qcnt, nullptr, nullptr, nullptr, 0, P->nC, P->q_idx, T + 7, P->scan_tmp, s), "scan");
@@ -895,9 +906,12 @@ void evaluate(hfx_plan* P, const double* L, hfx_stats* st) {
     ck(hfx::launch_vblocks(D, P->v_list, (int)P->tot[3], s), "vblocks");
     ck(hfx::launch_vpieces(D, X, P->np, P->v_list, (int)P->tot[3], s), "vpieces");
     ck(hfx::launch_cpieces(D, X, P->np, s), "cpieces");
-    int wide = 0;
-    for (int t = 0; t < P->S; ++t) wide |= P->n_ao[t] > 16;
-    ck(hfx::launch_ybuild_mma(D, X, P->np, P->y_list, (int)P->tot[1], wide, s), "ybuild");
+    if (!P->zero512) {
+      P->zero512 = P->mem.alloc<uint16_t>(512);
+      ck(cudaMemsetAsync(P->zero512, 0, 512 * sizeof(uint16_t), s), "memset");
+    }
+    ck(hfx::launch_ybuild_mma(D, X, P->np, P->y_list, P->gX, P->gS, P->gN, (int)P->tot[9], P->MC, P->zero512, P->d_err, s),
+       "ybuild");
     tm.mark();  // 3
     ck(hfx::launch_term1_mma(D, X, P->np, P->t1q_list, (int)P->tot[7], P->MAmax, P->MBmax, P->KSmax, P->YRmax,
                              P->smem_m1, s),

@@ -134,7 +134,10 @@ long long mixed_launch_count();
 cudaError_t launch_dsplit(const DevPlan& P, const MixPlan& X, int np, cudaStream_t s);
 cudaError_t launch_cpieces(const DevPlan& P, const MixPlan& X, int np, cudaStream_t s);
 cudaError_t launch_vpieces(const DevPlan& P, const MixPlan& X, int np, const int* list, int n, cudaStream_t s);
-cudaError_t launch_ybuild_mma(const DevPlan& P, const MixPlan& X, int np, const int* list, int n, int wide,
+cudaError_t launch_ygroups(const DevPlan& P, const long long* y_idx, const long long* y_total, int* gcnt,
+                           const long long* goff, int* gX, int* gS, int* gN, int phase, cudaStream_t s);
+cudaError_t launch_ybuild_mma(const DevPlan& P, const MixPlan& X, int np, const int* ylist, const int* gX,
+                              const int* gS, const int* gN, int ngroups, int MC, const uint16_t* zero512, int* err,
                               cudaStream_t s);
 cudaError_t launch_t1_lists(const DevPlan& P, const MixPlan& X, int phase, cudaStream_t s);
 size_t term1_mma_smem(int np, int MAmax, int MBmax, int KSmax, int YRmax);

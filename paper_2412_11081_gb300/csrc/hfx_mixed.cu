@@ -192,25 +192,28 @@ __global__ void k_dsplit(DevPlan P, MixPlan X) {
 }
 
 // ------------------------------------------------------------------ pieces
-// C pair q: NP bf16 planes of C[(alpha,a)][rup16(n_ao(F))] then grad C (FP32).
+// C pair q: NP bf16 pieces of C[(alpha,a)][f] in 128-row tiles of the
+// tensor cores' core-matrix order ([tile][piece][128 x 16], f padded to 16),
+// then grad C in FP32 ([3][(alpha,a)][f]).
 template <int NP>
 __global__ void k_cpieces(DevPlan P, MixPlan X) {
   for (int q = blockIdx.x; q < P.nC; q += gridDim.x) {
     if (!P.c_keep[q]) continue;
     const int A = P.c_home[q], f = P.c_j[q];
     const int sA = P.species[A], sF = P.species[f];
-    const int rows = P.n_abf[sA] * P.n_ao[sA], nF = P.n_ao[sF], pF = rup16(nF);
+    const int rows = P.n_abf[sA] * P.n_ao[sA], nF = P.n_ao[sF];
+    const int nt = (rows + 127) >> 7;
     const double* C = P.Cst + P.c_off[q];
     const double* dC = P.dCst + 3 * P.c_off[q];
     uint16_t* out = X.Cm + X.cm_off[q];
-    for (int e = threadIdx.x; e < rows * pF; e += blockDim.x) {
-      const int r = e / pF, c = e - r * pF;
+    for (int e = threadIdx.x; e < nt * 128 * 16; e += blockDim.x) {
+      const int r = e >> 4, c = e & 15;
       uint16_t pc[NP];
-      split_f<NP>(c < nF ? (float)C[r * nF + c] : 0.f, pc);
+      split_f<NP>((r < rows && c < nF) ? (float)C[r * nF + c] : 0.f, pc);
 #pragma unroll
-      for (int p = 0; p < NP; ++p) out[p * rows * pF + e] = pc[p];
+      for (int p = 0; p < NP; ++p) out[((r >> 7) * NP + p) * 2048 + tix(r & 127, c)] = pc[p];
     }
-    float* g = reinterpret_cast<float*>(out + NP * rows * pF);
+    float* g = reinterpret_cast<float*>(out + NP * nt * 2048);
     for (int e = threadIdx.x; e < 3 * rows * nF; e += blockDim.x) g[e] = (float)dC[e];
   }
 }
@@ -233,131 +236,6 @@ __global__ void k_vpieces(DevPlan P, MixPlan X, const int* list, int n_list) {
     }
     float* v32 = reinterpret_cast<float*>(out + NP * mA * MB);
     for (int e = threadIdx.x; e < 4 * mA * mB; e += blockDim.x) v32[e] = (float)V[e];
-  }
-}
-
-// ------------------------------------------------------------------ Y build
-// One CTA per needed key (X; Z).  Rows (alpha, x), columns z, K = (W, w):
-// Y[(alpha,x)][z] = sum_W sum_w C_XW[(alpha,x)][w] D_WZ[w][z].  The B
-// fragments come from the mirror block D_ZW = D_WZ^T (row z, column w).
-// Output: NP planes of [alpha][z][rup16(n_ao(X))], x padding zeroed.
-template <int NP, int NTM>
-__global__ void __launch_bounds__(kWarps * 32, 2) k_ybuild_mma(DevPlan P, MixPlan X, const int* list, int n_list) {
-  __shared__ int dsel[kMaxCPerAtom];   // mirror D block (index into Dsp) per C slot, -1 = none
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gid = lane >> 2, tig = lane & 3;
-  for (int kk = blockIdx.x; kk < n_list; kk += gridDim.x) {
-    const int y = list[kk];
-    const int Xa = P.y_home[y], z = P.y_j[y];
-    const int* Rz = P.y_R + 3 * y;
-    const int q0 = P.c_ptr[Xa], nq = P.c_ptr[Xa + 1] - q0;
-    __syncthreads();
-    for (int t = threadIdx.x; t < nq; t += blockDim.x) {
-      const int q = q0 + t;
-      int sel = -1;
-      if (P.c_keep[q]) {
-        const int* Rw = P.c_R + 3 * q;
-        const int w = P.c_j[q];
-        const int di = dlut_get(P, w, z, Rz[0] - Rw[0], Rz[1] - Rw[1], Rz[2] - Rw[2]);
-        if (di >= 0 && P.Dkept[di] != 0.0) sel = dlut_get(P, z, w, Rw[0] - Rz[0], Rw[1] - Rz[1], Rw[2] - Rz[2]);
-      }
-      dsel[t] = sel;
-    }
-    __syncthreads();
-    const int sX = P.species[Xa], sZ = P.species[z];
-    const int mX = P.n_abf[sX], nX = P.n_ao[sX], nZ = P.n_ao[sZ];
-    const int pX = rup16(nX), pZ = rup16(nZ);
-    const int rows = mX * nX;
-    const int MT = (rows + 15) >> 4;
-    const int NT = pZ >> 3;                 // <= NTM
-    uint16_t* Yo = X.Ysp + P.y_off[y];
-    const long long plane = (long long)mX * nZ * pX;
-    for (int mbase = 0; mbase < MT; mbase += kYT * kWarps) {
-    float acc[kYT][NTM][4];
-#pragma unroll
-    for (int i = 0; i < kYT; ++i)
-#pragma unroll
-      for (int j = 0; j < NTM; ++j)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) acc[i][j][c] = 0.f;
-    for (int t = 0; t < nq; ++t) {
-      const int sel = dsel[t];
-      if (sel < 0) continue;
-      const int q = q0 + t;
-      const int nW = P.n_ao[P.species[P.c_j[q]]];
-      const int pW = rup16(nW);
-      const uint16_t* Cq = X.Cm + X.cm_off[q];          // planes [(alpha,x)][pW]
-      const long long cplane = (long long)rows * pW;
-      const uint16_t* Dm = X.Dsp + X.dsp_off[sel];   // mirror block, [z][w] planes of pZ x pW
-      for (int k0 = 0; k0 < pW; k0 += 16) {
-        uint32_t bf[NTM][NP][2];
-#pragma unroll
-        for (int nt = 0; nt < NTM; ++nt) {
-          if (nt < NT) {
-#pragma unroll
-            for (int p = 0; p < NP; ++p) {
-              const uint16_t* Db = Dm + p * 256 + tix(nt * 8 + gid, 2 * tig);
-              bf[nt][p][0] = *reinterpret_cast<const uint32_t*>(Db);
-              bf[nt][p][1] = *reinterpret_cast<const uint32_t*>(Db + 64);
-            }
-          }
-        }
-#pragma unroll
-        for (int i = 0; i < kYT; ++i) {
-          const int mt = mbase + warp + i * kWarps;
-          if (mt >= MT) break;
-          uint32_t af[NP][4];
-#pragma unroll
-          for (int h = 0; h < 4; ++h) {
-            const int r = mt * 16 + gid + ((h & 1) ? 8 : 0);
-            const int kc = k0 + 2 * tig + ((h & 2) ? 8 : 0);
-#pragma unroll
-            for (int p = 0; p < NP; ++p)
-              af[p][h] = r < rows ? *reinterpret_cast<const uint32_t*>(Cq + p * cplane + (long long)r * pW + kc) : 0u;
-          }
-#pragma unroll
-          for (int nt = 0; nt < NTM; nt += 2)
-            if (nt < NT) mma_split2<NP>(acc[i][nt], af, bf[nt], acc[i][nt + 1], af, bf[nt + 1]);
-        }
-      }
-    }
-    // store Y planes [alpha][z][x], x padding zeroed
-#pragma unroll
-    for (int i = 0; i < kYT; ++i) {
-      const int mt = mbase + warp + i * kWarps;
-      if (mt >= MT) break;
-#pragma unroll
-      for (int nt = 0; nt < NTM; ++nt) {
-        if (nt >= NT) continue;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const int r = mt * 16 + gid + ((c & 2) ? 8 : 0);
-          const int zc = nt * 8 + 2 * tig + (c & 1);
-          if (r < rows && zc < nZ) {
-            const int al = r / nX, x = r - al * nX;
-            uint16_t pc[NP];
-            split_f<NP>(acc[i][nt][c], pc);
-            const long long o = ((long long)al * nZ + zc) * pX + x;
-#pragma unroll
-            for (int p = 0; p < NP; ++p) Yo[p * plane + o] = pc[p];
-          }
-        }
-      }
-    }
-    }  // m-tile groups
-    if (pX > nX) {
-      for (long long e = threadIdx.x; e < (long long)mX * nZ * (pX - nX); e += blockDim.x) {
-        const long long rz = e / (pX - nX);
-        const int x = nX + (int)(e - rz * (pX - nX));
-#pragma unroll
-        for (int p = 0; p < NP; ++p) Yo[p * plane + rz * pX + x] = 0;
-      }
-    }
-    if (threadIdx.x == 0) {
-      double fl = 0.0;
-      for (int t = 0; t < nq; ++t)
-        if (dsel[t] >= 0) fl += 2.0 * rows * nZ * P.n_ao[P.species[P.c_j[q0 + t]]];
-      atomicAdd(&P.acc[ACC_FY], fl);
-    }
   }
 }
 
@@ -436,16 +314,16 @@ __global__ void __launch_bounds__(kWarps1 * 32) k_term1_mma(DevPlan P, MixPlan X
       sprev = -1;
     }
     // C_AF pieces -> Cs[alpha][a*nF + f] (zero padded)
-    const int pF = rup16(nF);
     const uint16_t* Cq = X.Cm + X.cm_off[q];
-    const long long cplane = (long long)mA * nA * pF;
+    const int ctiles = (mA * nA + 127) >> 7;
     for (int e = threadIdx.x; e < MA * KS; e += blockDim.x) {
       const int al = e / KS, k = e - al * KS;
       const bool in = al < mA && k < KAF;
       const int a = in ? k / nF : 0, ff = in ? k - a * nF : 0;
+      const int r = al * nA + a;
 #pragma unroll
       for (int pp = 0; pp < NP; ++pp)
-        Cs[(size_t)pp * MA * KS + e] = in ? Cq[pp * cplane + ((long long)al * nA + a) * pF + ff] : (uint16_t)0;
+        Cs[(size_t)pp * MA * KS + e] = in ? Cq[((r >> 7) * NP + pp) * 2048 + tix(r & 127, ff)] : (uint16_t)0;
     }
     float qacc[kQT][4];
 #pragma unroll
@@ -453,7 +331,7 @@ __global__ void __launch_bounds__(kWarps1 * 32) k_term1_mma(DevPlan P, MixPlan X
 #pragma unroll
       for (int c = 0; c < 4; ++c) qacc[i][c] = 0.f;
     double g[3] = {0.0, 0.0, 0.0};
-    const float* dC = reinterpret_cast<const float*>(Cq + NP * cplane);   // grad C, FP32
+    const float* dC = reinterpret_cast<const float*>(Cq + (long long)NP * ctiles * 2048);   // grad C, FP32
     const long long ncq = (long long)mA * KAF;
     const long long b0i = X.qoff[q], nbt = X.qcnt[q];
     unsigned long long fl = 0ull;
@@ -1107,8 +985,8 @@ __global__ void __launch_bounds__(192) k_q2_umma(DevPlan P, MixPlan X, const int
           if (!rv || qf[i] < 0) continue;
           const int KAF = nA * nF[i];
           const long long ncq = (long long)mA * KAF;
-          const int pF = rup16(nF[i]);
-          const float* dC = reinterpret_cast<const float*>(X.Cm + X.cm_off[qf[i]] + (long long)NP * rows * pF);
+          const float* dC =
+              reinterpret_cast<const float*>(X.Cm + X.cm_off[qf[i]] + (long long)NP * ((rows + 127) >> 7) * 2048);
           const long long o = (long long)al * KAF + a * nF[i];
           float g0 = 0.f, g1 = 0.f, g2 = 0.f;
 #pragma unroll
@@ -1158,6 +1036,239 @@ __global__ void __launch_bounds__(192) k_q2_umma(DevPlan P, MixPlan X, const int
   }
 }
 
+// ------------------------------------------------------------ tcgen05 Y build
+// Y^{XZ}[(alpha,x)][z] = sum_W sum_w C_XW[(alpha,x)][w] D_WZ[w][z] for a
+// group of up to 8 needed keys Z of one home atom X and 128 rows: K runs over
+// the kept C pairs (X,W) (one k16 step each); the B operand of key i is the
+// mirror block D_ZW = D_WZ^T (rows z, columns w).  Same warp roles as
+// k_q2_umma; one accumulation run; the epilogue splits the FP32 result into
+// bf16 pieces and writes the Y store ([alpha][z][16], x padding zeroed).
+template <int NP>
+__global__ void __launch_bounds__(192) k_ybuild_umma(DevPlan P, MixPlan X, const int* ylist, const int* gX,
+                                                     const int* gS, const int* gN, int MC, const uint16_t* zero512,
+                                                     int* err) {
+  using namespace umma;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  uint16_t* stA = reinterpret_cast<uint16_t*>(smem_raw);
+  uint16_t* stB = stA + (size_t)kStages * NP * kTileElems;
+  int* m_d = reinterpret_cast<int*>(stB + (size_t)kStages * NP * kTileElems);   // [kMaxCPerAtom][8]
+  __shared__ int m_q[kMaxCPerAtom];
+  __shared__ int s_nsteps;
+  __shared__ __align__(8) uint64_t bar_full[kStages], bar_empty[kStages], bar_accf;
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_abort;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int g = blockIdx.x / MC, mc = blockIdx.x - g * MC;
+  const int Xa = gX[g], kstart = gS[g], nk = gN[g];
+  const int sX = P.species[Xa];
+  const int mX = P.n_abf[sX], nX = P.n_ao[sX];
+  const int rows = mX * nX;
+  if (mc * 128 >= rows) return;
+  const int row0 = mc * 128;
+  const int q0 = P.c_ptr[Xa], nq = P.c_ptr[Xa + 1] - q0;
+  int ykey[8], zat[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    ykey[i] = i < nk ? ylist[kstart + i] : -1;
+    zat[i] = ykey[i] >= 0 ? P.y_j[ykey[i]] : 0;
+  }
+  for (int e = tid; e < nq * 8; e += blockDim.x) {
+    const int t = e >> 3, i = e & 7;
+    int md = -1;
+    if (ykey[i] >= 0 && P.c_keep[q0 + t]) {
+      const int* Rz = P.y_R + 3 * ykey[i];
+      const int* Rw = P.c_R + 3 * (q0 + t);
+      const int w = P.c_j[q0 + t], z = zat[i];
+      const int di = dlut_get(P, w, z, Rz[0] - Rw[0], Rz[1] - Rw[1], Rz[2] - Rw[2]);
+      if (di >= 0 && P.Dkept[di] != 0.0) {
+        const int mi = dlut_get(P, z, w, Rw[0] - Rz[0], Rw[1] - Rz[1], Rw[2] - Rz[2]);
+        md = (int)(X.dsp_off[mi] >> 8);
+      }
+    }
+    m_d[e] = md;
+  }
+  const uint32_t mfull = (uint32_t)__cvta_generic_to_shared(&bar_full[0]);
+  const uint32_t mempty = (uint32_t)__cvta_generic_to_shared(&bar_empty[0]);
+  const uint32_t maccf = (uint32_t)__cvta_generic_to_shared(&bar_accf);
+  if (tid == 0) {
+    s_abort = 0;
+    for (int s = 0; s < kStages; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mfull + 8 * s));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mempty + 8 * s));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(maccf));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
+  }
+  if (warp == 1) {
+    const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&tmem_base);
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(dst), "r"(128));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
+  }
+  __syncthreads();
+  if (tid == 0) {   // K steps: kept C pairs with at least one D block among the keys
+    int n = 0;
+    for (int t = 0; t < nq; ++t) {
+      bool any = false;
+      for (int i = 0; i < 8; ++i) any = any || m_d[t * 8 + i] >= 0;
+      if (any) m_q[n++] = t;
+    }
+    s_nsteps = n;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t taddr = tmem_base;
+  const int nsteps = s_nsteps;
+
+  if (warp == 0) {
+    const uint32_t bytes = (uint32_t)NP * 2 * kTileElems * 2;
+    for (int k = 0; k < nsteps; ++k) {
+      const int s = k % kStages;
+      if (k >= kStages && !mbar_wait(mempty + 8 * s, (uint32_t)((k / kStages - 1) & 1))) s_abort = 1;
+      __syncwarp();
+      if (s_abort) break;
+      if (lane == 0)
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mfull + 8 * s), "r"(bytes)
+                     : "memory");
+      const int t = m_q[k];
+      for (int c = lane; c < NP * 9; c += 32) {
+        uint32_t dst;
+        const uint16_t* src;
+        uint32_t nb;
+        if (c < NP) {
+          dst = (uint32_t)__cvta_generic_to_shared(stA + ((size_t)s * NP + c) * kTileElems);
+          src = X.Cm + X.cm_off[q0 + t] + ((long long)mc * NP + c) * kTileElems;
+          nb = kTileElems * 2;
+        } else {
+          const int pp = (c - NP) >> 3, i = (c - NP) & 7;
+          const int md = m_d[t * 8 + i];
+          dst = (uint32_t)__cvta_generic_to_shared(stB + ((size_t)s * NP + pp) * kTileElems + i * 256);
+          src = md >= 0 ? X.Dsp + (long long)md * 256 + pp * 256 : zero512;
+          nb = 512;
+        }
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+                     "l"(src), "r"(nb), "r"(mfull + 8 * s)
+                     : "memory");
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && nsteps > 0) {
+      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+      bool first = true;
+      for (int k = 0; k < nsteps; ++k) {
+        const int s = k % kStages;
+        if (!mbar_wait(mfull + 8 * s, (uint32_t)((k / kStages) & 1))) {
+          s_abort = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        const uint32_t a0 = (uint32_t)__cvta_generic_to_shared(stA + (size_t)s * NP * kTileElems);
+        const uint32_t b0 = (uint32_t)__cvta_generic_to_shared(stB + (size_t)s * NP * kTileElems);
+#pragma unroll
+        for (int sum = NP - 1; sum >= 0; --sum)
+#pragma unroll
+          for (int ia = 0; ia <= sum; ++ia) {
+            const uint64_t ad = sdesc(a0 + ia * kTileElems * 2);
+            const uint64_t bd = sdesc(b0 + (sum - ia) * kTileElems * 2);
+            const uint32_t acc = first ? 0u : 1u;
+            asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(taddr),
+                         "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+            first = false;
+          }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mempty + 8 * s)
+                     : "memory");
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(maccf)
+                   : "memory");
+    }
+  } else {
+    // epilogue: split the accumulator into bf16 pieces and store the Y rows
+    const int q = warp & 3;
+    const int r = row0 + q * 32 + lane;
+    const bool rv = r < rows;
+    const int al = rv ? r / nX : 0, x = rv ? r - al * nX : 0;
+    bool have = nsteps > 0;
+    if (have) {
+      if (!mbar_wait(maccf, 0u)) {
+        s_abort = 1;
+        have = false;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    }
+#pragma unroll
+    for (int c0 = 0; c0 < 128; c0 += 32) {
+      uint32_t v[32];
+      if (have) {
+        tmem_ld32(taddr + ((uint32_t)(q * 32) << 16) + c0, v);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] = 0u;
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int i = (c0 >> 4) + h;
+        if (!rv || ykey[i] < 0) continue;
+        const int nZ = P.n_ao[P.species[zat[i]]];
+        uint16_t* Yo = X.Ysp + P.y_off[ykey[i]];
+        const long long plane = (long long)mX * nZ * 16;
+#pragma unroll
+        for (int zz = 0; zz < 16; ++zz) {
+          if (zz >= nZ) break;
+          uint16_t pc[NP];
+          split_f<NP>(__uint_as_float(v[h * 16 + zz]), pc);
+          const long long o = ((long long)al * nZ + zz) * 16;
+#pragma unroll
+          for (int pp = 0; pp < NP; ++pp) Yo[pp * plane + o + x] = pc[pp];
+          if (x == nX - 1)
+            for (int xp = nX; xp < 16; ++xp)
+#pragma unroll
+              for (int pp = 0; pp < NP; ++pp) Yo[pp * plane + o + xp] = 0;
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(128));
+  if (tid == 0) {
+    if (s_abort) atomicExch(err, 1);
+    if (mc == 0) {
+      unsigned long long fl = 0ull;
+      for (int t = 0; t < nq; ++t)
+        for (int i = 0; i < 8; ++i)
+          if (m_d[t * 8 + i] >= 0) fl += 2ull * rows * P.n_ao[P.species[zat[i]]] * P.n_ao[P.species[P.c_j[q0 + t]]];
+      if (fl) atomicAdd(&P.acc[ACC_FY], (double)fl);
+    }
+  }
+}
+
+// Groups of up to 8 consecutive needed keys of one home atom (the needed keys
+// of atom X sit at positions [y_idx[y_ptr[X]], y_idx[y_ptr[X+1]]) of the list).
+__global__ void k_ygroups(DevPlan P, const long long* y_idx, const long long* y_total, int* gcnt, const long long* goff,
+                          int* gX, int* gS, int* gN, int phase) {
+  for (int Xa = blockIdx.x * blockDim.x + threadIdx.x; Xa < P.N; Xa += gridDim.x * blockDim.x) {
+    const long long first = P.y_ptr[Xa] < P.nY ? y_idx[P.y_ptr[Xa]] : *y_total;
+    const long long last = Xa + 1 < P.N && P.y_ptr[Xa + 1] < P.nY ? y_idx[P.y_ptr[Xa + 1]] : *y_total;
+    const int n = (int)(last - first);
+    if (phase == 0) {
+      gcnt[Xa] = (n + 7) / 8;
+    } else {
+      const long long o = goff[Xa];
+      for (int g = 0; g * 8 < n; ++g) {
+        gX[o + g] = Xa;
+        gS[o + g] = (int)(first + 8 * g);
+        gN[o + g] = min(8, n - 8 * g);
+      }
+    }
+  }
+}
+
+size_t ybuild_umma_smem(int np) {
+  return (size_t)2 * umma::kStages * np * umma::kTileElems * sizeof(uint16_t) + (size_t)kMaxCPerAtom * 8 * sizeof(int);
+}
+
 size_t q2_umma_smem(int np) {
   return (size_t)2 * umma::kStages * np * umma::kTileElems * sizeof(uint16_t) + (size_t)umma::kMetaPairs * 8 * sizeof(int);
 }
@@ -1197,15 +1308,23 @@ cudaError_t launch_vpieces(const DevPlan& P, const MixPlan& X, int np, const int
   return cudaGetLastError();
 }
 
-cudaError_t launch_ybuild_mma(const DevPlan& P, const MixPlan& X, int np, const int* list, int n, int wide,
-                              cudaStream_t s) {
-  if (n == 0) return cudaSuccess;
+cudaError_t launch_ygroups(const DevPlan& P, const long long* y_idx, const long long* y_total, int* gcnt,
+                           const long long* goff, int* gX, int* gS, int* gN, int phase, cudaStream_t s) {
   ++g_mix_launches;
-  const int g = grid_for(n, 152 * 32);
-  if (np == 2 && !wide) k_ybuild_mma<2, 2><<<g, kWarps * 32, 0, s>>>(P, X, list, n);
-  else if (np == 2) k_ybuild_mma<2, 4><<<g, kWarps * 32, 0, s>>>(P, X, list, n);
-  else if (!wide) k_ybuild_mma<3, 2><<<g, kWarps * 32, 0, s>>>(P, X, list, n);
-  else k_ybuild_mma<3, 4><<<g, kWarps * 32, 0, s>>>(P, X, list, n);
+  k_ygroups<<<(P.N + 255) / 256, 256, 0, s>>>(P, y_idx, y_total, gcnt, goff, gX, gS, gN, phase);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ybuild_mma(const DevPlan& P, const MixPlan& X, int np, const int* ylist, const int* gX,
+                              const int* gS, const int* gN, int ngroups, int MC, const uint16_t* zero512, int* err,
+                              cudaStream_t s) {
+  if (ngroups == 0) return cudaSuccess;
+  ++g_mix_launches;
+  const long long grid = (long long)ngroups * MC;
+  if (np == 2)
+    k_ybuild_umma<2><<<(unsigned)grid, 192, ybuild_umma_smem(2), s>>>(P, X, ylist, gX, gS, gN, MC, zero512, err);
+  else
+    k_ybuild_umma<3><<<(unsigned)grid, 192, ybuild_umma_smem(3), s>>>(P, X, ylist, gX, gS, gN, MC, zero512, err);
   return cudaGetLastError();
 }
 
@@ -1228,6 +1347,9 @@ size_t term2_mma_smem(int np, int MAmax, int KZmax) {
 
 cudaError_t set_mixed_smem_limits(int np, size_t t1, size_t t2) {
   cudaError_t e;
+  e = cudaFuncSetAttribute(np == 2 ? (const void*)k_ybuild_umma<2> : (const void*)k_ybuild_umma<3>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ybuild_umma_smem(np));
+  if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(np == 2 ? (const void*)k_q2_umma<2> : (const void*)k_q2_umma<3>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)q2_umma_smem(np));
   if (e != cudaSuccess) return e;
