@@ -19,7 +19,7 @@
 #include <unordered_map>
 #include <vector>
 
-#include "../../include/hfx.h"
+#include "hfx.h"
 #include "hfx_internal.h"
 
 using hfx::DevPlan;
