@@ -9,6 +9,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <functional>
 #include <limits>
@@ -193,6 +194,18 @@ struct hfx_plan {
   uint16_t* zero512 = nullptr;   // 512 zero bf16 (absent D blocks in tensor-core tiles)
   int maxV = 0;                  // most V-pair candidates of one home atom
   size_t smem_m1 = 0, smem_m2 = 0;
+  // tcgen05 first product (n_abf <= 64, n_ao <= 16): operand stores and shape
+  bool t1u = false;
+  int t1u_KP = 0, t1u_NS = 0, t1u_seg = 32;
+  size_t smem_t1u = 0;
+  uint16_t* Cu = nullptr;
+  long long Cucap = 0;
+  uint16_t* Vu = nullptr;
+  long long Vucap = 0;
+  float* Yf = nullptr;
+  long long Yfcap = 0;
+  float* Df = nullptr;
+  int* d_work = nullptr;       // item counter of the tcgen05 first-product kernel
 
   bool timing = false;
   bool noalloc_call = false;   // set only inside hfx_energy_force_stress_noalloc
@@ -761,9 +774,32 @@ void setup_shapes(hfx_plan* P) {
     // the second product's GEMM holds two column tiles per F (n_ao <= 16)
     const int MT = P->MAmax / 16, wpm = MT > 0 ? 16 / MT : 0;
     const int qtiles = wpm > 0 ? ((maxKAF + 7) / 8 + wpm - 1) / wpm : 1 << 20;
-    if (P->smem_m1 > limit || P->smem_m2 > limit || qtiles > 16 || maxAO > 16)
+    // First product: the tcgen05 kernel where the shapes allow it (HFX_T1_KERNEL=mma
+    // selects the warp-level MMA kernel instead), else the warp-level one.
+    const char* t1k = std::getenv("HFX_T1_KERNEL");
+    const bool want_umma = !(t1k && std::string(t1k) == "mma");
+    P->t1u = false;
+    if (want_umma && maxABF <= 64 && maxAO <= 16) {
+      P->t1u_KP = 16 * maxAO;
+      const size_t base = hfx::t1u_smem(P->np, P->t1u_KP, 0);
+      const long long ns = base < limit ? (long long)((limit - base) / 4096) : 0;
+      P->t1u_NS = (int)std::min<long long>(ns, hfx::t1u_max_slots());
+      if (P->t1u_NS >= 2) {
+        P->t1u = true;
+        P->smem_t1u = hfx::t1u_smem(P->np, P->t1u_KP, P->t1u_NS);
+        const char* sg = std::getenv("HFX_T1_SEG");
+        P->t1u_seg = sg ? std::max(1, std::atoi(sg)) : 32;
+        ck(hfx::t1u_set_smem(P->np, P->smem_t1u), "smem attributes");
+      }
+    }
+    if (!P->t1u) {
+      if (t1k && std::string(t1k) == "umma")
+        fail(HFX_ERR_UNSUPPORTED, "HFX_T1_KERNEL=umma: shapes outside the tcgen05 first-product kernel");
+      if (P->smem_m1 > limit || qtiles > 16) fail(HFX_ERR_UNSUPPORTED, "block shapes too large for the split-precision kernels");
+    }
+    if (P->smem_m2 > limit || maxAO > 16)
       fail(HFX_ERR_UNSUPPORTED, "block shapes too large for the split-precision kernels");
-    ck(hfx::set_mixed_smem_limits(P->np, P->smem_m1, P->smem_m2), "smem attributes");
+    ck(hfx::set_mixed_smem_limits(P->np, P->t1u ? 0 : P->smem_m1, P->smem_m2), "smem attributes");
   }
 }
 
@@ -782,6 +818,13 @@ void split_density(hfx_plan* P) {
   DevPlan D = make_devplan(P, P->lat_ref.data());
   hfx::MixPlan X{P->Dsp, P->dsp_off, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   ck(hfx::launch_dsplit(D, X, P->np, P->stream), "dsplit");
+  if (P->t1u) {
+    P->d_work = P->mem.alloc<int>(1);
+    P->Df = P->mem.alloc<float>((size_t)P->n_d * 256);
+    hfx::T1UPlan U{};
+    U.Df = P->Df;
+    ck(hfx::launch_t1u_stores(D, U, P->np, nullptr, 0, nullptr, 0, true, P->stream), "D FP32 store");
+  }
   ck(cudaStreamSynchronize(P->stream), "dsplit");
 }
 
@@ -835,7 +878,7 @@ struct Timer {
 void evaluate(hfx_plan* P, const double* L, hfx_stats* st) {
   cudaStream_t s = P->stream;
   DevPlan D = make_devplan(P, L);
-  const long long launches0 = hfx::launch_count() + hfx::mixed_launch_count();
+  const long long launches0 = hfx::launch_count() + hfx::mixed_launch_count() + hfx::t1u_launch_count();
   hfx::MixPlan X{P->Dsp, P->dsp_off, P->Ysp, P->Cm, P->cm_off, P->Vm, P->vm_off, P->Zst, P->qcnt, P->qoff, P->blist};
   const bool reuse = P->opt.freeze_lists && P->frozen_ready;
   Timer tm(P->timing, s);
@@ -910,12 +953,34 @@ void evaluate(hfx_plan* P, const double* L, hfx_stats* st) {
       P->zero512 = P->mem.alloc<uint16_t>(512);
       ck(cudaMemsetAsync(P->zero512, 0, 512 * sizeof(uint16_t), s), "memset");
     }
+    hfx::T1UPlan U{};
+    if (P->t1u) {
+      U.KP = P->t1u_KP;
+      U.NS = P->t1u_NS;
+      U.seg = P->t1u_seg;
+      U.cu_blk = (long long)P->np * 64 * U.KP + 2LL * 4 * 64 * U.KP;
+      U.vu_blk = (long long)P->np * 4096 + 2LL * 3 * 4096;
+      ensure_buf(P, P->Cu, P->Cucap, std::max(1LL, P->tot[7]) * U.cu_blk);
+      ensure_buf(P, P->Vu, P->Vucap, std::max(1LL, P->tot[4]) * U.vu_blk);
+      ensure_buf(P, P->Yf, P->Yfcap, std::max(1LL, P->tot[0] / P->np));
+      U.Cu = P->Cu;
+      U.Vu = P->Vu;
+      U.Yf = P->Yf;
+      U.Df = P->Df;
+      U.t1_idx = P->t1_idx;
+      X.Yf = P->Yf;
+      ck(hfx::launch_t1u_stores(D, U, P->np, P->t1q_list, (int)P->tot[7], P->t1_list, (int)P->tot[4], false, s),
+         "term-1 operand stores");
+    }
     ck(hfx::launch_ybuild_mma(D, X, P->np, P->y_list, P->gX, P->gS, P->gN, (int)P->tot[9], P->MC, P->zero512, P->d_err, s),
        "ybuild");
     tm.mark();  // 3
-    ck(hfx::launch_term1_mma(D, X, P->np, P->t1q_list, (int)P->tot[7], P->MAmax, P->MBmax, P->KSmax, P->YRmax,
-                             P->smem_m1, s),
-       "term1");
+    if (P->t1u)
+      ck(hfx::launch_t1_umma(D, X, U, P->np, P->t1q_list, (int)P->tot[7], P->smem_t1u, P->d_work, P->d_err, s), "term1");
+    else
+      ck(hfx::launch_term1_mma(D, X, P->np, P->t1q_list, (int)P->tot[7], P->MAmax, P->MBmax, P->KSmax, P->YRmax,
+                               P->smem_m1, s),
+         "term1");
     tm.mark();  // 4
     if (P->tot[5] * P->zblk > P->Zcap) {
       ensure_buf(P, P->Zst, P->Zcap, P->tot[5] * P->zblk);
@@ -968,7 +1033,7 @@ void evaluate(hfx_plan* P, const double* L, hfx_stats* st) {
     S.ms_reduce = tm.ms(5, 6);
     S.ms_total = tm.ms(0, 6);
     S.device_bytes = P->mem.bytes;
-    S.kernel_launches = hfx::launch_count() + hfx::mixed_launch_count() - launches0;
+    S.kernel_launches = hfx::launch_count() + hfx::mixed_launch_count() + hfx::t1u_launch_count() - launches0;
     *st = S;
   }
 }

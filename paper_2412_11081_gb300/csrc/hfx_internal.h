@@ -105,6 +105,21 @@ struct MixPlan {
   int* qcnt;                   // [nC] kept B per (A,F)
   long long* qoff;             // [nC] offsets into blist
   int* blist;                  // V pairs (A,B) per (A,F), in V-pair order
+  float* Yf = nullptr;         // Y^{XZ} in FP32 as [z][alpha][16], offsets y_off / np (tcgen05 term 1 only)
+};
+
+// Operand stores of the tcgen05 first-product kernel (hfx_t1umma.cu).
+struct T1UPlan {
+  uint16_t* Cu;                // per item (A,F): np bf16 pieces of C as [alpha 64][(f,a) KP], then C, grad C FP32 [4][64][KP]
+  long long cu_blk;            // uint16 units per item
+  uint16_t* Vu;                // per term-1 V pair: np pieces of V [alpha 64][beta 64], then grad V FP32 [3][64][64]
+  long long vu_blk;            // uint16 units per V pair
+  const long long* t1_idx;     // V pair -> its position in the term-1 V list
+  float* Yf;                   // see MixPlan::Yf
+  float* Df;                   // D blocks in FP32, [16][16] each
+  int KP;                      // columns (f,a) = 16 f + a: 16 * max n_ao
+  int NS;                      // Y ring slots
+  int seg;                     // B per FP32 run of the Q accumulator
 };
 
 enum AccSlot { ACC_E = 0, ACC_W = 1, ACC_FY = 10, ACC_F1 = 11, ACC_F2 = 12, ACC_N = 16 };
@@ -149,6 +164,16 @@ cudaError_t launch_term2_mma(const DevPlan& P, const MixPlan& X, int np, const i
                              int n, int MAmax, int KZmax, long long zblk, int zrows, int FC, int MC, int nseg,
                              const uint16_t* zero512, size_t smem, int* err, cudaStream_t s);
 int q2_umma_segments(int max_pairs_per_atom);
+
+// tcgen05 first exchange product (hfx_t1umma.cu): shapes n_abf <= 64, n_ao <= 16.
+long long t1u_launch_count();
+size_t t1u_smem(int np, int KP, int NS);
+int t1u_max_slots();
+cudaError_t t1u_set_smem(int np, size_t smem);
+cudaError_t launch_t1u_stores(const DevPlan& P, const T1UPlan& U, int np, const int* qlist, int nq, const int* vlist,
+                              int nv, bool dstore, cudaStream_t s);
+cudaError_t launch_t1_umma(const DevPlan& P, const MixPlan& X, const T1UPlan& U, int np, const int* qlist, int n,
+                           size_t smem, int* work, int* err, cudaStream_t s);
 
 // Exclusive scan helpers.  `mode` selects what is summed per element i:
 //   0: flag[i] != 0 (int32 flags)

@@ -28,19 +28,18 @@
 
 #include <cstdint>
 
-#include "hfx_internal.h"
+#include "hfx_device.cuh"
 
 namespace hfx {
 namespace {
 
+using namespace dev;
+
 constexpr int kWarps1 = 16;     // warps per CTA of the term-1 kernel
 constexpr int kWarps = 8;       // warps per CTA of the other mixed kernels
 constexpr int kQT = 16;         // Q accumulator tiles per warp (term 1)
-constexpr int kYT = 4;          // m-tiles per warp per pass (Y build)
 constexpr int kFlush = 8;       // B per FP32 run of the Q accumulators
 long long g_mix_launches = 0;
-
-__device__ __forceinline__ int rup16(int x) { return (x + 15) & ~15; }
 
 // Element offset of (row r, column c < 16) inside a tile stored in the
 // K-major core-matrix order of the tensor cores: 8-row x 8-column core
@@ -48,18 +47,6 @@ __device__ __forceinline__ int rup16(int x) { return (x + 15) & ~15; }
 // 8-row groups 128 elements apart.  D piece blocks (16 x 16) and the Z store
 // (128-row tiles) use it, so a tile is copied to shared memory as one block.
 __device__ __forceinline__ int tix(int r, int c) { return ((r >> 3) << 7) + ((c >> 3) << 6) + ((r & 7) << 3) + (c & 7); }
-
-__device__ __forceinline__ double warp_sum_d(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-__device__ __forceinline__ float warp_sum_f(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
 
 // Block sum of NV doubles (all threads get the sums).  red: >= 32*NV doubles.
 template <int NV>
@@ -79,17 +66,6 @@ __device__ void block_sum_n(double (&v)[NV], double* red) {
     v[i] = t;
   }
   __syncthreads();
-}
-
-template <int NP>
-__device__ __forceinline__ void split_f(float x, uint16_t (&p)[NP]) {
-  float r = x;
-#pragma unroll
-  for (int i = 0; i < NP; ++i) {
-    const __nv_bfloat16 h = __float2bfloat16_rn(r);
-    p[i] = __bfloat16_as_ushort(h);
-    r -= __bfloat162float(h);
-  }
 }
 
 __device__ __forceinline__ uint32_t pack2(uint16_t lo, uint16_t hi) { return (uint32_t)lo | ((uint32_t)hi << 16); }
@@ -155,20 +131,6 @@ __device__ __forceinline__ void ldm_x2(uint32_t (&r)[2], const void* p) {
 __device__ __forceinline__ void ldm_x2_trans(uint32_t (&r)[2], const void* p) {
   const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
   asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];\n" : "=r"(r[0]), "=r"(r[1]) : "r"(a));
-}
-
-__device__ __forceinline__ int ylut_get(const DevPlan& P, int i, int j, int r0, int r1, int r2) {
-  if (r0 < -P.HY0 || r0 > P.HY0 || r1 < -P.HY1 || r1 > P.HY1 || r2 < -P.HY2 || r2 > P.HY2) return -1;
-  const long long n0 = 2 * P.HY0 + 1, n1 = 2 * P.HY1 + 1, n2 = 2 * P.HY2 + 1;
-  const long long idx = (((((long long)i * P.N + j) * n0 + (r0 + P.HY0)) * n1 + (r1 + P.HY1)) * n2) + (r2 + P.HY2);
-  return P.ylut[idx];
-}
-
-__device__ __forceinline__ int dlut_get(const DevPlan& P, int i, int j, int r0, int r1, int r2) {
-  if (r0 < -P.HD0 || r0 > P.HD0 || r1 < -P.HD1 || r1 > P.HD1 || r2 < -P.HD2 || r2 > P.HD2) return -1;
-  const long long n0 = 2 * P.HD0 + 1, n1 = 2 * P.HD1 + 1, n2 = 2 * P.HD2 + 1;
-  const long long idx = (((((long long)i * P.N + j) * n0 + (r0 + P.HD0)) * n1 + (r1 + P.HD1)) * n2) + (r2 + P.HD2);
-  return P.dlut[idx];
 }
 
 // ------------------------------------------------------------------ D split
@@ -711,8 +673,8 @@ __global__ void __launch_bounds__(kWarps * 32) k_term2_pairs(DevPlan P, MixPlan 
             uint16_t p0[NP], p1[NP];
             split_f<NP>(acc[2 * h], p0);
             split_f<NP>(acc[2 * h + 1], p1);
-#pragma unroll
             const int r = al * nA + a;
+#pragma unroll
             for (int pp = 0; pp < NP; ++pp)
               *reinterpret_cast<uint32_t*>(Zo + ((long long)(r >> 7) * NP + pp) * 2048 + tix(r & 127, bb)) =
                   pack2(p0[pp], p1[pp]);
@@ -755,43 +717,9 @@ constexpr int kStages = 4;
 constexpr int kTileElems = 128 * 16;     // bf16 elements of one 128 x 16 operand tile (one piece)
 constexpr int kMetaPairs = 1024;         // pairs per CTA segment (metadata in shared memory)
 constexpr int kFlushPairs = 32;
-constexpr long long kSpin = 1ll << 26;   // bounded mbarrier wait
 
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
-  d |= (uint64_t)(128 >> 4) << 16;       // LBO: K-adjacent core matrices
-  d |= (uint64_t)(256 >> 4) << 32;       // SBO: 8-row groups
-  d |= (uint64_t)1 << 46;                // descriptor version of the sm_100 family
-  return d;
-}
-
-// element offset (uint16 units) of (row r, k) inside one 128 x 16 tile
-__device__ __forceinline__ int toff(int r, int kh) { return (r >> 3) * 128 + kh * 64 + (r & 7) * 8; }
-
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-  for (long long it = 0; it < kSpin; ++it) {
-    uint32_t done;
-    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-                 : "=r"(done)
-                 : "r"(mbar), "r"(parity)
-                 : "memory");
-    if (done) return true;
-  }
-  return false;
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-}
+// K-major operand tiles: K-adjacent core matrices 128 bytes apart, 8-row groups 256 bytes apart
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) { return sdesc2(saddr, 128, 256); }
 
 }  // namespace umma
 
@@ -1211,6 +1139,7 @@ __global__ void __launch_bounds__(192) k_ybuild_umma(DevPlan P, MixPlan X, const
         if (!rv || ykey[i] < 0) continue;
         const int nZ = P.n_ao[P.species[zat[i]]];
         uint16_t* Yo = X.Ysp + P.y_off[ykey[i]];
+        float* Yf = X.Yf ? X.Yf + P.y_off[ykey[i]] / NP : nullptr;
         const long long plane = (long long)mX * nZ * 16;
 #pragma unroll
         for (int zz = 0; zz < 16; ++zz) {
@@ -1224,6 +1153,16 @@ __global__ void __launch_bounds__(192) k_ybuild_umma(DevPlan P, MixPlan X, const
             for (int xp = nX; xp < 16; ++xp)
 #pragma unroll
               for (int pp = 0; pp < NP; ++pp) Yo[pp * plane + o + xp] = 0;
+          if (Yf) {
+            // FP32 copy as [z][alpha][16]; chunk c (16 bytes) of row alpha is
+            // stored at c ^ (2 ((alpha >> 1) & 1)), so that four consecutive rows
+            // reading two adjacent chunks each hit distinct shared-memory banks
+            const int sw = 2 * ((al >> 1) & 1);
+            float* yr = Yf + ((long long)zz * mX + al) * 16;
+            yr[(((x >> 2) ^ sw) << 2) + (x & 3)] = __uint_as_float(v[h * 16 + zz]);
+            if (x == nX - 1)
+              for (int xp = nX; xp < 16; ++xp) yr[(((xp >> 2) ^ sw) << 2) + (xp & 3)] = 0.f;
+          }
         }
       }
     }

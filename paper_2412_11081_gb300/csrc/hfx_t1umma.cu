@@ -1,0 +1,722 @@
+// First exchange product of the HFX force/stress on the 5th-generation tensor
+// cores (tcgen05 MMAs with accumulators in tensor memory), split-bf16 operands.
+//
+// For a kept C pair (A,F) (an "item") and its kept V pairs (A,B), the first
+// product of Eq. exx_expand, factorised through Y^{BF} = sum_W C_BW D_WF:
+//   U_B[beta][(f,a)] = sum_b Y^{BF}[f][beta][b] D_AB[a][b]   (CUDA cores, FP32)
+//   R_B = C_AF . U_B^T        (M = alpha, N = beta, K = (f,a))  -> g^V_AB = -<grad V_AB, R_B>
+//   Q  += V_AB . U_B          (M = alpha, N = (f,a), K = beta)  -> E = -<C_AF, Q>, g^C_AF = -2 <grad C_AF, Q>
+// (E through Q: <V_AB, C U^T> = <C, V_AB U>, so the per-B epilogue carries
+// only the three gradient planes of V.)
+//
+// Column order (f,a) = 16 f + a with a padded to 16: a U row of one f is two
+// whole core matrices, so the CUDA cores write U with 8-byte stores and no
+// bank conflicts.  All matrices sit in shared memory in the no-swizzle
+// core-matrix order (8 rows x 16 bytes); U serves R as a K-major B operand
+// and Q as an MN-major B operand without a second copy.
+//
+// Warp roles (16 warps, one CTA per SM, persistent over items):
+//   warp 0      Y producer: bulk copies of Y^{BF}[f] rows (FP32) into a ring
+//   warp 1      C (per item), D_AB (FP32) and V_AB pieces (per B) producer
+//   warp 2      tensor-memory owner; lane 0 issues every MMA
+//   warp 3      scheduler: takes items from a global counter (dynamic load
+//               balance) and hands them to the other roles through a ring
+//   warps 4-7   epilogue: R -> g^V per B; Q -> E, g^C per run of B
+//   warps 8-15  U: one thread per (beta, 4 columns a) of each f
+// All hand-offs are mbarriers (bounded waits; a timeout sets the error flag
+// and every role stops), no block barrier inside the pipeline.
+#include "hfx_device.cuh"
+
+namespace hfx {
+namespace {
+
+using namespace dev;
+
+long long g_t1u_launches = 0;
+
+constexpr int kThreads = 512;
+constexpr int kWarpY = 0, kWarpV = 1, kWarpM = 2, kWarpE = 4, kWarpU = 8;
+constexpr int kWarpS = 3;
+constexpr int kNE = 4, kNU = 8;
+constexpr int kItemRing = 4;
+constexpr int kItemReaders = 3 + kNE + kNU;   // Y, V, MMA, epilogue warps, U warps
+constexpr int kMaxNS = 16;
+constexpr int kRCol = 256;   // tensor-memory column of the first R accumulator (Q sits at column 0)
+
+__device__ __forceinline__ bool aborted(const volatile int* f) { return *f != 0; }
+
+// Every lane waits (bounded); the result is the same on all lanes.
+__device__ __forceinline__ bool wait_all(uint32_t mbar, uint32_t parity) {
+  return __all_sync(0xffffffffu, mbar_wait(mbar, parity)) != 0;
+}
+
+// ------------------------------------------------------------ operand stores
+// Item kk (C pair q = list[kk]): NP bf16 pieces of C_AF as [alpha (64)][(f,a) (KP)]
+// in core-matrix order (8-row groups of KP/8 core matrices), then C and
+// grad C in FP32 as [4][64][KP].  Zero padded.
+template <int NP>
+__global__ void k_t1u_cstore(DevPlan P, T1UPlan U, const int* list, int n) {
+  const int KP = U.KP;
+  for (int kk = blockIdx.x; kk < n; kk += gridDim.x) {
+    const int q = list[kk];
+    const int A = P.c_home[q], F = P.c_j[q];
+    const int sA = P.species[A];
+    const int nA = P.n_ao[sA], mA = P.n_abf[sA], nF = P.n_ao[P.species[F]];
+    const long long ncq = (long long)mA * nA * nF;
+    const double* C = P.Cst + P.c_off[q];
+    const double* dC = P.dCst + 3 * P.c_off[q];
+    uint16_t* out = U.Cu + (long long)kk * U.cu_blk;
+    float* pl = reinterpret_cast<float*>(out + (long long)NP * 64 * KP);
+    for (int e = threadIdx.x; e < 64 * KP; e += blockDim.x) {
+      const int al = e / KP, c = e - al * KP;
+      const int f = c >> 4, a = c & 15;
+      const bool in = al < mA && f < nF && a < nA;
+      const long long o = in ? ((long long)al * nA + a) * nF + f : 0;
+      const double v = in ? C[o] : 0.0;
+      uint16_t pc[NP];
+      split_f<NP>((float)v, pc);
+      const int t = (al >> 3) * KP * 8 + (c >> 3) * 64 + (al & 7) * 8 + (c & 7);
+#pragma unroll
+      for (int pp = 0; pp < NP; ++pp) out[(long long)pp * 64 * KP + t] = pc[pp];
+      pl[e] = (float)v;
+      pl[64 * KP + e] = in ? (float)dC[o] : 0.f;
+      pl[2 * 64 * KP + e] = in ? (float)dC[ncq + o] : 0.f;
+      pl[3 * 64 * KP + e] = in ? (float)dC[2 * ncq + o] : 0.f;
+    }
+  }
+}
+
+// Term-1 V pair k (p = list[k]): NP bf16 pieces of V_AB as [alpha (64)][beta (64)]
+// in core-matrix order, then grad V in FP32 as [3][64][64].  Zero padded.
+template <int NP>
+__global__ void k_t1u_vstore(DevPlan P, T1UPlan U, const int* list, int n) {
+  for (int k = blockIdx.x; k < n; k += gridDim.x) {
+    const int p = list[k];
+    const int mA = P.n_abf[P.species[P.v_home[p]]], mB = P.n_abf[P.species[P.v_j[p]]];
+    const long long nv = (long long)mA * mB;
+    const double* V = P.Vst + P.v_off[p];
+    uint16_t* out = U.Vu + (long long)k * U.vu_blk;
+    float* pl = reinterpret_cast<float*>(out + NP * 4096);
+    for (int e = threadIdx.x; e < 4096; e += blockDim.x) {
+      const int al = e >> 6, be = e & 63;
+      const bool in = al < mA && be < mB;
+      const long long o = in ? (long long)al * mB + be : 0;
+      uint16_t pc[NP];
+      split_f<NP>(in ? (float)V[o] : 0.f, pc);
+      const int t = (al >> 3) * 512 + (be >> 3) * 64 + (al & 7) * 8 + (be & 7);
+#pragma unroll
+      for (int pp = 0; pp < NP; ++pp) out[pp * 4096 + t] = pc[pp];
+      pl[e] = in ? (float)V[nv + o] : 0.f;
+      pl[4096 + e] = in ? (float)V[2 * nv + o] : 0.f;
+      pl[2 * 4096 + e] = in ? (float)V[3 * nv + o] : 0.f;
+    }
+  }
+}
+
+// D block k as FP32 [16][16], zero padded; the four 16-byte chunks of row a
+// are permuted by (a >> 2) & 3, so that rows 4 apart read the same chunk from
+// different banks.
+__global__ void k_t1u_dstore(DevPlan P, float* Df) {
+  for (long long k = blockIdx.x; k < P.n_d; k += gridDim.x) {
+    const int na = P.n_ao[P.species[P.Didx[5 * k]]], nb = P.n_ao[P.species[P.Didx[5 * k + 1]]];
+    const double* src = P.Dval + P.Doff[k];
+    for (int e = threadIdx.x; e < 256; e += blockDim.x) {
+      const int a = e >> 4, b = e & 15;
+      Df[k * 256 + a * 16 + (((b >> 2) ^ ((a >> 2) & 3)) << 2) + (b & 3)] =
+          (a < na && b < nb) ? (float)src[a * nb + b] : 0.f;
+    }
+  }
+}
+
+// ------------------------------------------------------------------- kernel
+template <int NP>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_t1_umma(DevPlan P, MixPlan X, T1UPlan U, const int* qlist, int n_list, int* work, int* err) {
+  const int KP = U.KP, NF = KP >> 4, FH = (NF + 1) >> 1, NS = U.NS, SEG = U.seg;
+  const uint32_t CPB = 64u * KP * 2u;            // bytes of one piece of C or U
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  uint16_t* Cs = reinterpret_cast<uint16_t*>(smem_raw);
+  uint16_t* Us = Cs + (size_t)NP * 64 * KP;
+  uint16_t* Vs = Us + (size_t)NP * 64 * KP;
+  float* Ds = reinterpret_cast<float*>(Vs + NP * 4096);
+  float* Ys = Ds + 2 * 256;
+  __shared__ __align__(8) uint64_t b_yf[kMaxNS], b_ye[kMaxNS], b_cf, b_ce, b_vf, b_ve, b_df[2], b_de[2], b_uf[2],
+      b_ue[2], b_rf[2], b_re[2], b_qf, b_qe, b_if[kItemRing], b_ie[kItemRing];
+  __shared__ int s_item[kItemRing];
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_abort;
+  volatile int* abort_flag = &s_abort;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  auto sa = [](const void* p) { return (uint32_t)__cvta_generic_to_shared(p); };
+  const uint32_t yf = sa(b_yf), ye = sa(b_ye), cf = sa(&b_cf), ce = sa(&b_ce), vf = sa(&b_vf), ve = sa(&b_ve),
+                 df = sa(b_df), de = sa(b_de), uf = sa(b_uf), ue = sa(b_ue), rf = sa(b_rf), re = sa(b_re),
+                 qf = sa(&b_qf), qe = sa(&b_qe), itf = sa(b_if), ite = sa(b_ie);
+  if (tid == 0) {
+    s_abort = 0;
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(yf + 8 * s, 1);
+      mbar_init(ye + 8 * s, kNU);
+    }
+    mbar_init(cf, 1);
+    mbar_init(ce, 1);
+    mbar_init(vf, 1);
+    mbar_init(ve, 1);
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(df + 8 * s, 1);
+      mbar_init(de + 8 * s, kNU);
+      mbar_init(uf + 8 * s, kNU);
+      mbar_init(ue + 8 * s, 1);
+      mbar_init(rf + 8 * s, 1);
+      mbar_init(re + 8 * s, kNE);
+    }
+    mbar_init(qf, 1);
+    mbar_init(qe, kNE);
+    for (int s = 0; s < kItemRing; ++s) {
+      mbar_init(itf + 8 * s, 1);
+      mbar_init(ite + 8 * s, kItemReaders);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
+  }
+  if (warp == kWarpM) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(sa(&tmem_base)), "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t T = tmem_base;
+  // Next item of the ring for a role (one reader per warp; lane 0 releases
+  // the slot).  n_list marks the end.  Every lane of the warp calls it.
+  auto next_item = [&](uint32_t& k) -> int {
+    const int s = k & (kItemRing - 1);
+    int kk = n_list;
+    if (wait_all(itf + 8 * s, (k / kItemRing) & 1)) kk = *reinterpret_cast<volatile int*>(&s_item[s]);
+    else *abort_flag = 1;
+    __syncwarp();
+    if (lane == 0) mbar_arrive(ite + 8 * s);
+    ++k;
+    return kk;
+  };
+
+  if (warp == kWarpY) {
+    // ---------------------------------------------------------- Y producer
+    uint32_t ys = 0, ik = 0;
+    for (int kk = next_item(ik); kk < n_list && !aborted(abort_flag); kk = next_item(ik)) {
+      const int q = qlist[kk];
+      const int F = P.c_j[q];
+      const int nF = P.n_ao[P.species[F]];
+      const int* Rf = P.c_R + 3 * q;
+      const long long b0 = X.qoff[q];
+      const int nbt = X.qcnt[q];
+      for (int i0 = 0; i0 < nbt && !aborted(abort_flag); i0 += 32) {
+        long long yo = 0;
+        int mB = 0;
+        if (i0 + lane < nbt) {
+          const int p = X.blist[b0 + i0 + lane];
+          const int b = P.v_j[p];
+          const int* Rb = P.v_R + 3 * p;
+          const int yc = ylut_get(P, b, F, Rf[0] - Rb[0], Rf[1] - Rb[1], Rf[2] - Rb[2]);
+          yo = yc >= 0 ? P.y_off[yc] / NP : -1;
+          mB = P.n_abf[P.species[b]];
+        }
+        const int nb = min(32, nbt - i0);
+        for (int j = 0; j < nb; ++j) {
+          const long long yoj = __shfl_sync(0xffffffffu, yo, j);
+          const int mBj = __shfl_sync(0xffffffffu, mB, j);
+          if (lane == 0 && !aborted(abort_flag)) {
+            if (yoj < 0) *abort_flag = 1;   // a kept triplet always has its Y block
+            for (int f = 0; f < nF && !aborted(abort_flag); ++f) {
+              const int s = (int)(ys % NS);
+              if (ys >= (uint32_t)NS && !mbar_wait(ye + 8 * s, ((ys / NS) - 1) & 1)) {
+                *abort_flag = 1;
+                break;
+              }
+              mbar_expect_tx(yf + 8 * s, (uint32_t)mBj * 64u);
+              bulk_g2s(sa(Ys + s * 1024), U.Yf + yoj + (long long)f * mBj * 16, (uint32_t)mBj * 64u, yf + 8 * s);
+              ++ys;
+            }
+          }
+          __syncwarp();
+        }
+      }
+    }
+    if (lane == 0)   // copies in flight land before the CTA leaves
+      for (int s = 0; s < NS; ++s) {
+        const uint32_t n = ys / NS + ((uint32_t)s < ys % NS ? 1u : 0u);
+        if (n) mbar_wait(yf + 8 * s, (n - 1) & 1);
+      }
+  } else if (warp == kWarpV) {
+    // ------------------------------------------------- C, D and V producer
+    uint32_t vb = 0, db = 0, it = 0, ca = 0, ik = 0;
+    for (int kk = next_item(ik); kk < n_list && !aborted(abort_flag); kk = next_item(ik), ++it) {
+      const int q = qlist[kk];
+      const long long b0 = X.qoff[q];
+      const int nbt = X.qcnt[q];
+      if (lane == 0) {
+        if (it >= 1 && !mbar_wait(ce, (it - 1) & 1)) *abort_flag = 1;
+        if (!aborted(abort_flag)) {
+          mbar_expect_tx(cf, (uint32_t)NP * CPB);
+          const uint16_t* src = U.Cu + (long long)kk * U.cu_blk;
+#pragma unroll
+          for (int pp = 0; pp < NP; ++pp) bulk_g2s(sa(Cs) + pp * CPB, src + (long long)pp * 64 * KP, CPB, cf);
+          ++ca;
+        }
+      }
+      __syncwarp();
+      for (int i0 = 0; i0 < nbt && !aborted(abort_flag); i0 += 32) {
+        long long vo = 0, dofs = 0;
+        if (i0 + lane < nbt) {
+          const int p = X.blist[b0 + i0 + lane];
+          vo = U.t1_idx[p] * U.vu_blk;
+          const int di = P.v_didx[p];
+          dofs = di >= 0 ? (long long)di * 256 : -1;   // a kept triplet always has its D block
+        }
+        const int nb = min(32, nbt - i0);
+        for (int j = 0; j < nb; ++j) {
+          const long long voj = __shfl_sync(0xffffffffu, vo, j);
+          const long long doj = __shfl_sync(0xffffffffu, dofs, j);
+          if (lane == 0 && doj < 0) *abort_flag = 1;
+          if (lane == 0 && !aborted(abort_flag)) {
+            const int s = db & 1;
+            bool ok = db < 2 || mbar_wait(de + 8 * s, ((db >> 1) - 1) & 1);
+            if (ok) {
+              mbar_expect_tx(df + 8 * s, 1024u);
+              bulk_g2s(sa(Ds + s * 256), U.Df + doj, 1024u, df + 8 * s);
+              ++db;
+            }
+            ok = ok && (vb < 1 || mbar_wait(ve, (vb - 1) & 1));
+            if (ok) {
+              mbar_expect_tx(vf, (uint32_t)NP * 8192u);
+              const uint16_t* src = U.Vu + voj;
+#pragma unroll
+              for (int pp = 0; pp < NP; ++pp) bulk_g2s(sa(Vs) + pp * 8192, src + pp * 4096, 8192u, vf);
+              ++vb;
+            } else {
+              *abort_flag = 1;
+            }
+          }
+          __syncwarp();
+        }
+      }
+    }
+    if (lane == 0) {
+      if (ca) mbar_wait(cf, (ca - 1) & 1);
+      if (vb) mbar_wait(vf, (vb - 1) & 1);
+      for (int s = 0; s < 2; ++s) {
+        const uint32_t n = db / 2 + ((uint32_t)s < db % 2 ? 1u : 0u);
+        if (n) mbar_wait(df + 8 * s, (n - 1) & 1);
+      }
+    }
+  } else if (warp == kWarpM) {
+    // ------------------------------------------------------------- MMA issue
+    const uint32_t idR = idesc_bf16(64, 64, 0);
+    const int N0 = 16 * FH, N1 = 16 * (NF - FH);
+    const uint32_t idQ0 = idesc_bf16(64, N0, 1), idQ1 = N1 > 0 ? idesc_bf16(64, N1, 1) : 0u;
+    const uint32_t rowg = 16u * KP;   // bytes between 8-row groups of C and U
+    // descriptors at the buffer bases; an offset of o bytes adds o >> 4
+    const uint64_t dC = sdesc2(sa(Cs), 128, rowg), dUR = sdesc2(sa(Us), 128, rowg);
+    const uint64_t dV = sdesc2(sa(Vs), 128, 1024), dUQ = sdesc2(sa(Us), rowg, 128);
+    uint32_t rb = 0, seg = 0, it = 0, ik = 0;
+    bool ok = true;
+    for (int kk = next_item(ik); kk < n_list; kk = next_item(ik), ++it) {
+      const int q = qlist[kk];
+      const int nbt = X.qcnt[q];
+      if (lane == 0 && ok) {
+        ok = mbar_wait(cf, it & 1);
+        tc_fence_after();
+        for (int i = 0; i < nbt && ok; ++i) {
+          if (aborted(abort_flag)) {
+            ok = false;
+            break;
+          }
+          const bool first = (i % SEG) == 0, last = (i % SEG) == SEG - 1 || i == nbt - 1;
+          const int rbuf = rb & 1;
+          const uint32_t dR = T + kRCol + 64u * rbuf;
+          if (rb >= 2) ok = ok && mbar_wait(re + 8 * rbuf, ((rb >> 1) - 1) & 1);
+          for (int c = 0; c < 2 && ok; ++c) {
+            ok = mbar_wait(uf + 8 * c, rb & 1);
+            if (!ok) break;
+            tc_fence_after();
+            const int f0 = c ? FH : 0, f1 = c ? NF : FH;
+            // R += C[:, f] . U[:, f]^T over the chunk's k steps (one f each)
+            for (int f = f0; f < f1; ++f) {
+              int k = 0;
+#pragma unroll
+              for (int sum = NP - 1; sum >= 0; --sum)
+#pragma unroll
+                for (int ia = 0; ia <= sum; ++ia, ++k) {
+                  const int ib = sum - ia;
+                  umma_bf16(dR, dC + ((ia * CPB + f * 256) >> 4), dUR + ((ib * CPB + f * 256) >> 4), idR,
+                            (f > 0 || k > 0) ? 1u : 0u);
+                }
+            }
+            if (c == 1) umma_commit(rf + 8 * rbuf);
+            if (c == 0) {
+              ok = mbar_wait(vf, rb & 1) && (!first || seg == 0 || mbar_wait(qe, (seg - 1) & 1));
+              if (!ok) break;
+              tc_fence_after();
+            }
+            // Q[:, chunk] += V . U[:, chunk] (K = beta, four k steps; U read MN-major)
+            const int Nc = c ? N1 : N0;
+            if (Nc > 0) {
+              const uint32_t idQ = c ? idQ1 : idQ0;
+              for (int kb = 0; kb < 4; ++kb) {
+                int k = 0;
+#pragma unroll
+                for (int sum = NP - 1; sum >= 0; --sum)
+#pragma unroll
+                  for (int ia = 0; ia <= sum; ++ia, ++k) {
+                    const int ib = sum - ia;
+                    umma_bf16(T + 16u * f0, dV + ((ia * 8192 + kb * 256) >> 4),
+                              dUQ + ((ib * CPB + kb * 2 * rowg + f0 * 256) >> 4), idQ,
+                              (first && kb == 0 && k == 0) ? 0u : 1u);
+                  }
+              }
+            }
+            umma_commit(ue + 8 * c);
+          }
+          if (!ok) break;
+          umma_commit(ve);
+          if (last) {
+            umma_commit(qf);
+            ++seg;
+          }
+          ++rb;
+        }
+        if (ok) umma_commit(ce);
+        if (!ok) *abort_flag = 1;
+      }
+      __syncwarp();
+    }
+  } else if (warp == kWarpS) {
+    // -------------------------------------------------------------- scheduler
+    if (lane == 0) {
+      for (uint32_t k = 0;; ++k) {
+        const int s = k & (kItemRing - 1);
+        if (k >= kItemRing && !mbar_wait(ite + 8 * s, ((k / kItemRing) - 1) & 1)) {
+          *abort_flag = 1;
+          break;
+        }
+        int kk = aborted(abort_flag) ? n_list : atomicAdd(work, 1);
+        if (kk > n_list) kk = n_list;
+        s_item[s] = kk;
+        mbar_arrive(itf + 8 * s);
+        if (kk >= n_list) break;
+      }
+    }
+    __syncwarp();
+  } else if (warp >= kWarpE && warp < kWarpE + kNE) {
+    // --------------------------------------------------------------- epilogue
+    const int qd = warp & 3;                 // tensor-memory lane quarter
+    const int ew = warp - kWarpE;
+    const int alpha = qd * 16 + (lane & 15); // accumulator row held by this thread
+    const int half = lane >> 4;              // columns [0,16) or [16,32) of a 32-column load
+    const uint32_t tl = T + ((uint32_t)(qd * 32) << 16);
+    uint32_t rb = 0, seg = 0, it = 0, ik = 0;
+    double fl = 0.0;
+    bool ok = true;
+    for (int kk = next_item(ik); kk < n_list && ok; kk = next_item(ik), ++it) {
+      const int q = qlist[kk];
+      const int A = P.c_home[q], F = P.c_j[q];
+      const int sA = P.species[A];
+      const int nA = P.n_ao[sA], mA = P.n_abf[sA], nF = P.n_ao[P.species[F]];
+      const long long b0 = X.qoff[q];
+      const int nbt = X.qcnt[q];
+      const float* Cf = reinterpret_cast<const float*>(U.Cu + (long long)kk * U.cu_blk + (long long)NP * 64 * KP);
+      double e_it = 0.0, g_it[3] = {0.0, 0.0, 0.0};
+      for (int i0 = 0; i0 < nbt && ok; i0 += 32) {
+        int p_l = 0, mB_l = 0, nB_l = 0;
+        long long vo_l = 0;
+        if (i0 + lane < nbt) {
+          p_l = X.blist[b0 + i0 + lane];
+          const int sb = P.species[P.v_j[p_l]];
+          mB_l = P.n_abf[sb];
+          nB_l = P.n_ao[sb];
+          vo_l = U.t1_idx[p_l] * U.vu_blk;
+        }
+        const int nb = min(32, nbt - i0);
+        for (int j = 0; j < nb && ok; ++j) {
+          ok = __all_sync(0xffffffffu, !aborted(abort_flag)) != 0;
+          if (!ok) break;
+          const int i = i0 + j;
+          const int p = __shfl_sync(0xffffffffu, p_l, j);
+          const int mB = __shfl_sync(0xffffffffu, mB_l, j);
+          const int nB = __shfl_sync(0xffffffffu, nB_l, j);
+          const long long vo = __shfl_sync(0xffffffffu, vo_l, j);
+          const float* dV = reinterpret_cast<const float*>(U.Vu + vo + NP * 4096);
+          const bool last = (i % SEG) == SEG - 1 || i == nbt - 1;
+          const int rbuf = rb & 1;
+          // ---- R_B -> g^V_AB (the grad V rows of the first 32 columns are
+          // fetched before the wait; they do not depend on R)
+          float gv[3] = {0.f, 0.f, 0.f};
+          float4 w[3][4];
+          {
+            const int cb = 16 * half;
+            if (alpha < mA && cb < mB)
+#pragma unroll
+              for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int t4 = 0; t4 < 4; ++t4)
+                  w[c][t4] = reinterpret_cast<const float4*>(dV + c * 4096 + alpha * 64 + cb)[t4];
+          }
+          ok = wait_all(rf + 8 * rbuf, (rb >> 1) & 1);
+          tc_fence_after();
+          if (ok) {
+            for (int c0 = 0; c0 < 64; c0 += 32) {
+              if (c0 >= mB) break;
+              const int cb = c0 + 16 * half;
+              const bool act = alpha < mA && cb < mB;
+              if (c0 > 0 && act)
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+#pragma unroll
+                  for (int t4 = 0; t4 < 4; ++t4)
+                    w[c][t4] = reinterpret_cast<const float4*>(dV + c * 4096 + alpha * 64 + cb)[t4];
+              uint32_t v[32];
+              tmem_ld32(tl + kRCol + 64u * rbuf + c0, v);
+              float x[16];
+#pragma unroll
+              for (int t = 0; t < 16; ++t) {
+                const float hi = __shfl_sync(0xffffffffu, __uint_as_float(v[16 + t]), lane & 15);
+                x[t] = half ? hi : __uint_as_float(v[t]);
+              }
+              if (act) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                  float s = 0.f;
+#pragma unroll
+                  for (int t4 = 0; t4 < 4; ++t4) {
+                    s = fmaf(w[c][t4].x, x[4 * t4], s);
+                    s = fmaf(w[c][t4].y, x[4 * t4 + 1], s);
+                    s = fmaf(w[c][t4].z, x[4 * t4 + 2], s);
+                    s = fmaf(w[c][t4].w, x[4 * t4 + 3], s);
+                  }
+                  gv[c] += s;
+                }
+              }
+            }
+          }
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(re + 8 * rbuf);
+#pragma unroll
+          for (int c = 0; c < 3; ++c) gv[c] = warp_sum_f(gv[c]);
+          if (lane == 0 && ok)
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+              if (gv[c] != 0.f) atomicAdd(&P.gV[3 * p + c], -(double)gv[c]);
+          if (ew == 0 && lane == 0) fl += 2.0 * mB * nA * nB * nF + 4.0 * mA * mB * nA * nF;
+          ++rb;
+          // ---- end of a run: Q -> E, g^C
+          if (last && ok) {
+            ok = wait_all(qf, seg & 1);
+            tc_fence_after();
+            if (ok) {
+              for (int c0 = 0; c0 < KP; c0 += 32) {
+                uint32_t v[32];
+                tmem_ld32(tl + c0, v);
+                float x[16];
+#pragma unroll
+                for (int t = 0; t < 16; ++t) {
+                  const float hi = __shfl_sync(0xffffffffu, __uint_as_float(v[16 + t]), lane & 15);
+                  x[t] = half ? hi : __uint_as_float(v[t]);
+                }
+                const int cb = c0 + 16 * half;
+                if (alpha < mA && cb < KP) {
+                  float s4[4];
+#pragma unroll
+                  for (int c = 0; c < 4; ++c) {
+                    const float4* src = reinterpret_cast<const float4*>(Cf + (long long)c * 64 * KP + alpha * KP + cb);
+                    float s = 0.f;
+#pragma unroll
+                    for (int t4 = 0; t4 < 4; ++t4) {
+                      const float4 w = src[t4];
+                      s = fmaf(w.x, x[4 * t4], s);
+                      s = fmaf(w.y, x[4 * t4 + 1], s);
+                      s = fmaf(w.z, x[4 * t4 + 2], s);
+                      s = fmaf(w.w, x[4 * t4 + 3], s);
+                    }
+                    s4[c] = s;
+                  }
+                  e_it += (double)s4[0];
+                  g_it[0] += (double)s4[1];
+                  g_it[1] += (double)s4[2];
+                  g_it[2] += (double)s4[3];
+                }
+              }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(qe);
+            ++seg;
+          }
+        }
+      }
+      // item totals: E and g^C_AF
+      e_it = warp_sum_d(e_it);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) g_it[c] = warp_sum_d(g_it[c]);
+      if (lane == 0 && ok) {
+        if (e_it != 0.0) atomicAdd(&P.acc[ACC_E], -e_it);
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          if (g_it[c] != 0.0) atomicAdd(&P.gC[3 * q + c], -2.0 * g_it[c]);
+      }
+    }
+    if (!ok) *abort_flag = 1;
+    if (ew == 0 && lane == 0 && fl != 0.0) atomicAdd(&P.acc[ACC_F1], fl);
+  } else if (warp >= kWarpU) {
+    // ---------------------------------------------------------------------- U
+    // Lane l of U warp uw: row beta = 8 uw + ((l >> 1) & 7), columns
+    // a = 4 qa .. 4 qa + 3 with qa = 2 (l >> 4) + (l & 1).  A half warp then
+    // stores one contiguous 128-byte run of U, and the four lanes of a row
+    // each read one 16-byte chunk of the Y row (the row is gathered by
+    // shuffles instead of four shared-memory reads per lane).
+    const int uw = warp - kWarpU;
+    const int r8 = (lane >> 1) & 7, qa = 2 * (lane >> 4) + (lane & 1);
+    const int beta = 8 * uw + r8;
+    const int ych = qa ^ (2 * ((beta >> 1) & 1));   // stored position of chunk qa of row beta
+    uint16_t* urow = Us + (beta >> 3) * KP * 8 + (beta & 7) * 8 + (qa & 1) * 4;
+    uint32_t ub = 0, ys = 0, ik = 0;
+    bool ok = true;
+    for (int kk = next_item(ik); kk < n_list && ok; kk = next_item(ik)) {
+      const int q = qlist[kk];
+      const int nF = P.n_ao[P.species[P.c_j[q]]];
+      const long long b0 = X.qoff[q];
+      const int nbt = X.qcnt[q];
+      for (int i0 = 0; i0 < nbt && ok; i0 += 32) {
+        int mB_l = 0;
+        if (i0 + lane < nbt) mB_l = P.n_abf[P.species[P.v_j[X.blist[b0 + i0 + lane]]]];
+        const int nb = min(32, nbt - i0);
+        for (int j = 0; j < nb && ok; ++j) {
+          ok = __all_sync(0xffffffffu, !aborted(abort_flag)) != 0;
+          if (!ok) break;
+          const int mB = __shfl_sync(0xffffffffu, mB_l, j);
+          const int s = ub & 1;
+          ok = wait_all(df + 8 * s, (ub >> 1) & 1);
+          if (!ok) break;
+          float d[4][16];   // D_AB[4 qa + i][b]
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int c4 = 0; c4 < 4; ++c4) {
+              const float4 w = *reinterpret_cast<const float4*>(Ds + s * 256 + (4 * qa + i) * 16 + 4 * (c4 ^ qa));
+              d[i][4 * c4] = w.x;
+              d[i][4 * c4 + 1] = w.y;
+              d[i][4 * c4 + 2] = w.z;
+              d[i][4 * c4 + 3] = w.w;
+            }
+          __syncwarp();
+          if (lane == 0) mbar_arrive(de + 8 * s);
+          for (int c = 0; c < 2 && ok; ++c) {
+            if (ub >= 1) ok = wait_all(ue + 8 * c, (ub - 1) & 1);
+            if (!ok) break;
+            const int f0 = c ? FH : 0, f1 = c ? NF : FH;
+            for (int f = f0; f < f1; ++f) {
+              float u[4] = {0.f, 0.f, 0.f, 0.f};
+              if (f < nF) {
+                const int sl = (int)(ys % NS);
+                ok = wait_all(yf + 8 * sl, (ys / NS) & 1);
+                if (!ok) break;
+                float4 mine = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (beta < mB) mine = *reinterpret_cast<const float4*>(Ys + sl * 1024 + beta * 16 + 4 * ych);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(ye + 8 * sl);
+                ++ys;
+                float y[16];
+#pragma unroll
+                for (int c4 = 0; c4 < 4; ++c4) {
+                  const int src = 16 * (c4 >> 1) + 2 * r8 + (c4 & 1);   // lane holding chunk c4 of this row
+                  y[4 * c4] = __shfl_sync(0xffffffffu, mine.x, src);
+                  y[4 * c4 + 1] = __shfl_sync(0xffffffffu, mine.y, src);
+                  y[4 * c4 + 2] = __shfl_sync(0xffffffffu, mine.z, src);
+                  y[4 * c4 + 3] = __shfl_sync(0xffffffffu, mine.w, src);
+                }
+                if (beta < mB)
+#pragma unroll
+                  for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int b = 0; b < 16; ++b) u[i] = fmaf(y[b], d[i][b], u[i]);
+              }
+              uint2 pk[NP];
+              split4<NP>(u, pk);
+#pragma unroll
+              for (int pp = 0; pp < NP; ++pp)
+                *reinterpret_cast<uint2*>(urow + (size_t)pp * 64 * KP + (2 * f + (qa >> 1)) * 64) = pk[pp];
+            }
+            fence_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(uf + 8 * c);
+          }
+          ++ub;
+        }
+      }
+    }
+    if (!ok) *abort_flag = 1;
+  }
+  // ------------------------------------------------------------------ teardown
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == kWarpM) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(T), "r"(512));
+  if (tid == 0 && s_abort) atomicExch(err, 1);
+}
+
+int g_num_sms = 0;
+
+}  // namespace
+
+long long t1u_launch_count() { return g_t1u_launches; }
+
+size_t t1u_smem(int np, int KP, int NS) {
+  return (size_t)np * 64 * KP * 2 * 2 + (size_t)np * 8192 + 2 * 256 * 4 + (size_t)NS * 1024 * 4;
+}
+
+int t1u_max_slots() { return kMaxNS; }
+
+cudaError_t t1u_set_smem(int np, size_t smem) {
+  return cudaFuncSetAttribute(np == 2 ? (const void*)k_t1_umma<2> : (const void*)k_t1_umma<3>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t launch_t1u_stores(const DevPlan& P, const T1UPlan& U, int np, const int* qlist, int nq, const int* vlist,
+                              int nv, bool dstore, cudaStream_t s) {
+  if (nq > 0) {
+    ++g_t1u_launches;
+    const int g = nq < 152 * 8 ? nq : 152 * 8;
+    if (np == 2) k_t1u_cstore<2><<<g, 256, 0, s>>>(P, U, qlist, nq);
+    else k_t1u_cstore<3><<<g, 256, 0, s>>>(P, U, qlist, nq);
+  }
+  if (nv > 0) {
+    ++g_t1u_launches;
+    const int g = nv < 152 * 16 ? nv : 152 * 16;
+    if (np == 2) k_t1u_vstore<2><<<g, 256, 0, s>>>(P, U, vlist, nv);
+    else k_t1u_vstore<3><<<g, 256, 0, s>>>(P, U, vlist, nv);
+  }
+  if (dstore && P.n_d > 0) {
+    ++g_t1u_launches;
+    const long long g = P.n_d < 152 * 16 ? P.n_d : 152 * 16;
+    k_t1u_dstore<<<(unsigned)g, 256, 0, s>>>(P, U.Df);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_t1_umma(const DevPlan& P, const MixPlan& X, const T1UPlan& U, int np, const int* qlist, int n,
+                           size_t smem, int* work, int* err, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  if (g_num_sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_num_sms <= 0) g_num_sms = 152;
+  }
+  ++g_t1u_launches;
+  const int grid = n < g_num_sms ? n : g_num_sms;
+  cudaError_t e = cudaMemsetAsync(work, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  if (np == 2) k_t1_umma<2><<<grid, kThreads, smem, s>>>(P, X, U, qlist, n, work, err);
+  else k_t1_umma<3><<<grid, kThreads, smem, s>>>(P, X, U, qlist, n, work, err);
+  return cudaGetLastError();
+}
+
+}  // namespace hfx
