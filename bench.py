@@ -5,10 +5,10 @@ One step = one full evaluation of the hot path (block generation, two-step
 screening, Y build, both exchange products, force/stress/energy reduction)
 on a warm plan, at a new geometry (small seeded jitter within the pair-list
 skin, so every block, norm and screening decision is recomputed).  The
-headline precision is HFX_BF16X6 (split bf16 on the tensor cores, within
-1e-5 relative force/stress error of FP64); FP64 and BF16X3 are reported
-beside it, with the error of each split measured against the FP64 GPU
-result of the same geometry.
+headline precision (`--precision auto`, the default) is the faster split
+of HFX_BF16X3 / HFX_BF16X6 whose energy, force and stress errors against the
+FP64 GPU result of the same geometry are all within 1e-5 relative; the other
+split and FP64 are reported beside it, each with its measured error.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -206,7 +206,6 @@ def run_ours(args):
     geoms = geometry_sequence(w, args.warmup + args.steps + 8)
     d_pos = [torch.tensor(g, dtype=torch.float64, device=dev) for g in geoms]
     d_out = torch.zeros(1 + 3 * n + 9, dtype=torch.float64, device=dev)
-    head_prec = {"bf16x6": hfx.HFX_BF16X6, "bf16x3": hfx.HFX_BF16X3, "fp64": hfx.HFX_FP64}[args.precision]
 
     def barrier():
         if dist is not None:
@@ -228,6 +227,12 @@ def run_ours(args):
         pl = hfx.Plan(w, precision=prec, stream=stream.cuda_stream, device=local)
         E, F, S = pl.evaluate(w.lattice, geoms[0])
         variants[name] = dict(plan=pl, errE=abs(E - ref[0]) / abs(ref[0]), errF=_rel(F, ref[1]), errS=_rel(S, ref[2]))
+    auto = args.precision == "auto"
+    if auto:
+        # BF16X3 runs half the piece products of BF16X6; it is the headline when
+        # it meets the 1e-5 contract on this geometry
+        x3 = variants["bf16x3"]
+        args.precision = "bf16x3" if max(x3["errE"], x3["errF"], x3["errS"]) <= 1e-5 else "bf16x6"
     plan = variants[args.precision]["plan"] if args.precision != "fp64" else \
         hfx.Plan(w, precision=hfx.HFX_FP64, stream=stream.cuda_stream, device=local)
 
@@ -291,6 +296,8 @@ def run_ours(args):
         dom_ms = stage_ms["ms_" + dom]
         achieved = dom_flops / (dom_ms / 1e3) / 1e12
         kname = {"y": "k_ybuild", "term1": "k_term1", "term2": "k_term2"}[dom]
+        if args.precision != "fp64":
+            kname = {"y": "k_ybuild_umma", "term1": "k_t1_umma", "term2": "k_term2_pairs+k_q2_umma"}[dom]
         if args.precision == "fp64":
             roofline = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
                         "frac": achieved / fp64_peak, "traffic": None,
@@ -298,7 +305,7 @@ def run_ours(args):
         else:
             pk = peaks.get("bf16_tflops_sustained") or 1717.3
             pieces = 6 if args.precision == "bf16x6" else 3
-            roofline = {"kernel": kname + "_mma", "bound": "tensor", "achieved": achieved, "peak": pk,
+            roofline = {"kernel": kname, "bound": "tensor", "achieved": achieved, "peak": pk,
                         "unit": "TFLOP/s", "frac": achieved / pk, "traffic": None,
                         "peak_source": "bf16 dense, sustained, of measured (MEASURED_PEAKS.json)",
                         "note": f"achieved counts algorithmic FLOPs only; the {pieces} bf16 piece products per "
@@ -316,6 +323,8 @@ def run_ours(args):
                 "dtype": "bf16" if args.precision != "fp64" else "f64",
                 "data": "synthetic",
                 "config": {"workload": WORKLOAD, "precision": args.precision,
+                           "headline_rule": "fastest split with max(errE, errF, errS) <= 1e-5 vs FP64 GPU"
+                           if auto else "fixed by --precision",
                            "arithmetic": "bf16 pieces on tensor cores, fp32 accumulate, fp64 screening/reduction"
                            if args.precision != "fp64" else "fp64",
                            "parallelism": f"replicas{world}" if world > 1 else "single",
@@ -354,7 +363,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--precision", default="bf16x6", choices=["bf16x6", "bf16x3", "fp64"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "bf16x6", "bf16x3", "fp64"])
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
