@@ -1,0 +1,46 @@
+"""Run one synthetic workload through the C ABI and print per-stage times.
+
+  python -m paper_2412_11081_gb300.run_case [--cell si8|si64|diamond8|perovskite]
+        [--precision fp64|bf16x3|bf16x6] [--evals N]
+
+Meant for profiling a single plan (e.g. under ncu with -k on one kernel):
+the plan is created once and evaluated N times at the same geometry; the
+last evaluation's stage times (CUDA events on the plan's stream) and counts
+are printed as one line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+from . import hfx, inputs
+
+CELLS = {
+    "diamond8": lambda: inputs.diamond8(),
+    "si8": lambda: inputs.si_supercell(1),
+    "si64": lambda: inputs.si_supercell(2),
+    "perovskite": lambda: inputs.perovskite_supercell(1),
+}
+PRECISIONS = {"fp64": hfx.HFX_FP64, "bf16x3": hfx.HFX_BF16X3, "bf16x6": hfx.HFX_BF16X6}
+
+
+def main(argv=None) -> int:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--cell", default="si8", choices=sorted(CELLS))
+    ap.add_argument("--precision", default="bf16x3", choices=sorted(PRECISIONS))
+    ap.add_argument("--evals", type=int, default=2)
+    args = ap.parse_args(argv)
+    w = CELLS[args.cell]()
+    with hfx.Plan(w, precision=PRECISIONS[args.precision]) as p:
+        p.set_timing(True)
+        for _ in range(max(1, args.evals)):
+            E, F, S = p.evaluate(w.lattice, w.positions, stats=True)
+        st = p.stats.as_dict()
+    keep = ("ms_blocks", "ms_screen", "ms_y", "ms_term1", "ms_term2", "ms_reduce", "ms_total", "triplets",
+            "term1_pairs", "term2_pairs", "y_blocks", "flops_total", "kernel_launches", "device_bytes")
+    print(json.dumps({"cell": args.cell, "precision": args.precision, "E": E, **{k: st[k] for k in keep}}))
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())
