@@ -196,7 +196,7 @@ struct hfx_plan {
   size_t smem_m1 = 0, smem_m2 = 0;
   // tcgen05 first product (n_abf <= 64, n_ao <= 16): operand stores and shape
   bool t1u = false;
-  int t1u_KP = 0, t1u_NS = 0, t1u_seg = 32;
+  int t1u_KP = 0, t1u_NS = 0, t1u_FS = 1, t1u_seg = 32;
   size_t smem_t1u = 0;
   uint16_t* Cu = nullptr;
   long long Cucap = 0;
@@ -781,12 +781,23 @@ void setup_shapes(hfx_plan* P) {
     P->t1u = false;
     if (want_umma && maxABF <= 64 && maxAO <= 16) {
       P->t1u_KP = 16 * maxAO;
-      const size_t base = hfx::t1u_smem(P->np, P->t1u_KP, 0);
-      const long long ns = base < limit ? (long long)((limit - base) / 4096) : 0;
-      P->t1u_NS = (int)std::min<long long>(ns, hfx::t1u_max_slots());
+      // Y ring: slots of FS rows f (at most half of them, the first U chunk),
+      // the largest FS that still leaves three slots (two when nothing else fits)
+      const size_t base = hfx::t1u_smem(P->np, P->t1u_KP, 0, 1);
+      const int fh = (P->t1u_KP / 16 + 1) / 2;
+      P->t1u_NS = 0;
+      for (int want = 3; want >= 2 && P->t1u_NS == 0; --want)
+        for (int fs = fh; fs >= 1; --fs) {
+          const long long ns = base < limit ? (long long)((limit - base) / ((size_t)fs * 4096)) : 0;
+          if (ns >= want) {
+            P->t1u_FS = fs;
+            P->t1u_NS = (int)std::min<long long>(ns, hfx::t1u_max_slots());
+            break;
+          }
+        }
       if (P->t1u_NS >= 2) {
         P->t1u = true;
-        P->smem_t1u = hfx::t1u_smem(P->np, P->t1u_KP, P->t1u_NS);
+        P->smem_t1u = hfx::t1u_smem(P->np, P->t1u_KP, P->t1u_NS, P->t1u_FS);
         const char* sg = std::getenv("HFX_T1_SEG");
         P->t1u_seg = sg ? std::max(1, std::atoi(sg)) : 32;
         ck(hfx::t1u_set_smem(P->np, P->smem_t1u), "smem attributes");
@@ -957,6 +968,7 @@ void evaluate(hfx_plan* P, const double* L, hfx_stats* st) {
     if (P->t1u) {
       U.KP = P->t1u_KP;
       U.NS = P->t1u_NS;
+      U.FS = P->t1u_FS;
       U.seg = P->t1u_seg;
       U.cu_blk = (long long)P->np * 64 * U.KP + 2LL * 4 * 64 * U.KP;
       U.vu_blk = (long long)P->np * 4096 + 2LL * 3 * 4096;

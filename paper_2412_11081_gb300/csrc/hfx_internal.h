@@ -119,6 +119,7 @@ struct T1UPlan {
   float* Df;                   // D blocks in FP32, [16][16] each
   int KP;                      // columns (f,a) = 16 f + a: 16 * max n_ao
   int NS;                      // Y ring slots
+  int FS;                      // rows f per Y slot (a run never crosses a U chunk)
   int seg;                     // B per FP32 run of the Q accumulator
 };
 
@@ -167,7 +168,7 @@ int q2_umma_segments(int max_pairs_per_atom);
 
 // tcgen05 first exchange product (hfx_t1umma.cu): shapes n_abf <= 64, n_ao <= 16.
 long long t1u_launch_count();
-size_t t1u_smem(int np, int KP, int NS);
+size_t t1u_smem(int np, int KP, int NS, int FS);
 int t1u_max_slots();
 cudaError_t t1u_set_smem(int np, size_t smem);
 cudaError_t launch_t1u_stores(const DevPlan& P, const T1UPlan& U, int np, const int* qlist, int nq, const int* vlist,

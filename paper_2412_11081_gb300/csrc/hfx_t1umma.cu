@@ -16,11 +16,15 @@
 // and Q as an MN-major B operand without a second copy.
 //
 // Warp roles (16 warps, one CTA per SM, persistent over items):
-//   warp 0      Y producer: bulk copies of Y^{BF}[f] rows (FP32) into a ring
-//   warp 1      C (per item), D_AB (FP32) and V_AB pieces (per B) producer
-//   warp 2      tensor-memory owner; lane 0 issues every MMA
-//   warp 3      scheduler: takes items from a global counter (dynamic load
-//               balance) and hands them to the other roles through a ring
+//   warp 0      Y producer: bulk copies of runs of up to FS rows Y^{BF}[f]
+//               (FP32, never crossing a U chunk) into a ring of NS slots
+//   warp 1      scheduler and producer: takes items from a global counter
+//               (dynamic load balance), hands them to the other roles through
+//               a ring two items ahead, and copies C (per item), D_AB (FP32)
+//               and V_AB pieces (per B)
+//   warp 2      tensor-memory owner; lane 0 issues the R products
+//   warp 3      lane 0 issues the Q products (a second issuing thread on
+//               another SMSP: one thread issues an MMA only every ~50 cycles)
 //   warps 4-7   epilogue: R -> g^V per B; Q -> E, g^C per run of B
 //   warps 8-15  U: one thread per (beta, 4 columns a) of each f
 // All hand-offs are mbarriers (bounded waits; a timeout sets the error flag
@@ -35,11 +39,10 @@ using namespace dev;
 long long g_t1u_launches = 0;
 
 constexpr int kThreads = 512;
-constexpr int kWarpY = 0, kWarpV = 1, kWarpM = 2, kWarpE = 4, kWarpU = 8;
-constexpr int kWarpS = 3;
+constexpr int kWarpY = 0, kWarpV = 1, kWarpM = 2, kWarpQ = 3, kWarpE = 4, kWarpU = 8;
 constexpr int kNE = 4, kNU = 8;
 constexpr int kItemRing = 4;
-constexpr int kItemReaders = 3 + kNE + kNU;   // Y, V, MMA, epilogue warps, U warps
+constexpr int kItemReaders = 3 + kNE + kNU;   // Y, R issuer, Q issuer, epilogue warps, U warps
 constexpr int kMaxNS = 16;
 constexpr int kRCol = 256;   // tensor-memory column of the first R accumulator (Q sits at column 0)
 
@@ -132,7 +135,9 @@ __global__ void k_t1u_dstore(DevPlan P, float* Df) {
 template <int NP>
 __global__ void __launch_bounds__(kThreads, 1)
     k_t1_umma(DevPlan P, MixPlan X, T1UPlan U, const int* qlist, int n_list, int* work, int* err) {
-  const int KP = U.KP, NF = KP >> 4, FH = (NF + 1) >> 1, NS = U.NS, SEG = U.seg;
+  const int KP = U.KP, NF = KP >> 4, FH = (NF + 1) >> 1, NS = U.NS, SEG = U.seg, FS = U.FS;
+  const int SLOT = FS * 64 * 16;                 // floats of one Y slot (FS rows f of up to 64 beta)
+  constexpr int NPROD = NP * (NP + 1) / 2;       // piece products (i, j) with i + j < NP
   const uint32_t CPB = 64u * KP * 2u;            // bytes of one piece of C or U
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   uint16_t* Cs = reinterpret_cast<uint16_t*>(smem_raw);
@@ -165,7 +170,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(df + 8 * s, 1);
       mbar_init(de + 8 * s, kNU);
       mbar_init(uf + 8 * s, kNU);
-      mbar_init(ue + 8 * s, 1);
+      mbar_init(ue + 8 * s, 2);   // released by both issuers
       mbar_init(rf + 8 * s, 1);
       mbar_init(re + 8 * s, kNE);
     }
@@ -225,15 +230,21 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int mBj = __shfl_sync(0xffffffffu, mB, j);
           if (lane == 0 && !aborted(abort_flag)) {
             if (yoj < 0) *abort_flag = 1;   // a kept triplet always has its Y block
-            for (int f = 0; f < nF && !aborted(abort_flag); ++f) {
-              const int s = (int)(ys % NS);
-              if (ys >= (uint32_t)NS && !mbar_wait(ye + 8 * s, ((ys / NS) - 1) & 1)) {
-                *abort_flag = 1;
-                break;
+            // runs [fa, fb) of at most FS rows, within each U chunk, rows f < nF only
+            for (int c = 0; c < 2 && !aborted(abort_flag); ++c) {
+              const int e = min(c ? NF : FH, nF);
+              for (int fa = c ? FH : 0; fa < e && !aborted(abort_flag); fa += FS) {
+                const int fb = min(fa + FS, e);
+                const int s = (int)(ys % NS);
+                if (ys >= (uint32_t)NS && !mbar_wait(ye + 8 * s, ((ys / NS) - 1) & 1)) {
+                  *abort_flag = 1;
+                  break;
+                }
+                const uint32_t bytes = (uint32_t)((fb - fa) * mBj) * 64u;
+                mbar_expect_tx(yf + 8 * s, bytes);
+                bulk_g2s(sa(Ys + s * SLOT), U.Yf + yoj + (long long)fa * mBj * 16, bytes, yf + 8 * s);
+                ++ys;
               }
-              mbar_expect_tx(yf + 8 * s, (uint32_t)mBj * 64u);
-              bulk_g2s(sa(Ys + s * 1024), U.Yf + yoj + (long long)f * mBj * 16, (uint32_t)mBj * 64u, yf + 8 * s);
-              ++ys;
             }
           }
           __syncwarp();
@@ -246,13 +257,44 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (n) mbar_wait(yf + 8 * s, (n - 1) & 1);
       }
   } else if (warp == kWarpV) {
-    // ------------------------------------------------- C, D and V producer
-    uint32_t vb = 0, db = 0, it = 0, ca = 0, ik = 0;
-    for (int kk = next_item(ik); kk < n_list && !aborted(abort_flag); kk = next_item(ik), ++it) {
+    // -------------------------------------- scheduler, C, D and V producer
+    // Lane 0 publishes item indices two items ahead of this warp's own
+    // position (a slot is reused once every reader has taken its item).
+    uint32_t pub = 0;
+    bool pub_done = false;
+    auto publish = [&]() {
+      const int s = pub & (kItemRing - 1);
+      if (pub >= kItemRing && !mbar_wait(ite + 8 * s, ((pub / kItemRing) - 1) & 1)) {
+        *abort_flag = 1;
+        s_item[s] = n_list;   // best effort: readers also stop on the flag
+        pub_done = true;
+        return;
+      }
+      int kk = aborted(abort_flag) ? n_list : atomicAdd(work, 1);
+      if (kk > n_list) kk = n_list;
+      s_item[s] = kk;
+      mbar_arrive(itf + 8 * s);
+      ++pub;
+      if (kk >= n_list) pub_done = true;
+    };
+    if (lane == 0) {
+      publish();
+      if (!pub_done) publish();
+    }
+    __syncwarp();
+    uint32_t vb = 0, db = 0, it = 0, ca = 0, own = 0;
+    auto own_item = [&]() -> int {
+      int kk = n_list;
+      if (lane == 0 && own < pub) kk = *reinterpret_cast<volatile int*>(&s_item[own & (kItemRing - 1)]);
+      ++own;
+      return __shfl_sync(0xffffffffu, kk, 0);
+    };
+    for (int kk = own_item(); kk < n_list && !aborted(abort_flag); kk = own_item(), ++it) {
       const int q = qlist[kk];
       const long long b0 = X.qoff[q];
       const int nbt = X.qcnt[q];
       if (lane == 0) {
+        if (!pub_done) publish();
         if (it >= 1 && !mbar_wait(ce, (it - 1) & 1)) *abort_flag = 1;
         if (!aborted(abort_flag)) {
           mbar_expect_tx(cf, (uint32_t)NP * CPB);
@@ -308,15 +350,25 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   } else if (warp == kWarpM) {
-    // ------------------------------------------------------------- MMA issue
+    // ------------------------------------------------------------ R issuer
+    // R_B = C_AF . U_B^T (M = 64 alpha, N = 64 beta, K = (f,a), one f per k
+    // step), every piece product, into one of two accumulators.  Descriptors
+    // of the products are formed once; a k step adds 16 (256 bytes).
     const uint32_t idR = idesc_bf16(64, 64, 0);
-    const int N0 = 16 * FH, N1 = 16 * (NF - FH);
-    const uint32_t idQ0 = idesc_bf16(64, N0, 1), idQ1 = N1 > 0 ? idesc_bf16(64, N1, 1) : 0u;
     const uint32_t rowg = 16u * KP;   // bytes between 8-row groups of C and U
-    // descriptors at the buffer bases; an offset of o bytes adds o >> 4
     const uint64_t dC = sdesc2(sa(Cs), 128, rowg), dUR = sdesc2(sa(Us), 128, rowg);
-    const uint64_t dV = sdesc2(sa(Vs), 128, 1024), dUQ = sdesc2(sa(Us), rowg, 128);
-    uint32_t rb = 0, seg = 0, it = 0, ik = 0;
+    uint64_t pa[NPROD], pb[NPROD];
+    {
+      int k = 0;
+#pragma unroll
+      for (int sum = NP - 1; sum >= 0; --sum)
+#pragma unroll
+        for (int ia = 0; ia <= sum; ++ia, ++k) {
+          pa[k] = dC + ((uint64_t)(ia * CPB) >> 4);
+          pb[k] = dUR + ((uint64_t)((sum - ia) * CPB) >> 4);
+        }
+    }
+    uint32_t rb = 0, it = 0, ik = 0;
     bool ok = true;
     for (int kk = next_item(ik); kk < n_list; kk = next_item(ik), ++it) {
       const int q = qlist[kk];
@@ -329,49 +381,75 @@ __global__ void __launch_bounds__(kThreads, 1)
             ok = false;
             break;
           }
-          const bool first = (i % SEG) == 0, last = (i % SEG) == SEG - 1 || i == nbt - 1;
           const int rbuf = rb & 1;
           const uint32_t dR = T + kRCol + 64u * rbuf;
-          if (rb >= 2) ok = ok && mbar_wait(re + 8 * rbuf, ((rb >> 1) - 1) & 1);
+          if (rb >= 2) ok = mbar_wait(re + 8 * rbuf, ((rb >> 1) - 1) & 1);
           for (int c = 0; c < 2 && ok; ++c) {
             ok = mbar_wait(uf + 8 * c, rb & 1);
             if (!ok) break;
             tc_fence_after();
             const int f0 = c ? FH : 0, f1 = c ? NF : FH;
-            // R += C[:, f] . U[:, f]^T over the chunk's k steps (one f each)
             for (int f = f0; f < f1; ++f) {
-              int k = 0;
+              const uint64_t o = 16u * (uint32_t)f;
 #pragma unroll
-              for (int sum = NP - 1; sum >= 0; --sum)
-#pragma unroll
-                for (int ia = 0; ia <= sum; ++ia, ++k) {
-                  const int ib = sum - ia;
-                  umma_bf16(dR, dC + ((ia * CPB + f * 256) >> 4), dUR + ((ib * CPB + f * 256) >> 4), idR,
-                            (f > 0 || k > 0) ? 1u : 0u);
-                }
+              for (int k = 0; k < NPROD; ++k) umma_bf16(dR, pa[k] + o, pb[k] + o, idR, (f > 0 || k > 0) ? 1u : 0u);
             }
+            umma_commit(ue + 8 * c);
             if (c == 1) umma_commit(rf + 8 * rbuf);
-            if (c == 0) {
-              ok = mbar_wait(vf, rb & 1) && (!first || seg == 0 || mbar_wait(qe, (seg - 1) & 1));
-              if (!ok) break;
-              tc_fence_after();
-            }
-            // Q[:, chunk] += V . U[:, chunk] (K = beta, four k steps; U read MN-major)
+          }
+          ++rb;
+        }
+        if (ok) umma_commit(ce);
+        if (!ok) *abort_flag = 1;
+      }
+      __syncwarp();
+    }
+  } else if (warp == kWarpQ) {
+    // ------------------------------------------------------------ Q issuer
+    // Q[:, chunk] += V_AB . U_B[:, chunk] (M = 64 alpha, N = the chunk's
+    // (f,a) columns, K = beta in four k steps; U read MN-major).
+    const int N0 = 16 * FH, N1 = 16 * (NF - FH);
+    const uint32_t idQ0 = idesc_bf16(64, N0, 1), idQ1 = N1 > 0 ? idesc_bf16(64, N1, 1) : 0u;
+    const uint32_t rowg = 16u * KP;
+    const uint64_t dV = sdesc2(sa(Vs), 128, 1024), dUQ = sdesc2(sa(Us), rowg, 128);
+    uint64_t pa[NPROD], pb[NPROD];
+    {
+      int k = 0;
+#pragma unroll
+      for (int sum = NP - 1; sum >= 0; --sum)
+#pragma unroll
+        for (int ia = 0; ia <= sum; ++ia, ++k) {
+          pa[k] = dV + ((uint64_t)(ia * 8192) >> 4);
+          pb[k] = dUQ + ((uint64_t)((sum - ia) * CPB) >> 4);
+        }
+    }
+    const uint64_t kbA = 256 >> 4, kbB = (uint64_t)(2 * rowg) >> 4;
+    uint32_t rb = 0, seg = 0, ik = 0;
+    bool ok = true;
+    for (int kk = next_item(ik); kk < n_list; kk = next_item(ik)) {
+      const int q = qlist[kk];
+      const int nbt = X.qcnt[q];
+      if (lane == 0 && ok) {
+        for (int i = 0; i < nbt && ok; ++i) {
+          if (aborted(abort_flag)) {
+            ok = false;
+            break;
+          }
+          const bool first = (i % SEG) == 0, last = (i % SEG) == SEG - 1 || i == nbt - 1;
+          for (int c = 0; c < 2 && ok; ++c) {
+            ok = mbar_wait(uf + 8 * c, rb & 1);
+            if (ok && c == 0) ok = mbar_wait(vf, rb & 1) && (!first || seg == 0 || mbar_wait(qe, (seg - 1) & 1));
+            if (!ok) break;
+            tc_fence_after();
+            const int f0 = c ? FH : 0;
             const int Nc = c ? N1 : N0;
             if (Nc > 0) {
-              const uint32_t idQ = c ? idQ1 : idQ0;
-              for (int kb = 0; kb < 4; ++kb) {
-                int k = 0;
+              const uint32_t idQ = c ? idQ1 : idQ0, tq = T + 16u * f0;
+              const uint64_t oB = (uint64_t)(f0 * 256) >> 4;
+              for (int kb = 0; kb < 4; ++kb)
 #pragma unroll
-                for (int sum = NP - 1; sum >= 0; --sum)
-#pragma unroll
-                  for (int ia = 0; ia <= sum; ++ia, ++k) {
-                    const int ib = sum - ia;
-                    umma_bf16(T + 16u * f0, dV + ((ia * 8192 + kb * 256) >> 4),
-                              dUQ + ((ib * CPB + kb * 2 * rowg + f0 * 256) >> 4), idQ,
-                              (first && kb == 0 && k == 0) ? 0u : 1u);
-                  }
-              }
+                for (int k = 0; k < NPROD; ++k)
+                  umma_bf16(tq, pa[k] + kbA * kb, pb[k] + oB + kbB * kb, idQ, (first && kb == 0 && k == 0) ? 0u : 1u);
             }
             umma_commit(ue + 8 * c);
           }
@@ -383,28 +461,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           ++rb;
         }
-        if (ok) umma_commit(ce);
         if (!ok) *abort_flag = 1;
       }
       __syncwarp();
     }
-  } else if (warp == kWarpS) {
-    // -------------------------------------------------------------- scheduler
-    if (lane == 0) {
-      for (uint32_t k = 0;; ++k) {
-        const int s = k & (kItemRing - 1);
-        if (k >= kItemRing && !mbar_wait(ite + 8 * s, ((k / kItemRing) - 1) & 1)) {
-          *abort_flag = 1;
-          break;
-        }
-        int kk = aborted(abort_flag) ? n_list : atomicAdd(work, 1);
-        if (kk > n_list) kk = n_list;
-        s_item[s] = kk;
-        mbar_arrive(itf + 8 * s);
-        if (kk >= n_list) break;
-      }
-    }
-    __syncwarp();
   } else if (warp >= kWarpE && warp < kWarpE + kNE) {
     // --------------------------------------------------------------- epilogue
     const int qd = warp & 3;                 // tensor-memory lane quarter
@@ -612,38 +672,64 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (ub >= 1) ok = wait_all(ue + 8 * c, (ub - 1) & 1);
             if (!ok) break;
             const int f0 = c ? FH : 0, f1 = c ? NF : FH;
-            for (int f = f0; f < f1; ++f) {
-              float u[4] = {0.f, 0.f, 0.f, 0.f};
-              if (f < nF) {
-                const int sl = (int)(ys % NS);
-                ok = wait_all(yf + 8 * sl, (ys / NS) & 1);
-                if (!ok) break;
-                float4 mine = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (beta < mB) mine = *reinterpret_cast<const float4*>(Ys + sl * 1024 + beta * 16 + 4 * ych);
-                __syncwarp();
-                if (lane == 0) mbar_arrive(ye + 8 * sl);
-                ++ys;
-                float y[16];
+            const int e = min(f1, nF);
+            // rows f < nF, one Y slot per run [fa, fb); two f per pass (eight
+            // independent FMA chains per lane)
+            for (int fa = f0; fa < e && ok; fa += FS) {
+              const int fb = min(fa + FS, e);
+              const int sl = (int)(ys % NS);
+              ok = wait_all(yf + 8 * sl, (ys / NS) & 1);
+              if (!ok) break;
+              const float* yrow = Ys + sl * SLOT + beta * 16 + 4 * ych;
+              for (int f = fa; f < fb; f += 2) {
+                const bool two = f + 1 < fb;
+                float4 m0 = make_float4(0.f, 0.f, 0.f, 0.f), m1 = m0;
+                if (beta < mB) {
+                  m0 = *reinterpret_cast<const float4*>(yrow + (f - fa) * mB * 16);
+                  if (two) m1 = *reinterpret_cast<const float4*>(yrow + (f + 1 - fa) * mB * 16);
+                }
+                float y0[16], y1[16];
 #pragma unroll
                 for (int c4 = 0; c4 < 4; ++c4) {
                   const int src = 16 * (c4 >> 1) + 2 * r8 + (c4 & 1);   // lane holding chunk c4 of this row
-                  y[4 * c4] = __shfl_sync(0xffffffffu, mine.x, src);
-                  y[4 * c4 + 1] = __shfl_sync(0xffffffffu, mine.y, src);
-                  y[4 * c4 + 2] = __shfl_sync(0xffffffffu, mine.z, src);
-                  y[4 * c4 + 3] = __shfl_sync(0xffffffffu, mine.w, src);
+                  y0[4 * c4] = __shfl_sync(0xffffffffu, m0.x, src);
+                  y0[4 * c4 + 1] = __shfl_sync(0xffffffffu, m0.y, src);
+                  y0[4 * c4 + 2] = __shfl_sync(0xffffffffu, m0.z, src);
+                  y0[4 * c4 + 3] = __shfl_sync(0xffffffffu, m0.w, src);
+                  y1[4 * c4] = __shfl_sync(0xffffffffu, m1.x, src);
+                  y1[4 * c4 + 1] = __shfl_sync(0xffffffffu, m1.y, src);
+                  y1[4 * c4 + 2] = __shfl_sync(0xffffffffu, m1.z, src);
+                  y1[4 * c4 + 3] = __shfl_sync(0xffffffffu, m1.w, src);
                 }
+                if (f + 2 >= fb && lane == 0) mbar_arrive(ye + 8 * sl);   // every row of the slot is in registers
+                float u0[4] = {0.f, 0.f, 0.f, 0.f}, u1[4] = {0.f, 0.f, 0.f, 0.f};
                 if (beta < mB)
 #pragma unroll
-                  for (int i = 0; i < 4; ++i)
+                  for (int b = 0; b < 16; ++b)
 #pragma unroll
-                    for (int b = 0; b < 16; ++b) u[i] = fmaf(y[b], d[i][b], u[i]);
+                    for (int i = 0; i < 4; ++i) {
+                      u0[i] = fmaf(y0[b], d[i][b], u0[i]);
+                      u1[i] = fmaf(y1[b], d[i][b], u1[i]);
+                    }
+                uint2 pk[NP];
+                split4<NP>(u0, pk);
+#pragma unroll
+                for (int pp = 0; pp < NP; ++pp)
+                  *reinterpret_cast<uint2*>(urow + (size_t)pp * 64 * KP + (2 * f + (qa >> 1)) * 64) = pk[pp];
+                if (two) {
+                  split4<NP>(u1, pk);
+#pragma unroll
+                  for (int pp = 0; pp < NP; ++pp)
+                    *reinterpret_cast<uint2*>(urow + (size_t)pp * 64 * KP + (2 * (f + 1) + (qa >> 1)) * 64) = pk[pp];
+                }
               }
-              uint2 pk[NP];
-              split4<NP>(u, pk);
+              ++ys;
+            }
+            // rows f >= nF of the chunk are zero
+            for (int f = max(f0, e); f < f1; ++f)
 #pragma unroll
               for (int pp = 0; pp < NP; ++pp)
-                *reinterpret_cast<uint2*>(urow + (size_t)pp * 64 * KP + (2 * f + (qa >> 1)) * 64) = pk[pp];
-            }
+                *reinterpret_cast<uint2*>(urow + (size_t)pp * 64 * KP + (2 * f + (qa >> 1)) * 64) = make_uint2(0u, 0u);
             fence_async_smem();
             __syncwarp();
             if (lane == 0) mbar_arrive(uf + 8 * c);
@@ -668,8 +754,8 @@ int g_num_sms = 0;
 
 long long t1u_launch_count() { return g_t1u_launches; }
 
-size_t t1u_smem(int np, int KP, int NS) {
-  return (size_t)np * 64 * KP * 2 * 2 + (size_t)np * 8192 + 2 * 256 * 4 + (size_t)NS * 1024 * 4;
+size_t t1u_smem(int np, int KP, int NS, int FS) {
+  return (size_t)np * 64 * KP * 2 * 2 + (size_t)np * 8192 + 2 * 256 * 4 + (size_t)NS * FS * 1024 * 4;
 }
 
 int t1u_max_slots() { return kMaxNS; }
