@@ -781,20 +781,20 @@ void setup_shapes(hfx_plan* P) {
     P->t1u = false;
     if (want_umma && maxABF <= 64 && maxAO <= 16) {
       P->t1u_KP = 16 * maxAO;
-      // Y ring: slots of FS rows f (at most half of them, the first U chunk),
-      // the largest FS that still leaves three slots (two when nothing else fits)
+      // Y ring: slots of FS rows f.  Half a U chunk per slot (one wait and one
+      // release per run of rows) when three such slots fit, else runs of two
+      // rows (measured best for BF16X6 on si64), else single rows
+      // (HFX_T1_FS overrides the run length).
       const size_t base = hfx::t1u_smem(P->np, P->t1u_KP, 0, 1);
       const int fh = (P->t1u_KP / 16 + 1) / 2;
-      P->t1u_NS = 0;
-      for (int want = 3; want >= 2 && P->t1u_NS == 0; --want)
-        for (int fs = fh; fs >= 1; --fs) {
-          const long long ns = base < limit ? (long long)((limit - base) / ((size_t)fs * 4096)) : 0;
-          if (ns >= want) {
-            P->t1u_FS = fs;
-            P->t1u_NS = (int)std::min<long long>(ns, hfx::t1u_max_slots());
-            break;
-          }
-        }
+      auto slots = [&](int fs) {
+        return base < limit ? (long long)((limit - base) / ((size_t)fs * 4096)) : 0LL;
+      };
+      const char* fse = std::getenv("HFX_T1_FS");
+      int fs = fse ? std::max(1, std::min(fh, std::atoi(fse))) : (slots(fh) >= 3 ? fh : (slots(2) >= 3 ? 2 : 1));
+      while (fs > 1 && slots(fs) < 2) --fs;
+      P->t1u_FS = fs;
+      P->t1u_NS = (int)std::min<long long>(slots(fs), hfx::t1u_max_slots());
       if (P->t1u_NS >= 2) {
         P->t1u = true;
         P->smem_t1u = hfx::t1u_smem(P->np, P->t1u_KP, P->t1u_NS, P->t1u_FS);

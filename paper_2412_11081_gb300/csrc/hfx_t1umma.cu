@@ -635,7 +635,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int uw = warp - kWarpU;
     const int r8 = (lane >> 1) & 7, qa = 2 * (lane >> 4) + (lane & 1);
     const int beta = 8 * uw + r8;
-    const int ych = qa ^ (2 * ((beta >> 1) & 1));   // stored position of chunk qa of row beta
+    const int ysw = 2 * ((beta >> 1) & 1);          // chunk c of row beta is stored at c ^ ysw
     uint16_t* urow = Us + (beta >> 3) * KP * 8 + (beta & 7) * 8 + (qa & 1) * 4;
     uint32_t ub = 0, ys = 0, ik = 0;
     bool ok = true;
@@ -655,16 +655,17 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int s = ub & 1;
           ok = wait_all(df + 8 * s, (ub >> 1) & 1);
           if (!ok) break;
-          float d[4][16];   // D_AB[4 qa + i][b]
+          float2 dd[2][16];   // (D_AB[4 qa + 2 j][b], D_AB[4 qa + 2 j + 1][b])
 #pragma unroll
           for (int i = 0; i < 4; ++i)
 #pragma unroll
             for (int c4 = 0; c4 < 4; ++c4) {
               const float4 w = *reinterpret_cast<const float4*>(Ds + s * 256 + (4 * qa + i) * 16 + 4 * (c4 ^ qa));
-              d[i][4 * c4] = w.x;
-              d[i][4 * c4 + 1] = w.y;
-              d[i][4 * c4 + 2] = w.z;
-              d[i][4 * c4 + 3] = w.w;
+              float* col = (i & 1) ? &dd[i >> 1][0].y : &dd[i >> 1][0].x;
+              col[2 * (4 * c4)] = w.x;
+              col[2 * (4 * c4 + 1)] = w.y;
+              col[2 * (4 * c4 + 2)] = w.z;
+              col[2 * (4 * c4 + 3)] = w.w;
             }
           __syncwarp();
           if (lane == 0) mbar_arrive(de + 8 * s);
@@ -680,47 +681,100 @@ __global__ void __launch_bounds__(kThreads, 1)
               const int sl = (int)(ys % NS);
               ok = wait_all(yf + 8 * sl, (ys / NS) & 1);
               if (!ok) break;
-              const float* yrow = Ys + sl * SLOT + beta * 16 + 4 * ych;
-              for (int f = fa; f < fb; f += 2) {
-                const bool two = f + 1 < fb;
-                float4 m0 = make_float4(0.f, 0.f, 0.f, 0.f), m1 = m0;
-                if (beta < mB) {
-                  m0 = *reinterpret_cast<const float4*>(yrow + (f - fa) * mB * 16);
-                  if (two) m1 = *reinterpret_cast<const float4*>(yrow + (f + 1 - fa) * mB * 16);
-                }
-                float y0[16], y1[16];
+              if (NP == 3) {
+                // BF16X6 (tighter on registers): one row per pass, each lane
+                // reads one 16-byte chunk and the row is gathered by shuffles
+                for (int f = fa; f < fb; ++f) {
+                  float4 mine = make_float4(0.f, 0.f, 0.f, 0.f);
+                  if (beta < mB)
+                    mine = *reinterpret_cast<const float4*>(Ys + sl * SLOT + ((f - fa) * mB + beta) * 16 + 4 * (qa ^ ysw));
+                  float y[16];
 #pragma unroll
-                for (int c4 = 0; c4 < 4; ++c4) {
-                  const int src = 16 * (c4 >> 1) + 2 * r8 + (c4 & 1);   // lane holding chunk c4 of this row
-                  y0[4 * c4] = __shfl_sync(0xffffffffu, m0.x, src);
-                  y0[4 * c4 + 1] = __shfl_sync(0xffffffffu, m0.y, src);
-                  y0[4 * c4 + 2] = __shfl_sync(0xffffffffu, m0.z, src);
-                  y0[4 * c4 + 3] = __shfl_sync(0xffffffffu, m0.w, src);
-                  y1[4 * c4] = __shfl_sync(0xffffffffu, m1.x, src);
-                  y1[4 * c4 + 1] = __shfl_sync(0xffffffffu, m1.y, src);
-                  y1[4 * c4 + 2] = __shfl_sync(0xffffffffu, m1.z, src);
-                  y1[4 * c4 + 3] = __shfl_sync(0xffffffffu, m1.w, src);
-                }
-                if (f + 2 >= fb && lane == 0) mbar_arrive(ye + 8 * sl);   // every row of the slot is in registers
-                float u0[4] = {0.f, 0.f, 0.f, 0.f}, u1[4] = {0.f, 0.f, 0.f, 0.f};
-                if (beta < mB)
+                  for (int c4 = 0; c4 < 4; ++c4) {
+                    const int src = 16 * (c4 >> 1) + 2 * r8 + (c4 & 1);   // lane holding chunk c4 of this row
+                    y[4 * c4] = __shfl_sync(0xffffffffu, mine.x, src);
+                    y[4 * c4 + 1] = __shfl_sync(0xffffffffu, mine.y, src);
+                    y[4 * c4 + 2] = __shfl_sync(0xffffffffu, mine.z, src);
+                    y[4 * c4 + 3] = __shfl_sync(0xffffffffu, mine.w, src);
+                  }
+                  if (f + 1 >= fb && lane == 0) mbar_arrive(ye + 8 * sl);   // the slot's rows are in registers
+                  float uf4[4] = {0.f, 0.f, 0.f, 0.f};
+                  if (beta < mB)
 #pragma unroll
-                  for (int b = 0; b < 16; ++b)
+                    for (int b = 0; b < 16; ++b)
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                      u0[i] = fmaf(y0[b], d[i][b], u0[i]);
-                      u1[i] = fmaf(y1[b], d[i][b], u1[i]);
-                    }
-                uint2 pk[NP];
-                split4<NP>(u0, pk);
-#pragma unroll
-                for (int pp = 0; pp < NP; ++pp)
-                  *reinterpret_cast<uint2*>(urow + (size_t)pp * 64 * KP + (2 * f + (qa >> 1)) * 64) = pk[pp];
-                if (two) {
-                  split4<NP>(u1, pk);
+                      for (int j = 0; j < 2; ++j) {
+                        uf4[2 * j] = fmaf(y[b], dd[j][b].x, uf4[2 * j]);
+                        uf4[2 * j + 1] = fmaf(y[b], dd[j][b].y, uf4[2 * j + 1]);
+                      }
+                  uint2 pk[NP];
+                  split4<NP>(uf4, pk);
 #pragma unroll
                   for (int pp = 0; pp < NP; ++pp)
-                    *reinterpret_cast<uint2*>(urow + (size_t)pp * 64 * KP + (2 * (f + 1) + (qa >> 1)) * 64) = pk[pp];
+                    *reinterpret_cast<uint2*>(urow + (size_t)pp * 64 * KP + (2 * f + (qa >> 1)) * 64) = pk[pp];
+                }
+              } else {
+                const float* yrow = Ys + sl * SLOT + beta * 16;
+                for (int f = fa; f < fb; f += 2) {
+                  const bool two = f + 1 < fb;
+                  // the two Y rows of this lane (16-byte chunk c stored at c ^ ysw)
+                  float y0[16], y1[16];
+  #pragma unroll
+                  for (int c4 = 0; c4 < 4; ++c4) {
+                    float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
+                    if (beta < mB) {
+                      a0 = *reinterpret_cast<const float4*>(yrow + (f - fa) * mB * 16 + 4 * (c4 ^ ysw));
+                      if (two) a1 = *reinterpret_cast<const float4*>(yrow + (f + 1 - fa) * mB * 16 + 4 * (c4 ^ ysw));
+                    }
+                    y0[4 * c4] = a0.x;
+                    y0[4 * c4 + 1] = a0.y;
+                    y0[4 * c4 + 2] = a0.z;
+                    y0[4 * c4 + 3] = a0.w;
+                    y1[4 * c4] = a1.x;
+                    y1[4 * c4 + 1] = a1.y;
+                    y1[4 * c4 + 2] = a1.z;
+                    y1[4 * c4 + 3] = a1.w;
+                  }
+                  // u[a] = sum_b y[b] D[a][b], two a per packed FP32 FMA
+                  float2 u0[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}, u1[2] = {u0[0], u0[1]};
+                  if (beta < mB) {
+                    if (two) {
+  #pragma unroll
+                      for (int b = 0; b < 16; ++b)
+  #pragma unroll
+                        for (int j = 0; j < 2; ++j) {
+                          u0[j].x = fmaf(y0[b], dd[j][b].x, u0[j].x);
+                          u0[j].y = fmaf(y0[b], dd[j][b].y, u0[j].y);
+                          u1[j].x = fmaf(y1[b], dd[j][b].x, u1[j].x);
+                          u1[j].y = fmaf(y1[b], dd[j][b].y, u1[j].y);
+                        }
+                    } else {
+  #pragma unroll
+                      for (int b = 0; b < 16; ++b)
+  #pragma unroll
+                        for (int j = 0; j < 2; ++j) {
+                          u0[j].x = fmaf(y0[b], dd[j][b].x, u0[j].x);
+                          u0[j].y = fmaf(y0[b], dd[j][b].y, u0[j].y);
+                        }
+                    }
+                  }
+                  if (f + 2 >= fb) {   // every row of the slot has been read and used
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(ye + 8 * sl);
+                  }
+                  uint2 pk[NP];
+                  float uf4[4] = {u0[0].x, u0[0].y, u0[1].x, u0[1].y};
+                  split4<NP>(uf4, pk);
+  #pragma unroll
+                  for (int pp = 0; pp < NP; ++pp)
+                    *reinterpret_cast<uint2*>(urow + (size_t)pp * 64 * KP + (2 * f + (qa >> 1)) * 64) = pk[pp];
+                  if (two) {
+                    float ug4[4] = {u1[0].x, u1[0].y, u1[1].x, u1[1].y};
+                    split4<NP>(ug4, pk);
+  #pragma unroll
+                    for (int pp = 0; pp < NP; ++pp)
+                      *reinterpret_cast<uint2*>(urow + (size_t)pp * 64 * KP + (2 * (f + 1) + (qa >> 1)) * 64) = pk[pp];
+                  }
                 }
               }
               ++ys;
