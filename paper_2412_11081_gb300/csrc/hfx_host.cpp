@@ -113,7 +113,7 @@ struct hfx_plan {
   // device model
   int *d_species = nullptr, *d_n_ao = nullptr, *d_n_abf = nullptr;
   long long *d_G_off = nullptr, *d_M_off = nullptr;
-  double *d_G = nullptr, *d_Gp = nullptr, *d_M = nullptr;
+  double *d_G = nullptr, *d_Gp = nullptr, *d_M = nullptr, *d_Mnorm = nullptr;
   double* d_Dval = nullptr;
   long long* d_Doff = nullptr;
   int* d_Didx = nullptr;
@@ -266,7 +266,7 @@ void upload_model(hfx_plan* P, const hfx_system* sys, const hfx_model* m) {
       gsz += (long long)P->n_abf[a] * P->n_ao[a] * P->n_ao[b];
       msz += (long long)P->n_abf[a] * P->n_abf[b];
     }
-  std::vector<double> G(gsz), M(msz), Gp;
+  std::vector<double> G(gsz), M(msz), Gp, Mnorm(S * S);
   if (m->G_aniso) Gp.resize(gsz);
   double mmax = 0;
   for (int a = 0; a < S; ++a)
@@ -282,7 +282,8 @@ void upload_model(hfx_plan* P, const hfx_system* sys, const hfx_model* m) {
       }
       double s2 = 0;
       for (long long k = 0; k < nm; ++k) s2 += M[moff[a * S + b] + k] * M[moff[a * S + b] + k];
-      mmax = std::max(mmax, std::sqrt(s2));
+      Mnorm[a * S + b] = std::sqrt(s2);
+      mmax = std::max(mmax, Mnorm[a * S + b]);
     }
   if (!finite_all(G.data(), G.size()) || !finite_all(M.data(), M.size()) || !finite_all(Gp.data(), Gp.size()))
     fail(HFX_ERR_INVALID, "non-finite template");
@@ -303,6 +304,7 @@ void upload_model(hfx_plan* P, const hfx_system* sys, const hfx_model* m) {
   P->d_M_off = P->mem.alloc<long long>(S * S);
   P->d_G = P->mem.alloc<double>(gsz);
   P->d_M = P->mem.alloc<double>(msz);
+  P->d_Mnorm = P->mem.alloc<double>(S * S);
   upload(P->d_species, P->species, s);
   upload(P->d_n_ao, P->n_ao, s);
   upload(P->d_n_abf, P->n_abf, s);
@@ -310,6 +312,7 @@ void upload_model(hfx_plan* P, const hfx_system* sys, const hfx_model* m) {
   upload(P->d_M_off, moff, s);
   upload(P->d_G, G, s);
   upload(P->d_M, M, s);
+  upload(P->d_Mnorm, Mnorm, s);
   if (m->G_aniso) {
     P->d_Gp = P->mem.alloc<double>(gsz);
     upload(P->d_Gp, Gp, s);
@@ -413,6 +416,7 @@ DevPlan make_devplan(hfx_plan* P, const double* lattice) {
   D.Gp = P->aniso ? P->d_Gp : nullptr;
   D.M_off = P->d_M_off;
   D.M = P->d_M;
+  D.Mnorm = P->d_Mnorm;
   for (int k = 0; k < 3; ++k) D.e[k] = P->e[k];
   D.RC = P->RC;
   D.omega = P->omega;

@@ -28,6 +28,7 @@ struct DevPlan {
   const double* Gp;            // anisotropic templates or nullptr
   const long long* M_off;
   const double* M;
+  const double* Mnorm;         // [S*S] ||M_st||_F
   double e[3];
   double RC, omega;
   double thC, thdC, thV, thdV, thD, thCS;

@@ -183,49 +183,32 @@ __global__ void k_cblocks(DevPlan P, int frozen) {
 }
 
 // ---------------------------------------------------------------- K1: V norms
-// One warp per V pair: ||V|| and ||grad V|| over the block values
-// V = M h(r), grad_d V = M h'(r) d/r (on-site: V = M, grad V = 0).
+// One thread per V pair.  V = M h(r) and grad_d V = M h'(r) d/r (on-site:
+// V = M, grad V = 0), so ||V|| = |h| ||M|| and ||grad V|| = |h'| ||M|| (the
+// three components of d/r have unit length): the template norm ||M_st||_F is
+// taken once per species pair when the plan is made.
 __global__ void k_vnorm(DevPlan P, int frozen) {
-  const int lane = threadIdx.x & 31;
-  const int wpb = blockDim.x >> 5;
-  for (int p = blockIdx.x * wpb + (threadIdx.x >> 5); p < P.nV; p += gridDim.x * wpb) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P.nV; p += gridDim.x * blockDim.x) {
     const int A = P.v_home[p], j = P.v_j[p];
     const int* R = P.v_R + 3 * p;
-    double d[3];
-    pair_vector(P, A, j, R, d);
     const bool onsite = (A == j) && R[0] == 0 && R[1] == 0 && R[2] == 0;
-    const double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
     double h = 1.0, hp = 0.0;
-    if (!onsite) radial_h(r, P.omega, h, hp);
-    double g[3] = {0.0, 0.0, 0.0};
     if (!onsite) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) g[c] = hp * d[c] / r;
+      double d[3];
+      pair_vector(P, A, j, R, d);
+      radial_h(sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]), P.omega, h, hp);
     }
-    const int sA = P.species[A], sj = P.species[j];
-    const double* M = P.M + P.M_off[sA * P.S + sj];
-    const int n = P.n_abf[sA] * P.n_abf[sj];
-    double sv = 0.0, sg = 0.0;
-    for (int t = lane; t < n; t += 32) {
-      const double m = M[t];
-      const double v = m * h, g0 = m * g[0], g1 = m * g[1], g2 = m * g[2];
-      sv += v * v;
-      sg += g0 * g0 + g1 * g1 + g2 * g2;
+    const double mn = P.Mnorm[P.species[A] * P.S + P.species[j]];
+    const double nv = fabs(h) * mn, ng = fabs(hp) * mn;
+    bool keep;
+    if (frozen) {
+      keep = P.v_keep[p] != 0;
+    } else {
+      keep = (nv > P.thV) || (ng > P.thdV);
+      P.v_keep[p] = keep;
     }
-    sv = warp_sum(sv);
-    sg = warp_sum(sg);
-    if (lane == 0) {
-      const double nv = sqrt(sv), ng = sqrt(sg);
-      bool keep;
-      if (frozen) {
-        keep = P.v_keep[p] != 0;
-      } else {
-        keep = (nv > P.thV) || (ng > P.thdV);
-        P.v_keep[p] = keep;
-      }
-      P.v_norm[p] = keep ? fmax(nv, ng) : 0.0;
-      if (keep) atomicAdd(&P.cnt[CNT_V], 1ull);
-    }
+    P.v_norm[p] = keep ? fmax(nv, ng) : 0.0;
+    if (keep) atomicAdd(&P.cnt[CNT_V], 1ull);
   }
 }
 
@@ -829,7 +812,7 @@ cudaError_t launch_cblocks(const DevPlan& P, int frozen, cudaStream_t s) {
 cudaError_t launch_vnorm(const DevPlan& P, int frozen, cudaStream_t s) {
   if (P.nV == 0) return cudaSuccess;
   ++g_launches;
-  k_vnorm<<<grid_for(P.nV, kThreads / 32, 152 * 64), kThreads, 0, s>>>(P, frozen);
+  k_vnorm<<<grid_for(P.nV, kThreads), kThreads, 0, s>>>(P, frozen);
   return cudaGetLastError();
 }
 

@@ -741,6 +741,7 @@ __global__ void __launch_bounds__(192) k_q2_umma(DevPlan P, MixPlan X, const int
   __shared__ __align__(8) uint64_t bar_full[kStages], bar_empty[kStages], bar_accf[2], bar_acce[2];
   __shared__ uint32_t tmem_base;
   __shared__ double sg[8][3];
+  __shared__ unsigned long long s_fl;
   __shared__ int s_abort;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   int rem = blockIdx.x;
@@ -768,7 +769,9 @@ __global__ void __launch_bounds__(192) k_q2_umma(DevPlan P, MixPlan X, const int
     qf[i] = (j < nq && P.c_keep[q0 + j]) ? q0 + j : -1;
     nF[i] = qf[i] >= 0 ? P.n_ao[P.species[P.c_j[qf[i]]]] : 0;
   }
-  // D block (units of 256 elements) of every (pair, F), or -1
+  // D block (units of 256 elements) of every (pair, F), or -1; the flops of
+  // the kept (pair, F) are counted here (once per pair, by the mc = 0 CTA)
+  unsigned long long fl = 0ull;
   for (int e = tid; e < np * 8; e += blockDim.x) {
     const int t = e >> 3, i = e & 7;
     int db = -1;
@@ -778,7 +781,10 @@ __global__ void __launch_bounds__(192) k_q2_umma(DevPlan P, MixPlan X, const int
       const int* Rb = P.v_R + 3 * p;
       const int* Rf = P.c_R + 3 * qf[i];
       const int d = dlut_get(P, P.c_j[qf[i]], b, Rb[0] - Rf[0], Rb[1] - Rf[1], Rb[2] - Rf[2]);
-      if (d >= 0 && P.Dkept[d] != 0.0) db = (int)(X.dsp_off[d] >> 8);
+      if (d >= 0 && P.Dkept[d] != 0.0) {
+        db = (int)(X.dsp_off[d] >> 8);
+        if (mc == 0) fl += 2ull * mA * nA * P.n_ao[P.species[b]] * nF[i];
+      }
     }
     m_dblk[e] = db;
   }
@@ -789,6 +795,7 @@ __global__ void __launch_bounds__(192) k_q2_umma(DevPlan P, MixPlan X, const int
   if (tid < 24) sg[tid / 3][tid % 3] = 0.0;
   if (tid == 0) {
     s_abort = 0;
+    s_fl = 0ull;
     for (int s = 0; s < kStages; ++s) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mfull + 8 * s));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mempty + 8 * s));
@@ -809,7 +816,8 @@ __global__ void __launch_bounds__(192) k_q2_umma(DevPlan P, MixPlan X, const int
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t taddr = tmem_base;
   const int nruns = (np + kFlushPairs - 1) / kFlushPairs;
-  unsigned long long fl = 0ull;
+  fl = warp_sum_u64(fl);
+  if (lane == 0 && fl) atomicAdd(&s_fl, fl);
 
   if (warp == 0) {
     // producer warp: every lane waits for the stage, then lanes issue the
@@ -942,14 +950,6 @@ __global__ void __launch_bounds__(192) k_q2_umma(DevPlan P, MixPlan X, const int
         if (lane == 0 && w != 0.0) atomicAdd(&sg[i][c], w);
       }
   }
-  if (tid == 0 && mc == 0) {
-    for (int t = 0; t < np; ++t) {
-      const int nB = P.n_ao[P.species[P.v_j[list[p0 + t]]]];
-#pragma unroll
-      for (int i = 0; i < 8; ++i)
-        if (m_dblk[t * 8 + i] >= 0) fl += 2ull * mA * nA * nB * nF[i];
-    }
-  }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
@@ -960,7 +960,7 @@ __global__ void __launch_bounds__(192) k_q2_umma(DevPlan P, MixPlan X, const int
   }
   if (tid == 0) {
     if (s_abort) atomicExch(err, 1);
-    if (fl) atomicAdd(&P.acc[ACC_F2], (double)fl);
+    if (s_fl) atomicAdd(&P.acc[ACC_F2], (double)s_fl);
   }
 }
 
@@ -982,6 +982,7 @@ __global__ void __launch_bounds__(192) k_ybuild_umma(DevPlan P, MixPlan X, const
   int* m_d = reinterpret_cast<int*>(stB + (size_t)kStages * NP * kTileElems);   // [kMaxCPerAtom][8]
   __shared__ int m_q[kMaxCPerAtom];
   __shared__ int s_nsteps;
+  __shared__ unsigned long long s_fl;
   __shared__ __align__(8) uint64_t bar_full[kStages], bar_empty[kStages], bar_accf;
   __shared__ uint32_t tmem_base;
   __shared__ int s_abort;
@@ -1000,6 +1001,9 @@ __global__ void __launch_bounds__(192) k_ybuild_umma(DevPlan P, MixPlan X, const
     ykey[i] = i < nk ? ylist[kstart + i] : -1;
     zat[i] = ykey[i] >= 0 ? P.y_j[ykey[i]] : 0;
   }
+  // D block of every (C pair, key), or -1; the flops of the kept ones are
+  // counted here (once per key group, by the mc = 0 CTA)
+  unsigned long long fl = 0ull;
   for (int e = tid; e < nq * 8; e += blockDim.x) {
     const int t = e >> 3, i = e & 7;
     int md = -1;
@@ -1011,6 +1015,7 @@ __global__ void __launch_bounds__(192) k_ybuild_umma(DevPlan P, MixPlan X, const
       if (di >= 0 && P.Dkept[di] != 0.0) {
         const int mi = dlut_get(P, z, w, Rw[0] - Rz[0], Rw[1] - Rz[1], Rw[2] - Rz[2]);
         md = (int)(X.dsp_off[mi] >> 8);
+        if (mc == 0) fl += 2ull * rows * P.n_ao[P.species[z]] * P.n_ao[P.species[w]];
       }
     }
     m_d[e] = md;
@@ -1020,6 +1025,7 @@ __global__ void __launch_bounds__(192) k_ybuild_umma(DevPlan P, MixPlan X, const
   const uint32_t maccf = (uint32_t)__cvta_generic_to_shared(&bar_accf);
   if (tid == 0) {
     s_abort = 0;
+    s_fl = 0ull;
     for (int s = 0; s < kStages; ++s) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mfull + 8 * s));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mempty + 8 * s));
@@ -1033,14 +1039,23 @@ __global__ void __launch_bounds__(192) k_ybuild_umma(DevPlan P, MixPlan X, const
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
   }
   __syncthreads();
-  if (tid == 0) {   // K steps: kept C pairs with at least one D block among the keys
+  fl = warp_sum_u64(fl);
+  if (lane == 0 && fl) atomicAdd(&s_fl, fl);
+  if (warp == 0) {   // K steps: kept C pairs with at least one D block among the keys, in order
     int n = 0;
-    for (int t = 0; t < nq; ++t) {
+    for (int t0 = 0; t0 < nq; t0 += 32) {
+      const int t = t0 + lane;
       bool any = false;
-      for (int i = 0; i < 8; ++i) any = any || m_d[t * 8 + i] >= 0;
-      if (any) m_q[n++] = t;
+      if (t < nq) {
+        const int4 u = *reinterpret_cast<const int4*>(m_d + t * 8);
+        const int4 v = *reinterpret_cast<const int4*>(m_d + t * 8 + 4);
+        any = !(u.x < 0 && u.y < 0 && u.z < 0 && u.w < 0 && v.x < 0 && v.y < 0 && v.z < 0 && v.w < 0);
+      }
+      const unsigned bal = __ballot_sync(0xffffffffu, any);
+      if (any) m_q[n + __popc(bal & ((1u << lane) - 1u))] = t;
+      n += __popc(bal);
     }
-    s_nsteps = n;
+    if (lane == 0) s_nsteps = n;
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
@@ -1111,11 +1126,20 @@ __global__ void __launch_bounds__(192) k_ybuild_umma(DevPlan P, MixPlan X, const
                    : "memory");
     }
   } else {
-    // epilogue: split the accumulator into bf16 pieces and store the Y rows
+    // epilogue (warps 2..5): the accumulator (rows (alpha, x), columns
+    // (key, z)) passes through shared memory, two keys at a time, in the
+    // stage ring (idle once the last MMA has completed), so that the Y store
+    // and its FP32 copy are written as whole 16-byte chunks of complete
+    // (alpha, z) rows, x padding included.  An alpha whose rows straddle two
+    // row tiles is written element by element by both; the tile that holds
+    // x = n_ao - 1 writes its padding.
     const int q = warp & 3;
-    const int r = row0 + q * 32 + lane;
-    const bool rv = r < rows;
-    const int al = rv ? r / nX : 0, x = rv ? r - al * nX : 0;
+    const int et = tid - 64;
+    float* ep = reinterpret_cast<float*>(smem_raw);   // [128][33]
+    const int rend = min(row0 + 128, rows);
+    const int alF = (row0 + nX - 1) / nX, alL = rend / nX - 1;
+    const int nal = max(0, alL - alF + 1);
+    const int alA = row0 / nX, alB = (rend - 1) / nX;
     bool have = nsteps > 0;
     if (have) {
       if (!mbar_wait(maccf, 0u)) {
@@ -1124,47 +1148,91 @@ __global__ void __launch_bounds__(192) k_ybuild_umma(DevPlan P, MixPlan X, const
       }
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     }
-#pragma unroll
     for (int c0 = 0; c0 < 128; c0 += 32) {
-      uint32_t v[32];
-      if (have) {
-        tmem_ld32(taddr + ((uint32_t)(q * 32) << 16) + c0, v);
-      } else {
+      {
+        uint32_t v[32];
+        if (have) {
+          tmem_ld32(taddr + ((uint32_t)(q * 32) << 16) + c0, v);
+        } else {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) v[j] = 0u;
+          for (int j = 0; j < 32; ++j) v[j] = 0u;
+        }
+        float* er = ep + (q * 32 + lane) * 33;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) er[j] = __uint_as_float(v[j]);
       }
-#pragma unroll
+      asm volatile("bar.sync 1, 128;\n" ::: "memory");
+#pragma unroll 1
       for (int h = 0; h < 2; ++h) {
         const int i = (c0 >> 4) + h;
-        if (!rv || ykey[i] < 0) continue;
+        if (ykey[i] < 0) continue;
         const int nZ = P.n_ao[P.species[zat[i]]];
         uint16_t* Yo = X.Ysp + P.y_off[ykey[i]];
         float* Yf = X.Yf ? X.Yf + P.y_off[ykey[i]] / NP : nullptr;
         const long long plane = (long long)mX * nZ * 16;
+        const float* eh = ep + h * 16;
+        // bf16 pieces: chunk (alpha, z, half) holds x = 8 half .. 8 half + 7
+        for (int c = et; c < nal * nZ * 2; c += 128) {
+          const int hf = c & 1, az = c >> 1, al = alF + az / nZ, zz = az - (az / nZ) * nZ;
+          const int rl = al * nX - row0 + 8 * hf;
+          float f0[4], f1[4];
 #pragma unroll
-        for (int zz = 0; zz < 16; ++zz) {
-          if (zz >= nZ) break;
-          uint16_t pc[NP];
-          split_f<NP>(__uint_as_float(v[h * 16 + zz]), pc);
-          const long long o = ((long long)al * nZ + zz) * 16;
+          for (int k = 0; k < 4; ++k) {
+            f0[k] = 8 * hf + k < nX ? eh[(rl + k) * 33 + zz] : 0.f;
+            f1[k] = 8 * hf + 4 + k < nX ? eh[(rl + 4 + k) * 33 + zz] : 0.f;
+          }
+          uint2 p0[NP], p1[NP];
+          split4<NP>(f0, p0);
+          split4<NP>(f1, p1);
+          uint16_t* yo = Yo + ((long long)al * nZ + zz) * 16 + 8 * hf;
 #pragma unroll
-          for (int pp = 0; pp < NP; ++pp) Yo[pp * plane + o + x] = pc[pp];
-          if (x == nX - 1)
-            for (int xp = nX; xp < 16; ++xp)
-#pragma unroll
-              for (int pp = 0; pp < NP; ++pp) Yo[pp * plane + o + xp] = 0;
-          if (Yf) {
-            // FP32 copy as [z][alpha][16]; chunk c (16 bytes) of row alpha is
-            // stored at c ^ (2 ((alpha >> 1) & 1)), so that four consecutive rows
-            // reading two adjacent chunks each hit distinct shared-memory banks
+          for (int pp = 0; pp < NP; ++pp)
+            *reinterpret_cast<uint4*>(yo + pp * plane) = make_uint4(p0[pp].x, p0[pp].y, p1[pp].x, p1[pp].y);
+        }
+        // FP32 copy as [z][alpha][16]; chunk c (16 bytes) of row alpha holds
+        // x = 4 (c ^ sw) .. + 3 with sw = 2 ((alpha >> 1) & 1), so that four
+        // consecutive rows read two adjacent chunks each from distinct
+        // shared-memory banks
+        if (Yf) {
+          for (int c = et; c < nal * nZ * 4; c += 128) {
+            const int cq = c & 3, za = c >> 2, zz = za / nal, al = alF + (za - zz * nal);
+            const int x0 = 4 * (cq ^ (2 * ((al >> 1) & 1)));
+            const int rl = al * nX - row0 + x0;
+            float4 o;
+            o.x = x0 < nX ? eh[rl * 33 + zz] : 0.f;
+            o.y = x0 + 1 < nX ? eh[(rl + 1) * 33 + zz] : 0.f;
+            o.z = x0 + 2 < nX ? eh[(rl + 2) * 33 + zz] : 0.f;
+            o.w = x0 + 3 < nX ? eh[(rl + 3) * 33 + zz] : 0.f;
+            *reinterpret_cast<float4*>(Yf + ((long long)zz * mX + al) * 16 + 4 * cq) = o;
+          }
+        }
+        // alphas shared with a neighbouring row tile
+#pragma unroll 1
+        for (int pa = 0; pa < 2; ++pa) {
+          const int al = pa ? alB : alA;
+          if (pa ? (alB <= alL || alB == alA) : (alA >= alF)) continue;
+          const int r0 = max(row0, al * nX), nr = min(rend, (al + 1) * nX) - r0;
+          for (int c = et; c < nr * nZ; c += 128) {
+            const int zz = c / nr, r = r0 + (c - zz * nr), x = r - al * nX;
+            const float y = eh[(r - row0) * 33 + zz];
+            uint16_t pc[NP];
+            split_f<NP>(y, pc);
+            const long long o = ((long long)al * nZ + zz) * 16;
             const int sw = 2 * ((al >> 1) & 1);
-            float* yr = Yf + ((long long)zz * mX + al) * 16;
-            yr[(((x >> 2) ^ sw) << 2) + (x & 3)] = __uint_as_float(v[h * 16 + zz]);
+            float* yr = Yf ? Yf + ((long long)zz * mX + al) * 16 : nullptr;
+#pragma unroll
+            for (int pp = 0; pp < NP; ++pp) Yo[pp * plane + o + x] = pc[pp];
+            if (yr) yr[(((x >> 2) ^ sw) << 2) + (x & 3)] = y;
             if (x == nX - 1)
-              for (int xp = nX; xp < 16; ++xp) yr[(((xp >> 2) ^ sw) << 2) + (xp & 3)] = 0.f;
+              for (int xp = nX; xp < 16; ++xp) {
+#pragma unroll
+                for (int pp = 0; pp < NP; ++pp) Yo[pp * plane + o + xp] = 0;
+                if (yr) yr[(((xp >> 2) ^ sw) << 2) + (xp & 3)] = 0.f;
+              }
           }
         }
       }
+      asm volatile("bar.sync 1, 128;\n" ::: "memory");
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -1173,13 +1241,7 @@ __global__ void __launch_bounds__(192) k_ybuild_umma(DevPlan P, MixPlan X, const
   if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(128));
   if (tid == 0) {
     if (s_abort) atomicExch(err, 1);
-    if (mc == 0) {
-      unsigned long long fl = 0ull;
-      for (int t = 0; t < nq; ++t)
-        for (int i = 0; i < 8; ++i)
-          if (m_d[t * 8 + i] >= 0) fl += 2ull * rows * P.n_ao[P.species[zat[i]]] * P.n_ao[P.species[P.c_j[q0 + t]]];
-      if (fl) atomicAdd(&P.acc[ACC_FY], (double)fl);
-    }
+    if (s_fl) atomicAdd(&P.acc[ACC_FY], (double)s_fl);
   }
 }
 
