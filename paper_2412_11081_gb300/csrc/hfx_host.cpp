@@ -185,6 +185,8 @@ struct hfx_plan {
   int* qcnt = nullptr;
   long long *qoff = nullptr, *q_idx = nullptr;
   int* t1q_list = nullptr;
+  int* t1q_lpt = nullptr;      // the same items, longest (most kept B) first
+  int* lpt_hist = nullptr;
   int* blist = nullptr;
   long long blist_cap = 0;
   int MAmax = 0, MBmax = 0, KSmax = 0, YRmax = 0, ZROWS = 0, KZmax = 0, FC = 0, MC = 0;
@@ -686,6 +688,8 @@ void build_lists(hfx_plan* P, const double* L, const double* pos) {
     P->qoff = P->lalloc<long long>(nC);
     P->q_idx = P->lalloc<long long>(nC);
     P->t1q_list = P->lalloc<int>(nC);
+    P->t1q_lpt = P->lalloc<int>(nC);
+    P->lpt_hist = P->lalloc<int>(hfx::kLptBuckets);
   }
   upload(P->c_ptr, c_ptr, s);
   upload(P->c_home, c_home, s);
@@ -931,6 +935,8 @@ void evaluate(hfx_plan* P, const double* L, hfx_stats* st) {
       ck(hfx::scan_flags(P->qcnt, nullptr, nullptr, nullptr, 4, P->nC, P->qoff, T + 6, P->scan_tmp, s), "scan");
       ck(hfx::scan_flags(P->qcnt, nullptr, nullptr, nullptr, 0, P->nC, P->q_idx, T + 7, P->scan_tmp, s), "scan");
       ck(hfx::scatter_list(P->qcnt, nullptr, nullptr, 0, P->nC, P->q_idx, P->t1q_list, s), "scatter");
+      ck(hfx::launch_lpt_order(P->qcnt, P->t1q_list, P->nC, P->d_tot + 7, P->lpt_hist, P->t1q_lpt, s),
+         "item order");
     }
   }
   ck(cudaMemcpyAsync(P->tot, P->d_tot, kTot * sizeof(long long), cudaMemcpyDeviceToHost, s), "D2H totals");
@@ -974,7 +980,7 @@ void evaluate(hfx_plan* P, const double* L, hfx_stats* st) {
       U.NS = P->t1u_NS;
       U.FS = P->t1u_FS;
       U.seg = P->t1u_seg;
-      U.cu_blk = (long long)P->np * 64 * U.KP + 2LL * 4 * 64 * U.KP;
+      U.cu_blk = (long long)P->np * 64 * U.KP + 2LL * 4 * 64 * hfx::t1u_kp32(U.KP);
       U.vu_blk = (long long)P->np * 4096 + 2LL * 3 * 4096;
       ensure_buf(P, P->Cu, P->Cucap, std::max(1LL, P->tot[7]) * U.cu_blk);
       ensure_buf(P, P->Vu, P->Vucap, std::max(1LL, P->tot[4]) * U.vu_blk);
@@ -985,16 +991,16 @@ void evaluate(hfx_plan* P, const double* L, hfx_stats* st) {
       U.Df = P->Df;
       U.t1_idx = P->t1_idx;
       X.Yf = P->Yf;
-      ck(hfx::launch_t1u_stores(D, U, P->np, P->t1q_list, (int)P->tot[7], P->t1_list, (int)P->tot[4], false, s),
+      ck(hfx::launch_t1u_stores(D, U, P->np, P->t1q_lpt, (int)P->tot[7], P->t1_list, (int)P->tot[4], false, s),
          "term-1 operand stores");
     }
     ck(hfx::launch_ybuild_mma(D, X, P->np, P->y_list, P->gX, P->gS, P->gN, (int)P->tot[9], P->MC, P->zero512, P->d_err, s),
        "ybuild");
     tm.mark();  // 3
     if (P->t1u)
-      ck(hfx::launch_t1_umma(D, X, U, P->np, P->t1q_list, (int)P->tot[7], P->smem_t1u, P->d_work, P->d_err, s), "term1");
+      ck(hfx::launch_t1_umma(D, X, U, P->np, P->t1q_lpt, (int)P->tot[7], P->smem_t1u, P->d_work, P->d_err, s), "term1");
     else
-      ck(hfx::launch_term1_mma(D, X, P->np, P->t1q_list, (int)P->tot[7], P->MAmax, P->MBmax, P->KSmax, P->YRmax,
+      ck(hfx::launch_term1_mma(D, X, P->np, P->t1q_lpt, (int)P->tot[7], P->MAmax, P->MBmax, P->KSmax, P->YRmax,
                                P->smem_m1, s),
          "term1");
     tm.mark();  // 4

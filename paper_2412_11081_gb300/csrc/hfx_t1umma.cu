@@ -29,6 +29,8 @@
 //   warps 8-15  U: one thread per (beta, 4 columns a) of each f
 // All hand-offs are mbarriers (bounded waits; a timeout sets the error flag
 // and every role stops), no block barrier inside the pipeline.
+#include <algorithm>
+
 #include "hfx_device.cuh"
 
 namespace hfx {
@@ -54,12 +56,30 @@ __device__ __forceinline__ bool wait_all(uint32_t mbar, uint32_t parity) {
 }
 
 // ------------------------------------------------------------ operand stores
+// Offset (floats) of element (alpha, col) of a 64-row FP32 plane in the
+// order the epilogue warps load it: epilogue warp qd = alpha >> 4 holds row
+// alpha in lane (alpha & 15) + 16 h and reads columns 32 j + 16 h + 4 t .. + 3
+// as one float4, so that for each (j, t) a warp's 32 loads are 512
+// consecutive bytes.
+__device__ __forceinline__ int ep_off(int alpha, int col) {
+  const int j = col >> 5, h = (col >> 4) & 1, t = (col >> 2) & 3;
+  return ((((j * 4 + t) * 4 + (alpha >> 4)) * 32 + (alpha & 15) + 16 * h) << 2) + (col & 3);
+}
+
+// Inverse of ep_off: the (alpha, col) stored at float w.
+__device__ __forceinline__ void ep_at(int w, int& alpha, int& col) {
+  const int k = w & 3, l = (w >> 2) & 31, qd = (w >> 7) & 3, t = (w >> 9) & 3, j = w >> 11;
+  alpha = qd * 16 + (l & 15);
+  col = 32 * j + 16 * (l >> 4) + 4 * t + k;
+}
+
 // Item kk (C pair q = list[kk]): NP bf16 pieces of C_AF as [alpha (64)][(f,a) (KP)]
 // in core-matrix order (8-row groups of KP/8 core matrices), then C and
-// grad C in FP32 as [4][64][KP].  Zero padded.
+// grad C in FP32 as four planes of 64 x KP32 (KP rounded up to 32) in
+// epilogue load order (ep_off).  Zero padded.
 template <int NP>
 __global__ void k_t1u_cstore(DevPlan P, T1UPlan U, const int* list, int n) {
-  const int KP = U.KP;
+  const int KP = U.KP, KP32 = t1u_kp32(KP), PL = 64 * KP32;
   for (int kk = blockIdx.x; kk < n; kk += gridDim.x) {
     const int q = list[kk];
     const int A = P.c_home[q], F = P.c_j[q];
@@ -74,23 +94,29 @@ __global__ void k_t1u_cstore(DevPlan P, T1UPlan U, const int* list, int n) {
       const int al = e / KP, c = e - al * KP;
       const int f = c >> 4, a = c & 15;
       const bool in = al < mA && f < nF && a < nA;
-      const long long o = in ? ((long long)al * nA + a) * nF + f : 0;
-      const double v = in ? C[o] : 0.0;
       uint16_t pc[NP];
-      split_f<NP>((float)v, pc);
+      split_f<NP>(in ? (float)C[((long long)al * nA + a) * nF + f] : 0.f, pc);
       const int t = (al >> 3) * KP * 8 + (c >> 3) * 64 + (al & 7) * 8 + (c & 7);
 #pragma unroll
       for (int pp = 0; pp < NP; ++pp) out[(long long)pp * 64 * KP + t] = pc[pp];
-      pl[e] = (float)v;
-      pl[64 * KP + e] = in ? (float)dC[o] : 0.f;
-      pl[2 * 64 * KP + e] = in ? (float)dC[ncq + o] : 0.f;
-      pl[3 * 64 * KP + e] = in ? (float)dC[2 * ncq + o] : 0.f;
+    }
+    for (int w = threadIdx.x; w < PL; w += blockDim.x) {   // written in storage order
+      int al, c;
+      ep_at(w, al, c);
+      const int f = c >> 4, a = c & 15;
+      const bool in = al < mA && c < KP && f < nF && a < nA;
+      const long long o = in ? ((long long)al * nA + a) * nF + f : 0;
+      pl[w] = in ? (float)C[o] : 0.f;
+      pl[PL + w] = in ? (float)dC[o] : 0.f;
+      pl[2 * PL + w] = in ? (float)dC[ncq + o] : 0.f;
+      pl[3 * PL + w] = in ? (float)dC[2 * ncq + o] : 0.f;
     }
   }
 }
 
 // Term-1 V pair k (p = list[k]): NP bf16 pieces of V_AB as [alpha (64)][beta (64)]
-// in core-matrix order, then grad V in FP32 as [3][64][64].  Zero padded.
+// in core-matrix order, then grad V in FP32 as three 64 x 64 planes in
+// epilogue load order (ep_off).  Zero padded.
 template <int NP>
 __global__ void k_t1u_vstore(DevPlan P, T1UPlan U, const int* list, int n) {
   for (int k = blockIdx.x; k < n; k += gridDim.x) {
@@ -103,15 +129,20 @@ __global__ void k_t1u_vstore(DevPlan P, T1UPlan U, const int* list, int n) {
     for (int e = threadIdx.x; e < 4096; e += blockDim.x) {
       const int al = e >> 6, be = e & 63;
       const bool in = al < mA && be < mB;
-      const long long o = in ? (long long)al * mB + be : 0;
       uint16_t pc[NP];
-      split_f<NP>(in ? (float)V[o] : 0.f, pc);
+      split_f<NP>(in ? (float)V[(long long)al * mB + be] : 0.f, pc);
       const int t = (al >> 3) * 512 + (be >> 3) * 64 + (al & 7) * 8 + (be & 7);
 #pragma unroll
       for (int pp = 0; pp < NP; ++pp) out[pp * 4096 + t] = pc[pp];
-      pl[e] = in ? (float)V[nv + o] : 0.f;
-      pl[4096 + e] = in ? (float)V[2 * nv + o] : 0.f;
-      pl[2 * 4096 + e] = in ? (float)V[3 * nv + o] : 0.f;
+    }
+    for (int w = threadIdx.x; w < 4096; w += blockDim.x) {   // written in storage order
+      int al, be;
+      ep_at(w, al, be);
+      const bool in = al < mA && be < mB;
+      const long long o = in ? (long long)al * mB + be : 0;
+      pl[w] = in ? (float)V[nv + o] : 0.f;
+      pl[4096 + w] = in ? (float)V[2 * nv + o] : 0.f;
+      pl[2 * 4096 + w] = in ? (float)V[3 * nv + o] : 0.f;
     }
   }
 }
@@ -131,11 +162,56 @@ __global__ void k_t1u_dstore(DevPlan P, float* Df) {
   }
 }
 
+// ------------------------------------------------- longest-first item order
+// Items run on a dynamic queue; handing out the ones with the most kept B
+// first keeps the last items short, so the SMs finish together.  Counting
+// sort on the key (kLptBuckets - 1 - min(qcnt, kLptBuckets - 1)); the order
+// of equal keys is not fixed (it does not change any item's result).
+__global__ void k_lpt_hist(const int* qcnt, const int* list, const long long* n_dev, int* hist) {
+  const int n = (int)*n_dev;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    atomicAdd(&hist[kLptBuckets - 1 - min(qcnt[list[i]], kLptBuckets - 1)], 1);
+}
+
+// Exclusive scan of the histogram, one block of 1024 threads.
+__global__ void __launch_bounds__(1024) k_lpt_scan(int* hist) {
+  constexpr int kPer = kLptBuckets / 1024;
+  __shared__ int part[1024];
+  int v[kPer], t = 0;
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    v[j] = hist[threadIdx.x * kPer + j];
+    t += v[j];
+  }
+  part[threadIdx.x] = t;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    const int add = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0;
+    __syncthreads();
+    part[threadIdx.x] += add;
+    __syncthreads();
+  }
+  int run = part[threadIdx.x] - t;
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    hist[threadIdx.x * kPer + j] = run;
+    run += v[j];
+  }
+}
+
+__global__ void k_lpt_scatter(const int* qcnt, const int* list, const long long* n_dev, int* hist, int* out) {
+  const int n = (int)*n_dev;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int q = list[i];
+    out[atomicAdd(&hist[kLptBuckets - 1 - min(qcnt[q], kLptBuckets - 1)], 1)] = q;
+  }
+}
+
 // ------------------------------------------------------------------- kernel
 template <int NP>
 __global__ void __launch_bounds__(kThreads, 1)
     k_t1_umma(DevPlan P, MixPlan X, T1UPlan U, const int* qlist, int n_list, int* work, int* err) {
-  const int KP = U.KP, NF = KP >> 4, FH = (NF + 1) >> 1, NS = U.NS, SEG = U.seg, FS = U.FS;
+  const int KP = U.KP, KP32 = t1u_kp32(KP), NF = KP >> 4, FH = (NF + 1) >> 1, NS = U.NS, SEG = U.seg, FS = U.FS;
   const int SLOT = FS * 64 * 16;                 // floats of one Y slot (FS rows f of up to 64 beta)
   constexpr int NPROD = NP * (NP + 1) / 2;       // piece products (i, j) with i + j < NP
   const uint32_t CPB = 64u * KP * 2u;            // bytes of one piece of C or U
@@ -510,14 +586,14 @@ __global__ void __launch_bounds__(kThreads, 1)
           // fetched before the wait; they do not depend on R)
           float gv[3] = {0.f, 0.f, 0.f};
           float4 w[3][4];
+          const float4* dV4 = reinterpret_cast<const float4*>(dV) + qd * 32 + lane;   // ep_off order
           {
             const int cb = 16 * half;
             if (alpha < mA && cb < mB)
 #pragma unroll
               for (int c = 0; c < 3; ++c)
 #pragma unroll
-                for (int t4 = 0; t4 < 4; ++t4)
-                  w[c][t4] = reinterpret_cast<const float4*>(dV + c * 4096 + alpha * 64 + cb)[t4];
+                for (int t4 = 0; t4 < 4; ++t4) w[c][t4] = dV4[c * 1024 + t4 * 128];
           }
           ok = wait_all(rf + 8 * rbuf, (rb >> 1) & 1);
           tc_fence_after();
@@ -530,8 +606,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                 for (int c = 0; c < 3; ++c)
 #pragma unroll
-                  for (int t4 = 0; t4 < 4; ++t4)
-                    w[c][t4] = reinterpret_cast<const float4*>(dV + c * 4096 + alpha * 64 + cb)[t4];
+                  for (int t4 = 0; t4 < 4; ++t4) w[c][t4] = dV4[c * 1024 + 512 + t4 * 128];
               uint32_t v[32];
               tmem_ld32(tl + kRCol + 64u * rbuf + c0, v);
               float x[16];
@@ -586,11 +661,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                   float s4[4];
 #pragma unroll
                   for (int c = 0; c < 4; ++c) {
-                    const float4* src = reinterpret_cast<const float4*>(Cf + (long long)c * 64 * KP + alpha * KP + cb);
+                    const float4* src =
+                        reinterpret_cast<const float4*>(Cf + (long long)c * 64 * KP32) + (c0 >> 5) * 512 + qd * 32 + lane;
                     float s = 0.f;
 #pragma unroll
                     for (int t4 = 0; t4 < 4; ++t4) {
-                      const float4 w = src[t4];
+                      const float4 w = src[t4 * 128];
                       s = fmaf(w.x, x[4 * t4], s);
                       s = fmaf(w.y, x[4 * t4 + 1], s);
                       s = fmaf(w.z, x[4 * t4 + 2], s);
@@ -838,6 +914,19 @@ cudaError_t launch_t1u_stores(const DevPlan& P, const T1UPlan& U, int np, const 
     const long long g = P.n_d < 152 * 16 ? P.n_d : 152 * 16;
     k_t1u_dstore<<<(unsigned)g, 256, 0, s>>>(P, U.Df);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lpt_order(const int* qcnt, const int* list, int n_max, const long long* n_dev, int* hist, int* out,
+                             cudaStream_t s) {
+  if (n_max <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(hist, 0, kLptBuckets * sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  g_t1u_launches += 3;
+  const int g = std::min((n_max + 255) / 256, 152 * 8);
+  k_lpt_hist<<<g, 256, 0, s>>>(qcnt, list, n_dev, hist);
+  k_lpt_scan<<<1, 1024, 0, s>>>(hist);
+  k_lpt_scatter<<<g, 256, 0, s>>>(qcnt, list, n_dev, hist, out);
   return cudaGetLastError();
 }
 
