@@ -113,23 +113,33 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, int b_mn) {
 // memory pipe (which the tensor cores' operand reads also use).
 constexpr uint32_t kTryNs = 20000;
 
+template <uint32_t HintNs = kTryNs>
 __device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
   uint32_t done;
-  asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
-               : "=r"(done)
-               : "r"(mbar), "r"(parity), "r"(kTryNs)
-               : "memory");
+  if (HintNs) {
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(done)
+                 : "r"(mbar), "r"(parity), "r"(HintNs)
+                 : "memory");
+  } else {
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(done)
+                 : "r"(mbar), "r"(parity)
+                 : "memory");
+  }
   return done != 0;
 }
 
 // Wait for the phase of the given parity to complete; false once kWaitNs has
-// passed without it (the caller then records an error and stops).
+// passed without it (the caller then records an error and stops).  HintNs is
+// the suspend-time hint of each test (0: the hardware's own default).
+template <uint32_t HintNs = kTryNs>
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-  if (mbar_try(mbar, parity)) return true;
+  if (mbar_try<HintNs>(mbar, parity)) return true;
   const unsigned long long t0 = global_ns();
   for (;;) {
     for (int i = 0; i < 64; ++i)
-      if (mbar_try(mbar, parity)) return true;
+      if (mbar_try<HintNs>(mbar, parity)) return true;
     if (global_ns() - t0 > kWaitNs) return false;
   }
 }

@@ -186,6 +186,10 @@ struct hfx_plan {
   long long *qoff = nullptr, *q_idx = nullptr;
   int* t1q_list = nullptr;
   int* t1q_lpt = nullptr;      // the same items, longest (most kept B) first
+  int q2_flush = 32;           // pairs per FP32 run of the second product's Q2 accumulator
+  int* ytab = nullptr;         // D-block tables of the Y build and the second product
+  int* q2tab = nullptr;
+  long long ytabcap = 0, q2tabcap = 0;
   int* lpt_hist = nullptr;
   int* blist = nullptr;
   long long blist_cap = 0;
@@ -193,7 +197,7 @@ struct hfx_plan {
   long long zblk = 0;
   uint16_t* Zst = nullptr;
   long long Zcap = 0;
-  uint16_t* zero512 = nullptr;   // 512 zero bf16 (absent D blocks in tensor-core tiles)
+  hfx::DRows drows{};          // tensor map of the D piece rows
   int maxV = 0;                  // most V-pair candidates of one home atom
   size_t smem_m1 = 0, smem_m2 = 0;
   // tcgen05 first product (n_abf <= 64, n_ao <= 16): operand stores and shape
@@ -666,7 +670,7 @@ void build_lists(hfx_plan* P, const double* L, const double* pos) {
       const int sA = P->species[c_home[p]], sj = P->species[c_j[p]];
       const long long rows = (long long)P->n_abf[sA] * P->n_ao[sA];
       // bf16 tiles then FP32 grad C; each block rounded to 128 bytes (bulk copies need 16-byte alignment)
-      const long long sz = P->np * ((rows + 127) / 128) * 2048 + 2 * 3 * rows * P->n_ao[sj];
+      const long long sz = P->np * ((rows + 127) / 128) * 2048 + 2 * 3 * ((rows + 127) / 128) * 2048;
       cm_off[p + 1] = cm_off[p] + (sz + 63) / 64 * 64;
     }
     for (int p = 0; p < nV; ++p) {
@@ -818,6 +822,8 @@ void setup_shapes(hfx_plan* P) {
     }
     if (P->smem_m2 > limit || maxAO > 16)
       fail(HFX_ERR_UNSUPPORTED, "block shapes too large for the split-precision kernels");
+    const char* qf = std::getenv("HFX_Q2_FLUSH");
+    P->q2_flush = qf ? std::max(1, std::atoi(qf)) : 32;
     ck(hfx::set_mixed_smem_limits(P->np, P->t1u ? 0 : P->smem_m1, P->smem_m2), "smem attributes");
   }
 }
@@ -832,8 +838,28 @@ void split_density(hfx_plan* P) {
     off[k + 1] = off[k] + (long long)P->np * a * b;
   }
   P->dsp_off = P->mem.alloc<long long>(P->n_d + 1);
-  P->Dsp = P->mem.alloc<uint16_t>(off[P->n_d]);
+  P->Dsp = P->mem.alloc<uint16_t>(off[P->n_d] + 256);   // + one zero row (absent blocks)
   upload(P->dsp_off, off, P->stream);
+  ck(cudaMemsetAsync(P->Dsp + off[P->n_d], 0, 256 * sizeof(uint16_t), P->stream), "memset");
+  {   // the split path holds n_ao <= 16: every piece is one 16 x 16 block of 512 bytes
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    ck(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q), "driver entry");
+    if (!fn || q != cudaDriverEntryPointSuccess) fail(HFX_ERR_CUDA, "cuTensorMapEncodeTiled not available");
+    using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    const long long rows = off[P->n_d] / 256 + 1;
+    const cuuint64_t dims[2] = {256, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {512};
+    const cuuint32_t box[2] = {256, 1}, estr[2] = {1, 1};
+    const CUresult r = reinterpret_cast<Encode>(fn)(&P->drows.map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, P->Dsp, dims,
+                                                    strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) fail(HFX_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+    P->drows.zero_row = (int)(rows - 1);
+  }
   DevPlan D = make_devplan(P, P->lat_ref.data());
   hfx::MixPlan X{P->Dsp, P->dsp_off, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   ck(hfx::launch_dsplit(D, X, P->np, P->stream), "dsplit");
@@ -970,10 +996,6 @@ void evaluate(hfx_plan* P, const double* L, hfx_stats* st) {
     ck(hfx::launch_vblocks(D, P->v_list, (int)P->tot[3], s), "vblocks");
     ck(hfx::launch_vpieces(D, X, P->np, P->v_list, (int)P->tot[3], s), "vpieces");
     ck(hfx::launch_cpieces(D, X, P->np, s), "cpieces");
-    if (!P->zero512) {
-      P->zero512 = P->mem.alloc<uint16_t>(512);
-      ck(cudaMemsetAsync(P->zero512, 0, 512 * sizeof(uint16_t), s), "memset");
-    }
     hfx::T1UPlan U{};
     if (P->t1u) {
       U.KP = P->t1u_KP;
@@ -994,7 +1016,10 @@ void evaluate(hfx_plan* P, const double* L, hfx_stats* st) {
       ck(hfx::launch_t1u_stores(D, U, P->np, P->t1q_lpt, (int)P->tot[7], P->t1_list, (int)P->tot[4], false, s),
          "term-1 operand stores");
     }
-    ck(hfx::launch_ybuild_mma(D, X, P->np, P->y_list, P->gX, P->gS, P->gN, (int)P->tot[9], P->MC, P->zero512, P->d_err, s),
+    ensure_buf(P, P->ytab, P->ytabcap, std::max(1LL, hfx::ytab_size((int)P->tot[9], P->maxC)));
+    X.ytab = P->ytab;
+    X.ytab_stride = 8 * P->maxC;
+    ck(hfx::launch_ybuild_mma(D, X, P->np, P->y_list, P->gX, P->gS, P->gN, (int)P->tot[9], P->MC, P->drows, P->d_err, s),
        "ybuild");
     tm.mark();  // 3
     if (P->t1u)
@@ -1008,14 +1033,12 @@ void evaluate(hfx_plan* P, const double* L, hfx_stats* st) {
       ensure_buf(P, P->Zst, P->Zcap, P->tot[5] * P->zblk);
       ck(cudaMemsetAsync(P->Zst, 0, (size_t)P->Zcap * sizeof(uint16_t), s), "memset");   // tile padding rows stay zero
     }
-    if (!P->zero512) {
-      P->zero512 = P->mem.alloc<uint16_t>(512);
-      ck(cudaMemsetAsync(P->zero512, 0, 512 * sizeof(uint16_t), s), "memset");
-    }
     X.Zst = P->Zst;
     const int FC = (P->maxC + 3) / 4;
+    ensure_buf(P, P->q2tab, P->q2tabcap, std::max(1LL, hfx::q2tab_size((int)P->tot[5], FC)));
+    X.q2tab = P->q2tab;
     ck(hfx::launch_term2_mma(D, X, P->np, P->t2_list, P->t2_idx, (int)P->tot[5], P->MAmax, P->KZmax, P->zblk, P->ZROWS,
-                             FC, P->MC, hfx::q2_umma_segments(P->maxV), P->zero512, P->smem_m2, P->d_err, s),
+                             FC, P->MC, hfx::q2_umma_segments(P->maxV), P->q2_flush, P->drows, P->smem_m2, P->d_err, s),
        "term2");
     tm.mark();  // 5
   }

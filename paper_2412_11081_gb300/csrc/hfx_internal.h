@@ -5,6 +5,7 @@
 #include <cstddef>
 #include <cstdint>
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace hfx {
@@ -107,7 +108,19 @@ struct MixPlan {
   long long* qoff;             // [nC] offsets into blist
   int* blist;                  // V pairs (A,B) per (A,F), in V-pair order
   float* Yf = nullptr;         // Y^{XZ} in FP32 as [z][alpha][16], offsets y_off / np (tcgen05 term 1 only)
+  int* ytab = nullptr;         // Y build: D block (256-element units) per (key group, C slot t, key i), or -1
+  int ytab_stride = 0;         // ints per key group (8 * most C pairs of an atom)
+  int* q2tab = nullptr;        // second product: D block per (group of 8 C slots, pair slot, i), or -1
 };
+
+// Element (row, f < 16) of one component of grad C_AF (FP32) in the C operand
+// store, rows (alpha, a) in 128-row tiles: within a tile, four 128 x 4 column
+// groups, a row's four values contiguous, so that 32 consecutive rows read
+// one column group as 512 consecutive bytes.  A component spans
+// ceil(rows / 128) * 2048 floats.
+__host__ __device__ inline int gc_off(int row, int f) {
+  return ((((row >> 7) * 4 + (f >> 2)) * 128 + (row & 127)) << 2) + (f & 3);
+}
 
 // Operand stores of the tcgen05 first-product kernel (hfx_t1umma.cu).
 struct T1UPlan {
@@ -153,9 +166,19 @@ cudaError_t launch_cpieces(const DevPlan& P, const MixPlan& X, int np, cudaStrea
 cudaError_t launch_vpieces(const DevPlan& P, const MixPlan& X, int np, const int* list, int n, cudaStream_t s);
 cudaError_t launch_ygroups(const DevPlan& P, const long long* y_idx, const long long* y_total, int* gcnt,
                            const long long* goff, int* gX, int* gS, int* gN, int phase, cudaStream_t s);
+// The D piece store viewed as a 2-D tensor of 512-byte rows (one row per
+// bf16 piece of a 16 x 16 block, row dsp_off / 256 + piece; the last row is
+// zero), fetched four rows at a time by the tensor-core kernels.
+struct DRows {
+  CUtensorMap map;             // box: one row of 256 bf16
+  int zero_row;
+};
 cudaError_t launch_ybuild_mma(const DevPlan& P, const MixPlan& X, int np, const int* ylist, const int* gX,
-                              const int* gS, const int* gN, int ngroups, int MC, const uint16_t* zero512, int* err,
+                              const int* gS, const int* gN, int ngroups, int MC, const DRows& drows, int* err,
                               cudaStream_t s);
+// ints of the D-block tables (MixPlan::ytab, MixPlan::q2tab)
+long long ytab_size(int ngroups, int maxC);
+long long q2tab_size(int n_slots, int FC);
 cudaError_t launch_t1_lists(const DevPlan& P, const MixPlan& X, int phase, cudaStream_t s);
 size_t term1_mma_smem(int np, int MAmax, int MBmax, int KSmax, int YRmax);
 size_t term2_mma_smem(int np, int MAmax, int KZmax);
@@ -164,7 +187,7 @@ cudaError_t launch_term1_mma(const DevPlan& P, const MixPlan& X, int np, const i
                              int MBmax, int KSmax, int YRmax, size_t smem, cudaStream_t s);
 cudaError_t launch_term2_mma(const DevPlan& P, const MixPlan& X, int np, const int* list, const long long* slot0,
                              int n, int MAmax, int KZmax, long long zblk, int zrows, int FC, int MC, int nseg,
-                             const uint16_t* zero512, size_t smem, int* err, cudaStream_t s);
+                             int flush, const DRows& drows, size_t smem, int* err, cudaStream_t s);
 int q2_umma_segments(int max_pairs_per_atom);
 
 // tcgen05 first exchange product (hfx_t1umma.cu): shapes n_abf <= 64, n_ao <= 16.

@@ -175,8 +175,13 @@ __global__ void k_cpieces(DevPlan P, MixPlan X) {
 #pragma unroll
       for (int p = 0; p < NP; ++p) out[((r >> 7) * NP + p) * 2048 + tix(r & 127, c)] = pc[p];
     }
+    // grad C in FP32, three components in the tile order of gc_off (written in storage order)
     float* g = reinterpret_cast<float*>(out + NP * nt * 2048);
-    for (int e = threadIdx.x; e < 3 * rows * nF; e += blockDim.x) g[e] = (float)dC[e];
+    for (int w = threadIdx.x; w < 3 * nt * 2048; w += blockDim.x) {
+      const int c = w / (nt * 2048), wi = w - c * nt * 2048;
+      const int r = ((wi >> 11) << 7) + ((wi >> 2) & 127), ff = (((wi >> 9) & 3) << 2) + (wi & 3);
+      g[w] = (r < rows && ff < nF) ? (float)dC[(long long)c * rows * nF + (long long)r * nF + ff] : 0.f;
+    }
   }
 }
 
@@ -294,7 +299,7 @@ __global__ void __launch_bounds__(kWarps1 * 32) k_term1_mma(DevPlan P, MixPlan X
       for (int c = 0; c < 4; ++c) qacc[i][c] = 0.f;
     double g[3] = {0.0, 0.0, 0.0};
     const float* dC = reinterpret_cast<const float*>(Cq + (long long)NP * ctiles * 2048);   // grad C, FP32
-    const long long ncq = (long long)mA * KAF;
+    const long long ncq = (long long)ctiles * 2048;   // floats per grad C component
     const long long b0i = X.qoff[q], nbt = X.qcnt[q];
     unsigned long long fl = 0ull;
     int lastmB = -1;
@@ -530,7 +535,8 @@ __global__ void __launch_bounds__(kWarps1 * 32) k_term1_mma(DevPlan P, MixPlan X
               const int al = mt * 16 + gid + ((c & 2) ? 8 : 0);
               const int n = nt * 8 + 2 * tig + (c & 1);
               if (al < mA && n < KAF) {
-                const long long o = (long long)al * KAF + n;
+                const int a = n / nF;
+                const int o = gc_off(al * nA + a, n - a * nF);
                 const float v = qacc[i][c];
                 gf[0] = fmaf(dC[o], v, gf[0]);
                 gf[1] = fmaf(dC[ncq + o], v, gf[1]);
@@ -714,19 +720,50 @@ __global__ void __launch_bounds__(kWarps * 32) k_term2_pairs(DevPlan P, MixPlan 
 namespace umma {
 
 constexpr int kStages = 4;
+constexpr uint32_t kMixTryNs = kTryNs;   // suspend hint of the pipeline waits
 constexpr int kTileElems = 128 * 16;     // bf16 elements of one 128 x 16 operand tile (one piece)
 constexpr int kMetaPairs = 1024;         // pairs per CTA segment (metadata in shared memory)
-constexpr int kFlushPairs = 32;
 
 // K-major operand tiles: K-adjacent core matrices 128 bytes apart, 8-row groups 256 bytes apart
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) { return sdesc2(saddr, 128, 256); }
+
+// Four 512-byte rows r0..r3 of the D piece store (tensor map of DRows) to
+// consecutive shared memory at sdst (128-byte aligned), completion counted in
+// bytes on mbar.
+__device__ __forceinline__ void gather4_rows(uint32_t sdst, const CUtensorMap* map, int r0, int r1, int r2, int r3,
+                                             uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cta.global.tile::gather4.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+      "%5, %6}], [%7];\n" ::"r"(sdst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(r0), "r"(r1), "r"(r2), "r"(r3), "r"(mbar)
+      : "memory");
+}
+
+// Stage the B operand of one K step: D rows of the eight keys i (row md[i] +
+// piece, the zero row where md[i] < 0), piece pp and key half h by lane
+// 1 + 2 pp + h.
+template <int NP>
+__device__ __forceinline__ void stage_d(int lane, uint16_t* stB, const int* md, const CUtensorMap* map, int zrow,
+                                        uint32_t mbar) {
+  if (lane >= 1 && lane <= 2 * NP) {
+    const int pp = (lane - 1) >> 1, h = (lane - 1) & 1;
+    int r[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int d = md[4 * h + j];
+      r[j] = d >= 0 ? d + pp : zrow;
+    }
+    gather4_rows((uint32_t)__cvta_generic_to_shared(stB + (size_t)pp * kTileElems + 4 * h * 256), map, r[0], r[1], r[2],
+                 r[3], mbar);
+  }
+}
 
 }  // namespace umma
 
 template <int NP>
 __global__ void __launch_bounds__(192) k_q2_umma(DevPlan P, MixPlan X, const int* list, const long long* slot0,
                                                  int n_slots, int FC8, int MC, int NSEG, long long zblk,
-                                                 const uint16_t* zero512, int* err) {
+                                                 int flush, const __grid_constant__ DRows drows, int* err) {
   // Warp roles: warp 0 lane 0 produces (bulk async copies into a 4-stage
   // ring, completion counted in bytes on full[s]); warp 1 lane 0 issues the
   // MMAs (all piece products of a pair into one of two TMEM accumulators,
@@ -741,7 +778,8 @@ __global__ void __launch_bounds__(192) k_q2_umma(DevPlan P, MixPlan X, const int
   __shared__ __align__(8) uint64_t bar_full[kStages], bar_empty[kStages], bar_accf[2], bar_acce[2];
   __shared__ uint32_t tmem_base;
   __shared__ double sg[8][3];
-  __shared__ unsigned long long s_fl;
+  __shared__ int m_q[kMetaPairs];
+  __shared__ int s_nsteps;
   __shared__ int s_abort;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   int rem = blockIdx.x;
@@ -753,7 +791,7 @@ __global__ void __launch_bounds__(192) k_q2_umma(DevPlan P, MixPlan X, const int
   const int A = rem / FC8;
   const int sA = P.species[A];
   const int nA = P.n_ao[sA], mA = P.n_abf[sA];
-  const int rows = mA * nA;
+  const int rows = mA * nA, nt = (rows + 127) >> 7;
   const int q0 = P.c_ptr[A], nq = P.c_ptr[A + 1] - q0;
   if (fc * 8 >= nq || mc * 128 >= rows) return;
   const long long s0 = slot0[P.v_ptr[A]];
@@ -762,31 +800,16 @@ __global__ void __launch_bounds__(192) k_q2_umma(DevPlan P, MixPlan X, const int
   const int np = (int)max(0ll, min((long long)kMetaPairs, s1 - p0));
   if (np <= 0) return;
   const int row0 = mc * 128;
-  int qf[8], nF[8];
+  int qf[8];
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     const int j = fc * 8 + i;
     qf[i] = (j < nq && P.c_keep[q0 + j]) ? q0 + j : -1;
-    nF[i] = qf[i] >= 0 ? P.n_ao[P.species[P.c_j[qf[i]]]] : 0;
   }
-  // D block (units of 256 elements) of every (pair, F), or -1; the flops of
-  // the kept (pair, F) are counted here (once per pair, by the mc = 0 CTA)
-  unsigned long long fl = 0ull;
-  for (int e = tid; e < np * 8; e += blockDim.x) {
-    const int t = e >> 3, i = e & 7;
-    int db = -1;
-    if (qf[i] >= 0) {
-      const int p = list[p0 + t];
-      const int b = P.v_j[p];
-      const int* Rb = P.v_R + 3 * p;
-      const int* Rf = P.c_R + 3 * qf[i];
-      const int d = dlut_get(P, P.c_j[qf[i]], b, Rb[0] - Rf[0], Rb[1] - Rf[1], Rb[2] - Rf[2]);
-      if (d >= 0 && P.Dkept[d] != 0.0) {
-        db = (int)(X.dsp_off[d] >> 8);
-        if (mc == 0) fl += 2ull * mA * nA * P.n_ao[P.species[b]] * nF[i];
-      }
-    }
-    m_dblk[e] = db;
+  // D block (units of 256 elements) of every (pair, F), or -1, from the table
+  {
+    const int4* tab = reinterpret_cast<const int4*>(X.q2tab + ((long long)fc * n_slots + p0) * 8);
+    for (int e = tid; e < np * 2; e += blockDim.x) reinterpret_cast<int4*>(m_dblk)[e] = tab[e];
   }
   const uint32_t mfull = (uint32_t)__cvta_generic_to_shared(&bar_full[0]);
   const uint32_t mempty = (uint32_t)__cvta_generic_to_shared(&bar_empty[0]);
@@ -795,7 +818,6 @@ __global__ void __launch_bounds__(192) k_q2_umma(DevPlan P, MixPlan X, const int
   if (tid < 24) sg[tid / 3][tid % 3] = 0.0;
   if (tid == 0) {
     s_abort = 0;
-    s_fl = 0ull;
     for (int s = 0; s < kStages; ++s) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mfull + 8 * s));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mempty + 8 * s));
@@ -813,44 +835,46 @@ __global__ void __launch_bounds__(192) k_q2_umma(DevPlan P, MixPlan X, const int
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
+  if (warp == 0) {   // K steps: pairs with a kept D block for at least one of the 8 F, in order
+    int n = 0;
+    for (int t0 = 0; t0 < np; t0 += 32) {
+      const int t = t0 + lane;
+      bool any = false;
+      if (t < np) {
+        const int4 u = *reinterpret_cast<const int4*>(m_dblk + t * 8);
+        const int4 v = *reinterpret_cast<const int4*>(m_dblk + t * 8 + 4);
+        any = !(u.x < 0 && u.y < 0 && u.z < 0 && u.w < 0 && v.x < 0 && v.y < 0 && v.z < 0 && v.w < 0);
+      }
+      const unsigned bal = __ballot_sync(0xffffffffu, any);
+      if (any) m_q[n + __popc(bal & ((1u << lane) - 1u))] = t;
+      n += __popc(bal);
+    }
+    if (lane == 0) s_nsteps = n;
+  }
+  __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t taddr = tmem_base;
-  const int nruns = (np + kFlushPairs - 1) / kFlushPairs;
-  fl = warp_sum_u64(fl);
-  if (lane == 0 && fl) atomicAdd(&s_fl, fl);
+  const int nsteps = s_nsteps;
+  const int nruns = (nsteps + flush - 1) / flush;
 
   if (warp == 0) {
     // producer warp: every lane waits for the stage, then lanes issue the
     // copies of one stage in parallel (lane 0 also posts the byte count)
     const uint32_t bytes = (uint32_t)NP * 2 * kTileElems * 2;
-    for (int k = 0; k < np; ++k) {
+    for (int k = 0; k < nsteps; ++k) {
       const int s = k % kStages;
-      if (k >= kStages && !mbar_wait(mempty + 8 * s, (uint32_t)((k / kStages - 1) & 1))) s_abort = 1;
+      const int t = m_q[k];
+      if (k >= kStages && !mbar_wait<kMixTryNs>(mempty + 8 * s, (uint32_t)((k / kStages - 1) & 1))) s_abort = 1;
       __syncwarp();
       if (s_abort) break;
-      if (lane == 0)
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mfull + 8 * s), "r"(bytes)
-                     : "memory");
-      // copy c < NP: Z piece tile (4 KB); c = NP + pp * 8 + i: D block i of piece pp (512 B)
-      for (int c = lane; c < NP * 9; c += 32) {
-        uint32_t dst;
-        const uint16_t* src;
-        uint32_t nb;
-        if (c < NP) {
-          dst = (uint32_t)__cvta_generic_to_shared(stA + ((size_t)s * NP + c) * kTileElems);
-          src = X.Zst + (p0 + k) * zblk + ((long long)mc * NP + c) * kTileElems;
-          nb = kTileElems * 2;
-        } else {
-          const int pp = (c - NP) >> 3, i = (c - NP) & 7;
-          const int db = m_dblk[k * 8 + i];
-          dst = (uint32_t)__cvta_generic_to_shared(stB + ((size_t)s * NP + pp) * kTileElems + i * 256);
-          src = db >= 0 ? X.Dsp + (long long)db * 256 + pp * 256 : zero512;
-          nb = 512;
-        }
-        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
-                     "l"(src), "r"(nb), "r"(mfull + 8 * s)
-                     : "memory");
+      // lane 0: the NP Z piece tiles of row tile mc (contiguous, one copy);
+      // lanes 1 .. 2 NP: the eight D blocks of each piece, four per gather
+      if (lane == 0) {
+        mbar_expect_tx(mfull + 8 * s, bytes);
+        bulk_g2s((uint32_t)__cvta_generic_to_shared(stA + (size_t)s * NP * kTileElems),
+                 X.Zst + (p0 + t) * zblk + (long long)mc * NP * kTileElems, (uint32_t)NP * kTileElems * 2, mfull + 8 * s);
       }
+      stage_d<NP>(lane, stB + (size_t)s * NP * kTileElems, m_dblk + t * 8, &drows.map, drows.zero_row, mfull + 8 * s);
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -858,17 +882,17 @@ __global__ void __launch_bounds__(192) k_q2_umma(DevPlan P, MixPlan X, const int
       const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
       for (int r = 0; r < nruns && !s_abort; ++r) {
         const int b = r & 1;
-        if (r >= 2 && !mbar_wait(macce + 8 * b, (uint32_t)((r / 2 - 1) & 1))) {
+        if (r >= 2 && !mbar_wait<kMixTryNs>(macce + 8 * b, (uint32_t)((r / 2 - 1) & 1))) {
           s_abort = 1;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         const uint32_t dacc = taddr + 128u * b;
-        const int k1 = min(np, (r + 1) * kFlushPairs);
+        const int k1 = min(nsteps, (r + 1) * flush);
         bool first = true;
-        for (int k = r * kFlushPairs; k < k1; ++k) {
+        for (int k = r * flush; k < k1; ++k) {
           const int s = k % kStages;
-          if (!mbar_wait(mfull + 8 * s, (uint32_t)((k / kStages) & 1))) {
+          if (!mbar_wait<kMixTryNs>(mfull + 8 * s, (uint32_t)((k / kStages) & 1))) {
             s_abort = 1;
             break;
           }
@@ -900,13 +924,12 @@ __global__ void __launch_bounds__(192) k_q2_umma(DevPlan P, MixPlan X, const int
     const int q = warp & 3;
     const int r = row0 + q * 32 + lane;
     const bool rv = r < rows;
-    const int al = rv ? r / nA : 0, a = rv ? r - al * nA : 0;
     double gd[8][3];
 #pragma unroll
     for (int i = 0; i < 8; ++i) gd[i][0] = gd[i][1] = gd[i][2] = 0.0;
     for (int run = 0; run < nruns; ++run) {
       const int b = run & 1;
-      if (!mbar_wait(maccf + 8 * b, (uint32_t)((run / 2) & 1))) {
+      if (!mbar_wait<kMixTryNs>(maccf + 8 * b, (uint32_t)((run / 2) & 1))) {
         s_abort = 1;
         break;
       }
@@ -919,19 +942,24 @@ __global__ void __launch_bounds__(192) k_q2_umma(DevPlan P, MixPlan X, const int
         for (int h = 0; h < 2; ++h) {
           const int i = (c0 >> 4) + h;
           if (!rv || qf[i] < 0) continue;
-          const int KAF = nA * nF[i];
-          const long long ncq = (long long)mA * KAF;
-          const float* dC =
-              reinterpret_cast<const float*>(X.Cm + X.cm_off[qf[i]] + (long long)NP * ((rows + 127) >> 7) * 2048);
-          const long long o = (long long)al * KAF + a * nF[i];
+          // grad C_AF rows in gc_off order: the warp's 32 rows of one 4-column
+          // group are 512 consecutive bytes; columns f >= n_ao(F) are zero on
+          // both sides
+          const float4* dC4 = reinterpret_cast<const float4*>(X.Cm + X.cm_off[qf[i]] + (long long)NP * nt * 2048) +
+                              (r >> 7) * 512 + (r & 127);
+          float4 w[3][4];
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int f4 = 0; f4 < 4; ++f4) w[c][f4] = dC4[c * nt * 512 + f4 * 128];
           float g0 = 0.f, g1 = 0.f, g2 = 0.f;
 #pragma unroll
-          for (int ff = 0; ff < 16; ++ff) {
-            if (ff >= nF[i]) break;
-            const float x = __uint_as_float(v[h * 16 + ff]);
-            g0 = fmaf(dC[o + ff], x, g0);
-            g1 = fmaf(dC[ncq + o + ff], x, g1);
-            g2 = fmaf(dC[2 * ncq + o + ff], x, g2);
+          for (int f4 = 0; f4 < 4; ++f4) {
+            const float x0 = __uint_as_float(v[h * 16 + 4 * f4]), x1 = __uint_as_float(v[h * 16 + 4 * f4 + 1]);
+            const float x2 = __uint_as_float(v[h * 16 + 4 * f4 + 2]), x3 = __uint_as_float(v[h * 16 + 4 * f4 + 3]);
+            g0 = fmaf(w[0][f4].x, x0, fmaf(w[0][f4].y, x1, fmaf(w[0][f4].z, x2, fmaf(w[0][f4].w, x3, g0))));
+            g1 = fmaf(w[1][f4].x, x0, fmaf(w[1][f4].y, x1, fmaf(w[1][f4].z, x2, fmaf(w[1][f4].w, x3, g1))));
+            g2 = fmaf(w[2][f4].x, x0, fmaf(w[2][f4].y, x1, fmaf(w[2][f4].z, x2, fmaf(w[2][f4].w, x3, g2))));
           }
           gd[i][0] += (double)g0;
           gd[i][1] += (double)g1;
@@ -958,10 +986,7 @@ __global__ void __launch_bounds__(192) k_q2_umma(DevPlan P, MixPlan X, const int
     const int i = tid / 3, c = tid % 3;
     if (qf[i] >= 0 && sg[i][c] != 0.0) atomicAdd(&P.gC[3 * qf[i] + c], -2.0 * sg[i][c]);
   }
-  if (tid == 0) {
-    if (s_abort) atomicExch(err, 1);
-    if (s_fl) atomicAdd(&P.acc[ACC_F2], (double)s_fl);
-  }
+  if (tid == 0 && s_abort) atomicExch(err, 1);
 }
 
 // ------------------------------------------------------------ tcgen05 Y build
@@ -973,8 +998,8 @@ __global__ void __launch_bounds__(192) k_q2_umma(DevPlan P, MixPlan X, const int
 // bf16 pieces and writes the Y store ([alpha][z][16], x padding zeroed).
 template <int NP>
 __global__ void __launch_bounds__(192) k_ybuild_umma(DevPlan P, MixPlan X, const int* ylist, const int* gX,
-                                                     const int* gS, const int* gN, int MC, const uint16_t* zero512,
-                                                     int* err) {
+                                                     const int* gS, const int* gN, int MC,
+                                                     const __grid_constant__ DRows drows, int* err) {
   using namespace umma;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   uint16_t* stA = reinterpret_cast<uint16_t*>(smem_raw);
@@ -982,7 +1007,6 @@ __global__ void __launch_bounds__(192) k_ybuild_umma(DevPlan P, MixPlan X, const
   int* m_d = reinterpret_cast<int*>(stB + (size_t)kStages * NP * kTileElems);   // [kMaxCPerAtom][8]
   __shared__ int m_q[kMaxCPerAtom];
   __shared__ int s_nsteps;
-  __shared__ unsigned long long s_fl;
   __shared__ __align__(8) uint64_t bar_full[kStages], bar_empty[kStages], bar_accf;
   __shared__ uint32_t tmem_base;
   __shared__ int s_abort;
@@ -1001,31 +1025,16 @@ __global__ void __launch_bounds__(192) k_ybuild_umma(DevPlan P, MixPlan X, const
     ykey[i] = i < nk ? ylist[kstart + i] : -1;
     zat[i] = ykey[i] >= 0 ? P.y_j[ykey[i]] : 0;
   }
-  // D block of every (C pair, key), or -1; the flops of the kept ones are
-  // counted here (once per key group, by the mc = 0 CTA)
-  unsigned long long fl = 0ull;
-  for (int e = tid; e < nq * 8; e += blockDim.x) {
-    const int t = e >> 3, i = e & 7;
-    int md = -1;
-    if (ykey[i] >= 0 && P.c_keep[q0 + t]) {
-      const int* Rz = P.y_R + 3 * ykey[i];
-      const int* Rw = P.c_R + 3 * (q0 + t);
-      const int w = P.c_j[q0 + t], z = zat[i];
-      const int di = dlut_get(P, w, z, Rz[0] - Rw[0], Rz[1] - Rw[1], Rz[2] - Rw[2]);
-      if (di >= 0 && P.Dkept[di] != 0.0) {
-        const int mi = dlut_get(P, z, w, Rw[0] - Rz[0], Rw[1] - Rz[1], Rw[2] - Rz[2]);
-        md = (int)(X.dsp_off[mi] >> 8);
-        if (mc == 0) fl += 2ull * rows * P.n_ao[P.species[z]] * P.n_ao[P.species[w]];
-      }
-    }
-    m_d[e] = md;
+  // D block of every (C pair, key), or -1, from the table
+  {
+    const int4* tab = reinterpret_cast<const int4*>(X.ytab + (long long)g * X.ytab_stride);
+    for (int e = tid; e < nq * 2; e += blockDim.x) reinterpret_cast<int4*>(m_d)[e] = tab[e];
   }
   const uint32_t mfull = (uint32_t)__cvta_generic_to_shared(&bar_full[0]);
   const uint32_t mempty = (uint32_t)__cvta_generic_to_shared(&bar_empty[0]);
   const uint32_t maccf = (uint32_t)__cvta_generic_to_shared(&bar_accf);
   if (tid == 0) {
     s_abort = 0;
-    s_fl = 0ull;
     for (int s = 0; s < kStages; ++s) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mfull + 8 * s));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mempty + 8 * s));
@@ -1039,8 +1048,6 @@ __global__ void __launch_bounds__(192) k_ybuild_umma(DevPlan P, MixPlan X, const
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
   }
   __syncthreads();
-  fl = warp_sum_u64(fl);
-  if (lane == 0 && fl) atomicAdd(&s_fl, fl);
   if (warp == 0) {   // K steps: kept C pairs with at least one D block among the keys, in order
     int n = 0;
     for (int t0 = 0; t0 < nq; t0 += 32) {
@@ -1067,32 +1074,18 @@ __global__ void __launch_bounds__(192) k_ybuild_umma(DevPlan P, MixPlan X, const
     const uint32_t bytes = (uint32_t)NP * 2 * kTileElems * 2;
     for (int k = 0; k < nsteps; ++k) {
       const int s = k % kStages;
-      if (k >= kStages && !mbar_wait(mempty + 8 * s, (uint32_t)((k / kStages - 1) & 1))) s_abort = 1;
+      if (k >= kStages && !mbar_wait<kMixTryNs>(mempty + 8 * s, (uint32_t)((k / kStages - 1) & 1))) s_abort = 1;
       __syncwarp();
       if (s_abort) break;
-      if (lane == 0)
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mfull + 8 * s), "r"(bytes)
-                     : "memory");
       const int t = m_q[k];
-      for (int c = lane; c < NP * 9; c += 32) {
-        uint32_t dst;
-        const uint16_t* src;
-        uint32_t nb;
-        if (c < NP) {
-          dst = (uint32_t)__cvta_generic_to_shared(stA + ((size_t)s * NP + c) * kTileElems);
-          src = X.Cm + X.cm_off[q0 + t] + ((long long)mc * NP + c) * kTileElems;
-          nb = kTileElems * 2;
-        } else {
-          const int pp = (c - NP) >> 3, i = (c - NP) & 7;
-          const int md = m_d[t * 8 + i];
-          dst = (uint32_t)__cvta_generic_to_shared(stB + ((size_t)s * NP + pp) * kTileElems + i * 256);
-          src = md >= 0 ? X.Dsp + (long long)md * 256 + pp * 256 : zero512;
-          nb = 512;
-        }
-        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
-                     "l"(src), "r"(nb), "r"(mfull + 8 * s)
-                     : "memory");
+      // lane 0: the NP C piece tiles of row tile mc (contiguous, one copy);
+      // lanes 1 .. 2 NP: the eight mirror D blocks of each piece, four per gather
+      if (lane == 0) {
+        mbar_expect_tx(mfull + 8 * s, bytes);
+        bulk_g2s((uint32_t)__cvta_generic_to_shared(stA + (size_t)s * NP * kTileElems),
+                 X.Cm + X.cm_off[q0 + t] + (long long)mc * NP * kTileElems, (uint32_t)NP * kTileElems * 2, mfull + 8 * s);
       }
+      stage_d<NP>(lane, stB + (size_t)s * NP * kTileElems, m_d + t * 8, &drows.map, drows.zero_row, mfull + 8 * s);
     }
   } else if (warp == 1) {
     if (lane == 0 && nsteps > 0) {
@@ -1100,7 +1093,7 @@ __global__ void __launch_bounds__(192) k_ybuild_umma(DevPlan P, MixPlan X, const
       bool first = true;
       for (int k = 0; k < nsteps; ++k) {
         const int s = k % kStages;
-        if (!mbar_wait(mfull + 8 * s, (uint32_t)((k / kStages) & 1))) {
+        if (!mbar_wait<kMixTryNs>(mfull + 8 * s, (uint32_t)((k / kStages) & 1))) {
           s_abort = 1;
           break;
         }
@@ -1142,7 +1135,7 @@ __global__ void __launch_bounds__(192) k_ybuild_umma(DevPlan P, MixPlan X, const
     const int alA = row0 / nX, alB = (rend - 1) / nX;
     bool have = nsteps > 0;
     if (have) {
-      if (!mbar_wait(maccf, 0u)) {
+      if (!mbar_wait<kMixTryNs>(maccf, 0u)) {
         s_abort = 1;
         have = false;
       }
@@ -1239,10 +1232,7 @@ __global__ void __launch_bounds__(192) k_ybuild_umma(DevPlan P, MixPlan X, const
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(128));
-  if (tid == 0) {
-    if (s_abort) atomicExch(err, 1);
-    if (s_fl) atomicAdd(&P.acc[ACC_FY], (double)s_fl);
-  }
+  if (tid == 0 && s_abort) atomicExch(err, 1);
 }
 
 // Groups of up to 8 consecutive needed keys of one home atom (the needed keys
@@ -1266,6 +1256,73 @@ __global__ void k_ygroups(DevPlan P, const long long* y_idx, const long long* y_
   }
 }
 
+// D block (256-element units) of every (key group g, C slot t of its home
+// atom X, key i) of the Y build, or -1 (C pair dropped, key absent, D block
+// screened out); the Y build's flops are counted here.
+__global__ void k_ytab(DevPlan P, MixPlan X, const int* ylist, const int* gX, const int* gS, const int* gN,
+                       int ngroups) {
+  const int TC = X.ytab_stride >> 3;
+  const long long total = (long long)ngroups * X.ytab_stride;
+  double fl = 0.0;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e & 7);
+    const long long gt = e >> 3;
+    const int g = (int)(gt / TC), t = (int)(gt - (long long)g * TC);
+    const int Xa = gX[g];
+    const int q0 = P.c_ptr[Xa], nq = P.c_ptr[Xa + 1] - q0;
+    if (t >= nq) continue;
+    const int key = i < gN[g] ? ylist[gS[g] + i] : -1;
+    int md = -1;
+    if (key >= 0 && P.c_keep[q0 + t]) {
+      const int* Rz = P.y_R + 3 * key;
+      const int* Rw = P.c_R + 3 * (q0 + t);
+      const int w = P.c_j[q0 + t], z = P.y_j[key];
+      const int di = dlut_get(P, w, z, Rz[0] - Rw[0], Rz[1] - Rw[1], Rz[2] - Rw[2]);
+      if (di >= 0 && P.Dkept[di] != 0.0) {
+        const int mi = dlut_get(P, z, w, Rw[0] - Rz[0], Rw[1] - Rz[1], Rw[2] - Rz[2]);
+        md = (int)(X.dsp_off[mi] >> 8);
+        const int sX = P.species[Xa];
+        fl += 2.0 * P.n_abf[sX] * P.n_ao[sX] * P.n_ao[P.species[z]] * P.n_ao[P.species[w]];
+      }
+    }
+    X.ytab[e] = md;
+  }
+  fl = warp_sum_d(fl);
+  if ((threadIdx.x & 31) == 0 && fl != 0.0) atomicAdd(&P.acc[ACC_FY], fl);
+}
+
+// D block of every (group fc of 8 C slots of the pair's home atom A, pair
+// slot of the second product, i), or -1; the Q2 product's flops are counted
+// here.
+__global__ void k_q2tab(DevPlan P, MixPlan X, const int* list, int n_slots, int FC8) {
+  const long long total = (long long)n_slots * FC8 * 8;
+  double fl = 0.0;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e & 7);
+    const long long r = e >> 3;
+    const int fc = (int)(r / n_slots), slot = (int)(r - (long long)fc * n_slots);
+    const int p = list[slot];
+    const int A = P.v_home[p];
+    const int q0 = P.c_ptr[A], nq = P.c_ptr[A + 1] - q0;
+    const int j = fc * 8 + i;
+    int db = -1;
+    if (j < nq && P.c_keep[q0 + j]) {
+      const int qf = q0 + j, b = P.v_j[p];
+      const int* Rb = P.v_R + 3 * p;
+      const int* Rf = P.c_R + 3 * qf;
+      const int d = dlut_get(P, P.c_j[qf], b, Rb[0] - Rf[0], Rb[1] - Rf[1], Rb[2] - Rf[2]);
+      if (d >= 0 && P.Dkept[d] != 0.0) {
+        db = (int)(X.dsp_off[d] >> 8);
+        const int sA = P.species[A];
+        fl += 2.0 * P.n_abf[sA] * P.n_ao[sA] * P.n_ao[P.species[b]] * P.n_ao[P.species[P.c_j[qf]]];
+      }
+    }
+    X.q2tab[e] = db;
+  }
+  fl = warp_sum_d(fl);
+  if ((threadIdx.x & 31) == 0 && fl != 0.0) atomicAdd(&P.acc[ACC_F2], fl);
+}
+
 size_t ybuild_umma_smem(int np) {
   return (size_t)2 * umma::kStages * np * umma::kTileElems * sizeof(uint16_t) + (size_t)kMaxCPerAtom * 8 * sizeof(int);
 }
@@ -1282,6 +1339,9 @@ int grid_for(long long n, int cap) {
 }  // namespace
 
 long long mixed_launch_count() { return g_mix_launches; }
+
+long long ytab_size(int ngroups, int maxC) { return (long long)ngroups * 8 * maxC; }
+long long q2tab_size(int n_slots, int FC) { return (long long)n_slots * ((FC * 4 + 7) / 8) * 8; }
 
 int q2_umma_segments(int max_pairs_per_atom) { return (max_pairs_per_atom + umma::kMetaPairs - 1) / umma::kMetaPairs; }
 
@@ -1317,15 +1377,17 @@ cudaError_t launch_ygroups(const DevPlan& P, const long long* y_idx, const long 
 }
 
 cudaError_t launch_ybuild_mma(const DevPlan& P, const MixPlan& X, int np, const int* ylist, const int* gX,
-                              const int* gS, const int* gN, int ngroups, int MC, const uint16_t* zero512, int* err,
+                              const int* gS, const int* gN, int ngroups, int MC, const DRows& drows, int* err,
                               cudaStream_t s) {
   if (ngroups == 0) return cudaSuccess;
-  ++g_mix_launches;
+  g_mix_launches += 2;
+  k_ytab<<<grid_for(((long long)ngroups * X.ytab_stride + 255) / 256, 152 * 16), 256, 0, s>>>(P, X, ylist, gX, gS, gN,
+                                                                                          ngroups);
   const long long grid = (long long)ngroups * MC;
   if (np == 2)
-    k_ybuild_umma<2><<<(unsigned)grid, 192, ybuild_umma_smem(2), s>>>(P, X, ylist, gX, gS, gN, MC, zero512, err);
+    k_ybuild_umma<2><<<(unsigned)grid, 192, ybuild_umma_smem(2), s>>>(P, X, ylist, gX, gS, gN, MC, drows, err);
   else
-    k_ybuild_umma<3><<<(unsigned)grid, 192, ybuild_umma_smem(3), s>>>(P, X, ylist, gX, gS, gN, MC, zero512, err);
+    k_ybuild_umma<3><<<(unsigned)grid, 192, ybuild_umma_smem(3), s>>>(P, X, ylist, gX, gS, gN, MC, drows, err);
   return cudaGetLastError();
 }
 
@@ -1377,18 +1439,19 @@ cudaError_t launch_term1_mma(const DevPlan& P, const MixPlan& X, int np, const i
 
 cudaError_t launch_term2_mma(const DevPlan& P, const MixPlan& X, int np, const int* list, const long long* slot0,
                              int n, int MAmax, int KZmax, long long zblk, int zrows, int FC, int MC, int nseg,
-                             const uint16_t* zero512, size_t smem, int* err, cudaStream_t s) {
+                             int flush, const DRows& drows, size_t smem, int* err, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  g_mix_launches += 2;
+  g_mix_launches += 3;
   const int FC8 = (FC * 4 + 7) / 8;     // groups of 8 C slots for the tcgen05 kernel
+  k_q2tab<<<grid_for(((long long)n * FC8 * 8 + 255) / 256, 152 * 16), 256, 0, s>>>(P, X, list, n, FC8);
   const size_t sq = q2_umma_smem(np);
   const long long grid = (long long)P.N * FC8 * MC * nseg;
   if (np == 2) {
     k_term2_pairs<2><<<grid_for(n, 152 * 32), kWarps * 32, smem, s>>>(P, X, list, n, MAmax, KZmax, zblk, zrows);
-    k_q2_umma<2><<<(unsigned)grid, 192, sq, s>>>(P, X, list, slot0, n, FC8, MC, nseg, zblk, zero512, err);
+    k_q2_umma<2><<<(unsigned)grid, 192, sq, s>>>(P, X, list, slot0, n, FC8, MC, nseg, zblk, flush, drows, err);
   } else {
     k_term2_pairs<3><<<grid_for(n, 152 * 32), kWarps * 32, smem, s>>>(P, X, list, n, MAmax, KZmax, zblk, zrows);
-    k_q2_umma<3><<<(unsigned)grid, 192, sq, s>>>(P, X, list, slot0, n, FC8, MC, nseg, zblk, zero512, err);
+    k_q2_umma<3><<<(unsigned)grid, 192, sq, s>>>(P, X, list, slot0, n, FC8, MC, nseg, zblk, flush, drows, err);
   }
   return cudaGetLastError();
 }
