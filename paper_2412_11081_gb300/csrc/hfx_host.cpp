@@ -138,6 +138,7 @@ struct hfx_plan {
   unsigned char* c_keep = nullptr;
   int *v_ptr = nullptr, *v_home = nullptr, *v_j = nullptr, *v_R = nullptr, *v_didx = nullptr;
   double* v_norm = nullptr;
+  double* v_hg = nullptr;
   unsigned char *v_keep = nullptr, *v_t2 = nullptr;
   unsigned* v_mask = nullptr;
   int* v_flag = nullptr;
@@ -461,6 +462,7 @@ DevPlan make_devplan(hfx_plan* P, const double* lattice) {
   D.v_R = P->v_R;
   D.v_didx = P->v_didx;
   D.v_norm = P->v_norm;
+  D.v_hg = P->v_hg;
   D.v_keep = P->v_keep;
   D.v_mask = P->v_mask;
   D.v_t2 = P->v_t2;
@@ -639,6 +641,7 @@ void build_lists(hfx_plan* P, const double* L, const double* pos) {
   P->v_R = P->lalloc<int>(3 * (size_t)nV);
   P->v_didx = P->lalloc<int>(nV);
   P->v_norm = P->lalloc<double>(nV);
+  P->v_hg = P->lalloc<double>(4 * (size_t)nV);
   P->v_keep = P->lalloc<unsigned char>(nV);
   P->v_t2 = P->lalloc<unsigned char>(nV);
   P->v_mask = P->lalloc<unsigned>((size_t)nV * hfx::kMaskWords);
@@ -970,9 +973,9 @@ void evaluate(hfx_plan* P, const double* L, hfx_stats* st) {
   ck(cudaStreamSynchronize(s), "screening");
   if (P->opt.freeze_lists) P->frozen_ready = true;
   tm.mark();  // 2
-  ensure_store(P, P->Vst, P->Vcap, P->tot[2]);
-  D.Vst = P->Vst;
   if (!P->np) {
+    ensure_store(P, P->Vst, P->Vcap, P->tot[2]);
+    D.Vst = P->Vst;
     ensure_store(P, P->Yst, P->Ycap, P->tot[0]);
     D.Yst = P->Yst;
     ck(hfx::launch_vblocks(D, P->v_list, (int)P->tot[3], s), "vblocks");
@@ -993,7 +996,8 @@ void evaluate(hfx_plan* P, const double* L, hfx_stats* st) {
     X.blist = P->blist;
     ensure_buf(P, P->Vm, P->Vmcap, P->tot[8]);
     X.Vm = P->Vm;
-    ck(hfx::launch_vblocks(D, P->v_list, (int)P->tot[3], s), "vblocks");
+    // the split path evaluates V and grad V from the block model inside the
+    // store kernels (k_vpieces, k_t1u_vstore): no FP64 V store
     ck(hfx::launch_vpieces(D, X, P->np, P->v_list, (int)P->tot[3], s), "vpieces");
     ck(hfx::launch_cpieces(D, X, P->np, s), "cpieces");
     hfx::T1UPlan U{};

@@ -67,6 +67,7 @@ struct DevPlan {
   const int* v_R;
   const int* v_didx;           // D block of (home, j, R) or -1
   double* v_norm;              // max(||V||, ||grad V||) if kept, else 0
+  double* v_hg;                // [nV*4] h(r) and g = h'(r) d / r of the pair's V = M h, grad V = M g
   unsigned char* v_keep;
   unsigned int* v_mask;        // [nV*kMaskWords] kept F (C-pair slots of home)
   unsigned char* v_t2;         // kept for the second exchange product

@@ -22,9 +22,12 @@
 #include <cstdio>
 
 #include "hfx_internal.h"
+#include "hfx_model.cuh"
 
 namespace hfx {
 namespace {
+
+using namespace model;
 
 constexpr int kThreads = 256;
 long long g_launches = 0;   // host-side count of kernel launches
@@ -49,15 +52,6 @@ __device__ double block_sum(double v, double* red) {
   return t;
 }
 
-__device__ __forceinline__ void pair_vector(const DevPlan& P, int i, int j, const int* R, double d[3]) {
-  const double r0 = (double)R[0], r1 = (double)R[1], r2 = (double)R[2];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    const double RL = r0 * P.L[k] + r1 * P.L[3 + k] + r2 * P.L[6 + k];
-    d[k] = (P.pos[3 * j + k] + RL) - P.pos[3 * i + k];
-  }
-}
-
 __device__ __forceinline__ int dlut_get(const DevPlan& P, int i, int j, int r0, int r1, int r2) {
   if (r0 < -P.HD0 || r0 > P.HD0 || r1 < -P.HD1 || r1 > P.HD1 || r2 < -P.HD2 || r2 > P.HD2) return -1;
   const long long n0 = 2 * P.HD0 + 1, n1 = 2 * P.HD1 + 1, n2 = 2 * P.HD2 + 1;
@@ -70,29 +64,6 @@ __device__ __forceinline__ int ylut_get(const DevPlan& P, int i, int j, int r0, 
   const long long n0 = 2 * P.HY0 + 1, n1 = 2 * P.HY1 + 1, n2 = 2 * P.HY2 + 1;
   const long long idx = (((((long long)i * P.N + j) * n0 + (r0 + P.HY0)) * n1 + (r1 + P.HY1)) * n2) + (r2 + P.HY2);
   return P.ylut[idx];
-}
-
-// Block model radial functions: f(r) = (1-(r/R_C)^2)^3 exp(-r^2/2) for r < R_C,
-// h(r) = erfc(omega r)/(r+1), and their first derivatives.
-__device__ __forceinline__ void radial_f(double r, double RC, double& f, double& fp) {
-  if (r >= RC) {
-    f = 0.0;
-    fp = 0.0;
-    return;
-  }
-  const double q = r / RC;
-  const double x = 1.0 - q * q;
-  const double e = exp(-0.5 * r * r);
-  f = x * x * x * e;
-  fp = 3.0 * x * x * (-2.0 * r / (RC * RC)) * e - r * (x * x * x) * e;
-}
-
-__device__ __forceinline__ void radial_h(double r, double om, double& h, double& hp) {
-  const double ec = erfc(om * r);
-  const double r1 = r + 1.0;
-  h = ec / r1;
-  const double two_over_sqrt_pi = 1.1283791670955126;
-  hp = (-2.0 * om * 0.5 * two_over_sqrt_pi) * exp(-(om * r) * (om * r)) / r1 - ec / (r1 * r1);
 }
 
 // ---------------------------------------------------------------- K2: D norms
@@ -192,12 +163,20 @@ __global__ void k_vnorm(DevPlan P, int frozen) {
     const int A = P.v_home[p], j = P.v_j[p];
     const int* R = P.v_R + 3 * p;
     const bool onsite = (A == j) && R[0] == 0 && R[1] == 0 && R[2] == 0;
-    double h = 1.0, hp = 0.0;
+    double h = 1.0, hp = 0.0, g[3] = {0.0, 0.0, 0.0};
     if (!onsite) {
       double d[3];
       pair_vector(P, A, j, R, d);
-      radial_h(sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]), P.omega, h, hp);
+      const double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+      radial_h(r, P.omega, h, hp);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) g[c] = hp * d[c] / r;
     }
+    double* hg = P.v_hg + 4 * (long long)p;   // for the kernels that evaluate V = M h, grad V = M g
+    hg[0] = h;
+    hg[1] = g[0];
+    hg[2] = g[1];
+    hg[3] = g[2];
     const double mn = P.Mnorm[P.species[A] * P.S + P.species[j]];
     const double nv = fabs(h) * mn, ng = fabs(hp) * mn;
     bool keep;
@@ -294,18 +273,8 @@ __global__ void k_vblocks(DevPlan P, const int* list, int n_list) {
   for (int k = blockIdx.x; k < n_list; k += gridDim.x) {
     const int p = list[k];
     const int A = P.v_home[p], j = P.v_j[p];
-    const int* R = P.v_R + 3 * p;
-    double d[3];
-    pair_vector(P, A, j, R, d);
-    const bool onsite = (A == j) && R[0] == 0 && R[1] == 0 && R[2] == 0;
-    const double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-    double h = 1.0, hp = 0.0;
-    if (!onsite) radial_h(r, P.omega, h, hp);
-    double g[3] = {0.0, 0.0, 0.0};
-    if (!onsite) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) g[c] = hp * d[c] / r;
-    }
+    double h, g[3];
+    v_pair(P, p, h, g);
     const int sA = P.species[A], sj = P.species[j];
     const double* M = P.M + P.M_off[sA * P.S + sj];
     const int n = P.n_abf[sA] * P.n_abf[sj];

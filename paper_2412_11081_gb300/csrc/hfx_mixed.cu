@@ -29,6 +29,7 @@
 #include <cstdint>
 
 #include "hfx_device.cuh"
+#include "hfx_model.cuh"
 
 namespace hfx {
 namespace {
@@ -185,24 +186,35 @@ __global__ void k_cpieces(DevPlan P, MixPlan X) {
   }
 }
 
-// needed V pair p: NP bf16 planes of V[alpha][rup16(n_abf(B))] then V, grad V (FP32).
+// needed V pair p: NP bf16 planes of V[alpha][rup16(n_abf(B))] then V, grad V (FP32),
+// evaluated from the block model (V = M h, grad V = M g) without an FP64 store.
 template <int NP>
 __global__ void k_vpieces(DevPlan P, MixPlan X, const int* list, int n_list) {
   for (int k = blockIdx.x; k < n_list; k += gridDim.x) {
     const int p = list[k];
-    const int mA = P.n_abf[P.species[P.v_home[p]]], mB = P.n_abf[P.species[P.v_j[p]]];
+    const int sA = P.species[P.v_home[p]], sB = P.species[P.v_j[p]];
+    const int mA = P.n_abf[sA], mB = P.n_abf[sB];
     const int MB = rup16(mB);
-    const double* V = P.Vst + P.v_off[p];
+    double h, g[3];
+    model::v_pair(P, p, h, g);
+    const double* M = P.M + P.M_off[sA * P.S + sB];
     uint16_t* out = X.Vm + X.vm_off[p];
     for (int e = threadIdx.x; e < mA * MB; e += blockDim.x) {
       const int al = e / MB, be = e - al * MB;
       uint16_t pc[NP];
-      split_f<NP>(be < mB ? (float)V[al * mB + be] : 0.f, pc);
+      split_f<NP>(be < mB ? (float)(M[al * mB + be] * h) : 0.f, pc);
 #pragma unroll
       for (int pp = 0; pp < NP; ++pp) out[pp * mA * MB + e] = pc[pp];
     }
     float* v32 = reinterpret_cast<float*>(out + NP * mA * MB);
-    for (int e = threadIdx.x; e < 4 * mA * mB; e += blockDim.x) v32[e] = (float)V[e];
+    const int n = mA * mB;
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+      const double m = M[e];
+      v32[e] = (float)(m * h);
+      v32[n + e] = (float)(m * g[0]);
+      v32[2 * n + e] = (float)(m * g[1]);
+      v32[3 * n + e] = (float)(m * g[2]);
+    }
   }
 }
 

@@ -32,6 +32,7 @@
 #include <algorithm>
 
 #include "hfx_device.cuh"
+#include "hfx_model.cuh"
 
 namespace hfx {
 namespace {
@@ -76,40 +77,51 @@ __device__ __forceinline__ void ep_at(int w, int& alpha, int& col) {
 // Item kk (C pair q = list[kk]): NP bf16 pieces of C_AF as [alpha (64)][(f,a) (KP)]
 // in core-matrix order (8-row groups of KP/8 core matrices), then C and
 // grad C in FP32 as four planes of 64 x KP32 (KP rounded up to 32) in
-// epilogue load order (ep_off).  Zero padded.
+// epilogue load order (ep_off).  Zero padded.  Each FP64 plane of the C pair
+// ([(alpha,a)][f]) is read once, coalesced, into shared memory as FP32; the
+// outputs are written in storage order, four elements per thread.
+constexpr int kCStoreSmem = 64 * 16 * 16 * 4;   // one plane of n_abf <= 64, n_ao <= 16
+
 template <int NP>
 __global__ void k_t1u_cstore(DevPlan P, T1UPlan U, const int* list, int n) {
+  extern __shared__ float cs[];
   const int KP = U.KP, KP32 = t1u_kp32(KP), PL = 64 * KP32;
   for (int kk = blockIdx.x; kk < n; kk += gridDim.x) {
     const int q = list[kk];
     const int A = P.c_home[q], F = P.c_j[q];
     const int sA = P.species[A];
     const int nA = P.n_ao[sA], mA = P.n_abf[sA], nF = P.n_ao[P.species[F]];
-    const long long ncq = (long long)mA * nA * nF;
-    const double* C = P.Cst + P.c_off[q];
-    const double* dC = P.dCst + 3 * P.c_off[q];
+    const int ncq = mA * nA * nF;
     uint16_t* out = U.Cu + (long long)kk * U.cu_blk;
     float* pl = reinterpret_cast<float*>(out + (long long)NP * 64 * KP);
-    for (int e = threadIdx.x; e < 64 * KP; e += blockDim.x) {
-      const int al = e / KP, c = e - al * KP;
-      const int f = c >> 4, a = c & 15;
-      const bool in = al < mA && f < nF && a < nA;
-      uint16_t pc[NP];
-      split_f<NP>(in ? (float)C[((long long)al * nA + a) * nF + f] : 0.f, pc);
-      const int t = (al >> 3) * KP * 8 + (c >> 3) * 64 + (al & 7) * 8 + (c & 7);
+    for (int c = 0; c < 4; ++c) {
+      const double* src = c == 0 ? P.Cst + P.c_off[q] : P.dCst + 3 * P.c_off[q] + (long long)(c - 1) * ncq;
+      __syncthreads();
+      for (int e = threadIdx.x; e < ncq; e += blockDim.x) cs[e] = (float)src[e];
+      __syncthreads();
+      auto val = [&](int al, int col) -> float {
+        const int f = col >> 4, a = col & 15;
+        return (al < mA && col < KP && f < nF && a < nA) ? cs[(al * nA + a) * nF + f] : 0.f;
+      };
+      if (c == 0) {
+        // pieces: core-matrix element t -> (alpha, col), four consecutive columns per thread
+        for (int t4 = threadIdx.x; t4 < 16 * KP; t4 += blockDim.x) {
+          const int t = 4 * t4;
+          const int g8 = t / (KP * 8), rem = t - g8 * KP * 8;
+          const int al = g8 * 8 + ((rem >> 3) & 7), col = (rem >> 6) * 8 + (rem & 7);
+          const float x[4] = {val(al, col), val(al, col + 1), val(al, col + 2), val(al, col + 3)};
+          uint2 pc[NP];
+          split4<NP>(x, pc);
 #pragma unroll
-      for (int pp = 0; pp < NP; ++pp) out[(long long)pp * 64 * KP + t] = pc[pp];
-    }
-    for (int w = threadIdx.x; w < PL; w += blockDim.x) {   // written in storage order
-      int al, c;
-      ep_at(w, al, c);
-      const int f = c >> 4, a = c & 15;
-      const bool in = al < mA && c < KP && f < nF && a < nA;
-      const long long o = in ? ((long long)al * nA + a) * nF + f : 0;
-      pl[w] = in ? (float)C[o] : 0.f;
-      pl[PL + w] = in ? (float)dC[o] : 0.f;
-      pl[2 * PL + w] = in ? (float)dC[ncq + o] : 0.f;
-      pl[3 * PL + w] = in ? (float)dC[2 * ncq + o] : 0.f;
+          for (int pp = 0; pp < NP; ++pp) *reinterpret_cast<uint2*>(out + (long long)pp * 64 * KP + t) = pc[pp];
+        }
+      }
+      for (int w4 = threadIdx.x; w4 < PL / 4; w4 += blockDim.x) {   // FP32 plane c, storage order
+        int al, col;
+        ep_at(4 * w4, al, col);
+        *reinterpret_cast<float4*>(pl + (long long)c * PL + 4 * w4) =
+            make_float4(val(al, col), val(al, col + 1), val(al, col + 2), val(al, col + 3));
+      }
     }
   }
 }
@@ -121,16 +133,18 @@ template <int NP>
 __global__ void k_t1u_vstore(DevPlan P, T1UPlan U, const int* list, int n) {
   for (int k = blockIdx.x; k < n; k += gridDim.x) {
     const int p = list[k];
-    const int mA = P.n_abf[P.species[P.v_home[p]]], mB = P.n_abf[P.species[P.v_j[p]]];
-    const long long nv = (long long)mA * mB;
-    const double* V = P.Vst + P.v_off[p];
+    const int sA = P.species[P.v_home[p]], sB = P.species[P.v_j[p]];
+    const int mA = P.n_abf[sA], mB = P.n_abf[sB];
+    double h, g[3];
+    model::v_pair(P, p, h, g);   // V = M h, grad V = M g (block model)
+    const double* M = P.M + P.M_off[sA * P.S + sB];
     uint16_t* out = U.Vu + (long long)k * U.vu_blk;
     float* pl = reinterpret_cast<float*>(out + NP * 4096);
     for (int e = threadIdx.x; e < 4096; e += blockDim.x) {
       const int al = e >> 6, be = e & 63;
       const bool in = al < mA && be < mB;
       uint16_t pc[NP];
-      split_f<NP>(in ? (float)V[(long long)al * mB + be] : 0.f, pc);
+      split_f<NP>(in ? (float)(M[al * mB + be] * h) : 0.f, pc);
       const int t = (al >> 3) * 512 + (be >> 3) * 64 + (al & 7) * 8 + (be & 7);
 #pragma unroll
       for (int pp = 0; pp < NP; ++pp) out[pp * 4096 + t] = pc[pp];
@@ -139,10 +153,10 @@ __global__ void k_t1u_vstore(DevPlan P, T1UPlan U, const int* list, int n) {
       int al, be;
       ep_at(w, al, be);
       const bool in = al < mA && be < mB;
-      const long long o = in ? (long long)al * mB + be : 0;
-      pl[w] = in ? (float)V[nv + o] : 0.f;
-      pl[4096 + w] = in ? (float)V[2 * nv + o] : 0.f;
-      pl[2 * 4096 + w] = in ? (float)V[3 * nv + o] : 0.f;
+      const double m = in ? M[al * mB + be] : 0.0;
+      pl[w] = (float)(m * g[0]);
+      pl[4096 + w] = (float)(m * g[1]);
+      pl[2 * 4096 + w] = (float)(m * g[2]);
     }
   }
 }
@@ -899,9 +913,15 @@ cudaError_t launch_t1u_stores(const DevPlan& P, const T1UPlan& U, int np, const 
                               int nv, bool dstore, cudaStream_t s) {
   if (nq > 0) {
     ++g_t1u_launches;
-    const int g = nq < 152 * 8 ? nq : 152 * 8;
-    if (np == 2) k_t1u_cstore<2><<<g, 256, 0, s>>>(P, U, qlist, nq);
-    else k_t1u_cstore<3><<<g, 256, 0, s>>>(P, U, qlist, nq);
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_t1u_cstore<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kCStoreSmem);
+      cudaFuncSetAttribute(k_t1u_cstore<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kCStoreSmem);
+      attr = true;
+    }
+    const int g = nq < 152 * 3 ? nq : 152 * 3;
+    if (np == 2) k_t1u_cstore<2><<<g, 256, kCStoreSmem, s>>>(P, U, qlist, nq);
+    else k_t1u_cstore<3><<<g, 256, kCStoreSmem, s>>>(P, U, qlist, nq);
   }
   if (nv > 0) {
     ++g_t1u_launches;
