@@ -188,6 +188,8 @@ struct hfx_plan {
   int* t1q_list = nullptr;
   int* t1q_lpt = nullptr;      // the same items, longest (most kept B) first
   int q2_flush = 32;           // pairs per FP32 run of the second product's Q2 accumulator
+  uint16_t* YspT = nullptr;    // transposed Y pieces (second product)
+  long long YspTcap = 0;
   int* ytab = nullptr;         // D-block tables of the Y build and the second product
   int* q2tab = nullptr;
   long long ytabcap = 0, q2tabcap = 0;
@@ -1020,6 +1022,10 @@ void evaluate(hfx_plan* P, const double* L, hfx_stats* st) {
       ck(hfx::launch_t1u_stores(D, U, P->np, P->t1q_lpt, (int)P->tot[7], P->t1_list, (int)P->tot[4], false, s),
          "term-1 operand stores");
     }
+    X.yT_blk = (long long)P->np * P->MC * 128 * 16;
+    ensure_buf(P, P->YspT, P->YspTcap, std::max(1LL, P->tot[1]) * X.yT_blk);
+    X.YspT = P->YspT;
+    X.y_idx = P->y_idx;
     ensure_buf(P, P->ytab, P->ytabcap, std::max(1LL, hfx::ytab_size((int)P->tot[9], P->maxC)));
     X.ytab = P->ytab;
     X.ytab_stride = 8 * P->maxC;

@@ -109,6 +109,9 @@ struct MixPlan {
   long long* qoff;             // [nC] offsets into blist
   int* blist;                  // V pairs (A,B) per (A,F), in V-pair order
   float* Yf = nullptr;         // Y^{XZ} in FP32 as [z][alpha][16], offsets y_off / np (tcgen05 term 1 only)
+  uint16_t* YspT = nullptr;    // Y^{XZ} transposed, bf16 pieces [piece][(alpha,x)][16 z] (z padded), yT_blk per key
+  long long yT_blk = 0;        // uint16 units per key of YspT (np x 128-row tiles x 16)
+  const long long* y_idx = nullptr;   // key -> its position in the needed-key list (YspT block)
   int* ytab = nullptr;         // Y build: D block (256-element units) per (key group, C slot t, key i), or -1
   int ytab_stride = 0;         // ints per key group (8 * most C pairs of an atom)
   int* q2tab = nullptr;        // second product: D block per (group of 8 C slots, pair slot, i), or -1

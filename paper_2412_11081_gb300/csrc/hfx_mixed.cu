@@ -583,7 +583,7 @@ __global__ void __launch_bounds__(kWarps1 * 32) k_term1_mma(DevPlan P, MixPlan X
 // Phase 1: one CTA per kept (A,B) pair of the second product (slot s of the
 // pair list).  Shared memory (bf16 planes, row stride KZ = n_ao(A)*pB + 8):
 //   Yb[NP][MB][KZ]  Y^{BA} as [beta][(a,b)]         (b padded to pB)
-//   Ya[NP][MA][KZ]  Y^{AB} transposed to [alpha][(a,b)]
+//   Ya[NP][MA][KZ]  Y^{AB} as [alpha][(a,b)], from the transposed store the Y build writes
 // R2^T[beta][alpha] = sum_{(a,b)} Yb[beta][(a,b)] Ya[alpha][(a,b)], dotted with V, grad V;
 // Z[alpha][(a,b)] = sum_beta V[alpha][beta] Yb[beta][(a,b)] -> Z store of slot s as
 // NP planes [(alpha,a)][pB].
@@ -601,32 +601,37 @@ __global__ void __launch_bounds__(kWarps * 32) k_term2_pairs(DevPlan P, MixPlan 
     const int* Rb = P.v_R + 3 * p;
     const int sA = P.species[A], sB = P.species[b];
     const int nA = P.n_ao[sA], nB = P.n_ao[sB], mA = P.n_abf[sA], mB = P.n_abf[sB];
-    const int pA = rup16(nA), pB = rup16(nB);
+    const int pB = rup16(nB);
     const int MA = rup16(mA), MB = rup16(mB);
     const int NAB = nA * pB, KZ = NAB + 8;
     const int y1 = ylut_get(P, A, b, Rb[0], Rb[1], Rb[2]);
     const int y2 = ylut_get(P, b, A, -Rb[0], -Rb[1], -Rb[2]);
-    const uint16_t* Yab = X.Ysp + P.y_off[y1];   // [alpha][b][pA]
-    const uint16_t* Yba = X.Ysp + P.y_off[y2];   // [beta][a][pB]
-    const long long pl_ab = (long long)mA * nB * pA, pl_ba = (long long)mB * nA * pB;
+    const uint16_t* YabT = X.YspT + X.y_idx[y1] * X.yT_blk;   // Y^{AB} transposed: [alpha][a][pB]
+    const uint16_t* Yba = X.Ysp + P.y_off[y2];                  // [beta][a][pB]
+    const long long pl_abT = X.yT_blk / NP, pl_ba = (long long)mB * nA * pB;
     const uint16_t* Vp = X.Vm + X.vm_off[p];
     const float* V = reinterpret_cast<const float*>(Vp + NP * mA * MB);
     const int nvb = mA * mB;
     __syncthreads();
-    // stage Y^{BA} rows (contiguous copy) and Y^{AB} transposed
-    for (int e = threadIdx.x; e < MB * KZ; e += blockDim.x) {
-      const int be = e / KZ, c = e - be * KZ;
-      const bool in = be < mB && c < NAB;
+    // stage the rows [(a,b)] of Y^{BA} (by beta) and of the transposed Y^{AB}
+    // (by alpha) with 16-byte copies (rows NAB long, shared-memory stride KZ;
+    // rows past n_abf zero, columns past NAB never read)
+    {
+      const int nch = NAB >> 3;
+      for (int e = threadIdx.x; e < (MB + MA) * nch; e += blockDim.x) {
+        const bool isA = e >= MB * nch;
+        const int e2 = isA ? e - MB * nch : e;
+        const int row = e2 / nch, ch = e2 - row * nch;
+        const bool in = row < (isA ? mA : mB);
 #pragma unroll
-      for (int pp = 0; pp < NP; ++pp) Yb[(size_t)pp * MB * KZ + e] = in ? Yba[pp * pl_ba + (long long)be * NAB + c] : (uint16_t)0;
-    }
-    for (int e = threadIdx.x; e < MA * KZ; e += blockDim.x) {
-      const int al = e / KZ, c = e - al * KZ;
-      const int a = c / pB, bb = c - a * pB;
-      const bool in = al < mA && c < NAB && bb < nB;
-#pragma unroll
-      for (int pp = 0; pp < NP; ++pp)
-        Ya[(size_t)pp * MA * KZ + e] = in ? Yab[pp * pl_ab + ((long long)al * nB + bb) * pA + a] : (uint16_t)0;
+        for (int pp = 0; pp < NP; ++pp) {
+          uint4 v = make_uint4(0u, 0u, 0u, 0u);
+          if (in)
+            v = *reinterpret_cast<const uint4*>((isA ? YabT + pp * pl_abT : Yba + pp * pl_ba) + (long long)row * NAB + 8 * ch);
+          uint16_t* dst = isA ? Ya + (size_t)pp * MA * KZ : Yb + (size_t)pp * MB * KZ;
+          *reinterpret_cast<uint4*>(dst + (size_t)row * KZ + 8 * ch) = v;
+        }
+      }
     }
     __syncthreads();
     // R2^T (M = beta, N = alpha, K = (a,b))
@@ -1209,6 +1214,28 @@ __global__ void __launch_bounds__(192) k_ybuild_umma(DevPlan P, MixPlan X, const
             o.z = x0 + 2 < nX ? eh[(rl + 2) * 33 + zz] : 0.f;
             o.w = x0 + 3 < nX ? eh[(rl + 3) * 33 + zz] : 0.f;
             *reinterpret_cast<float4*>(Yf + ((long long)zz * mX + al) * 16 + 4 * cq) = o;
+          }
+        }
+        // transposed pieces for the second product: accumulator row (alpha, x)
+        // with the 16 z of key i (z >= n_ao(Z) zero); every row of the tile
+        // is this CTA's own
+        if (X.YspT) {
+          uint16_t* yt = X.YspT + X.y_idx[ykey[i]] * X.yT_blk + (long long)row0 * 16;
+          const long long tplane = X.yT_blk / NP;
+          for (int c = et; c < (rend - row0) * 2; c += 128) {
+            const int rl = c >> 1, hz = c & 1;
+            float f0[4], f1[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              f0[k] = 8 * hz + k < nZ ? eh[rl * 33 + 8 * hz + k] : 0.f;
+              f1[k] = 8 * hz + 4 + k < nZ ? eh[rl * 33 + 8 * hz + 4 + k] : 0.f;
+            }
+            uint2 p0[NP], p1[NP];
+            split4<NP>(f0, p0);
+            split4<NP>(f1, p1);
+#pragma unroll
+            for (int pp = 0; pp < NP; ++pp)
+              *reinterpret_cast<uint4*>(yt + pp * tplane + rl * 16 + 8 * hz) = make_uint4(p0[pp].x, p0[pp].y, p1[pp].x, p1[pp].y);
           }
         }
         // alphas shared with a neighbouring row tile
