@@ -113,11 +113,13 @@ struct hfx_plan {
   // device model
   int *d_species = nullptr, *d_n_ao = nullptr, *d_n_abf = nullptr;
   long long *d_G_off = nullptr, *d_M_off = nullptr;
-  double *d_G = nullptr, *d_Gp = nullptr, *d_M = nullptr, *d_Mnorm = nullptr;
+  double *d_G = nullptr, *d_Gp = nullptr, *d_M = nullptr, *d_Mnorm = nullptr, *d_Gmom = nullptr;
   double* d_Dval = nullptr;
   long long* d_Doff = nullptr;
   int* d_Didx = nullptr;
   double* d_Dkept = nullptr;
+  bool dnorm_done = false;     // D norms taken (once per plan)
+  long long d_kept = 0;
   int* d_dlut = nullptr;
   int HD[3] = {0, 0, 0};
 
@@ -134,7 +136,7 @@ struct hfx_plan {
   std::vector<void*> list_bufs;   // freed on rebuild
   int *c_ptr = nullptr, *c_home = nullptr, *c_j = nullptr, *c_R = nullptr;
   long long* c_off = nullptr;
-  double *Cst = nullptr, *dCst = nullptr, *c_norm = nullptr;
+  double *Cst = nullptr, *dCst = nullptr, *c_norm = nullptr, *c_sc = nullptr;
   unsigned char* c_keep = nullptr;
   int *v_ptr = nullptr, *v_home = nullptr, *v_j = nullptr, *v_R = nullptr, *v_didx = nullptr;
   double* v_norm = nullptr;
@@ -275,7 +277,7 @@ void upload_model(hfx_plan* P, const hfx_system* sys, const hfx_model* m) {
       gsz += (long long)P->n_abf[a] * P->n_ao[a] * P->n_ao[b];
       msz += (long long)P->n_abf[a] * P->n_abf[b];
     }
-  std::vector<double> G(gsz), M(msz), Gp, Mnorm(S * S);
+  std::vector<double> G(gsz), M(msz), Gp, Mnorm(S * S), Gmom(3 * S * S, 0.0);
   if (m->G_aniso) Gp.resize(gsz);
   double mmax = 0;
   for (int a = 0; a < S; ++a)
@@ -291,6 +293,13 @@ void upload_model(hfx_plan* P, const hfx_system* sys, const hfx_model* m) {
       }
       double s2 = 0;
       for (long long k = 0; k < nm; ++k) s2 += M[moff[a * S + b] + k] * M[moff[a * S + b] + k];
+      double* gm = &Gmom[3 * (a * S + b)];   // moments of the C templates (closed-form C norms)
+      for (long long k = 0; k < ng; ++k) {
+        const double gv = G[goff[a * S + b] + k], gq = m->G_aniso ? Gp[goff[a * S + b] + k] : 0.0;
+        gm[0] += gv * gv;
+        gm[1] += gv * gq;
+        gm[2] += gq * gq;
+      }
       Mnorm[a * S + b] = std::sqrt(s2);
       mmax = std::max(mmax, Mnorm[a * S + b]);
     }
@@ -314,6 +323,7 @@ void upload_model(hfx_plan* P, const hfx_system* sys, const hfx_model* m) {
   P->d_G = P->mem.alloc<double>(gsz);
   P->d_M = P->mem.alloc<double>(msz);
   P->d_Mnorm = P->mem.alloc<double>(S * S);
+  P->d_Gmom = P->mem.alloc<double>(3 * S * S);
   upload(P->d_species, P->species, s);
   upload(P->d_n_ao, P->n_ao, s);
   upload(P->d_n_abf, P->n_abf, s);
@@ -322,6 +332,7 @@ void upload_model(hfx_plan* P, const hfx_system* sys, const hfx_model* m) {
   upload(P->d_G, G, s);
   upload(P->d_M, M, s);
   upload(P->d_Mnorm, Mnorm, s);
+  upload(P->d_Gmom, Gmom, s);
   if (m->G_aniso) {
     P->d_Gp = P->mem.alloc<double>(gsz);
     upload(P->d_Gp, Gp, s);
@@ -426,6 +437,7 @@ DevPlan make_devplan(hfx_plan* P, const double* lattice) {
   D.M_off = P->d_M_off;
   D.M = P->d_M;
   D.Mnorm = P->d_Mnorm;
+  D.Gmom = P->d_Gmom;
   for (int k = 0; k < 3; ++k) D.e[k] = P->e[k];
   D.RC = P->RC;
   D.omega = P->omega;
@@ -454,6 +466,7 @@ DevPlan make_devplan(hfx_plan* P, const double* lattice) {
   D.c_R = P->c_R;
   D.c_off = P->c_off;
   D.Cst = P->Cst;
+  D.c_sc = P->c_sc;
   D.dCst = P->dCst;
   D.c_norm = P->c_norm;
   D.c_keep = P->c_keep;
@@ -634,6 +647,7 @@ void build_lists(hfx_plan* P, const double* L, const double* pos) {
   P->c_R = P->lalloc<int>(3 * (size_t)nC);
   P->c_off = P->lalloc<long long>(nC + 1);
   P->Cst = P->lalloc<double>(P->c_elems);
+  P->c_sc = P->lalloc<double>(8 * (size_t)nC);
   P->dCst = P->lalloc<double>(3 * P->c_elems);
   P->c_norm = P->lalloc<double>(nC);
   P->c_keep = P->lalloc<unsigned char>(nC);
@@ -937,8 +951,15 @@ void evaluate(hfx_plan* P, const double* L, hfx_stats* st) {
   ck(cudaMemsetAsync(P->d_tot + kTot, 0, hfx::CNT_N * sizeof(long long), s), "memset");
   ck(cudaMemsetAsync(P->gC, 0, 3 * (size_t)P->nC * sizeof(double), s), "memset");
   ck(cudaMemsetAsync(P->gV, 0, 3 * (size_t)P->nV * sizeof(double), s), "memset");
-  ck(hfx::launch_dnorm(D, s), "dnorm");
-  ck(hfx::launch_cblocks(D, reuse ? 1 : 0, s), "cblocks");
+  // D is fixed for the plan: its norms and step-1 decisions are taken once
+  const bool dnorm_now = !P->dnorm_done;
+  if (dnorm_now) ck(hfx::launch_dnorm(D, s), "dnorm");
+  // the split path evaluates C from the block model where it stores the
+  // operands; only the FP64 path writes the FP64 C blocks
+  if (P->np)
+    ck(hfx::launch_cnorm(D, reuse ? 1 : 0, s), "cnorm");
+  else
+    ck(hfx::launch_cblocks(D, reuse ? 1 : 0, s), "cblocks");
   ck(hfx::launch_vnorm(D, reuse ? 1 : 0, s), "vnorm");
   tm.mark();  // 1
   if (!reuse) {
@@ -973,6 +994,10 @@ void evaluate(hfx_plan* P, const double* L, hfx_stats* st) {
   ck(cudaMemcpyAsync(P->tot, P->d_tot, kTot * sizeof(long long), cudaMemcpyDeviceToHost, s), "D2H totals");
   ck(cudaMemcpyAsync(P->cnt, P->d_tot + kTot, hfx::CNT_N * sizeof(long long), cudaMemcpyDeviceToHost, s), "D2H counts");
   ck(cudaStreamSynchronize(s), "screening");
+  if (dnorm_now) {
+    P->d_kept = (long long)P->cnt[hfx::CNT_D];
+    P->dnorm_done = true;
+  }
   if (P->opt.freeze_lists) P->frozen_ready = true;
   tm.mark();  // 2
   if (!P->np) {
@@ -1071,7 +1096,7 @@ void evaluate(hfx_plan* P, const double* L, hfx_stats* st) {
     hfx_stats S{};
     S.c_pairs = (long long)P->cnt[hfx::CNT_C];
     S.v_pairs = (long long)P->cnt[hfx::CNT_V];
-    S.d_blocks = (long long)P->cnt[hfx::CNT_D];
+    S.d_blocks = P->d_kept;
     S.triplets = (long long)P->cnt[hfx::CNT_TRIP];
     S.term1_pairs = P->tot[4];
     S.term2_pairs = P->tot[5];

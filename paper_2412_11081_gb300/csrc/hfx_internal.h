@@ -30,6 +30,7 @@ struct DevPlan {
   const long long* M_off;
   const double* M;
   const double* Mnorm;         // [S*S] ||M_st||_F
+  const double* Gmom;          // [S*S*3] sum G^2, sum G G', sum G'^2 of each template pair
   double e[3];
   double RC, omega;
   double thC, thdC, thV, thdV, thD, thCS;
@@ -57,6 +58,7 @@ struct DevPlan {
   double* Cst;
   double* dCst;
   double* c_norm;              // max(||C||, ||grad C||) if kept, else 0
+  double* c_sc;                // [nC*8] scalars of C = G f + G' fa, grad C = G g + G' ga (split path)
   unsigned char* c_keep;
 
   // V-pair candidates
@@ -151,6 +153,9 @@ long long launch_count();
 // Kernel launchers (hfx_kernels.cu).  Each returns the launch's cudaError_t.
 cudaError_t launch_dnorm(const DevPlan& P, cudaStream_t s);
 cudaError_t launch_cblocks(const DevPlan& P, int frozen, cudaStream_t s);
+// Split path: per-pair scalars of C and the step-1 decision from the
+// template moments, without writing the FP64 blocks.
+cudaError_t launch_cnorm(const DevPlan& P, int frozen, cudaStream_t s);
 cudaError_t launch_vnorm(const DevPlan& P, int frozen, cudaStream_t s);
 cudaError_t launch_yhat(const DevPlan& P, cudaStream_t s);
 cudaError_t launch_screen(const DevPlan& P, cudaStream_t s);

@@ -153,6 +153,37 @@ __global__ void k_cblocks(DevPlan P, int frozen) {
   }
 }
 
+// Split path: one thread per C pair.  The scalars of C = G f + G' fa and
+// grad_c C = G g_c + G' ga_c are stored for the kernels that write the
+// operand stores, and the norms come from the template moments:
+// ||C||^2 = f^2 S_GG + 2 f fa S_GG' + fa^2 S_G'G', and the same with
+// (g_c, ga_c) summed over c for ||grad C||^2.
+__global__ void k_cnorm(DevPlan P, int frozen) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P.nC; p += gridDim.x * blockDim.x) {
+    double sc[8];
+    c_pair_eval(P, p, sc);
+    double* o = P.c_sc + 8 * (long long)p;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) o[k] = sc[k];
+    const double* mo = P.Gmom + 3 * (P.species[P.c_home[p]] * P.S + P.species[P.c_j[p]]);
+    const double nc2 = sc[0] * sc[0] * mo[0] + 2.0 * sc[0] * sc[1] * mo[1] + sc[1] * sc[1] * mo[2];
+    double ng2 = 0.0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      ng2 += sc[2 + c] * sc[2 + c] * mo[0] + 2.0 * sc[2 + c] * sc[5 + c] * mo[1] + sc[5 + c] * sc[5 + c] * mo[2];
+    const double nc = sqrt(fmax(nc2, 0.0)), ng = sqrt(fmax(ng2, 0.0));
+    bool keep;
+    if (frozen) {
+      keep = P.c_keep[p] != 0;
+    } else {
+      keep = (nc > P.thC) || (ng > P.thdC);
+      P.c_keep[p] = keep;
+    }
+    P.c_norm[p] = keep ? fmax(nc, ng) : 0.0;
+    if (keep) atomicAdd(&P.cnt[CNT_C], 1ull);
+  }
+}
+
 // ---------------------------------------------------------------- K1: V norms
 // One thread per V pair.  V = M h(r) and grad_d V = M h'(r) d/r (on-site:
 // V = M, grad V = 0), so ||V|| = |h| ||M|| and ||grad V|| = |h'| ||M|| (the
@@ -775,6 +806,13 @@ cudaError_t launch_cblocks(const DevPlan& P, int frozen, cudaStream_t s) {
   if (P.nC == 0) return cudaSuccess;
   ++g_launches;
   k_cblocks<<<grid_for(P.nC, 1, 152 * 64), kThreads, 0, s>>>(P, frozen);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cnorm(const DevPlan& P, int frozen, cudaStream_t s) {
+  if (P.nC == 0) return cudaSuccess;
+  ++g_launches;
+  k_cnorm<<<grid_for(P.nC, kThreads), kThreads, 0, s>>>(P, frozen);
   return cudaGetLastError();
 }
 

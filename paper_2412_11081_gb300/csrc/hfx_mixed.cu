@@ -166,13 +166,14 @@ __global__ void k_cpieces(DevPlan P, MixPlan X) {
     const int sA = P.species[A], sF = P.species[f];
     const int rows = P.n_abf[sA] * P.n_ao[sA], nF = P.n_ao[sF];
     const int nt = (rows + 127) >> 7;
-    const double* C = P.Cst + P.c_off[q];
-    const double* dC = P.dCst + 3 * P.c_off[q];
+    // C and grad C evaluated from the block model (scalars of k_cnorm)
+    const double* sc = P.c_sc + 8 * (long long)q;
+    const long long go = P.G_off[sA * P.S + sF];
     uint16_t* out = X.Cm + X.cm_off[q];
     for (int e = threadIdx.x; e < nt * 128 * 16; e += blockDim.x) {
       const int r = e >> 4, c = e & 15;
       uint16_t pc[NP];
-      split_f<NP>((r < rows && c < nF) ? (float)C[r * nF + c] : 0.f, pc);
+      split_f<NP>((r < rows && c < nF) ? (float)model::c_value(P, sc, go, r * nF + c, 0) : 0.f, pc);
 #pragma unroll
       for (int p = 0; p < NP; ++p) out[((r >> 7) * NP + p) * 2048 + tix(r & 127, c)] = pc[p];
     }
@@ -181,7 +182,7 @@ __global__ void k_cpieces(DevPlan P, MixPlan X) {
     for (int w = threadIdx.x; w < 3 * nt * 2048; w += blockDim.x) {
       const int c = w / (nt * 2048), wi = w - c * nt * 2048;
       const int r = ((wi >> 11) << 7) + ((wi >> 2) & 127), ff = (((wi >> 9) & 3) << 2) + (wi & 3);
-      g[w] = (r < rows && ff < nF) ? (float)dC[(long long)c * rows * nF + (long long)r * nF + ff] : 0.f;
+      g[w] = (r < rows && ff < nF) ? (float)model::c_value(P, sc, go, r * nF + ff, c + 1) : 0.f;
     }
   }
 }

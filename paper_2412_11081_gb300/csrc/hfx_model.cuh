@@ -54,5 +54,40 @@ __device__ __forceinline__ void v_pair(const DevPlan& P, int p, double& h, doubl
   g[2] = s[3];
 }
 
+// C pair p of the block model: C = G f + G' fa and grad_c C = G g_c + G' ga_c
+// (G' the anisotropic template, fa = f (d.e)/R_C; on site C = G, grad C = 0).
+// s = {f, fa, g0, g1, g2, ga0, ga1, ga2}.
+__device__ __forceinline__ void c_pair_eval(const DevPlan& P, int p, double s[8]) {
+  const int A = P.c_home[p], j = P.c_j[p];
+  const int* R = P.c_R + 3 * p;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s[k] = 0.0;
+  s[0] = 1.0;
+  if (A == j && R[0] == 0 && R[1] == 0 && R[2] == 0) return;
+  double d[3];
+  pair_vector(P, A, j, R, d);
+  const double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+  double f, fp;
+  radial_f(r, P.RC, f, fp);
+  s[0] = f;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) s[2 + c] = fp * d[c] / r;
+  if (P.Gp) {
+    const double de = d[0] * P.e[0] + d[1] * P.e[1] + d[2] * P.e[2];
+    s[1] = f * de / P.RC;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) s[5 + c] = (fp * (d[c] / r) * de + f * P.e[c]) / P.RC;
+  }
+}
+
+// Element t of component c (0: C, 1..3: grad C) of C pair p from its stored
+// scalars cs (c_pair_eval) and the templates at offset go.
+__device__ __forceinline__ double c_value(const DevPlan& P, const double* cs, long long go, int t, int c) {
+  const double Gv = P.G[go + t];
+  double v = Gv * (c == 0 ? cs[0] : cs[1 + c]);
+  if (P.Gp) v = v + P.Gp[go + t] * (c == 0 ? cs[1] : cs[4 + c]);
+  return v;
+}
+
 }  // namespace model
 }  // namespace hfx

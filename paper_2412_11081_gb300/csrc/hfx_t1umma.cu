@@ -77,9 +77,9 @@ __device__ __forceinline__ void ep_at(int w, int& alpha, int& col) {
 // Item kk (C pair q = list[kk]): NP bf16 pieces of C_AF as [alpha (64)][(f,a) (KP)]
 // in core-matrix order (8-row groups of KP/8 core matrices), then C and
 // grad C in FP32 as four planes of 64 x KP32 (KP rounded up to 32) in
-// epilogue load order (ep_off).  Zero padded.  Each FP64 plane of the C pair
-// ([(alpha,a)][f]) is read once, coalesced, into shared memory as FP32; the
-// outputs are written in storage order, four elements per thread.
+// epilogue load order (ep_off).  Zero padded.  Each plane of the C pair
+// ([(alpha,a)][f]) is evaluated from the block model into shared memory as
+// FP32; the outputs are written in storage order, four elements per thread.
 constexpr int kCStoreSmem = 64 * 16 * 16 * 4;   // one plane of n_abf <= 64, n_ao <= 16
 
 template <int NP>
@@ -94,10 +94,11 @@ __global__ void k_t1u_cstore(DevPlan P, T1UPlan U, const int* list, int n) {
     const int ncq = mA * nA * nF;
     uint16_t* out = U.Cu + (long long)kk * U.cu_blk;
     float* pl = reinterpret_cast<float*>(out + (long long)NP * 64 * KP);
+    const double* sc = P.c_sc + 8 * (long long)q;   // C = G f + G' fa, grad C = G g + G' ga (block model)
+    const long long go = P.G_off[sA * P.S + P.species[F]];
     for (int c = 0; c < 4; ++c) {
-      const double* src = c == 0 ? P.Cst + P.c_off[q] : P.dCst + 3 * P.c_off[q] + (long long)(c - 1) * ncq;
       __syncthreads();
-      for (int e = threadIdx.x; e < ncq; e += blockDim.x) cs[e] = (float)src[e];
+      for (int e = threadIdx.x; e < ncq; e += blockDim.x) cs[e] = (float)model::c_value(P, sc, go, e, c);
       __syncthreads();
       auto val = [&](int al, int col) -> float {
         const int f = col >> 4, a = col & 15;
