@@ -887,7 +887,7 @@ void split_density(hfx_plan* P) {
     P->Df = P->mem.alloc<float>((size_t)P->n_d * 256);
     hfx::T1UPlan U{};
     U.Df = P->Df;
-    ck(hfx::launch_t1u_stores(D, U, P->np, nullptr, 0, nullptr, 0, true, P->stream), "D FP32 store");
+    ck(hfx::launch_t1u_stores(D, U, P->np, nullptr, 0, true, P->stream), "D FP32 store");
   }
   ck(cudaStreamSynchronize(P->stream), "dsplit");
 }
@@ -1023,9 +1023,6 @@ void evaluate(hfx_plan* P, const double* L, hfx_stats* st) {
     X.blist = P->blist;
     ensure_buf(P, P->Vm, P->Vmcap, P->tot[8]);
     X.Vm = P->Vm;
-    // the split path evaluates V and grad V from the block model inside the
-    // store kernels (k_vpieces, k_t1u_vstore): no FP64 V store
-    ck(hfx::launch_vpieces(D, X, P->np, P->v_list, (int)P->tot[3], s), "vpieces");
     ck(hfx::launch_cpieces(D, X, P->np, s), "cpieces");
     hfx::T1UPlan U{};
     if (P->t1u) {
@@ -1044,9 +1041,15 @@ void evaluate(hfx_plan* P, const double* L, hfx_stats* st) {
       U.Df = P->Df;
       U.t1_idx = P->t1_idx;
       X.Yf = P->Yf;
-      ck(hfx::launch_t1u_stores(D, U, P->np, P->t1q_lpt, (int)P->tot[7], P->t1_list, (int)P->tot[4], false, s),
-         "term-1 operand stores");
+      ck(hfx::launch_t1u_stores(D, U, P->np, P->t1q_lpt, (int)P->tot[7], false, s), "term-1 C store");
     }
+    // the split path evaluates V and grad V from the block model where it
+    // writes the operand stores (no FP64 V blocks): one pass per needed pair
+    // for both products when the tcgen05 first product runs
+    if (P->t1u)
+      ck(hfx::launch_vstores(D, X, U, P->np, P->v_list, (int)P->tot[3], s), "V stores");
+    else
+      ck(hfx::launch_vpieces(D, X, P->np, P->v_list, (int)P->tot[3], s), "vpieces");
     X.yT_blk = (long long)P->np * P->MC * 128 * 16;
     ensure_buf(P, P->YspT, P->YspTcap, std::max(1LL, P->tot[1]) * X.yT_blk);
     X.YspT = P->YspT;

@@ -212,8 +212,12 @@ cudaError_t launch_lpt_order(const int* qcnt, const int* list, int n_max, const 
                              cudaStream_t s);
 int t1u_max_slots();
 cudaError_t t1u_set_smem(int np, size_t smem);
-cudaError_t launch_t1u_stores(const DevPlan& P, const T1UPlan& U, int np, const int* qlist, int nq, const int* vlist,
-                              int nv, bool dstore, cudaStream_t s);
+// Needed V pairs: the second product's V store (MixPlan::Vm) and, with U.Vu
+// set, the tcgen05 first product's V store, in one pass per pair.
+cudaError_t launch_vstores(const DevPlan& P, const MixPlan& X, const T1UPlan& U, int np, const int* list, int n,
+                           cudaStream_t s);
+cudaError_t launch_t1u_stores(const DevPlan& P, const T1UPlan& U, int np, const int* qlist, int nq, bool dstore,
+                              cudaStream_t s);
 cudaError_t launch_t1_umma(const DevPlan& P, const MixPlan& X, const T1UPlan& U, int np, const int* qlist, int n,
                            size_t smem, int* work, int* err, cudaStream_t s);
 

@@ -127,37 +127,77 @@ __global__ void k_t1u_cstore(DevPlan P, T1UPlan U, const int* list, int n) {
   }
 }
 
-// Term-1 V pair k (p = list[k]): NP bf16 pieces of V_AB as [alpha (64)][beta (64)]
-// in core-matrix order, then grad V in FP32 as three 64 x 64 planes in
-// epilogue load order (ep_off).  Zero padded.
+// Every needed V pair p = list[k], in one pass: V and grad V evaluated once
+// from the block model into shared memory (FP32), then
+//   the second product's store X.Vm at vm_off[p]: NP bf16 planes
+//   [alpha][rup16(n_abf(B))] and V, grad V in FP32 [4][n_abf(A) n_abf(B)];
+//   for the pairs of the first product (any bit of v_mask), the tcgen05
+//   store U.Vu at t1_idx[p]: NP pieces [alpha 64][beta 64] in core-matrix
+//   order and grad V in three ep_off planes.
+// Outputs are written in storage order, four elements per thread.
+constexpr int kVStoreSmem = 4 * 64 * 64 * 4;
+
 template <int NP>
-__global__ void k_t1u_vstore(DevPlan P, T1UPlan U, const int* list, int n) {
+__global__ void k_vstores(DevPlan P, MixPlan X, T1UPlan U, const int* list, int n) {
+  extern __shared__ float vsm[];   // [4][mA * mB]: V, grad V
   for (int k = blockIdx.x; k < n; k += gridDim.x) {
     const int p = list[k];
     const int sA = P.species[P.v_home[p]], sB = P.species[P.v_j[p]];
-    const int mA = P.n_abf[sA], mB = P.n_abf[sB];
+    const int mA = P.n_abf[sA], mB = P.n_abf[sB], MB = rup16(mB), nv = mA * mB;
     double h, g[3];
     model::v_pair(P, p, h, g);   // V = M h, grad V = M g (block model)
     const double* M = P.M + P.M_off[sA * P.S + sB];
-    uint16_t* out = U.Vu + (long long)k * U.vu_blk;
-    float* pl = reinterpret_cast<float*>(out + NP * 4096);
-    for (int e = threadIdx.x; e < 4096; e += blockDim.x) {
-      const int al = e >> 6, be = e & 63;
-      const bool in = al < mA && be < mB;
-      uint16_t pc[NP];
-      split_f<NP>(in ? (float)(M[al * mB + be] * h) : 0.f, pc);
-      const int t = (al >> 3) * 512 + (be >> 3) * 64 + (al & 7) * 8 + (be & 7);
-#pragma unroll
-      for (int pp = 0; pp < NP; ++pp) out[pp * 4096 + t] = pc[pp];
+    __syncthreads();
+    for (int e = threadIdx.x; e < nv; e += blockDim.x) {
+      const double m = M[e];
+      vsm[e] = (float)(m * h);
+      vsm[nv + e] = (float)(m * g[0]);
+      vsm[2 * nv + e] = (float)(m * g[1]);
+      vsm[3 * nv + e] = (float)(m * g[2]);
     }
-    for (int w = threadIdx.x; w < 4096; w += blockDim.x) {   // written in storage order
+    __syncthreads();
+    // second-product store
+    uint16_t* out = X.Vm + X.vm_off[p];
+    for (int e4 = threadIdx.x; e4 < mA * MB / 4; e4 += blockDim.x) {
+      const int e = 4 * e4, al = e / MB, be = e - al * MB;
+      float x[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) x[j] = be + j < mB ? vsm[al * mB + be + j] : 0.f;
+      uint2 pc[NP];
+      split4<NP>(x, pc);
+#pragma unroll
+      for (int pp = 0; pp < NP; ++pp) *reinterpret_cast<uint2*>(out + (long long)pp * mA * MB + e) = pc[pp];
+    }
+    float* v32 = reinterpret_cast<float*>(out + (long long)NP * mA * MB);
+    for (int e = threadIdx.x; e < 4 * nv; e += blockDim.x) v32[e] = vsm[e];
+    // first-product store
+    bool t1 = false;
+#pragma unroll
+    for (int w = 0; w < kMaskWords; ++w) t1 = t1 || P.v_mask[(long long)p * kMaskWords + w] != 0u;
+    if (!U.Vu || !t1) continue;
+    uint16_t* vu = U.Vu + U.t1_idx[p] * U.vu_blk;
+    for (int t4 = threadIdx.x; t4 < 1024; t4 += blockDim.x) {   // core-matrix order, 4 columns per thread
+      const int t = 4 * t4;
+      const int al = ((t >> 9) << 3) + ((t >> 3) & 7), be = (((t >> 6) & 7) << 3) + (t & 7);
+      float x[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) x[j] = (al < mA && be + j < mB) ? vsm[al * mB + be + j] : 0.f;
+      uint2 pc[NP];
+      split4<NP>(x, pc);
+#pragma unroll
+      for (int pp = 0; pp < NP; ++pp) *reinterpret_cast<uint2*>(vu + pp * 4096 + t) = pc[pp];
+    }
+    float* pl = reinterpret_cast<float*>(vu + NP * 4096);
+    for (int w4 = threadIdx.x; w4 < 3 * 1024; w4 += blockDim.x) {   // grad V, ep_off order
+      const int c = w4 >> 10;
       int al, be;
-      ep_at(w, al, be);
-      const bool in = al < mA && be < mB;
-      const double m = in ? M[al * mB + be] : 0.0;
-      pl[w] = (float)(m * g[0]);
-      pl[4096 + w] = (float)(m * g[1]);
-      pl[2 * 4096 + w] = (float)(m * g[2]);
+      ep_at(4 * (w4 & 1023), al, be);
+      float4 o;
+      o.x = (al < mA && be < mB) ? vsm[(c + 1) * nv + al * mB + be] : 0.f;
+      o.y = (al < mA && be + 1 < mB) ? vsm[(c + 1) * nv + al * mB + be + 1] : 0.f;
+      o.z = (al < mA && be + 2 < mB) ? vsm[(c + 1) * nv + al * mB + be + 2] : 0.f;
+      o.w = (al < mA && be + 3 < mB) ? vsm[(c + 1) * nv + al * mB + be + 3] : 0.f;
+      *reinterpret_cast<float4*>(pl + 4 * w4) = o;
     }
   }
 }
@@ -910,8 +950,8 @@ cudaError_t t1u_set_smem(int np, size_t smem) {
                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-cudaError_t launch_t1u_stores(const DevPlan& P, const T1UPlan& U, int np, const int* qlist, int nq, const int* vlist,
-                              int nv, bool dstore, cudaStream_t s) {
+cudaError_t launch_t1u_stores(const DevPlan& P, const T1UPlan& U, int np, const int* qlist, int nq, bool dstore,
+                              cudaStream_t s) {
   if (nq > 0) {
     ++g_t1u_launches;
     static bool attr = false;
@@ -923,12 +963,6 @@ cudaError_t launch_t1u_stores(const DevPlan& P, const T1UPlan& U, int np, const 
     const int g = nq < 152 * 3 ? nq : 152 * 3;
     if (np == 2) k_t1u_cstore<2><<<g, 256, kCStoreSmem, s>>>(P, U, qlist, nq);
     else k_t1u_cstore<3><<<g, 256, kCStoreSmem, s>>>(P, U, qlist, nq);
-  }
-  if (nv > 0) {
-    ++g_t1u_launches;
-    const int g = nv < 152 * 16 ? nv : 152 * 16;
-    if (np == 2) k_t1u_vstore<2><<<g, 256, 0, s>>>(P, U, vlist, nv);
-    else k_t1u_vstore<3><<<g, 256, 0, s>>>(P, U, vlist, nv);
   }
   if (dstore && P.n_d > 0) {
     ++g_t1u_launches;
@@ -948,6 +982,22 @@ cudaError_t launch_lpt_order(const int* qcnt, const int* list, int n_max, const 
   k_lpt_hist<<<g, 256, 0, s>>>(qcnt, list, n_dev, hist);
   k_lpt_scan<<<1, 1024, 0, s>>>(hist);
   k_lpt_scatter<<<g, 256, 0, s>>>(qcnt, list, n_dev, hist, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_vstores(const DevPlan& P, const MixPlan& X, const T1UPlan& U, int np, const int* list, int n,
+                           cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  ++g_t1u_launches;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_vstores<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kVStoreSmem);
+    cudaFuncSetAttribute(k_vstores<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kVStoreSmem);
+    attr = true;
+  }
+  const int g = n < 152 * 3 ? n : 152 * 3;
+  if (np == 2) k_vstores<2><<<g, 256, kVStoreSmem, s>>>(P, X, U, list, n);
+  else k_vstores<3><<<g, 256, kVStoreSmem, s>>>(P, X, U, list, n);
   return cudaGetLastError();
 }
 
