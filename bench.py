@@ -95,6 +95,29 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def t1_traffic():
+    """DRAM bytes per si64 launch of the first-product kernel from its ncu
+    summary, or None once the kernel's sources differ from the captured ones."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "k_t1_umma_si8_bf16x3.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    vals = {}
+    for line in text.splitlines():
+        k, _, v = line.strip().partition(": ")
+        if k in ("kernel_sources_sha256_16", "traffic_bytes_per_si64_launch"):
+            vals[k] = v.strip()
+    h = hashlib.sha256()
+    for f in ("hfx_t1umma.cu", "hfx_device.cuh"):
+        with open(os.path.join(ROOT, "paper_2412_11081_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    if vals.get("kernel_sources_sha256_16") != h.hexdigest()[:16] or "traffic_bytes_per_si64_launch" not in vals:
+        return None
+    return float(vals["traffic_bytes_per_si64_launch"])
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -306,7 +329,10 @@ def run_ours(args):
             pk = peaks.get("bf16_tflops_sustained") or 1717.3
             pieces = 6 if args.precision == "bf16x6" else 3
             roofline = {"kernel": kname, "bound": "tensor", "achieved": achieved, "peak": pk,
-                        "unit": "TFLOP/s", "frac": achieved / pk, "traffic": None,
+                        "unit": "TFLOP/s", "frac": achieved / pk,
+                        "traffic": t1_traffic() if (kname == "k_t1_umma" and args.precision == "bf16x3") else None,
+                        "traffic_source": "profiles/k_t1_umma_si8_bf16x3.md: dram read+write of one si8 launch, "
+                                          "scaled to si64 by kept triplets (bytes per launch)",
                         "peak_source": "bf16 dense, sustained, of measured (MEASURED_PEAKS.json)",
                         "note": f"achieved counts algorithmic FLOPs only; the {pieces} bf16 piece products per "
                                 f"multiply and the 13->16 / 50->64 tile padding are not counted",
