@@ -845,18 +845,34 @@ __global__ void __launch_bounds__(kThreads, 1)
                     *reinterpret_cast<uint2*>(urow + (size_t)pp * 64 * KP + (2 * f + (qa >> 1)) * 64) = pk[pp];
                 }
               } else {
-                const float* yrow = Ys + sl * SLOT + beta * 16;
-                for (int f = fa; f < fb; f += 2) {
-                  const bool two = f + 1 < fb;
-                  // the two Y rows of this lane (16-byte chunk c stored at c ^ ysw)
+                // BF16X3: the run's rows rho = (f - fa) mB + beta (the slot's
+                // own order) are shared by all U warps, two per lane and pass
+                // (rho = 16 g + r8 and 16 g + 8 + r8 for row groups g = uw,
+                // uw + kNU, ...), so every warp gets the same share whatever
+                // n_abf(B) is; rows beta >= n_abf(B) are zeroed after the chunk
+                const int nrows = (fb - fa) * mB;
+                const float* ysl = Ys + sl * SLOT;
+                const float inv = 1.0f / (float)mB;
+                for (int g = uw; 16 * g < nrows; g += kNU) {
+                  int rho[2], fr[2], be[2];
+                  rho[0] = 16 * g + r8;
+                  rho[1] = rho[0] + 8;
+#pragma unroll
+                  for (int h = 0; h < 2; ++h) {   // (f - fa, beta) of row rho, exact after the correction
+                    int t = (int)((float)rho[h] * inv);
+                    if (t * mB > rho[h]) --t;
+                    else if ((t + 1) * mB <= rho[h]) ++t;
+                    fr[h] = t;
+                    be[h] = rho[h] - t * mB;
+                  }
+                  const bool v0 = rho[0] < nrows, v1 = rho[1] < nrows;
+                  // the two Y rows of this lane (16-byte chunk c stored at c ^ 2 ((beta >> 1) & 1))
                   float y0[16], y1[16];
   #pragma unroll
                   for (int c4 = 0; c4 < 4; ++c4) {
                     float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
-                    if (beta < mB) {
-                      a0 = *reinterpret_cast<const float4*>(yrow + (f - fa) * mB * 16 + 4 * (c4 ^ ysw));
-                      if (two) a1 = *reinterpret_cast<const float4*>(yrow + (f + 1 - fa) * mB * 16 + 4 * (c4 ^ ysw));
-                    }
+                    if (v0) a0 = *reinterpret_cast<const float4*>(ysl + rho[0] * 16 + 4 * (c4 ^ (2 * ((be[0] >> 1) & 1))));
+                    if (v1) a1 = *reinterpret_cast<const float4*>(ysl + rho[1] * 16 + 4 * (c4 ^ (2 * ((be[1] >> 1) & 1))));
                     y0[4 * c4] = a0.x;
                     y0[4 * c4 + 1] = a0.y;
                     y0[4 * c4 + 2] = a0.z;
@@ -866,51 +882,47 @@ __global__ void __launch_bounds__(kThreads, 1)
                     y1[4 * c4 + 2] = a1.z;
                     y1[4 * c4 + 3] = a1.w;
                   }
-                  // u[a] = sum_b y[b] D[a][b], two a per packed FP32 FMA
+                  // u[a] = sum_b y[b] D[a][b] for four a of each row
                   float2 u0[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}, u1[2] = {u0[0], u0[1]};
-                  if (beta < mB) {
-                    if (two) {
   #pragma unroll
-                      for (int b = 0; b < 16; ++b)
+                  for (int b = 0; b < 16; ++b)
   #pragma unroll
-                        for (int j = 0; j < 2; ++j) {
-                          u0[j].x = fmaf(y0[b], dd[j][b].x, u0[j].x);
-                          u0[j].y = fmaf(y0[b], dd[j][b].y, u0[j].y);
-                          u1[j].x = fmaf(y1[b], dd[j][b].x, u1[j].x);
-                          u1[j].y = fmaf(y1[b], dd[j][b].y, u1[j].y);
-                        }
-                    } else {
-  #pragma unroll
-                      for (int b = 0; b < 16; ++b)
-  #pragma unroll
-                        for (int j = 0; j < 2; ++j) {
-                          u0[j].x = fmaf(y0[b], dd[j][b].x, u0[j].x);
-                          u0[j].y = fmaf(y0[b], dd[j][b].y, u0[j].y);
-                        }
+                    for (int j = 0; j < 2; ++j) {
+                      u0[j].x = fmaf(y0[b], dd[j][b].x, u0[j].x);
+                      u0[j].y = fmaf(y0[b], dd[j][b].y, u0[j].y);
+                      u1[j].x = fmaf(y1[b], dd[j][b].x, u1[j].x);
+                      u1[j].y = fmaf(y1[b], dd[j][b].y, u1[j].y);
                     }
-                  }
-                  if (f + 2 >= fb) {   // every row of the slot has been read and used
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(ye + 8 * sl);
-                  }
                   uint2 pk[NP];
-                  float uf4[4] = {u0[0].x, u0[0].y, u0[1].x, u0[1].y};
-                  split4<NP>(uf4, pk);
+                  if (v0) {
+                    float uf4[4] = {u0[0].x, u0[0].y, u0[1].x, u0[1].y};
+                    split4<NP>(uf4, pk);
+                    uint16_t* ur = Us + (be[0] >> 3) * KP * 8 + (be[0] & 7) * 8 + (qa & 1) * 4 +
+                                   (2 * (fa + fr[0]) + (qa >> 1)) * 64;
   #pragma unroll
-                  for (int pp = 0; pp < NP; ++pp)
-                    *reinterpret_cast<uint2*>(urow + (size_t)pp * 64 * KP + (2 * f + (qa >> 1)) * 64) = pk[pp];
-                  if (two) {
+                    for (int pp = 0; pp < NP; ++pp) *reinterpret_cast<uint2*>(ur + (size_t)pp * 64 * KP) = pk[pp];
+                  }
+                  if (v1) {
                     float ug4[4] = {u1[0].x, u1[0].y, u1[1].x, u1[1].y};
                     split4<NP>(ug4, pk);
+                    uint16_t* ur = Us + (be[1] >> 3) * KP * 8 + (be[1] & 7) * 8 + (qa & 1) * 4 +
+                                   (2 * (fa + fr[1]) + (qa >> 1)) * 64;
   #pragma unroll
-                    for (int pp = 0; pp < NP; ++pp)
-                      *reinterpret_cast<uint2*>(urow + (size_t)pp * 64 * KP + (2 * (f + 1) + (qa >> 1)) * 64) = pk[pp];
+                    for (int pp = 0; pp < NP; ++pp) *reinterpret_cast<uint2*>(ur + (size_t)pp * 64 * KP) = pk[pp];
                   }
                 }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(ye + 8 * sl);   // every row of the slot has been read
               }
               ++ys;
             }
-            // rows f >= nF of the chunk are zero
+            // rows beta >= n_abf(B) (BF16X3 computes only the rows it reads)
+            // and rows f >= nF of the chunk are zero
+            if (NP == 2 && beta >= mB)
+              for (int f = f0; f < e; ++f)
+#pragma unroll
+                for (int pp = 0; pp < NP; ++pp)
+                  *reinterpret_cast<uint2*>(urow + (size_t)pp * 64 * KP + (2 * f + (qa >> 1)) * 64) = make_uint2(0u, 0u);
             for (int f = max(f0, e); f < f1; ++f)
 #pragma unroll
               for (int pp = 0; pp < NP; ++pp)
