@@ -670,23 +670,57 @@ __global__ void __launch_bounds__(kWarps * 32) k_term2_pairs(DevPlan P, MixPlan 
     {
       uint16_t* Zo = X.Zst + (long long)kk * zblk;
       const int MT = MA >> 4, NT = NAB >> 3;
-      for (int t = warp; t < MT * NT; t += kWarps) {
+      // With n_abf(B) <= 64 (four k steps) a warp keeps one row tile mt and
+      // its V fragments in registers across the column tiles it takes;
+      // larger n_abf(B) reload them per tile.
+      const bool keepA = MB <= 64;
+      const int nslot = keepA ? kWarps / MT : 1;
+      const int t0 = keepA ? (warp < nslot * MT ? (warp % MT) * NT + warp / MT : MT * NT) : warp;
+      const int tstep = keepA ? nslot : kWarps;
+      uint32_t ak[4][NP][4];
+      int mt_loaded = -1;
+      for (int t = t0; t < (keepA ? ((t0 / NT) + 1) * NT : MT * NT); t += tstep) {
         const int mt = t / NT, nt = t - mt * NT;
-        float acc[4] = {0.f, 0.f, 0.f, 0.f};
-        for (int k0 = 0; k0 < MB; k0 += 16) {
-          uint32_t af[NP][4], bf[NP][2];
+        if (keepA && mt != mt_loaded) {
 #pragma unroll
-          for (int h = 0; h < 4; ++h) {
-            const int al = mt * 16 + gid + ((h & 1) ? 8 : 0);
-            const int kc = k0 + 2 * tig + ((h & 2) ? 8 : 0);
+          for (int ks = 0; ks < 4; ++ks)
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+              const int al = mt * 16 + gid + ((h & 1) ? 8 : 0);
+              const int kc = ks * 16 + 2 * tig + ((h & 2) ? 8 : 0);
+#pragma unroll
+              for (int pp = 0; pp < NP; ++pp)
+                ak[ks][pp][h] = (al < mA && kc < MB) ? *reinterpret_cast<const uint32_t*>(Vp + pp * mA * MB + al * MB + kc) : 0u;
+            }
+          mt_loaded = mt;
+        }
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        if (keepA) {
+#pragma unroll
+          for (int ks = 0; ks < 4; ++ks) {
+            if (ks * 16 >= MB) break;
+            uint32_t bf[NP][2];
 #pragma unroll
             for (int pp = 0; pp < NP; ++pp)
-              af[pp][h] = al < mA ? *reinterpret_cast<const uint32_t*>(Vp + pp * mA * MB + al * MB + kc) : 0u;
+              ldm_x2_trans(bf[pp], Yb + (size_t)pp * MB * KZ + (size_t)(ks * 16 + (lane & 15)) * KZ + nt * 8);
+            mma_split<NP>(acc, ak[ks], bf);
           }
+        } else {
+          for (int k0 = 0; k0 < MB; k0 += 16) {
+            uint32_t af[NP][4], bf[NP][2];
 #pragma unroll
-          for (int pp = 0; pp < NP; ++pp)
-            ldm_x2_trans(bf[pp], Yb + (size_t)pp * MB * KZ + (size_t)(k0 + (lane & 15)) * KZ + nt * 8);
-          mma_split<NP>(acc, af, bf);
+            for (int h = 0; h < 4; ++h) {
+              const int al = mt * 16 + gid + ((h & 1) ? 8 : 0);
+              const int kc = k0 + 2 * tig + ((h & 2) ? 8 : 0);
+#pragma unroll
+              for (int pp = 0; pp < NP; ++pp)
+                af[pp][h] = al < mA ? *reinterpret_cast<const uint32_t*>(Vp + pp * mA * MB + al * MB + kc) : 0u;
+            }
+#pragma unroll
+            for (int pp = 0; pp < NP; ++pp)
+              ldm_x2_trans(bf[pp], Yb + (size_t)pp * MB * KZ + (size_t)(k0 + (lane & 15)) * KZ + nt * 8);
+            mma_split<NP>(acc, af, bf);
+          }
         }
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
