@@ -1076,7 +1076,7 @@ void evaluate(hfx_plan* P, const double* L, hfx_stats* st) {
     ensure_buf(P, P->q2tab, P->q2tabcap, std::max(1LL, hfx::q2tab_size((int)P->tot[5], FC)));
     X.q2tab = P->q2tab;
     ck(hfx::launch_term2_mma(D, X, P->np, P->t2_list, P->t2_idx, (int)P->tot[5], P->MAmax, P->KZmax, P->zblk, P->ZROWS,
-                             FC, P->MC, hfx::q2_umma_segments(P->maxV), P->q2_flush, P->drows, P->smem_m2, P->d_err, s),
+                             FC, P->MC, hfx::q2_umma_segments(P->maxV, P->np), P->q2_flush, P->drows, P->smem_m2, P->d_err, s),
        "term2");
     tm.mark();  // 5
   }

@@ -197,7 +197,7 @@ cudaError_t launch_term1_mma(const DevPlan& P, const MixPlan& X, int np, const i
 cudaError_t launch_term2_mma(const DevPlan& P, const MixPlan& X, int np, const int* list, const long long* slot0,
                              int n, int MAmax, int KZmax, long long zblk, int zrows, int FC, int MC, int nseg,
                              int flush, const DRows& drows, size_t smem, int* err, cudaStream_t s);
-int q2_umma_segments(int max_pairs_per_atom);
+int q2_umma_segments(int max_pairs_per_atom, int np);
 
 // tcgen05 first exchange product (hfx_t1umma.cu): shapes n_abf <= 64, n_ao <= 16.
 long long t1u_launch_count();

@@ -812,22 +812,35 @@ __device__ __forceinline__ void stage_d(int lane, uint16_t* stB, const int* md, 
 
 }  // namespace umma
 
-template <int NP>
+// TPC row tiles of 128 rows per CTA share each K step's D blocks (the B
+// operand): with TPC = 2 a step moves 3 NP tiles for two tiles' work instead
+// of 2 NP for one, in 3 stages, one accumulator per tile (no double buffer;
+// two CTAs per SM overlap one's epilogue with the other's MMAs) and 512 pairs
+// of metadata; TPC = 1 keeps 4 stages and two accumulators.
+template <int TPC>
+struct Q2Shape {
+  static constexpr int kS = TPC == 2 ? 3 : umma::kStages;          // stages
+  static constexpr int kMP = TPC == 2 ? 512 : umma::kMetaPairs;    // pairs per CTA segment
+  static constexpr int kNB = TPC == 2 ? 1 : 2;                     // accumulator buffers
+};
+
+template <int NP, int TPC>
 __global__ void __launch_bounds__(192) k_q2_umma(DevPlan P, MixPlan X, const int* list, const long long* slot0,
                                                  int n_slots, int FC8, int MC, int NSEG, long long zblk,
                                                  int flush, const __grid_constant__ DRows drows, int* err) {
-  // Warp roles: warp 0 lane 0 produces (bulk async copies into a 4-stage
+  // Warp roles: warp 0 lane 0 produces (bulk async copies into a stage
   // ring, completion counted in bytes on full[s]); warp 1 lane 0 issues the
-  // MMAs (all piece products of a pair into one of two TMEM accumulators,
-  // commits free the stage / hand the accumulator to the epilogue); warps 2..5
-  // read the accumulator (each its 32-lane quarter of tensor memory) and dot
-  // it with grad C_AF.  No block barrier inside the pipeline.
+  // MMAs (all piece products of a pair into the TMEM accumulators, commits
+  // free the stage / hand the accumulators to the epilogue); warps 2..5 read
+  // the accumulators (each its 32-lane quarter of tensor memory) and dot
+  // them with grad C_AF.  No block barrier inside the pipeline.
   using namespace umma;
+  constexpr int KS = Q2Shape<TPC>::kS, KMP = Q2Shape<TPC>::kMP, NB = Q2Shape<TPC>::kNB;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  uint16_t* stA = reinterpret_cast<uint16_t*>(smem_raw);                  // [kStages][NP][kTileElems]
-  uint16_t* stB = stA + (size_t)kStages * NP * kTileElems;                // [kStages][NP][kTileElems]
-  int* m_dblk = reinterpret_cast<int*>(stB + (size_t)kStages * NP * kTileElems);   // [kMetaPairs][8]
-  __shared__ __align__(8) uint64_t bar_full[kStages], bar_empty[kStages], bar_accf[2], bar_acce[2];
+  uint16_t* stA = reinterpret_cast<uint16_t*>(smem_raw);                  // [KS][TPC][NP][kTileElems]
+  uint16_t* stB = stA + (size_t)KS * TPC * NP * kTileElems;               // [KS][NP][kTileElems]
+  int* m_dblk = reinterpret_cast<int*>(stB + (size_t)KS * NP * kTileElems);   // [KMP][8]
+  __shared__ __align__(8) uint64_t bar_full[KS], bar_empty[KS], bar_accf[2], bar_acce[2];
   __shared__ uint32_t tmem_base;
   __shared__ double sg[8][3];
   __shared__ int m_q[kMetaPairs];
@@ -837,8 +850,9 @@ __global__ void __launch_bounds__(192) k_q2_umma(DevPlan P, MixPlan X, const int
   int rem = blockIdx.x;
   const int seg = rem % NSEG;
   rem /= NSEG;
-  const int mc = rem % MC;
-  rem /= MC;
+  const int MCP = (MC + TPC - 1) / TPC;
+  const int mc = (rem % MCP) * TPC;   // first row tile of this CTA
+  rem /= MCP;
   const int fc = rem % FC8;
   const int A = rem / FC8;
   const int sA = P.species[A];
@@ -846,10 +860,11 @@ __global__ void __launch_bounds__(192) k_q2_umma(DevPlan P, MixPlan X, const int
   const int rows = mA * nA, nt = (rows + 127) >> 7;
   const int q0 = P.c_ptr[A], nq = P.c_ptr[A + 1] - q0;
   if (fc * 8 >= nq || mc * 128 >= rows) return;
+  const int ntile = min(TPC, nt - mc);   // row tiles of this CTA
   const long long s0 = slot0[P.v_ptr[A]];
   const long long s1 = A + 1 < P.N ? slot0[P.v_ptr[A + 1]] : (long long)n_slots;
-  const long long p0 = s0 + (long long)seg * kMetaPairs;
-  const int np = (int)max(0ll, min((long long)kMetaPairs, s1 - p0));
+  const long long p0 = s0 + (long long)seg * KMP;
+  const int np = (int)max(0ll, min((long long)KMP, s1 - p0));
   if (np <= 0) return;
   const int row0 = mc * 128;
   int qf[8];
@@ -870,7 +885,7 @@ __global__ void __launch_bounds__(192) k_q2_umma(DevPlan P, MixPlan X, const int
   if (tid < 24) sg[tid / 3][tid % 3] = 0.0;
   if (tid == 0) {
     s_abort = 0;
-    for (int s = 0; s < kStages; ++s) {
+    for (int s = 0; s < KS; ++s) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mfull + 8 * s));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mempty + 8 * s));
     }
@@ -882,7 +897,7 @@ __global__ void __launch_bounds__(192) k_q2_umma(DevPlan P, MixPlan X, const int
   }
   if (warp == 1) {
     const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&tmem_base);
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(dst), "r"(256));
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(dst), "r"(256));   // NB * TPC * 128
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -912,19 +927,20 @@ __global__ void __launch_bounds__(192) k_q2_umma(DevPlan P, MixPlan X, const int
   if (warp == 0) {
     // producer warp: every lane waits for the stage, then lanes issue the
     // copies of one stage in parallel (lane 0 also posts the byte count)
-    const uint32_t bytes = (uint32_t)NP * 2 * kTileElems * 2;
+    const uint32_t abytes = (uint32_t)ntile * NP * kTileElems * 2;
+    const uint32_t bytes = abytes + (uint32_t)NP * kTileElems * 2;
     for (int k = 0; k < nsteps; ++k) {
-      const int s = k % kStages;
+      const int s = k % KS;
       const int t = m_q[k];
-      if (k >= kStages && !mbar_wait<kMixTryNs>(mempty + 8 * s, (uint32_t)((k / kStages - 1) & 1))) s_abort = 1;
+      if (k >= KS && !mbar_wait<kMixTryNs>(mempty + 8 * s, (uint32_t)((k / KS - 1) & 1))) s_abort = 1;
       __syncwarp();
       if (s_abort) break;
-      // lane 0: the NP Z piece tiles of row tile mc (contiguous, one copy);
-      // lanes 1 .. 2 NP: the eight D blocks of each piece, four per gather
+      // lane 0: the NP Z piece tiles of the CTA's row tiles (contiguous, one
+      // copy); lanes 1 .. 2 NP: the eight D blocks of each piece, four per gather
       if (lane == 0) {
         mbar_expect_tx(mfull + 8 * s, bytes);
-        bulk_g2s((uint32_t)__cvta_generic_to_shared(stA + (size_t)s * NP * kTileElems),
-                 X.Zst + (p0 + t) * zblk + (long long)mc * NP * kTileElems, (uint32_t)NP * kTileElems * 2, mfull + 8 * s);
+        bulk_g2s((uint32_t)__cvta_generic_to_shared(stA + (size_t)s * TPC * NP * kTileElems),
+                 X.Zst + (p0 + t) * zblk + (long long)mc * NP * kTileElems, abytes, mfull + 8 * s);
       }
       stage_d<NP>(lane, stB + (size_t)s * NP * kTileElems, m_dblk + t * 8, &drows.map, drows.zero_row, mfull + 8 * s);
     }
@@ -933,37 +949,37 @@ __global__ void __launch_bounds__(192) k_q2_umma(DevPlan P, MixPlan X, const int
       // MMA issuer: D f32, A/B bf16, both K-major, N = 128, M = 128
       const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
       for (int r = 0; r < nruns && !s_abort; ++r) {
-        const int b = r & 1;
-        if (r >= 2 && !mbar_wait<kMixTryNs>(macce + 8 * b, (uint32_t)((r / 2 - 1) & 1))) {
+        const int b = r % NB;
+        if (r >= NB && !mbar_wait<kMixTryNs>(macce + 8 * b, (uint32_t)((r / NB - 1) & 1))) {
           s_abort = 1;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        const uint32_t dacc = taddr + 128u * b;
+        const uint32_t dacc = taddr + 128u * TPC * b;
         const int k1 = min(nsteps, (r + 1) * flush);
-        bool first = true;
         for (int k = r * flush; k < k1; ++k) {
-          const int s = k % kStages;
-          if (!mbar_wait<kMixTryNs>(mfull + 8 * s, (uint32_t)((k / kStages) & 1))) {
+          const int s = k % KS;
+          if (!mbar_wait<kMixTryNs>(mfull + 8 * s, (uint32_t)((k / KS) & 1))) {
             s_abort = 1;
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-          const uint32_t a0 = (uint32_t)__cvta_generic_to_shared(stA + (size_t)s * NP * kTileElems);
+          const uint32_t a0 = (uint32_t)__cvta_generic_to_shared(stA + (size_t)s * TPC * NP * kTileElems);
           const uint32_t b0 = (uint32_t)__cvta_generic_to_shared(stB + (size_t)s * NP * kTileElems);
+          const bool fs = k == r * flush;   // first step of the run: each tile's first product overwrites
+          for (int j = 0; j < ntile; ++j)
 #pragma unroll
-          for (int sum = NP - 1; sum >= 0; --sum)
+            for (int sum = NP - 1; sum >= 0; --sum)
 #pragma unroll
-            for (int ia = 0; ia <= sum; ++ia) {
-              const int ib = sum - ia;
-              const uint64_t ad = sdesc(a0 + ia * kTileElems * 2);
-              const uint64_t bd = sdesc(b0 + ib * kTileElems * 2);
-              const uint32_t acc = first ? 0u : 1u;
-              asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                           " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dacc),
-                           "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-              first = false;
-            }
+              for (int ia = 0; ia <= sum; ++ia) {
+                const int ib = sum - ia;
+                const uint64_t ad = sdesc(a0 + (j * NP + ia) * kTileElems * 2);
+                const uint64_t bd = sdesc(b0 + ib * kTileElems * 2);
+                const uint32_t acc = (fs && sum == NP - 1 && ia == 0) ? 0u : 1u;
+                asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                             " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dacc + 128u * j),
+                             "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+              }
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mempty + 8 * s)
                        : "memory");
         }
@@ -974,22 +990,23 @@ __global__ void __launch_bounds__(192) k_q2_umma(DevPlan P, MixPlan X, const int
   } else {
     // epilogue: warps 2..5, tensor-memory lane quarter q = warp % 4
     const int q = warp & 3;
-    const int r = row0 + q * 32 + lane;
-    const bool rv = r < rows;
     double gd[8][3];
 #pragma unroll
     for (int i = 0; i < 8; ++i) gd[i][0] = gd[i][1] = gd[i][2] = 0.0;
     for (int run = 0; run < nruns; ++run) {
-      const int b = run & 1;
-      if (!mbar_wait<kMixTryNs>(maccf + 8 * b, (uint32_t)((run / 2) & 1))) {
+      const int b = run % NB;
+      if (!mbar_wait<kMixTryNs>(maccf + 8 * b, (uint32_t)((run / NB) & 1))) {
         s_abort = 1;
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      for (int j = 0; j < ntile; ++j) {
+      const int r = row0 + 128 * j + q * 32 + lane;
+      const bool rv = r < rows;
 #pragma unroll
       for (int c0 = 0; c0 < 128; c0 += 32) {
         uint32_t v[32];
-        tmem_ld32(taddr + ((uint32_t)(q * 32) << 16) + 128u * b + c0, v);
+        tmem_ld32(taddr + ((uint32_t)(q * 32) << 16) + 128u * (TPC * b + j) + c0, v);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int i = (c0 >> 4) + h;
@@ -1017,6 +1034,7 @@ __global__ void __launch_bounds__(192) k_q2_umma(DevPlan P, MixPlan X, const int
           gd[i][1] += (double)g1;
           gd[i][2] += (double)g2;
         }
+      }
       }
       asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
       __syncwarp();
@@ -1401,8 +1419,13 @@ size_t ybuild_umma_smem(int np) {
   return (size_t)2 * umma::kStages * np * umma::kTileElems * sizeof(uint16_t) + (size_t)kMaxCPerAtom * 8 * sizeof(int);
 }
 
+// row tiles per CTA of the Q2 GEMM: two for BF16X3 (the stages of BF16X6 would not leave room for two CTAs)
+constexpr int q2_tpc(int np) { return np == 2 ? 2 : 1; }
+
 size_t q2_umma_smem(int np) {
-  return (size_t)2 * umma::kStages * np * umma::kTileElems * sizeof(uint16_t) + (size_t)umma::kMetaPairs * 8 * sizeof(int);
+  if (q2_tpc(np) == 2)
+    return (size_t)Q2Shape<2>::kS * 3 * np * umma::kTileElems * sizeof(uint16_t) + (size_t)Q2Shape<2>::kMP * 8 * sizeof(int);
+  return (size_t)2 * Q2Shape<1>::kS * np * umma::kTileElems * sizeof(uint16_t) + (size_t)Q2Shape<1>::kMP * 8 * sizeof(int);
 }
 
 int grid_for(long long n, int cap) {
@@ -1417,7 +1440,10 @@ long long mixed_launch_count() { return g_mix_launches; }
 long long ytab_size(int ngroups, int maxC) { return (long long)ngroups * 8 * maxC; }
 long long q2tab_size(int n_slots, int FC) { return (long long)n_slots * ((FC * 4 + 7) / 8) * 8; }
 
-int q2_umma_segments(int max_pairs_per_atom) { return (max_pairs_per_atom + umma::kMetaPairs - 1) / umma::kMetaPairs; }
+int q2_umma_segments(int max_pairs_per_atom, int np) {
+  const int kmp = q2_tpc(np) == 2 ? Q2Shape<2>::kMP : Q2Shape<1>::kMP;
+  return (max_pairs_per_atom + kmp - 1) / kmp;
+}
 
 cudaError_t launch_dsplit(const DevPlan& P, const MixPlan& X, int np, cudaStream_t s) {
   if (P.n_d == 0) return cudaSuccess;
@@ -1487,7 +1513,7 @@ cudaError_t set_mixed_smem_limits(int np, size_t t1, size_t t2) {
   e = cudaFuncSetAttribute(np == 2 ? (const void*)k_ybuild_umma<2> : (const void*)k_ybuild_umma<3>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ybuild_umma_smem(np));
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(np == 2 ? (const void*)k_q2_umma<2> : (const void*)k_q2_umma<3>,
+  e = cudaFuncSetAttribute(np == 2 ? (const void*)k_q2_umma<2, q2_tpc(2)> : (const void*)k_q2_umma<3, q2_tpc(3)>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)q2_umma_smem(np));
   if (e != cudaSuccess) return e;
   if (np == 2) {
@@ -1519,13 +1545,13 @@ cudaError_t launch_term2_mma(const DevPlan& P, const MixPlan& X, int np, const i
   const int FC8 = (FC * 4 + 7) / 8;     // groups of 8 C slots for the tcgen05 kernel
   k_q2tab<<<grid_for(((long long)n * FC8 * 8 + 255) / 256, 152 * 16), 256, 0, s>>>(P, X, list, n, FC8);
   const size_t sq = q2_umma_smem(np);
-  const long long grid = (long long)P.N * FC8 * MC * nseg;
+  const long long grid = (long long)P.N * FC8 * ((MC + q2_tpc(np) - 1) / q2_tpc(np)) * nseg;
   if (np == 2) {
     k_term2_pairs<2><<<grid_for(n, 152 * 32), kWarps * 32, smem, s>>>(P, X, list, n, MAmax, KZmax, zblk, zrows);
-    k_q2_umma<2><<<(unsigned)grid, 192, sq, s>>>(P, X, list, slot0, n, FC8, MC, nseg, zblk, flush, drows, err);
+    k_q2_umma<2, q2_tpc(2)><<<(unsigned)grid, 192, sq, s>>>(P, X, list, slot0, n, FC8, MC, nseg, zblk, flush, drows, err);
   } else {
     k_term2_pairs<3><<<grid_for(n, 152 * 32), kWarps * 32, smem, s>>>(P, X, list, n, MAmax, KZmax, zblk, zrows);
-    k_q2_umma<3><<<(unsigned)grid, 192, sq, s>>>(P, X, list, slot0, n, FC8, MC, nseg, zblk, flush, drows, err);
+    k_q2_umma<3, q2_tpc(3)><<<(unsigned)grid, 192, sq, s>>>(P, X, list, slot0, n, FC8, MC, nseg, zblk, flush, drows, err);
   }
   return cudaGetLastError();
 }
