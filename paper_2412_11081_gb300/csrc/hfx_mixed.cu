@@ -1066,14 +1066,16 @@ __global__ void __launch_bounds__(192) k_q2_umma(DevPlan P, MixPlan X, const int
 // mirror block D_ZW = D_WZ^T (rows z, columns w).  Same warp roles as
 // k_q2_umma; one accumulation run; the epilogue splits the FP32 result into
 // bf16 pieces and writes the Y store ([alpha][z][16], x padding zeroed).
-template <int NP>
+// TPC row tiles of 128 rows per CTA share each K step's D blocks (one
+// accumulator of 128 columns per tile).
+template <int NP, int TPC>
 __global__ void __launch_bounds__(192) k_ybuild_umma(DevPlan P, MixPlan X, const int* ylist, const int* gX,
                                                      const int* gS, const int* gN, int MC,
                                                      const __grid_constant__ DRows drows, int* err) {
   using namespace umma;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  uint16_t* stA = reinterpret_cast<uint16_t*>(smem_raw);
-  uint16_t* stB = stA + (size_t)kStages * NP * kTileElems;
+  uint16_t* stA = reinterpret_cast<uint16_t*>(smem_raw);                     // [kStages][TPC][NP][kTileElems]
+  uint16_t* stB = stA + (size_t)kStages * TPC * NP * kTileElems;           // [kStages][NP][kTileElems]
   int* m_d = reinterpret_cast<int*>(stB + (size_t)kStages * NP * kTileElems);   // [kMaxCPerAtom][8]
   __shared__ int m_q[kMaxCPerAtom];
   __shared__ int s_nsteps;
@@ -1081,13 +1083,14 @@ __global__ void __launch_bounds__(192) k_ybuild_umma(DevPlan P, MixPlan X, const
   __shared__ uint32_t tmem_base;
   __shared__ int s_abort;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int g = blockIdx.x / MC, mc = blockIdx.x - g * MC;
+  const int MCP = (MC + TPC - 1) / TPC;
+  const int g = blockIdx.x / MCP, mc = (blockIdx.x - g * MCP) * TPC;   // first row tile of this CTA
   const int Xa = gX[g], kstart = gS[g], nk = gN[g];
   const int sX = P.species[Xa];
   const int mX = P.n_abf[sX], nX = P.n_ao[sX];
   const int rows = mX * nX;
   if (mc * 128 >= rows) return;
-  const int row0 = mc * 128;
+  const int ntile = min(TPC, ((rows + 127) >> 7) - mc);
   const int q0 = P.c_ptr[Xa], nq = P.c_ptr[Xa + 1] - q0;
   int ykey[8], zat[8];
 #pragma unroll
@@ -1114,7 +1117,7 @@ __global__ void __launch_bounds__(192) k_ybuild_umma(DevPlan P, MixPlan X, const
   }
   if (warp == 1) {
     const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&tmem_base);
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(dst), "r"(128));
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(dst), "r"(128 * TPC));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
   }
   __syncthreads();
@@ -1141,26 +1144,26 @@ __global__ void __launch_bounds__(192) k_ybuild_umma(DevPlan P, MixPlan X, const
   const int nsteps = s_nsteps;
 
   if (warp == 0) {
-    const uint32_t bytes = (uint32_t)NP * 2 * kTileElems * 2;
+    const uint32_t abytes = (uint32_t)ntile * NP * kTileElems * 2;
+    const uint32_t bytes = abytes + (uint32_t)NP * kTileElems * 2;
     for (int k = 0; k < nsteps; ++k) {
       const int s = k % kStages;
       if (k >= kStages && !mbar_wait<kMixTryNs>(mempty + 8 * s, (uint32_t)((k / kStages - 1) & 1))) s_abort = 1;
       __syncwarp();
       if (s_abort) break;
       const int t = m_q[k];
-      // lane 0: the NP C piece tiles of row tile mc (contiguous, one copy);
-      // lanes 1 .. 2 NP: the eight mirror D blocks of each piece, four per gather
+      // lane 0: the NP C piece tiles of the CTA's row tiles (contiguous, one
+      // copy); lanes 1 .. 2 NP: the eight mirror D blocks of each piece, four per gather
       if (lane == 0) {
         mbar_expect_tx(mfull + 8 * s, bytes);
-        bulk_g2s((uint32_t)__cvta_generic_to_shared(stA + (size_t)s * NP * kTileElems),
-                 X.Cm + X.cm_off[q0 + t] + (long long)mc * NP * kTileElems, (uint32_t)NP * kTileElems * 2, mfull + 8 * s);
+        bulk_g2s((uint32_t)__cvta_generic_to_shared(stA + (size_t)s * TPC * NP * kTileElems),
+                 X.Cm + X.cm_off[q0 + t] + (long long)mc * NP * kTileElems, abytes, mfull + 8 * s);
       }
       stage_d<NP>(lane, stB + (size_t)s * NP * kTileElems, m_d + t * 8, &drows.map, drows.zero_row, mfull + 8 * s);
     }
   } else if (warp == 1) {
     if (lane == 0 && nsteps > 0) {
       const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
-      bool first = true;
       for (int k = 0; k < nsteps; ++k) {
         const int s = k % kStages;
         if (!mbar_wait<kMixTryNs>(mfull + 8 * s, (uint32_t)((k / kStages) & 1))) {
@@ -1168,20 +1171,20 @@ __global__ void __launch_bounds__(192) k_ybuild_umma(DevPlan P, MixPlan X, const
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        const uint32_t a0 = (uint32_t)__cvta_generic_to_shared(stA + (size_t)s * NP * kTileElems);
+        const uint32_t a0 = (uint32_t)__cvta_generic_to_shared(stA + (size_t)s * TPC * NP * kTileElems);
         const uint32_t b0 = (uint32_t)__cvta_generic_to_shared(stB + (size_t)s * NP * kTileElems);
+        for (int j = 0; j < ntile; ++j)
 #pragma unroll
-        for (int sum = NP - 1; sum >= 0; --sum)
+          for (int sum = NP - 1; sum >= 0; --sum)
 #pragma unroll
-          for (int ia = 0; ia <= sum; ++ia) {
-            const uint64_t ad = sdesc(a0 + ia * kTileElems * 2);
-            const uint64_t bd = sdesc(b0 + (sum - ia) * kTileElems * 2);
-            const uint32_t acc = first ? 0u : 1u;
-            asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(taddr),
-                         "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-            first = false;
-          }
+            for (int ia = 0; ia <= sum; ++ia) {
+              const uint64_t ad = sdesc(a0 + (j * NP + ia) * kTileElems * 2);
+              const uint64_t bd = sdesc(b0 + (sum - ia) * kTileElems * 2);
+              const uint32_t acc = (k == 0 && sum == NP - 1 && ia == 0) ? 0u : 1u;
+              asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                           " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(taddr + 128u * j),
+                           "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+            }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mempty + 8 * s)
                      : "memory");
       }
@@ -1199,10 +1202,6 @@ __global__ void __launch_bounds__(192) k_ybuild_umma(DevPlan P, MixPlan X, const
     const int q = warp & 3;
     const int et = tid - 64;
     float* ep = reinterpret_cast<float*>(smem_raw);   // [128][33]
-    const int rend = min(row0 + 128, rows);
-    const int alF = (row0 + nX - 1) / nX, alL = rend / nX - 1;
-    const int nal = max(0, alL - alF + 1);
-    const int alA = row0 / nX, alB = (rend - 1) / nX;
     bool have = nsteps > 0;
     if (have) {
       if (!mbar_wait<kMixTryNs>(maccf, 0u)) {
@@ -1211,11 +1210,17 @@ __global__ void __launch_bounds__(192) k_ybuild_umma(DevPlan P, MixPlan X, const
       }
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     }
+    for (int jt = 0; jt < ntile; ++jt) {
+    const int row0 = (mc + jt) * 128;
+    const int rend = min(row0 + 128, rows);
+    const int alF = (row0 + nX - 1) / nX, alL = rend / nX - 1;
+    const int nal = max(0, alL - alF + 1);
+    const int alA = row0 / nX, alB = (rend - 1) / nX;
     for (int c0 = 0; c0 < 128; c0 += 32) {
       {
         uint32_t v[32];
         if (have) {
-          tmem_ld32(taddr + ((uint32_t)(q * 32) << 16) + c0, v);
+          tmem_ld32(taddr + ((uint32_t)(q * 32) << 16) + 128u * jt + c0, v);
         } else {
 #pragma unroll
           for (int j = 0; j < 32; ++j) v[j] = 0u;
@@ -1319,11 +1324,12 @@ __global__ void __launch_bounds__(192) k_ybuild_umma(DevPlan P, MixPlan X, const
       }
       asm volatile("bar.sync 1, 128;\n" ::: "memory");
     }
+    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(128));
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(128 * TPC));
   if (tid == 0 && s_abort) atomicExch(err, 1);
 }
 
@@ -1415,8 +1421,12 @@ __global__ void k_q2tab(DevPlan P, MixPlan X, const int* list, int n_slots, int 
   if ((threadIdx.x & 31) == 0 && fl != 0.0) atomicAdd(&P.acc[ACC_F2], fl);
 }
 
+// row tiles per CTA of the Y build: two for BF16X3
+constexpr int yb_tpc(int np) { return np == 2 ? 2 : 1; }
+
 size_t ybuild_umma_smem(int np) {
-  return (size_t)2 * umma::kStages * np * umma::kTileElems * sizeof(uint16_t) + (size_t)kMaxCPerAtom * 8 * sizeof(int);
+  return (size_t)(yb_tpc(np) + 1) * umma::kStages * np * umma::kTileElems * sizeof(uint16_t) +
+         (size_t)kMaxCPerAtom * 8 * sizeof(int);
 }
 
 // row tiles per CTA of the Q2 GEMM: two for BF16X3 (the stages of BF16X6 would not leave room for two CTAs)
@@ -1483,11 +1493,11 @@ cudaError_t launch_ybuild_mma(const DevPlan& P, const MixPlan& X, int np, const 
   g_mix_launches += 2;
   k_ytab<<<grid_for(((long long)ngroups * X.ytab_stride + 255) / 256, 152 * 16), 256, 0, s>>>(P, X, ylist, gX, gS, gN,
                                                                                           ngroups);
-  const long long grid = (long long)ngroups * MC;
+  const long long grid = (long long)ngroups * ((MC + yb_tpc(np) - 1) / yb_tpc(np));
   if (np == 2)
-    k_ybuild_umma<2><<<(unsigned)grid, 192, ybuild_umma_smem(2), s>>>(P, X, ylist, gX, gS, gN, MC, drows, err);
+    k_ybuild_umma<2, yb_tpc(2)><<<(unsigned)grid, 192, ybuild_umma_smem(2), s>>>(P, X, ylist, gX, gS, gN, MC, drows, err);
   else
-    k_ybuild_umma<3><<<(unsigned)grid, 192, ybuild_umma_smem(3), s>>>(P, X, ylist, gX, gS, gN, MC, drows, err);
+    k_ybuild_umma<3, yb_tpc(3)><<<(unsigned)grid, 192, ybuild_umma_smem(3), s>>>(P, X, ylist, gX, gS, gN, MC, drows, err);
   return cudaGetLastError();
 }
 
@@ -1510,7 +1520,7 @@ size_t term2_mma_smem(int np, int MAmax, int KZmax) {
 
 cudaError_t set_mixed_smem_limits(int np, size_t t1, size_t t2) {
   cudaError_t e;
-  e = cudaFuncSetAttribute(np == 2 ? (const void*)k_ybuild_umma<2> : (const void*)k_ybuild_umma<3>,
+  e = cudaFuncSetAttribute(np == 2 ? (const void*)k_ybuild_umma<2, yb_tpc(2)> : (const void*)k_ybuild_umma<3, yb_tpc(3)>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ybuild_umma_smem(np));
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(np == 2 ? (const void*)k_q2_umma<2, q2_tpc(2)> : (const void*)k_q2_umma<3, q2_tpc(3)>,
