@@ -222,24 +222,27 @@ __global__ void k_vpieces(DevPlan P, MixPlan X, const int* list, int n_list) {
 // --------------------------------------------------- term-1 transposed lists
 // Per home atom A: for every C slot of A, the V pairs (A,B) whose item list
 // keeps it, in V-pair order (deterministic).
-__global__ void k_t1_count(DevPlan P, MixPlan X) {
-  const int A = blockIdx.x;
-  const int q0 = P.c_ptr[A], nq = P.c_ptr[A + 1] - q0;
-  for (int s = threadIdx.x; s < nq; s += blockDim.x) {
+// (A,F) view of the first product's kept triplets: one warp per C pair
+// (A,F) = q, its lanes test 32 V pairs of A at a time.  Phase 0 counts the
+// kept B (qcnt), phase 1 writes them in V-pair order from qoff (ballot and
+// prefix count keep the order).
+__global__ void k_t1_lists(DevPlan P, MixPlan X, int phase) {
+  const int lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  for (int q = blockIdx.x * wpb + (threadIdx.x >> 5); q < P.nC; q += gridDim.x * wpb) {
+    const int A = P.c_home[q], s = q - P.c_ptr[A];
+    const int p0 = P.v_ptr[A], p1 = P.v_ptr[A + 1];
+    long long o = phase ? X.qoff[q] : 0;
     int cnt = 0;
-    for (int p = P.v_ptr[A]; p < P.v_ptr[A + 1]; ++p)
-      cnt += (P.v_mask[(size_t)p * kMaskWords + (s >> 5)] >> (s & 31)) & 1u;
-    X.qcnt[q0 + s] = cnt;
-  }
-}
-
-__global__ void k_t1_fill(DevPlan P, MixPlan X) {
-  const int A = blockIdx.x;
-  const int q0 = P.c_ptr[A], nq = P.c_ptr[A + 1] - q0;
-  for (int s = threadIdx.x; s < nq; s += blockDim.x) {
-    long long o = X.qoff[q0 + s];
-    for (int p = P.v_ptr[A]; p < P.v_ptr[A + 1]; ++p)
-      if ((P.v_mask[(size_t)p * kMaskWords + (s >> 5)] >> (s & 31)) & 1u) X.blist[o++] = p;
+    for (int pb = p0; pb < p1; pb += 32) {
+      const int p = pb + lane;
+      const bool kept = p < p1 && ((P.v_mask[(size_t)p * kMaskWords + (s >> 5)] >> (s & 31)) & 1u);
+      const unsigned bal = __ballot_sync(0xffffffffu, kept);
+      if (phase && kept) X.blist[o + __popc(bal & ((1u << lane) - 1u))] = p;
+      o += __popc(bal);
+      cnt += __popc(bal);
+    }
+    if (!phase && lane == 0) X.qcnt[q] = cnt;
   }
 }
 
@@ -1503,8 +1506,7 @@ cudaError_t launch_ybuild_mma(const DevPlan& P, const MixPlan& X, int np, const 
 
 cudaError_t launch_t1_lists(const DevPlan& P, const MixPlan& X, int phase, cudaStream_t s) {
   ++g_mix_launches;
-  if (phase == 0) k_t1_count<<<P.N, 256, 0, s>>>(P, X);
-  else k_t1_fill<<<P.N, 256, 0, s>>>(P, X);
+  if (P.nC > 0) k_t1_lists<<<grid_for((P.nC + 7) / 8, 152 * 16), 256, 0, s>>>(P, X, phase);
   return cudaGetLastError();
 }
 
