@@ -57,17 +57,13 @@ __device__ __forceinline__ bool wait_all(uint32_t mbar, uint32_t parity) {
 }
 
 // ------------------------------------------------------------ operand stores
-// Offset (floats) of element (alpha, col) of a 64-row FP32 plane in the
-// order the epilogue warps load it: epilogue warp qd = alpha >> 4 holds row
-// alpha in lane (alpha & 15) + 16 h and reads columns 32 j + 16 h + 4 t .. + 3
-// as one float4, so that for each (j, t) a warp's 32 loads are 512
-// consecutive bytes.
-__device__ __forceinline__ int ep_off(int alpha, int col) {
-  const int j = col >> 5, h = (col >> 4) & 1, t = (col >> 2) & 3;
-  return ((((j * 4 + t) * 4 + (alpha >> 4)) * 32 + (alpha & 15) + 16 * h) << 2) + (col & 3);
-}
-
-// Inverse of ep_off: the (alpha, col) stored at float w.
+// Order in which the epilogue warps load a 64-row FP32 plane (C, grad C,
+// grad V): epilogue warp qd = alpha >> 4 holds row alpha in lane
+// (alpha & 15) + 16 h and reads columns 32 j + 16 h + 4 t .. + 3 as one
+// float4, so that for each (j, t) a warp's 32 loads are 512 consecutive
+// bytes; element (alpha, col) sits at float
+// ((((j * 4 + t) * 4 + qd) * 32 + lane) << 2) + (col & 3).  ep_at gives the
+// (alpha, col) stored at float w (the stores are written in storage order).
 __device__ __forceinline__ void ep_at(int w, int& alpha, int& col) {
   const int k = w & 3, l = (w >> 2) & 31, qd = (w >> 7) & 3, t = (w >> 9) & 3, j = w >> 11;
   alpha = qd * 16 + (l & 15);
@@ -77,7 +73,7 @@ __device__ __forceinline__ void ep_at(int w, int& alpha, int& col) {
 // Item kk (C pair q = list[kk]): NP bf16 pieces of C_AF as [alpha (64)][(f,a) (KP)]
 // in core-matrix order (8-row groups of KP/8 core matrices), then C and
 // grad C in FP32 as four planes of 64 x KP32 (KP rounded up to 32) in
-// epilogue load order (ep_off).  Zero padded.  Each plane of the C pair
+// epilogue load order (ep_at).  Zero padded.  Each plane of the C pair
 // ([(alpha,a)][f]) is evaluated from the block model into shared memory as
 // FP32; the outputs are written in storage order, four elements per thread.
 constexpr int kCStoreSmem = 64 * 16 * 16 * 4;   // one plane of n_abf <= 64, n_ao <= 16
@@ -133,7 +129,7 @@ __global__ void k_t1u_cstore(DevPlan P, T1UPlan U, const int* list, int n) {
 //   [alpha][rup16(n_abf(B))] and V, grad V in FP32 [4][n_abf(A) n_abf(B)];
 //   for the pairs of the first product (any bit of v_mask), the tcgen05
 //   store U.Vu at t1_idx[p]: NP pieces [alpha 64][beta 64] in core-matrix
-//   order and grad V in three ep_off planes.
+//   order and grad V in three planes in epilogue load order (ep_at).
 // Outputs are written in storage order, four elements per thread.
 constexpr int kVStoreSmem = 4 * 64 * 64 * 4;
 
@@ -188,7 +184,7 @@ __global__ void k_vstores(DevPlan P, MixPlan X, T1UPlan U, const int* list, int 
       for (int pp = 0; pp < NP; ++pp) *reinterpret_cast<uint2*>(vu + pp * 4096 + t) = pc[pp];
     }
     float* pl = reinterpret_cast<float*>(vu + NP * 4096);
-    for (int w4 = threadIdx.x; w4 < 3 * 1024; w4 += blockDim.x) {   // grad V, ep_off order
+    for (int w4 = threadIdx.x; w4 < 3 * 1024; w4 += blockDim.x) {   // grad V, epilogue load order
       const int c = w4 >> 10;
       int al, be;
       ep_at(4 * (w4 & 1023), al, be);
@@ -641,7 +637,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           // fetched before the wait; they do not depend on R)
           float gv[3] = {0.f, 0.f, 0.f};
           float4 w[3][4];
-          const float4* dV4 = reinterpret_cast<const float4*>(dV) + qd * 32 + lane;   // ep_off order
+          const float4* dV4 = reinterpret_cast<const float4*>(dV) + qd * 32 + lane;   // epilogue load order (ep_at)
           {
             const int cb = 16 * half;
             if (alpha < mA && cb < mB)
