@@ -605,7 +605,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_term2_pairs(DevPlan P, MixPlan 
     const int* Rb = P.v_R + 3 * p;
     const int sA = P.species[A], sB = P.species[b];
     const int nA = P.n_ao[sA], nB = P.n_ao[sB], mA = P.n_abf[sA], mB = P.n_abf[sB];
-    const int pB = rup16(nB);
+    constexpr int pB = 16;   // the split path holds n_ao <= 16
     const int MA = rup16(mA), MB = rup16(mB);
     const int NAB = nA * pB, KZ = NAB + 8;
     const int y1 = ylut_get(P, A, b, Rb[0], Rb[1], Rb[2]);
@@ -621,19 +621,20 @@ __global__ void __launch_bounds__(kWarps * 32) k_term2_pairs(DevPlan P, MixPlan 
     // (by alpha) with 16-byte copies (rows NAB long, shared-memory stride KZ;
     // rows past n_abf zero, columns past NAB never read)
     {
-      const int nch = NAB >> 3;
-      for (int e = threadIdx.x; e < (MB + MA) * nch; e += blockDim.x) {
-        const bool isA = e >= MB * nch;
-        const int e2 = isA ? e - MB * nch : e;
-        const int row = e2 / nch, ch = e2 - row * nch;
+      const int nch = NAB >> 3;   // 16-byte chunks per row (2 n_ao(A) <= 32: one lane each)
+      for (int rr = warp; rr < MB + MA; rr += kWarps) {
+        const bool isA = rr >= MB;
+        const int row = isA ? rr - MB : rr;
         const bool in = row < (isA ? mA : mB);
+        if (lane < nch) {
 #pragma unroll
-        for (int pp = 0; pp < NP; ++pp) {
-          uint4 v = make_uint4(0u, 0u, 0u, 0u);
-          if (in)
-            v = *reinterpret_cast<const uint4*>((isA ? YabT + pp * pl_abT : Yba + pp * pl_ba) + (long long)row * NAB + 8 * ch);
-          uint16_t* dst = isA ? Ya + (size_t)pp * MA * KZ : Yb + (size_t)pp * MB * KZ;
-          *reinterpret_cast<uint4*>(dst + (size_t)row * KZ + 8 * ch) = v;
+          for (int pp = 0; pp < NP; ++pp) {
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (in)
+              v = *reinterpret_cast<const uint4*>((isA ? YabT + pp * pl_abT : Yba + pp * pl_ba) + (long long)row * NAB + 8 * lane);
+            uint16_t* dst = isA ? Ya + (size_t)pp * MA * KZ : Yb + (size_t)pp * MB * KZ;
+            *reinterpret_cast<uint4*>(dst + (size_t)row * KZ + 8 * lane) = v;
+          }
         }
       }
     }
@@ -730,7 +731,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_term2_pairs(DevPlan P, MixPlan 
           const int al = mt * 16 + gid + (h ? 8 : 0);
           const int col = nt * 8 + 2 * tig;          // even: (a, bb) and (a, bb+1)
           if (al < mA) {
-            const int a = col / pB, bb = col - a * pB;
+            const int a = col >> 4, bb = col & 15;
             uint16_t p0[NP], p1[NP];
             split_f<NP>(acc[2 * h], p0);
             split_f<NP>(acc[2 * h + 1], p1);
