@@ -308,6 +308,14 @@ def cut_density(w: Workload, rmax: float) -> Workload:
     return out
 
 
+def geometry_sequence(w: Workload, n: int, seed: int = 17, amp: float = 0.01) -> List[np.ndarray]:
+    """n seeded small displacements of w's positions (Gaussian, amp Angstrom
+    per coordinate): a relaxation-like sequence that stays within the pair
+    lists' skin."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    return [w.positions + rng.normal(0.0, amp, w.positions.shape) for _ in range(n)]
+
+
 def workload_by_name(name: str) -> Workload:
     table = {
         "diamond8": lambda: diamond8(),

@@ -4,7 +4,9 @@ FP64 screening and reductions) against the FP64 CPU oracle.
 Error metric: max|x - x_ref| / max|x_ref| per output (|dE|/|E| for E).
 HFX_BF16X6 keeps every piece product down to 2^-24 of the operands;
 HFX_BF16X3 drops the products below 2^-16 of them.  Both must meet the
-1e-5 relative force/stress contract: in the tcgen05 first product U is
+1e-5 relative force/stress contract on the unperturbed cells here (BF16X3
+misses it on the two-species cell and on some jittered si64 geometries,
+see the tests below): in the tcgen05 first product U is
 built in FP32 from FP32 Y and D, so the 16-bit truncation of BF16X3 only
 touches the operands of the two tensor-core products, and the FP32
 accumulators are flushed to FP64 every 32 B (the remaining error is the
@@ -24,6 +26,7 @@ from paper_2412_11081_gb300 import hfx, inputs
 
 pytestmark = pytest.mark.gpu
 HERE = os.path.dirname(os.path.abspath(__file__))
+SPLITS = [hfx.HFX_BF16X6, hfx.HFX_BF16X3]
 BOUND = {hfx.HFX_BF16X6: 1e-5, hfx.HFX_BF16X3: 1e-5}
 BOUND_MMA = {hfx.HFX_BF16X6: 1e-5, hfx.HFX_BF16X3: 3e-5}
 
@@ -46,7 +49,7 @@ def tiny_periodic(seed=7):
     return inputs.cut_density(w, 3.5)
 
 
-@pytest.mark.parametrize("prec", [hfx.HFX_BF16X6, hfx.HFX_BF16X3])
+@pytest.mark.parametrize("prec", SPLITS)
 @pytest.mark.parametrize("case", ["tiny", "diamond8"])
 def test_mixed_small_cells(case, prec):
     w = tiny_periodic() if case == "tiny" else inputs.diamond8()
@@ -70,25 +73,23 @@ def two_species_cell(seed=13):
     return inputs.cut_density(w, 4.5)
 
 
-@pytest.mark.parametrize("prec", [hfx.HFX_BF16X6, hfx.HFX_BF16X3])
+@pytest.mark.parametrize("prec", SPLITS)
 def test_mixed_two_species_shapes(prec):
     """BF16X6 meets 1e-5 here too.  BF16X3 does not on this cell: its
     second product (R2 and Z from two-piece Y, the 2^-16 piece product
     dropped) leaves 2.1e-5 in F on its own, the same with the warp-level and
-    the tcgen05 first product, so BF16X3 is held to 3e-5 on it; the bench
-    takes BF16X3 as its headline only where its error on the benchmark
-    geometry is within 1e-5."""
+    the tcgen05 first product, so BF16X3 is held to 3e-5 on it."""
     w = two_species_cell()
     r = evaluate(w)
     E, F, S, st = run(w, prec)
-    b = BOUND[prec] if prec == hfx.HFX_BF16X6 else 3e-5
+    b = 3e-5 if prec == hfx.HFX_BF16X3 else BOUND[prec]
     assert abs(E - r.E) <= b * abs(r.E)
     assert rel(F, r.F) <= b, rel(F, r.F)
     assert rel(S, r.sigma) <= b, rel(S, r.sigma)
     assert st["triplets"] == r.counts["triplets"] and st["term2_pairs"] == r.counts["term2_pairs"]
 
 
-@pytest.mark.parametrize("prec", [hfx.HFX_BF16X6, hfx.HFX_BF16X3])
+@pytest.mark.parametrize("prec", SPLITS)
 def test_mixed_si64_full_size(prec):
     """The 64-atom Si-like supercell of the benchmark against the stored oracle."""
     ref = json.load(open(os.path.join(HERE, "golden", "si64_oracle.json")))
@@ -99,6 +100,28 @@ def test_mixed_si64_full_size(prec):
     print(f"precision {prec}: errE {eE:.2e} errF {eF:.2e} errS {eS:.2e}")
     assert eE <= b and eF <= b and eS <= b
     assert st["triplets"] == ref["counts"]["triplets"]
+
+
+@pytest.mark.parametrize("prec", [hfx.HFX_BF16X6, hfx.HFX_BF16X3])
+def test_split_precisions_on_jittered_si64_geometries(prec):
+    """The first four geometries of the benchmark's jittered si64 sequence,
+    against the FP64 GPU path (itself within 1e-10 of the oracle).  BF16X6
+    stays within 1e-5 on each.  BF16X3 reaches 1.75e-5 in sigma on some of
+    them (its two-piece operands leave 2^-16-level errors in both exchange
+    products), so it is held to 2.5e-5 here, and the benchmark takes it as
+    its headline only where it meets 1e-5 on these geometries."""
+    w = inputs.si_supercell(2)
+    geoms = inputs.geometry_sequence(w, 4)
+    with hfx.Plan(w, precision=hfx.HFX_FP64) as p0:
+        refs = [p0.evaluate(w.lattice, g) for g in geoms]
+    with hfx.Plan(w, precision=prec) as p:
+        for k, g in enumerate(geoms):
+            E, F, S = p.evaluate(w.lattice, g)
+            E0, F0, S0 = refs[k]
+            eE, eF, eS = abs(E - E0) / abs(E0), rel(F, F0), rel(S, S0)
+            print(f"precision {prec} geometry {k}: errE {eE:.2e} errF {eF:.2e} errS {eS:.2e}")
+            b = 1e-5 if prec == hfx.HFX_BF16X6 else 2.5e-5
+            assert eE <= b and eF <= b and eS <= b, k
 
 
 def test_mixed_anisotropic_gradient_blocks():
@@ -124,7 +147,7 @@ def test_mixed_each_exchange_product_alone():
         assert rel(F, r.F) <= 1e-5 and rel(S, r.sigma) <= 1e-5
 
 
-@pytest.mark.parametrize("prec", [hfx.HFX_BF16X6, hfx.HFX_BF16X3])
+@pytest.mark.parametrize("prec", SPLITS)
 def test_first_product_kernels_agree(prec, monkeypatch):
     """The tcgen05 first product and the warp-level MMA one (selected at plan
     creation by HFX_T1_KERNEL) on the same cell: both within their bound of
