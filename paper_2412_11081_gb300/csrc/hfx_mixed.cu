@@ -818,12 +818,13 @@ __device__ __forceinline__ void stage_d(int lane, uint16_t* stB, const int* md, 
 
 // TPC row tiles of 128 rows per CTA share each K step's D blocks (the B
 // operand): with TPC = 2 a step moves 3 NP tiles for two tiles' work instead
-// of 2 NP for one, in 3 stages, one accumulator per tile (no double buffer;
-// two CTAs per SM overlap one's epilogue with the other's MMAs) and 512 pairs
-// of metadata; TPC = 1 keeps 4 stages and two accumulators.
-template <int TPC>
+// of 2 NP for one, in 3 stages (2 with NP = 3, so that two CTAs still fit an
+// SM), one accumulator per tile (no double buffer; two CTAs per SM overlap
+// one's epilogue with the other's MMAs) and 512 pairs of metadata; TPC = 1
+// keeps 4 stages and two accumulators.
+template <int NP, int TPC>
 struct Q2Shape {
-  static constexpr int kS = TPC == 2 ? 3 : umma::kStages;          // stages
+  static constexpr int kS = TPC == 2 ? (NP == 2 ? 3 : 2) : umma::kStages;   // stages
   static constexpr int kMP = TPC == 2 ? 512 : umma::kMetaPairs;    // pairs per CTA segment
   static constexpr int kNB = TPC == 2 ? 1 : 2;                     // accumulator buffers
 };
@@ -839,7 +840,7 @@ __global__ void __launch_bounds__(192) k_q2_umma(DevPlan P, MixPlan X, const int
   // the accumulators (each its 32-lane quarter of tensor memory) and dot
   // them with grad C_AF.  No block barrier inside the pipeline.
   using namespace umma;
-  constexpr int KS = Q2Shape<TPC>::kS, KMP = Q2Shape<TPC>::kMP, NB = Q2Shape<TPC>::kNB;
+  constexpr int KS = Q2Shape<NP, TPC>::kS, KMP = Q2Shape<NP, TPC>::kMP, NB = Q2Shape<NP, TPC>::kNB;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   uint16_t* stA = reinterpret_cast<uint16_t*>(smem_raw);                  // [KS][TPC][NP][kTileElems]
   uint16_t* stB = stA + (size_t)KS * TPC * NP * kTileElems;               // [KS][NP][kTileElems]
@@ -1072,11 +1073,17 @@ __global__ void __launch_bounds__(192) k_q2_umma(DevPlan P, MixPlan X, const int
 // bf16 pieces and writes the Y store ([alpha][z][16], x padding zeroed).
 // TPC row tiles of 128 rows per CTA share each K step's D blocks (one
 // accumulator of 128 columns per tile).
+__host__ __device__ constexpr int yb_tpc(int) { return 2; }
+// stages of the Y build's ring: 4, or 2 for two six-product tiles (so that
+// two CTAs still fit an SM)
+__host__ __device__ constexpr int yb_stages(int np, int tpc) { return tpc == 2 && np == 3 ? 2 : umma::kStages; }
+
 template <int NP, int TPC>
 __global__ void __launch_bounds__(192) k_ybuild_umma(DevPlan P, MixPlan X, const int* ylist, const int* gX,
                                                      const int* gS, const int* gN, int MC,
                                                      const __grid_constant__ DRows drows, int* err) {
   using namespace umma;
+  constexpr int kStages = yb_stages(NP, TPC);
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   uint16_t* stA = reinterpret_cast<uint16_t*>(smem_raw);                     // [kStages][TPC][NP][kTileElems]
   uint16_t* stB = stA + (size_t)kStages * TPC * NP * kTileElems;           // [kStages][NP][kTileElems]
@@ -1425,21 +1432,21 @@ __global__ void k_q2tab(DevPlan P, MixPlan X, const int* list, int n_slots, int 
   if ((threadIdx.x & 31) == 0 && fl != 0.0) atomicAdd(&P.acc[ACC_F2], fl);
 }
 
-// row tiles per CTA of the Y build: two for BF16X3
-constexpr int yb_tpc(int np) { return np == 2 ? 2 : 1; }
-
 size_t ybuild_umma_smem(int np) {
-  return (size_t)(yb_tpc(np) + 1) * umma::kStages * np * umma::kTileElems * sizeof(uint16_t) +
+  return (size_t)(yb_tpc(np) + 1) * yb_stages(np, yb_tpc(np)) * np * umma::kTileElems * sizeof(uint16_t) +
          (size_t)kMaxCPerAtom * 8 * sizeof(int);
 }
 
-// row tiles per CTA of the Q2 GEMM: two for BF16X3 (the stages of BF16X6 would not leave room for two CTAs)
-constexpr int q2_tpc(int np) { return np == 2 ? 2 : 1; }
+// row tiles per CTA of the Q2 GEMM
+constexpr int q2_tpc(int np) { return 2; }
 
 size_t q2_umma_smem(int np) {
-  if (q2_tpc(np) == 2)
-    return (size_t)Q2Shape<2>::kS * 3 * np * umma::kTileElems * sizeof(uint16_t) + (size_t)Q2Shape<2>::kMP * 8 * sizeof(int);
-  return (size_t)2 * Q2Shape<1>::kS * np * umma::kTileElems * sizeof(uint16_t) + (size_t)Q2Shape<1>::kMP * 8 * sizeof(int);
+  const int tpc = q2_tpc(np);
+  const int ks = np == 2 ? Q2Shape<2, 2>::kS : Q2Shape<3, 2>::kS;
+  const int kmp = Q2Shape<2, 2>::kMP;
+  if (tpc == 2) return (size_t)ks * 3 * np * umma::kTileElems * sizeof(uint16_t) + (size_t)kmp * 8 * sizeof(int);
+  return (size_t)2 * Q2Shape<2, 1>::kS * np * umma::kTileElems * sizeof(uint16_t) +
+         (size_t)Q2Shape<2, 1>::kMP * 8 * sizeof(int);
 }
 
 int grid_for(long long n, int cap) {
@@ -1455,7 +1462,7 @@ long long ytab_size(int ngroups, int maxC) { return (long long)ngroups * 8 * max
 long long q2tab_size(int n_slots, int FC) { return (long long)n_slots * ((FC * 4 + 7) / 8) * 8; }
 
 int q2_umma_segments(int max_pairs_per_atom, int np) {
-  const int kmp = q2_tpc(np) == 2 ? Q2Shape<2>::kMP : Q2Shape<1>::kMP;
+  const int kmp = q2_tpc(np) == 2 ? Q2Shape<2, 2>::kMP : Q2Shape<2, 1>::kMP;
   return (max_pairs_per_atom + kmp - 1) / kmp;
 }
 
