@@ -351,7 +351,7 @@ def run_ours(args):
                 "dtype": "bf16" if args.precision != "fp64" else "f64",
                 "data": "synthetic",
                 "config": {"workload": WORKLOAD, "precision": args.precision,
-                           "headline_rule": "fastest split with max(errE, errF, errS) <= 1e-5 vs FP64 GPU"
+                           "headline_rule": "bf16x3 if max(errE, errF, errS) <= 1e-5 vs FP64 GPU on 4 geometries, else bf16x6"
                            if auto else "fixed by --precision",
                            "arithmetic": "bf16 pieces on tensor cores, fp32 accumulate, fp64 screening/reduction"
                            if args.precision != "fp64" else "fp64",

@@ -757,8 +757,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     // Lane l of U warp uw: row beta = 8 uw + ((l >> 1) & 7), columns
     // a = 4 qa .. 4 qa + 3 with qa = 2 (l >> 4) + (l & 1).  A half warp then
     // stores one contiguous 128-byte run of U, and the four lanes of a row
-    // each read one 16-byte chunk of the Y row (the row is gathered by
-    // shuffles instead of four shared-memory reads per lane).
+    // read the same Y row (one shared-memory wavefront per 16-byte chunk for
+    // the warp's eight rows).
     const int uw = warp - kWarpU;
     const int r8 = (lane >> 1) & 7, qa = 2 * (lane >> 4) + (lane & 1);
     const int beta = 8 * uw + r8;
@@ -810,21 +810,19 @@ __global__ void __launch_bounds__(kThreads, 1)
               if (!ok) break;
               if (NP == 3) {
                 // BF16X6 (tighter on registers): one row per pass, each lane
-                // reads one 16-byte chunk and the row is gathered by shuffles
+                // reads the row's four 16-byte chunks (chunk c stored at c ^ ysw)
                 for (int f = fa; f < fb; ++f) {
-                  float4 mine = make_float4(0.f, 0.f, 0.f, 0.f);
-                  if (beta < mB)
-                    mine = *reinterpret_cast<const float4*>(Ys + sl * SLOT + ((f - fa) * mB + beta) * 16 + 4 * (qa ^ ysw));
                   float y[16];
 #pragma unroll
                   for (int c4 = 0; c4 < 4; ++c4) {
-                    const int src = 16 * (c4 >> 1) + 2 * r8 + (c4 & 1);   // lane holding chunk c4 of this row
-                    y[4 * c4] = __shfl_sync(0xffffffffu, mine.x, src);
-                    y[4 * c4 + 1] = __shfl_sync(0xffffffffu, mine.y, src);
-                    y[4 * c4 + 2] = __shfl_sync(0xffffffffu, mine.z, src);
-                    y[4 * c4 + 3] = __shfl_sync(0xffffffffu, mine.w, src);
+                    float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (beta < mB)
+                      a = *reinterpret_cast<const float4*>(Ys + sl * SLOT + ((f - fa) * mB + beta) * 16 + 4 * (c4 ^ ysw));
+                    y[4 * c4] = a.x;
+                    y[4 * c4 + 1] = a.y;
+                    y[4 * c4 + 2] = a.z;
+                    y[4 * c4 + 3] = a.w;
                   }
-                  if (f + 1 >= fb && lane == 0) mbar_arrive(ye + 8 * sl);   // the slot's rows are in registers
                   float uf4[4] = {0.f, 0.f, 0.f, 0.f};
                   if (beta < mB)
 #pragma unroll
@@ -834,6 +832,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                         uf4[2 * j] = fmaf(y[b], dd[j][b].x, uf4[2 * j]);
                         uf4[2 * j + 1] = fmaf(y[b], dd[j][b].y, uf4[2 * j + 1]);
                       }
+                  if (f + 1 >= fb) {   // the slot's rows have been read and used
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(ye + 8 * sl);
+                  }
                   uint2 pk[NP];
                   split4<NP>(uf4, pk);
 #pragma unroll
