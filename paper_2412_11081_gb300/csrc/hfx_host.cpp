@@ -781,7 +781,7 @@ void setup_shapes(hfx_plan* P) {
   const size_t base2 = (size_t)(3 * hfx::kMaxCPerAtom + hfx::kMaxAO * hfx::kMaxAO) * sizeof(double);
   P->alpha_chunk = (int)std::min<size_t>(maxABF, (limit - base2) / per1);
   P->smem_t2 = base2 + per1 * P->alpha_chunk;
-  ck(hfx::set_kernel_smem_limits(P->smem_t1, P->smem_t2), "smem attributes");
+  ck(hfx::set_kernel_smem_limits(), "smem attributes");
   if (P->np) {
     auto r16 = [](int x) { return (x + 15) / 16 * 16; };
     int maxKAF = 0, zrows = 0;
@@ -835,7 +835,7 @@ void setup_shapes(hfx_plan* P) {
         // and fewer FP64 flushes)
         const char* sg = std::getenv("HFX_T1_SEG");
         P->t1u_seg = sg ? std::max(1, std::atoi(sg)) : (P->np == 3 ? 128 : 32);
-        ck(hfx::t1u_set_smem(P->np, P->smem_t1u), "smem attributes");
+        ck(hfx::t1u_set_smem(P->np), "smem attributes");
       }
     }
     if (!P->t1u) {
@@ -847,7 +847,7 @@ void setup_shapes(hfx_plan* P) {
       fail(HFX_ERR_UNSUPPORTED, "block shapes too large for the split-precision kernels");
     const char* qf = std::getenv("HFX_Q2_FLUSH");
     P->q2_flush = qf ? std::max(1, std::atoi(qf)) : (P->np == 3 ? 128 : 32);   // as t1u_seg
-    ck(hfx::set_mixed_smem_limits(P->np, P->t1u ? 0 : P->smem_m1, P->smem_m2), "smem attributes");
+    ck(hfx::set_mixed_smem_limits(P->np), "smem attributes");
   }
 }
 

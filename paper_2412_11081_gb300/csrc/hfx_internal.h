@@ -166,7 +166,13 @@ cudaError_t launch_term1(const DevPlan& P, const int* list, int n, int beta_chun
 cudaError_t launch_term2(const DevPlan& P, const int* list, int n, int alpha_chunk, size_t smem,
                          cudaStream_t s);
 cudaError_t launch_reduce(const DevPlan& P, double* out, cudaStream_t s);
-cudaError_t set_kernel_smem_limits(size_t t1, size_t t2);
+// Plans created and evaluated from different host threads share the
+// kernels' attributes, so no plan sets a kernel's dynamic shared-memory cap
+// to its own size: allow_max_dynamic_smem raises the cap of f to the
+// device's opt-in maximum minus f's static shared memory, the same value
+// from every caller (each plan checks its own sizes against that limit).
+cudaError_t allow_max_dynamic_smem(const void* f);
+cudaError_t set_kernel_smem_limits();
 
 // Split-precision kernels (hfx_mixed.cu); np = bf16 pieces per operand (2 or 3).
 long long mixed_launch_count();
@@ -191,7 +197,7 @@ long long q2tab_size(int n_slots, int FC);
 cudaError_t launch_t1_lists(const DevPlan& P, const MixPlan& X, int phase, cudaStream_t s);
 size_t term1_mma_smem(int np, int MAmax, int MBmax, int KSmax, int YRmax);
 size_t term2_mma_smem(int np, int MAmax, int KZmax);
-cudaError_t set_mixed_smem_limits(int np, size_t t1, size_t t2);
+cudaError_t set_mixed_smem_limits(int np);
 cudaError_t launch_term1_mma(const DevPlan& P, const MixPlan& X, int np, const int* qlist, int n, int MAmax,
                              int MBmax, int KSmax, int YRmax, size_t smem, cudaStream_t s);
 cudaError_t launch_term2_mma(const DevPlan& P, const MixPlan& X, int np, const int* list, const long long* slot0,
@@ -211,7 +217,7 @@ constexpr int kLptBuckets = 4096;
 cudaError_t launch_lpt_order(const int* qcnt, const int* list, int n_max, const long long* n_dev, int* hist, int* out,
                              cudaStream_t s);
 int t1u_max_slots();
-cudaError_t t1u_set_smem(int np, size_t smem);
+cudaError_t t1u_set_smem(int np);
 // Needed V pairs: the second product's V store (MixPlan::Vm) and, with U.Vu
 // set, the tcgen05 first product's V store, in one pass per pair.
 cudaError_t launch_vstores(const DevPlan& P, const MixPlan& X, const T1UPlan& U, int np, const int* list, int n,

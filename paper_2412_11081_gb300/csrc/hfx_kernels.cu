@@ -18,6 +18,7 @@
 // CTAs meet in FP64 atomics (order-dependent only at the last bits).
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 
@@ -30,7 +31,7 @@ namespace {
 using namespace model;
 
 constexpr int kThreads = 256;
-long long g_launches = 0;   // host-side count of kernel launches
+std::atomic<long long> g_launches{0};   // host-side count of kernel launches (all threads)
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -851,10 +852,20 @@ cudaError_t launch_ybuild(const DevPlan& P, const int* list, int n, cudaStream_t
   return cudaGetLastError();
 }
 
-cudaError_t set_kernel_smem_limits(size_t t1, size_t t2) {
-  cudaError_t e = cudaFuncSetAttribute(k_term1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t1);
+cudaError_t allow_max_dynamic_smem(const void* f) {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes a{};
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, f);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_term2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t2);
+  return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)a.sharedSizeBytes);
+}
+
+cudaError_t set_kernel_smem_limits() {
+  cudaError_t e = allow_max_dynamic_smem((const void*)k_term1);
+  if (e != cudaSuccess) return e;
+  return allow_max_dynamic_smem((const void*)k_term2);
 }
 
 cudaError_t launch_term1(const DevPlan& P, const int* list, int n, int beta_chunk, size_t smem, cudaStream_t s) {

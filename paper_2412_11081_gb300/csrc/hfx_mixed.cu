@@ -26,6 +26,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 
 #include "hfx_device.cuh"
@@ -40,7 +41,7 @@ constexpr int kWarps1 = 16;     // warps per CTA of the term-1 kernel
 constexpr int kWarps = 8;       // warps per CTA of the other mixed kernels
 constexpr int kQT = 16;         // Q accumulator tiles per warp (term 1)
 constexpr int kFlush = 8;       // B per FP32 run of the Q accumulators
-long long g_mix_launches = 0;
+std::atomic<long long> g_mix_launches{0};
 
 // Element offset of (row r, column c < 16) inside a tile stored in the
 // K-major core-matrix order of the tensor cores: 8-row x 8-column core
@@ -1528,22 +1529,17 @@ size_t term2_mma_smem(int np, int MAmax, int KZmax) {
   return (size_t)np * 2 * MAmax * KZmax * sizeof(uint16_t);
 }
 
-cudaError_t set_mixed_smem_limits(int np, size_t t1, size_t t2) {
-  cudaError_t e;
-  e = cudaFuncSetAttribute(np == 2 ? (const void*)k_ybuild_umma<2, yb_tpc(2)> : (const void*)k_ybuild_umma<3, yb_tpc(3)>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ybuild_umma_smem(np));
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(np == 2 ? (const void*)k_q2_umma<2, q2_tpc(2)> : (const void*)k_q2_umma<3, q2_tpc(3)>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)q2_umma_smem(np));
-  if (e != cudaSuccess) return e;
-  if (np == 2) {
-    e = cudaFuncSetAttribute(k_term1_mma<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t1);
+cudaError_t set_mixed_smem_limits(int np) {
+  const void* f[4] = {
+      np == 2 ? (const void*)k_ybuild_umma<2, yb_tpc(2)> : (const void*)k_ybuild_umma<3, yb_tpc(3)>,
+      np == 2 ? (const void*)k_q2_umma<2, q2_tpc(2)> : (const void*)k_q2_umma<3, q2_tpc(3)>,
+      np == 2 ? (const void*)k_term1_mma<2> : (const void*)k_term1_mma<3>,
+      np == 2 ? (const void*)k_term2_pairs<2> : (const void*)k_term2_pairs<3>};
+  for (const void* k : f) {
+    const cudaError_t e = allow_max_dynamic_smem(k);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_term2_pairs<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t2);
   }
-  e = cudaFuncSetAttribute(k_term1_mma<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t1);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_term2_pairs<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t2);
+  return cudaSuccess;
 }
 
 cudaError_t launch_term1_mma(const DevPlan& P, const MixPlan& X, int np, const int* qlist, int n, int MAmax, int MBmax,

@@ -30,6 +30,8 @@
 // All hand-offs are mbarriers (bounded waits; a timeout sets the error flag
 // and every role stops), no block barrier inside the pipeline.
 #include <algorithm>
+#include <atomic>
+#include <mutex>
 
 #include "hfx_device.cuh"
 #include "hfx_model.cuh"
@@ -39,7 +41,7 @@ namespace {
 
 using namespace dev;
 
-long long g_t1u_launches = 0;
+std::atomic<long long> g_t1u_launches{0};
 
 constexpr int kThreads = 512;
 constexpr int kWarpY = 0, kWarpV = 1, kWarpM = 2, kWarpQ = 3, kWarpE = 4, kWarpU = 8;
@@ -943,7 +945,15 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (tid == 0 && s_abort) atomicExch(err, 1);
 }
 
-int g_num_sms = 0;
+int num_sms() {
+  static const int n = [] {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v > 0 ? v : 152;
+  }();
+  return n;
+}
 
 }  // namespace
 
@@ -955,21 +965,19 @@ size_t t1u_smem(int np, int KP, int NS, int FS) {
 
 int t1u_max_slots() { return kMaxNS; }
 
-cudaError_t t1u_set_smem(int np, size_t smem) {
-  return cudaFuncSetAttribute(np == 2 ? (const void*)k_t1_umma<2> : (const void*)k_t1_umma<3>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+cudaError_t t1u_set_smem(int np) {
+  return allow_max_dynamic_smem(np == 2 ? (const void*)k_t1_umma<2> : (const void*)k_t1_umma<3>);
 }
 
 cudaError_t launch_t1u_stores(const DevPlan& P, const T1UPlan& U, int np, const int* qlist, int nq, bool dstore,
                               cudaStream_t s) {
   if (nq > 0) {
     ++g_t1u_launches;
-    static bool attr = false;
-    if (!attr) {
+    static std::once_flag attr;
+    std::call_once(attr, [] {
       cudaFuncSetAttribute(k_t1u_cstore<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kCStoreSmem);
       cudaFuncSetAttribute(k_t1u_cstore<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kCStoreSmem);
-      attr = true;
-    }
+    });
     const int g = nq < 152 * 3 ? nq : 152 * 3;
     if (np == 2) k_t1u_cstore<2><<<g, 256, kCStoreSmem, s>>>(P, U, qlist, nq);
     else k_t1u_cstore<3><<<g, 256, kCStoreSmem, s>>>(P, U, qlist, nq);
@@ -999,12 +1007,11 @@ cudaError_t launch_vstores(const DevPlan& P, const MixPlan& X, const T1UPlan& U,
                            cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   ++g_t1u_launches;
-  static bool attr = false;
-  if (!attr) {
+  static std::once_flag attr;
+  std::call_once(attr, [] {
     cudaFuncSetAttribute(k_vstores<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kVStoreSmem);
     cudaFuncSetAttribute(k_vstores<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kVStoreSmem);
-    attr = true;
-  }
+  });
   const int g = n < 152 * 3 ? n : 152 * 3;
   if (np == 2) k_vstores<2><<<g, 256, kVStoreSmem, s>>>(P, X, U, list, n);
   else k_vstores<3><<<g, 256, kVStoreSmem, s>>>(P, X, U, list, n);
@@ -1014,14 +1021,8 @@ cudaError_t launch_vstores(const DevPlan& P, const MixPlan& X, const T1UPlan& U,
 cudaError_t launch_t1_umma(const DevPlan& P, const MixPlan& X, const T1UPlan& U, int np, const int* qlist, int n,
                            size_t smem, int* work, int* err, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  if (g_num_sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (g_num_sms <= 0) g_num_sms = 152;
-  }
   ++g_t1u_launches;
-  const int grid = n < g_num_sms ? n : g_num_sms;
+  const int grid = n < num_sms() ? n : num_sms();
   cudaError_t e = cudaMemsetAsync(work, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
   if (np == 2) k_t1_umma<2><<<grid, kThreads, smem, s>>>(P, X, U, qlist, n, work, err);
