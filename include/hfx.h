@@ -28,7 +28,10 @@
  *  - Every call returns an hfx_status; no C++ exception crosses the ABI.
  *  - Outputs are written only when the call returns HFX_OK.
  *  - A plan is bound to one CUDA stream and one device and is not thread
- *    safe; calls on one plan must be serialised by the caller.
+ *    safe; calls on one plan must be serialised by the caller.  Different
+ *    plans may be created and evaluated from different host threads at the
+ *    same time (each on its own stream); the library's shared state is only
+ *    the kernels' attributes, set to the same values by every plan.
  *  - Units: positions and lattice in Angstrom; E in model units; F in E/A;
  *    sigma in E/A^3, row-major 3x3, symmetric within rounding for the
  *    isotropic model.
@@ -123,7 +126,8 @@ typedef struct {
   double flops_y, flops_term1, flops_term2, flops_total;
   double ms_blocks, ms_screen, ms_y, ms_term1, ms_term2, ms_reduce, ms_total;
   long long device_bytes;                       /* device memory held by the plan */
-  long long kernel_launches;                    /* CUDA kernels this library launched in the call */
+  long long kernel_launches;                    /* CUDA kernels this library launched during the call
+                                                   (all threads: exact when one plan evaluates at a time) */
 } hfx_stats;
 
 /* Fill *opt with the defaults (all thresholds 1e-10, FP64, both terms,
