@@ -260,6 +260,12 @@ def run_ours(args):
         args.precision = "bf16x3" if max(x3["errE"], x3["errF"], x3["errS"]) <= 1e-5 else "bf16x6"
     plan = variants[args.precision]["plan"] if args.precision != "fp64" else \
         hfx.Plan(w, precision=hfx.HFX_FP64, stream=stream.cuda_stream, device=local)
+    # the split plans pick their launch shapes with the library's autotuner
+    # (hfx_plan_autotune, untimed; the arithmetic does not change)
+    tuned = {}
+    if not args.no_autotune:
+        for name, v in variants.items():
+            tuned[name] = v["plan"].autotune(w.lattice, geoms[0], reps=3)
 
     for k in range(args.warmup):
         plan.evaluate_device(w.lattice, d_pos[k].data_ptr(), d_out.data_ptr(), stats=True)
@@ -366,6 +372,7 @@ def run_ours(args):
                 "fp64": {"evals_per_s": 1.0 / t_fp64, "speedup_of_headline": value / world * t_fp64},
                 "other_precisions": other,
                 "stages_ms": stage_ms,
+                "autotune": tuned,
                 "gflop_per_eval": flops["flops_total"] / 1e9,
                 "achieved_tflops_total": flops["flops_total"] / (t_max / args.steps) / 1e12,
                 "counts": {k: flops[k] for k in ("c_pairs", "v_pairs", "triplets", "term1_pairs",
@@ -392,6 +399,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="auto", choices=["auto", "bf16x6", "bf16x3", "fp64"])
+    ap.add_argument("--no-autotune", action="store_true", help="keep the plans' initial launch shapes")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -187,6 +187,27 @@ hfx_status hfx_energy_force_stress_noalloc(hfx_plan* plan, const double* lattice
 /* Per-stage CUDA-event timing on (1) or off (0, default). */
 hfx_status hfx_set_timing(hfx_plan* plan, int on);
 
+/* Autotuner.  Times the evaluation of `positions` (host, [n_atoms*3], with
+ * `lattice` as in hfx_energy_force_stress) for each launch configuration of
+ * the plan that leaves the arithmetic unchanged, and keeps the fastest for
+ * the plan's later calls.  Today that is the shape of the tcgen05 first
+ * product's Y ring (rows f per slot and number of slots, bounded by shared
+ * memory): the shapes of the block pairs decide which run length balances
+ * the copy of Y rows against the U build.  Each candidate is timed as the
+ * median of `reps` >= 1 evaluations (CUDA events) after one warm-up.
+ * `report` (nullable) receives the choice and both times.  Plans without a
+ * tunable kernel (FP64, or the warp-level first product) return HFX_OK
+ * with candidates = 0.  On an error the plan keeps its initial choice. */
+typedef struct {
+  int candidates;          /* configurations timed, the initial one included */
+  int t1_rows_per_slot;    /* chosen rows f per Y slot */
+  int t1_slots;            /* chosen number of Y slots */
+  double default_ms;       /* median evaluation time with the initial choice */
+  double best_ms;          /* median evaluation time with the chosen one */
+} hfx_tune_report;
+hfx_status hfx_plan_autotune(hfx_plan* plan, const double* lattice, const double* positions, int reps,
+                             hfx_tune_report* report);
+
 /* Free every resource of the plan.  NULL is accepted. */
 hfx_status hfx_plan_destroy(hfx_plan* plan);
 

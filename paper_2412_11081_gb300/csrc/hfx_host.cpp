@@ -208,6 +208,7 @@ struct hfx_plan {
   // tcgen05 first product (n_abf <= 64, n_ao <= 16): operand stores and shape
   bool t1u = false;
   int t1u_KP = 0, t1u_NS = 0, t1u_FS = 1, t1u_seg = 32;
+  size_t t1u_limit = 0;        // dynamic shared memory the Y ring may fill up to
   size_t smem_t1u = 0;
   uint16_t* Cu = nullptr;
   long long Cucap = 0;
@@ -764,6 +765,12 @@ double list_drift(const hfx_plan* P, const double* L, const double* pos) {
   return 2.0 * disp + P->list_Rabs * dl;
 }
 
+// Y slots of fs rows that fit next to the first product's fixed shared memory.
+long long t1u_slots(const hfx_plan* P, int fs) {
+  const size_t base = hfx::t1u_smem(P->np, P->t1u_KP, 0, 1);
+  return base < P->t1u_limit ? (long long)((P->t1u_limit - base) / ((size_t)fs * 4096)) : 0LL;
+}
+
 void setup_shapes(hfx_plan* P) {
   int dev_smem = 0;
   ck(cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->dev), "attr");
@@ -816,11 +823,9 @@ void setup_shapes(hfx_plan* P) {
       // release per run of rows) when three such slots fit, else runs of two
       // rows (measured best for BF16X6 on si64), else single rows
       // (HFX_T1_FS overrides the run length).
-      const size_t base = hfx::t1u_smem(P->np, P->t1u_KP, 0, 1);
+      P->t1u_limit = limit;
       const int fh = (P->t1u_KP / 16 + 1) / 2;
-      auto slots = [&](int fs) {
-        return base < limit ? (long long)((limit - base) / ((size_t)fs * 4096)) : 0LL;
-      };
+      auto slots = [&](int fs) { return t1u_slots(P, fs); };
       const char* fse = std::getenv("HFX_T1_FS");
       int fs = fse ? std::max(1, std::min(fh, std::atoi(fse))) : (slots(fh) >= 3 ? fh : (slots(2) >= 3 ? 2 : 1));
       while (fs > 1 && slots(fs) < 2) --fs;
@@ -1272,6 +1277,72 @@ hfx_status hfx_energy_force_stress_device(hfx_plan* P, const double* lattice, co
 hfx_status hfx_set_timing(hfx_plan* P, int on) {
   if (!P) return HFX_ERR_INVALID;
   P->timing = on != 0;
+  return HFX_OK;
+}
+
+hfx_status hfx_plan_autotune(hfx_plan* P, const double* lattice, const double* positions, int reps,
+                             hfx_tune_report* report) {
+  if (!P || !lattice || !positions || reps < 1) return HFX_ERR_INVALID;
+  hfx_tune_report R{};
+  R.t1_rows_per_slot = P->t1u_FS;
+  R.t1_slots = P->t1u_NS;
+  if (!P->t1u) {
+    if (report) *report = R;
+    return HFX_OK;
+  }
+  const int fs0 = P->t1u_FS, ns0 = P->t1u_NS;
+  const size_t smem0 = P->smem_t1u;
+  const bool timing0 = P->timing;
+  auto use = [&](int fs, int ns) {
+    P->t1u_FS = fs;
+    P->t1u_NS = ns;
+    P->smem_t1u = hfx::t1u_smem(P->np, P->t1u_KP, ns, fs);
+  };
+  std::vector<double> F(3 * (size_t)P->N);
+  double E = 0.0, sig[9];
+  hfx_stats st{};
+  hfx_status status = HFX_OK;
+  auto time_it = [&](double& ms) -> bool {   // one warm-up, then the median of reps
+    std::vector<double> t;
+    for (int r = 0; r <= reps; ++r) {
+      status = hfx_energy_force_stress(P, lattice, positions, &E, F.data(), sig, &st);
+      if (status != HFX_OK) return false;
+      if (r > 0) t.push_back(st.ms_total);
+    }
+    std::sort(t.begin(), t.end());
+    ms = t[t.size() / 2];
+    return true;
+  };
+  P->timing = true;
+  bool ok = time_it(R.default_ms);
+  int best_fs = fs0, best_ns = ns0;
+  R.best_ms = R.default_ms;
+  R.candidates = ok ? 1 : 0;
+  const int fh = (P->t1u_KP / 16 + 1) / 2;   // a run never crosses a U column chunk
+  for (int fs = 1; ok && fs <= fh; ++fs) {
+    const int ns = (int)std::min<long long>(t1u_slots(P, fs), hfx::t1u_max_slots());
+    if (ns < 2 || (fs == fs0 && ns == ns0)) continue;
+    use(fs, ns);
+    double ms = 0.0;
+    ok = time_it(ms);
+    if (!ok) break;
+    ++R.candidates;
+    if (ms < R.best_ms) {
+      R.best_ms = ms;
+      best_fs = fs;
+      best_ns = ns;
+    }
+  }
+  P->timing = timing0;
+  if (!ok) {   // keep the initial choice
+    use(fs0, ns0);
+    P->smem_t1u = smem0;
+    return status;
+  }
+  use(best_fs, best_ns);
+  R.t1_rows_per_slot = best_fs;
+  R.t1_slots = best_ns;
+  if (report) *report = R;
   return HFX_OK;
 }
 

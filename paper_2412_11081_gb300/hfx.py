@@ -44,6 +44,11 @@ class HfxOptions(ct.Structure):
                 ("device", ct.c_int)]
 
 
+class HfxTuneReport(ct.Structure):
+    _fields_ = [("candidates", ct.c_int), ("t1_rows_per_slot", ct.c_int), ("t1_slots", ct.c_int),
+                ("default_ms", ct.c_double), ("best_ms", ct.c_double)]
+
+
 class HfxStats(ct.Structure):
     _fields_ = [("c_pairs", ct.c_longlong), ("v_pairs", ct.c_longlong), ("d_blocks", ct.c_longlong),
                 ("triplets", ct.c_longlong), ("term1_pairs", ct.c_longlong), ("term2_pairs", ct.c_longlong),
@@ -67,6 +72,7 @@ _SIGNATURES = {
                                                   ct.POINTER(HfxStats)]),
     "hfx_energy_force_stress_noalloc": (ct.c_int, [ct.c_void_p, _dp, _dp, _dp, _dp, _dp]),
     "hfx_set_timing": (ct.c_int, [ct.c_void_p, ct.c_int]),
+    "hfx_plan_autotune": (ct.c_int, [ct.c_void_p, _dp, _dp, ct.c_int, ct.c_void_p]),
     "hfx_plan_destroy": (ct.c_int, [ct.c_void_p]),
     "hfx_status_string": (ct.c_char_p, [ct.c_int]),
     "hfx_last_error": (ct.c_char_p, [ct.c_void_p]),
@@ -198,6 +204,19 @@ class Plan:
                                               ct.byref(self.stats) if stats else None)
         _check(self.lib, st, self.handle)
         return float(E.value), F, sig
+
+    def autotune(self, lattice, positions, reps: int = 3) -> dict:
+        """hfx_plan_autotune: time the launch configurations that leave the
+        arithmetic unchanged at this geometry and keep the fastest."""
+        lat = _f64(lattice).ravel()
+        pos = _f64(positions).ravel()
+        if pos.size != 3 * self.n_atoms:
+            raise ValueError("positions must be n_atoms x 3")
+        rep = HfxTuneReport()
+        st = self.lib.hfx_plan_autotune(self.handle, lat.ctypes.data_as(_dp), pos.ctypes.data_as(_dp), int(reps),
+                                        ct.byref(rep))
+        _check(self.lib, st, self.handle)
+        return {k: getattr(rep, k) for k, _ in rep._fields_}
 
     def evaluate_noalloc(self, lattice, positions):
         """hfx_energy_force_stress_noalloc: the FP64 evaluation with its

@@ -29,16 +29,21 @@ def main(argv=None) -> int:
     ap.add_argument("--cell", default="si8", choices=sorted(CELLS))
     ap.add_argument("--precision", default="bf16x3", choices=sorted(PRECISIONS))
     ap.add_argument("--evals", type=int, default=2)
+    ap.add_argument("--autotune", action="store_true", help="run hfx_plan_autotune before the evaluations")
     args = ap.parse_args(argv)
     w = CELLS[args.cell]()
+    tune = None
     with hfx.Plan(w, precision=PRECISIONS[args.precision]) as p:
+        if args.autotune:
+            tune = p.autotune(w.lattice, w.positions, reps=2)
         p.set_timing(True)
         for _ in range(max(1, args.evals)):
             E, F, S = p.evaluate(w.lattice, w.positions, stats=True)
         st = p.stats.as_dict()
     keep = ("ms_blocks", "ms_screen", "ms_y", "ms_term1", "ms_term2", "ms_reduce", "ms_total", "triplets",
             "term1_pairs", "term2_pairs", "y_blocks", "flops_total", "kernel_launches", "device_bytes")
-    print(json.dumps({"cell": args.cell, "precision": args.precision, "E": E, **{k: st[k] for k in keep}}))
+    print(json.dumps({"cell": args.cell, "precision": args.precision, "E": E, **{k: st[k] for k in keep},
+                      "autotune": tune}))
     return 0
 
 
