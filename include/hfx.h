@@ -208,6 +208,33 @@ typedef struct {
 hfx_status hfx_plan_autotune(hfx_plan* plan, const double* lattice, const double* positions, int reps,
                              hfx_tune_report* report);
 
+/* Block preparation: the LRI coefficient fit of Eq. C_VA and its nuclear
+ * gradient (Sec. 3.1, the equation after Eq. V_inverse), FP64 on the GPU,
+ * for `batch` atom pairs (I, K) of one species pair.  Per pair p, with
+ * n = n_abf(I) + n_abf(K) auxiliary functions (those of I first) and
+ * w = n_ao(I) n_ao(K) AO pairs (i, k), all row-major and contiguous per pair:
+ *   A   [batch][n][n]     two-centre Coulomb metric (V_II, V_IK; V_KI, V_KK),
+ *                         symmetric positive definite (only its lower
+ *                         triangle is read);
+ *   B   [batch][n][w]     three-centre integrals (P_beta | phi_i phi_k);
+ *   dA  [batch][3][n][n]  gradient of A in the position of K (c = x, y, z);
+ *   dB  [batch][3][n][w]  gradient of B in the position of K.
+ * Outputs (caller-allocated):
+ *   X   [batch][n][w]     X = A^-1 B: the C^I rows, then the C^K rows;
+ *   dX  [batch][3][n][w]  dX[c] = A^-1 (dB[c] - dA[c] X).
+ * dA, dB and dX must be all NULL (X only) or all non-NULL.  Pointers are
+ * host memory; the call copies them to device `device`, runs one CTA per
+ * pair (Cholesky factor in shared memory) on a stream of its own, copies the
+ * results back and returns when they are written.  It holds no state and
+ * may run beside any plan.
+ * Errors: HFX_ERR_INVALID for batch < 0, n < 1, w < 1, a NULL pointer or a
+ * mixed NULL set, or a metric that is not positive definite (outputs are
+ * then not written); HFX_ERR_UNSUPPORTED if n exceeds what the device's
+ * shared memory holds (n <= 160 on GB300); HFX_ERR_OOM / HFX_ERR_CUDA as
+ * elsewhere.  hfx_last_error(NULL) gives the message. */
+hfx_status hfx_lri_fit(int batch, int n, int w, const double* A, const double* B, const double* dA,
+                       const double* dB, double* X, double* dX, int device);
+
 /* Free every resource of the plan.  NULL is accepted. */
 hfx_status hfx_plan_destroy(hfx_plan* plan);
 

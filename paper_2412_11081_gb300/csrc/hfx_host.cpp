@@ -1369,6 +1369,65 @@ const char* hfx_status_string(hfx_status s) {
   return "unknown status";
 }
 
+hfx_status hfx_lri_fit(int batch, int n, int w, const double* A, const double* B, const double* dA,
+                       const double* dB, double* X, double* dX, int device) {
+  g_create_error.clear();
+  auto bad = [](hfx_status st, const char* msg) {
+    g_create_error = msg;
+    return st;
+  };
+  const bool grad = dA || dB || dX;
+  if (batch < 0 || n < 1 || w < 1 || !A || !B || !X) return bad(HFX_ERR_INVALID, "hfx_lri_fit: bad sizes or NULL");
+  if (grad && !(dA && dB && dX)) return bad(HFX_ERR_INVALID, "hfx_lri_fit: dA, dB, dX must be all set or all NULL");
+  if (batch == 0) return HFX_OK;
+  if (cudaSetDevice(device) != cudaSuccess) return bad(HFX_ERR_CUDA, "hfx_lri_fit: cudaSetDevice");
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  if (hfx::lri_fit_smem(n) + 2048 > (size_t)optin)
+    return bad(HFX_ERR_UNSUPPORTED, "hfx_lri_fit: n too large for the Cholesky factor in shared memory");
+  const size_t nn = (size_t)batch * n * n, nw = (size_t)batch * n * w;
+  const size_t bytes = (nn + 2 * nw) * sizeof(double) * (grad ? 4 : 1) + sizeof(int);
+  cudaStream_t s = nullptr;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess)
+    return bad(HFX_ERR_CUDA, "hfx_lri_fit: stream");
+  unsigned char* buf = nullptr;
+  if (cudaMalloc(&buf, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    cudaStreamDestroy(s);
+    return bad(HFX_ERR_OOM, "hfx_lri_fit: device memory");
+  }
+  double* A_dev = reinterpret_cast<double*>(buf);            // A, B, X [, dA, dB, dX]
+  double* B_dev = A_dev + nn;
+  double* X_dev = B_dev + nw;
+  double* gA = grad ? X_dev + nw : nullptr;
+  double* gB = grad ? gA + 3 * nn : nullptr;
+  double* gX = grad ? gB + 3 * nw : nullptr;
+  int* err = reinterpret_cast<int*>(buf + bytes - sizeof(int));
+  int herr = 0;
+  cudaError_t e = cudaMemcpyAsync(A_dev, A, nn * sizeof(double), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(B_dev, B, nw * sizeof(double), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && grad) e = cudaMemcpyAsync(gA, dA, 3 * nn * sizeof(double), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && grad) e = cudaMemcpyAsync(gB, dB, 3 * nw * sizeof(double), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = hfx::launch_lri_fit(batch, n, w, A_dev, B_dev, gA, gB, X_dev, gX, err, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  hfx_status st = HFX_OK;
+  if (e != cudaSuccess) {
+    st = bad(HFX_ERR_CUDA, cudaGetErrorString(e));
+  } else if (herr) {
+    st = bad(HFX_ERR_INVALID, "hfx_lri_fit: a metric block is not positive definite");
+  } else {
+    e = cudaMemcpyAsync(X, X_dev, nw * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && grad) e = cudaMemcpyAsync(dX, gX, 3 * nw * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = bad(HFX_ERR_CUDA, cudaGetErrorString(e));
+  }
+  cudaFree(buf);
+  cudaStreamDestroy(s);
+  return st;
+}
+
 const char* hfx_last_error(const hfx_plan* P) {
   if (!P) return g_create_error.c_str();
   return P->err.c_str();

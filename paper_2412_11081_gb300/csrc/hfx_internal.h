@@ -173,6 +173,12 @@ cudaError_t launch_reduce(const DevPlan& P, double* out, cudaStream_t s);
 // from every caller (each plan checks its own sizes against that limit).
 cudaError_t allow_max_dynamic_smem(const void* f);
 cudaError_t set_kernel_smem_limits();
+// Batched LRI fit (hfx_lri_fit): X = A^-1 B and dX[c] = A^-1 (dB[c] - dA[c] X)
+// per pair, device pointers, dA / dB / dX null for X alone; *err = 1 when a
+// metric is not positive definite.
+size_t lri_fit_smem(int n);
+cudaError_t launch_lri_fit(int batch, int n, int w, const double* A, const double* B, const double* dA,
+                           const double* dB, double* X, double* dX, int* err, cudaStream_t s);
 
 // Split-precision kernels (hfx_mixed.cu); np = bf16 pieces per operand (2 or 3).
 long long mixed_launch_count();

@@ -882,6 +882,110 @@ cudaError_t launch_term2(const DevPlan& P, const int* list, int n, int alpha_chu
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------ LRI fit
+// Eq. C_VA and the gradient equation after Eq. V_inverse, per atom pair p of
+// a batch (one CTA per pair, grid-stride over the batch):
+//   A X = B                       X = the C^I rows, then the C^K rows
+//   A dX[c] = dB[c] - dA[c] X     c = x, y, z (gradient in K's position)
+// A (n x n, SPD) is factored as L L^T (left-looking Cholesky, L in shared
+// memory); each thread then owns RHS columns and runs the forward and back
+// substitutions on them in place in the output (row-major [n][w], so the
+// threads of a warp touch consecutive columns of one row), reading L by
+// broadcast.  A pivot <= 0 (A not positive definite) sets *err and is
+// replaced by 1 so that the CTA finishes.
+namespace {
+
+__device__ void lri_cholesky(double* L, const double* A, int n, int* err) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int e = tid; e < n * n; e += blockDim.x) L[e] = A[e];
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    if (warp == 0) {
+      double sq = 0.0;
+      for (int k = lane; k < j; k += 32) sq += L[j * n + k] * L[j * n + k];
+      sq = warp_sum(sq);
+      if (lane == 0) {
+        double d = L[j * n + j] - sq;
+        if (!(d > 0.0)) {
+          atomicExch(err, 1);
+          d = 1.0;
+        }
+        L[j * n + j] = sqrt(d);
+      }
+    }
+    __syncthreads();
+    const double ljj = L[j * n + j];
+    for (int i = j + 1 + tid; i < n; i += blockDim.x) {
+      double a = L[i * n + j];
+      for (int k = 0; k < j; ++k) a -= L[i * n + k] * L[j * n + k];
+      L[i * n + j] = a / ljj;
+    }
+    __syncthreads();
+  }
+}
+
+// In-place solve L L^T x = r for the columns this thread owns of the
+// row-major n x w array R.
+__device__ void lri_substitute(const double* L, double* R, int n, int w) {
+  for (int col = threadIdx.x; col < w; col += blockDim.x) {
+    for (int i = 0; i < n; ++i) {   // L y = r
+      double a = R[(size_t)i * w + col];
+      for (int k = 0; k < i; ++k) a -= L[i * n + k] * R[(size_t)k * w + col];
+      R[(size_t)i * w + col] = a / L[i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {   // L^T x = y
+      double a = R[(size_t)i * w + col];
+      for (int k = i + 1; k < n; ++k) a -= L[k * n + i] * R[(size_t)k * w + col];
+      R[(size_t)i * w + col] = a / L[i * n + i];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_lri_fit(int batch, int n, int w, const double* A, const double* B,
+                                                     const double* dA, const double* dB, double* X, double* dX,
+                                                     int* err) {
+  extern __shared__ double L[];   // [n][n]
+  const size_t nn = (size_t)n * n, nw = (size_t)n * w;
+  for (int p = blockIdx.x; p < batch; p += gridDim.x) {
+    __syncthreads();   // the previous pair's L is no longer read
+    lri_cholesky(L, A + p * nn, n, err);
+    double* Xp = X + p * nw;
+    const double* Bp = B + p * nw;
+    for (size_t e = threadIdx.x; e < nw; e += blockDim.x) Xp[e] = Bp[e];
+    __syncthreads();
+    lri_substitute(L, Xp, n, w);
+    if (dX == nullptr) continue;
+    __syncthreads();   // X complete (each thread solved its own columns; rows mix below)
+    for (int c = 0; c < 3; ++c) {
+      const double* dAc = dA + (p * 3 + c) * nn;
+      const double* dBc = dB + (p * 3 + c) * nw;
+      double* R = dX + (p * 3 + c) * nw;
+      for (int col = threadIdx.x; col < w; col += blockDim.x)
+        for (int i = 0; i < n; ++i) {
+          double a = dBc[(size_t)i * w + col];
+          for (int j = 0; j < n; ++j) a -= dAc[(size_t)i * n + j] * Xp[(size_t)j * w + col];
+          R[(size_t)i * w + col] = a;
+        }
+      lri_substitute(L, R, n, w);
+    }
+  }
+}
+
+}  // namespace
+
+size_t lri_fit_smem(int n) { return (size_t)n * n * sizeof(double); }
+
+cudaError_t launch_lri_fit(int batch, int n, int w, const double* A, const double* B, const double* dA,
+                           const double* dB, double* X, double* dX, int* err, cudaStream_t s) {
+  if (batch <= 0) return cudaSuccess;
+  const size_t smem = lri_fit_smem(n);
+  cudaError_t e = allow_max_dynamic_smem((const void*)k_lri_fit);
+  if (e != cudaSuccess) return e;
+  ++g_launches;
+  k_lri_fit<<<grid_for(batch, 1, 152 * 2), kThreads, smem, s>>>(batch, n, w, A, B, dA, dB, X, dX, err);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_reduce(const DevPlan& P, double* out, cudaStream_t s) {
   double* F = out + 1;
   const int total = P.nC + P.nV;

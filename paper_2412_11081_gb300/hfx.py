@@ -73,6 +73,7 @@ _SIGNATURES = {
     "hfx_energy_force_stress_noalloc": (ct.c_int, [ct.c_void_p, _dp, _dp, _dp, _dp, _dp]),
     "hfx_set_timing": (ct.c_int, [ct.c_void_p, ct.c_int]),
     "hfx_plan_autotune": (ct.c_int, [ct.c_void_p, _dp, _dp, ct.c_int, ct.c_void_p]),
+    "hfx_lri_fit": (ct.c_int, [ct.c_int, ct.c_int, ct.c_int, _dp, _dp, _dp, _dp, _dp, _dp, ct.c_int]),
     "hfx_plan_destroy": (ct.c_int, [ct.c_void_p]),
     "hfx_status_string": (ct.c_char_p, [ct.c_int]),
     "hfx_last_error": (ct.c_char_p, [ct.c_void_p]),
@@ -257,6 +258,29 @@ class Plan:
 
     def __exit__(self, *a):
         self.close()
+
+
+def lri_fit(A, B, dA=None, dB=None, device: int = 0):
+    """hfx_lri_fit: X = A^-1 B per pair (Eq. C_VA) and, with dA and dB,
+    dX[c] = A^-1 (dB[c] - dA[c] X).  A [batch, n, n], B [batch, n, w],
+    dA [batch, 3, n, n], dB [batch, 3, n, w]; returns X (and dX)."""
+    lib = load_library()
+    A, B = _f64(A), _f64(B)
+    if A.ndim != 3 or B.ndim != 3 or A.shape[1] != A.shape[2] or B.shape[:2] != A.shape[:2]:
+        raise ValueError("A must be [batch, n, n] and B [batch, n, w]")
+    batch, n, w = B.shape
+    X = np.zeros((batch, n, w))
+    grad = dA is not None or dB is not None
+    if grad:
+        dA, dB = _f64(dA), _f64(dB)
+        if dA.shape != (batch, 3, n, n) or dB.shape != (batch, 3, n, w):
+            raise ValueError("dA must be [batch, 3, n, n] and dB [batch, 3, n, w]")
+        dX = np.zeros((batch, 3, n, w))
+    ptr = lambda a: a.ctypes.data_as(_dp) if a is not None else None
+    st = lib.hfx_lri_fit(batch, n, w, ptr(A), ptr(B), ptr(dA) if grad else None, ptr(dB) if grad else None,
+                         ptr(X), ptr(dX) if grad else None, device)
+    _check(lib, st, None)
+    return (X, dX) if grad else X
 
 
 def _current_stream() -> int:

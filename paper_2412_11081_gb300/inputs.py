@@ -316,6 +316,60 @@ def geometry_sequence(w: Workload, n: int, seed: int = 17, amp: float = 0.01) ->
     return [w.positions + rng.normal(0.0, amp, w.positions.shape) for _ in range(n)]
 
 
+def lri_pairs(batch: int, m_i: int, m_k: int, n_i: int, n_k: int, seed: int = 5, r_range=(1.8, 4.0)):
+    """Synthetic inputs of the LRI fit for `batch` pairs (I, K) of one
+    species pair: per pair a random separation vector d (|d| uniform in
+    r_range) and the blocks of a smooth model with their exact derivatives
+    in d (the position of K):
+        A(d)  = [[M_II, s(r) M_IK], [s(r) M_IK^T, M_KK]]
+        B(d)  = [[T_I t1(r)], [T_K t2(r)]]
+    with M_ss = X X^T / m + 1 (SPD), M_IK ~ N(0,1)/sqrt(m_i), T ~ N(0,1),
+    s(r) = 0.3 exp(-r^2/8), t1(r) = exp(-r^2/6), t2(r) = (1 + 0.2 r) exp(-r^2/5).
+    Returns (d [batch, 3], A, B, dA [batch, 3, n, n], dB [batch, 3, n, w],
+    templates) where templates rebuild A, B at any d via lri_blocks."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    Xi = rng.standard_normal((m_i, m_i))
+    Xk = rng.standard_normal((m_k, m_k))
+    tpl = {"M_II": Xi @ Xi.T / m_i + np.eye(m_i), "M_KK": Xk @ Xk.T / m_k + np.eye(m_k),
+           "M_IK": rng.standard_normal((m_i, m_k)) / math.sqrt(m_i),
+           "T_I": rng.standard_normal((m_i, n_i * n_k)), "T_K": rng.standard_normal((m_k, n_i * n_k))}
+    u = rng.standard_normal((batch, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    d = u * rng.uniform(r_range[0], r_range[1], (batch, 1))
+    blocks = [lri_blocks(tpl, d[p]) for p in range(batch)]
+    A, B, dA, dB = (np.stack([b[k] for b in blocks]) for k in range(4))
+    return d, A, B, dA, dB, tpl
+
+
+def lri_blocks(tpl: dict, d: np.ndarray):
+    """A, B, dA, dB of the lri_pairs model at separation d (3,)."""
+    d = np.asarray(d, np.float64)
+    r = float(np.linalg.norm(d))
+    s = 0.3 * math.exp(-r * r / 8.0)
+    ds = -r / 4.0 * s
+    t1 = math.exp(-r * r / 6.0)
+    dt1 = -r / 3.0 * t1
+    e2 = math.exp(-r * r / 5.0)
+    t2 = (1.0 + 0.2 * r) * e2
+    dt2 = 0.2 * e2 - (1.0 + 0.2 * r) * (2.0 * r / 5.0) * e2
+    mi, mk = tpl["M_II"].shape[0], tpl["M_KK"].shape[0]
+    n = mi + mk
+    A = np.zeros((n, n))
+    A[:mi, :mi] = tpl["M_II"]
+    A[mi:, mi:] = tpl["M_KK"]
+    A[:mi, mi:] = s * tpl["M_IK"]
+    A[mi:, :mi] = s * tpl["M_IK"].T
+    B = np.concatenate([tpl["T_I"] * t1, tpl["T_K"] * t2])
+    dA = np.zeros((3, n, n))
+    dB = np.zeros((3, n, B.shape[1]))
+    for c in range(3):
+        g = d[c] / r
+        dA[c, :mi, mi:] = ds * g * tpl["M_IK"]
+        dA[c, mi:, :mi] = ds * g * tpl["M_IK"].T
+        dB[c] = np.concatenate([tpl["T_I"] * dt1 * g, tpl["T_K"] * dt2 * g])
+    return A, B, dA, dB
+
+
 def workload_by_name(name: str) -> Workload:
     table = {
         "diamond8": lambda: diamond8(),

@@ -24,13 +24,38 @@ CELLS = {
 PRECISIONS = {"fp64": hfx.HFX_FP64, "bf16x3": hfx.HFX_BF16X3, "bf16x6": hfx.HFX_BF16X6}
 
 
+def lri_case(batch: int) -> int:
+    """Wall time of hfx_lri_fit (host in, host out) on `batch` Si-like pairs,
+    after one warm-up call, with its algorithmic FLOPs: per pair the Cholesky
+    factor (n^3 / 3), the four substitutions of w columns (4 * 2 n^2 w) and
+    the three dA X products (3 * 2 n^2 w)."""
+    import time
+    import numpy as np
+    d, A, B, dA, dB, _ = inputs.lri_pairs(batch, 50, 50, 13, 13, seed=6)
+    hfx.lri_fit(A[:2], B[:2], dA[:2], dB[:2])
+    t = time.perf_counter()
+    X, dX = hfx.lri_fit(A, B, dA, dB)
+    dt = time.perf_counter() - t
+    n, w = B.shape[1], B.shape[2]
+    flops = batch * (n ** 3 / 3 + 14 * n * n * w)
+    moved = A.nbytes + B.nbytes + dA.nbytes + dB.nbytes + X.nbytes + dX.nbytes
+    print(json.dumps({"lri_batch": batch, "n": n, "w": w, "seconds": dt, "gflop": flops / 1e9,
+                      "gflops_per_s": flops / dt / 1e9, "host_bytes_copied": moved,
+                      "finite": bool(np.isfinite(X).all() and np.isfinite(dX).all())}))
+    return 0
+
+
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser()
     ap.add_argument("--cell", default="si8", choices=sorted(CELLS))
     ap.add_argument("--precision", default="bf16x3", choices=sorted(PRECISIONS))
     ap.add_argument("--evals", type=int, default=2)
     ap.add_argument("--autotune", action="store_true", help="run hfx_plan_autotune before the evaluations")
+    ap.add_argument("--lri-batch", type=int, default=0,
+                    help="instead: time hfx_lri_fit on this many Si-like pairs (n_abf 50 + 50, n_ao 13 x 13)")
     args = ap.parse_args(argv)
+    if args.lri_batch > 0:
+        return lri_case(args.lri_batch)
     w = CELLS[args.cell]()
     tune = None
     with hfx.Plan(w, precision=PRECISIONS[args.precision]) as p:
