@@ -178,3 +178,28 @@ def test_auxiliary_basis_beyond_tcgen05_kernel(monkeypatch):
     with pytest.raises(hfx.HfxError) as ei:
         run(w, hfx.HFX_BF16X6)
     assert ei.value.status == 6
+
+
+@pytest.mark.parametrize("prec", SPLITS)
+def test_mixed_everything_screened_out(prec):
+    """No kept pair, triplet or term-2 pair: every split kernel sees empty
+    lists and the result is exactly zero."""
+    w = tiny_periodic()
+    th = dict(C=1e30, dC=1e30, V=1e30, dV=1e30, D=1e30, CS=1e30)
+    with hfx.Plan(w, precision=prec, theta=th) as p:
+        E, F, S = p.evaluate(w.lattice, w.positions, stats=True)
+        st = p.stats.as_dict()
+    assert E == 0.0 and not np.asarray(F).any() and not np.asarray(S).any()
+    assert st["triplets"] == 0 and st["term2_pairs"] == 0
+
+
+@pytest.mark.parametrize("prec", SPLITS)
+def test_mixed_single_atom_cell_self_images_only(prec):
+    """One atom per cell: every pair is a self-image, F = 0 to rounding and
+    E, sigma within the split's bound of the oracle."""
+    w = inputs.cut_density(inputs.tiny_model([3], [5], [0], np.eye(3) * 2.9, np.array([[0.2, 0.1, 0.3]]),
+                                             r_c=1.6, seed=5), 6.0)
+    r = evaluate(w)
+    E, F, S, _ = run(w, prec)
+    assert np.max(np.abs(F)) <= 1e-10 * abs(r.E)
+    assert abs(E - r.E) <= BOUND[prec] * abs(r.E) and rel(S, r.sigma) <= BOUND[prec]
