@@ -114,6 +114,7 @@ struct hfx_plan {
   int *d_species = nullptr, *d_n_ao = nullptr, *d_n_abf = nullptr;
   long long *d_G_off = nullptr, *d_M_off = nullptr;
   double *d_G = nullptr, *d_Gp = nullptr, *d_M = nullptr, *d_Mnorm = nullptr, *d_Gmom = nullptr;
+  float *d_Gf = nullptr, *d_Gpf = nullptr, *d_Mf = nullptr;
   double* d_Dval = nullptr;
   long long* d_Doff = nullptr;
   int* d_Didx = nullptr;
@@ -334,9 +335,17 @@ void upload_model(hfx_plan* P, const hfx_system* sys, const hfx_model* m) {
   upload(P->d_M, M, s);
   upload(P->d_Mnorm, Mnorm, s);
   upload(P->d_Gmom, Gmom, s);
+  // kept alive until the stream synchronisation below
+  const std::vector<float> Gf(G.begin(), G.end()), Mf(M.begin(), M.end()), Gpf(Gp.begin(), Gp.end());
+  P->d_Gf = P->mem.alloc<float>(gsz);
+  P->d_Mf = P->mem.alloc<float>(msz);
+  upload(P->d_Gf, Gf, s);
+  upload(P->d_Mf, Mf, s);
   if (m->G_aniso) {
     P->d_Gp = P->mem.alloc<double>(gsz);
     upload(P->d_Gp, Gp, s);
+    P->d_Gpf = P->mem.alloc<float>(gsz);
+    upload(P->d_Gpf, Gpf, s);
     P->aniso = true;
     for (int k = 0; k < 3; ++k) P->e[k] = m->aniso_dir[k];
     if (!finite_all(P->e, 3)) fail(HFX_ERR_INVALID, "non-finite anisotropy direction");
@@ -437,6 +446,9 @@ DevPlan make_devplan(hfx_plan* P, const double* lattice) {
   D.Gp = P->aniso ? P->d_Gp : nullptr;
   D.M_off = P->d_M_off;
   D.M = P->d_M;
+  D.Gf = P->d_Gf;
+  D.Gpf = P->aniso ? P->d_Gpf : nullptr;
+  D.Mf = P->d_Mf;
   D.Mnorm = P->d_Mnorm;
   D.Gmom = P->d_Gmom;
   for (int k = 0; k < 3; ++k) D.e[k] = P->e[k];

@@ -31,6 +31,13 @@ struct DevPlan {
   const double* M;
   const double* Mnorm;         // [S*S] ||M_st||_F
   const double* Gmom;          // [S*S*3] sum G^2, sum G G', sum G'^2 of each template pair
+  // FP32 copies of G, G' (nullptr without anisotropy) and M: the split path
+  // evaluates its FP32 operand stores from them (FP32 products of the
+  // rounded templates and the rounded per-pair scalars), since GB300's FP64
+  // pipe would otherwise bound those store kernels
+  const float* Gf;
+  const float* Gpf;
+  const float* Mf;
   double e[3];
   double RC, omega;
   double thC, thdC, thV, thdV, thD, thCS;

@@ -167,14 +167,16 @@ __global__ void k_cpieces(DevPlan P, MixPlan X) {
     const int sA = P.species[A], sF = P.species[f];
     const int rows = P.n_abf[sA] * P.n_ao[sA], nF = P.n_ao[sF];
     const int nt = (rows + 127) >> 7;
-    // C and grad C evaluated from the block model (scalars of k_cnorm)
-    const double* sc = P.c_sc + 8 * (long long)q;
+    // C and grad C evaluated in FP32 from the block model (scalars of k_cnorm)
+    float scf[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) scf[k] = (float)P.c_sc[8 * (long long)q + k];
     const long long go = P.G_off[sA * P.S + sF];
     uint16_t* out = X.Cm + X.cm_off[q];
     for (int e = threadIdx.x; e < nt * 128 * 16; e += blockDim.x) {
       const int r = e >> 4, c = e & 15;
       uint16_t pc[NP];
-      split_f<NP>((r < rows && c < nF) ? (float)model::c_value(P, sc, go, r * nF + c, 0) : 0.f, pc);
+      split_f<NP>((r < rows && c < nF) ? model::c_value_f(P, scf, go, r * nF + c, 0) : 0.f, pc);
 #pragma unroll
       for (int p = 0; p < NP; ++p) out[((r >> 7) * NP + p) * 2048 + tix(r & 127, c)] = pc[p];
     }
@@ -183,7 +185,7 @@ __global__ void k_cpieces(DevPlan P, MixPlan X) {
     for (int w = threadIdx.x; w < 3 * nt * 2048; w += blockDim.x) {
       const int c = w / (nt * 2048), wi = w - c * nt * 2048;
       const int r = ((wi >> 11) << 7) + ((wi >> 2) & 127), ff = (((wi >> 9) & 3) << 2) + (wi & 3);
-      g[w] = (r < rows && ff < nF) ? (float)model::c_value(P, sc, go, r * nF + ff, c + 1) : 0.f;
+      g[w] = (r < rows && ff < nF) ? model::c_value_f(P, scf, go, r * nF + ff, c + 1) : 0.f;
     }
   }
 }
@@ -199,23 +201,24 @@ __global__ void k_vpieces(DevPlan P, MixPlan X, const int* list, int n_list) {
     const int MB = rup16(mB);
     double h, g[3];
     model::v_pair(P, p, h, g);
-    const double* M = P.M + P.M_off[sA * P.S + sB];
+    const float hf = (float)h, g0 = (float)g[0], g1 = (float)g[1], g2 = (float)g[2];
+    const float* M = P.Mf + P.M_off[sA * P.S + sB];   // FP32 products, as k_vstores
     uint16_t* out = X.Vm + X.vm_off[p];
     for (int e = threadIdx.x; e < mA * MB; e += blockDim.x) {
       const int al = e / MB, be = e - al * MB;
       uint16_t pc[NP];
-      split_f<NP>(be < mB ? (float)(M[al * mB + be] * h) : 0.f, pc);
+      split_f<NP>(be < mB ? M[al * mB + be] * hf : 0.f, pc);
 #pragma unroll
       for (int pp = 0; pp < NP; ++pp) out[pp * mA * MB + e] = pc[pp];
     }
     float* v32 = reinterpret_cast<float*>(out + NP * mA * MB);
     const int n = mA * mB;
     for (int e = threadIdx.x; e < n; e += blockDim.x) {
-      const double m = M[e];
-      v32[e] = (float)(m * h);
-      v32[n + e] = (float)(m * g[0]);
-      v32[2 * n + e] = (float)(m * g[1]);
-      v32[3 * n + e] = (float)(m * g[2]);
+      const float m = M[e];
+      v32[e] = m * hf;
+      v32[n + e] = m * g0;
+      v32[2 * n + e] = m * g1;
+      v32[3 * n + e] = m * g2;
     }
   }
 }

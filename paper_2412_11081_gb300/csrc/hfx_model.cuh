@@ -81,11 +81,12 @@ __device__ __forceinline__ void c_pair_eval(const DevPlan& P, int p, double s[8]
 }
 
 // Element t of component c (0: C, 1..3: grad C) of C pair p from its stored
-// scalars cs (c_pair_eval) and the templates at offset go.
-__device__ __forceinline__ double c_value(const DevPlan& P, const double* cs, long long go, int t, int c) {
-  const double Gv = P.G[go + t];
-  double v = Gv * (c == 0 ? cs[0] : cs[1 + c]);
-  if (P.Gp) v = v + P.Gp[go + t] * (c == 0 ? cs[1] : cs[4 + c]);
+// scalars cs (c_pair_eval) rounded to FP32 (csf = (float)cs) and the FP32
+// templates at offset go: within a few FP32 ulps of the FP64 value, the
+// precision the split path's stores keep.
+__device__ __forceinline__ float c_value_f(const DevPlan& P, const float* csf, long long go, int t, int c) {
+  float v = P.Gf[go + t] * (c == 0 ? csf[0] : csf[1 + c]);
+  if (P.Gpf) v = fmaf(P.Gpf[go + t], c == 0 ? csf[1] : csf[4 + c], v);
   return v;
 }
 

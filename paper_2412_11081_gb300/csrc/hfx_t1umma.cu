@@ -92,11 +92,13 @@ __global__ void k_t1u_cstore(DevPlan P, T1UPlan U, const int* list, int n) {
     const int ncq = mA * nA * nF;
     uint16_t* out = U.Cu + (long long)kk * U.cu_blk;
     float* pl = reinterpret_cast<float*>(out + (long long)NP * 64 * KP);
-    const double* sc = P.c_sc + 8 * (long long)q;   // C = G f + G' fa, grad C = G g + G' ga (block model)
+    float scf[8];   // C = G f + G' fa, grad C = G g + G' ga (block model, FP32 as k_cpieces)
+#pragma unroll
+    for (int k = 0; k < 8; ++k) scf[k] = (float)P.c_sc[8 * (long long)q + k];
     const long long go = P.G_off[sA * P.S + P.species[F]];
     for (int c = 0; c < 4; ++c) {
       __syncthreads();
-      for (int e = threadIdx.x; e < ncq; e += blockDim.x) cs[e] = (float)model::c_value(P, sc, go, e, c);
+      for (int e = threadIdx.x; e < ncq; e += blockDim.x) cs[e] = model::c_value_f(P, scf, go, e, c);
       __syncthreads();
       auto val = [&](int al, int col) -> float {
         const int f = col >> 4, a = col & 15;
@@ -143,15 +145,16 @@ __global__ void k_vstores(DevPlan P, MixPlan X, T1UPlan U, const int* list, int 
     const int sA = P.species[P.v_home[p]], sB = P.species[P.v_j[p]];
     const int mA = P.n_abf[sA], mB = P.n_abf[sB], MB = rup16(mB), nv = mA * mB;
     double h, g[3];
-    model::v_pair(P, p, h, g);   // V = M h, grad V = M g (block model)
-    const double* M = P.M + P.M_off[sA * P.S + sB];
+    model::v_pair(P, p, h, g);   // V = M h, grad V = M g (block model), in FP32
+    const float hf = (float)h, g0 = (float)g[0], g1 = (float)g[1], g2 = (float)g[2];
+    const float* M = P.Mf + P.M_off[sA * P.S + sB];
     __syncthreads();
     for (int e = threadIdx.x; e < nv; e += blockDim.x) {
-      const double m = M[e];
-      vsm[e] = (float)(m * h);
-      vsm[nv + e] = (float)(m * g[0]);
-      vsm[2 * nv + e] = (float)(m * g[1]);
-      vsm[3 * nv + e] = (float)(m * g[2]);
+      const float m = M[e];
+      vsm[e] = m * hf;
+      vsm[nv + e] = m * g0;
+      vsm[2 * nv + e] = m * g1;
+      vsm[3 * nv + e] = m * g2;
     }
     __syncthreads();
     // second-product store
