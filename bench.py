@@ -43,6 +43,24 @@ def _env_rank():
         int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def max_over_ranks(values, dist=None, device=None):
+    """Each value's maximum over the ranks of the process group (the job's
+    time is the slowest rank's); the values themselves on one process."""
+    if dist is None:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t]
+
+
+def job_rates(steps_per_rank, world, t_dev, t_e2e, dist=None, device=None):
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time, device-timed and end to end."""
+    t_max, t_e2e_max = max_over_ranks([t_dev, t_e2e], dist, device)
+    return world * steps_per_rank / t_max, world * steps_per_rank / t_e2e_max, t_max
+
+
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during a region."""
     FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.hw_slowdown",
@@ -311,13 +329,7 @@ def run_ours(args):
     plan.set_timing(False)
     stage_ms = {k: statistics.mean(v) for k, v in stage.items()}
 
-    t_max, t_e2e_max = t_dev, t_e2e
-    if dist is not None:
-        tt = torch.tensor([t_dev, t_e2e], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max, t_e2e_max = float(tt[0]), float(tt[1])
-    value = world * args.steps / t_max
-    e2e_value = world * args.steps / t_e2e_max
+    value, e2e_value, t_max = job_rates(args.steps, world, t_dev, t_e2e, dist, dev)
 
     if rank == 0:
         peaks = measured_peaks()
