@@ -114,6 +114,19 @@ typedef struct {
   int deterministic;  /* reserved; must be 0 */
   void* stream;       /* cudaStream_t for every launch and copy; NULL = legacy default */
   int device;         /* CUDA device ordinal */
+  /* Device memory of the plan.  NULL (the default) = cudaMalloc / cudaFree.
+   * Otherwise alloc returns `bytes` of device memory on `device` for use on
+   * `stream` (the plan's stream), at least 256-byte aligned, or NULL when it
+   * cannot (the call then fails with HFX_ERR_OOM), and free gives back a
+   * block alloc returned, with its size.  Both are called on the thread
+   * that called into the plan: in hfx_plan_create, in evaluations that grow
+   * a per-call store, and in hfx_plan_destroy (after the plan's stream has
+   * drained).  A stream-ordered caching allocator, such as PyTorch's, fits;
+   * alloc_ctx is passed through unchanged.  alloc and free are set
+   * together or not at all. */
+  void* (*alloc)(size_t bytes, void* stream, void* ctx);
+  void (*free)(void* ptr, size_t bytes, void* stream, void* ctx);
+  void* alloc_ctx;
 } hfx_options;
 
 /* Counters of the last call (FLOPs are the algorithmic count of the

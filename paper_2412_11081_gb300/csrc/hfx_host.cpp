@@ -41,15 +41,17 @@ void ck(cudaError_t e, const char* what) {
   fail(HFX_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-// Device allocation tracked by the plan.
+// Device allocation tracked by the plan (through the caller's hooks when
+// hfx_options sets them).
 struct DevMem {
   std::vector<std::pair<void*, size_t>> ptrs;
   long long bytes = 0;
+  hfx::AllocHooks hooks;
   template <class T>
   T* alloc(size_t n) {
     if (n == 0) n = 1;
     void* p = nullptr;
-    ck(cudaMalloc(&p, n * sizeof(T)), "cudaMalloc");
+    ck(hooks.get(&p, n * sizeof(T)), "device allocation");
     ptrs.emplace_back(p, n * sizeof(T));
     bytes += (long long)(n * sizeof(T));
     return static_cast<T*>(p);
@@ -57,14 +59,14 @@ struct DevMem {
   void release(void* p) {
     for (auto it = ptrs.begin(); it != ptrs.end(); ++it)
       if (it->first == p) {
-        cudaFree(p);
+        hooks.put(p, it->second);
         bytes -= (long long)it->second;
         ptrs.erase(it);
         return;
       }
   }
   void free_all() {
-    for (auto& q : ptrs) cudaFree(q.first);
+    for (auto& q : ptrs) hooks.put(q.first, q.second);
     ptrs.clear();
     bytes = 0;
   }
@@ -249,6 +251,7 @@ void validate_options(const hfx_options* o) {
   if (o->terms < 1 || o->terms > 3) fail(HFX_ERR_INVALID, "terms must be 1, 2 or 3");
   if (!std::isfinite(o->skin) || o->skin < 0) fail(HFX_ERR_INVALID, "skin must be finite and >= 0");
   if (o->deterministic != 0) fail(HFX_ERR_UNSUPPORTED, "deterministic mode is not available");
+  if ((o->alloc == nullptr) != (o->free == nullptr)) fail(HFX_ERR_INVALID, "alloc and free must be set together");
 }
 
 void validate_geometry(int N, const double* lattice, const double* positions) {
@@ -1214,6 +1217,13 @@ hfx_status hfx_plan_create(const hfx_system* sys, const hfx_model* model, const 
     P->opt = *opt;
     P->dev = opt->device;
     P->stream = static_cast<cudaStream_t>(opt->stream);
+    hfx::AllocHooks hooks;
+    hooks.alloc = opt->alloc;
+    hooks.free = opt->free;
+    hooks.ctx = opt->alloc_ctx;
+    hooks.stream = opt->stream;
+    P->mem.hooks = hooks;
+    P->scan_tmp.mem = hooks;
     ck(cudaSetDevice(P->dev), "cudaSetDevice");
     P->N = sys->n_atoms;
     P->S = model->n_species;
@@ -1235,7 +1245,7 @@ hfx_status hfx_plan_create(const hfx_system* sys, const hfx_model* model, const 
   });
   if (st != HFX_OK) {
     g_create_error = P->err;
-    if (P->scan_tmp.buf) cudaFree(P->scan_tmp.buf);
+    P->scan_tmp.mem.put(P->scan_tmp.buf, P->scan_tmp.cap * sizeof(long long));
     P->mem.free_all();
     delete P;
     return st;
@@ -1362,7 +1372,7 @@ hfx_status hfx_plan_destroy(hfx_plan* P) {
   if (!P) return HFX_OK;
   cudaSetDevice(P->dev);
   cudaStreamSynchronize(P->stream);
-  if (P->scan_tmp.buf) cudaFree(P->scan_tmp.buf);
+  P->scan_tmp.mem.put(P->scan_tmp.buf, P->scan_tmp.cap * sizeof(long long));
   P->mem.free_all();
   delete P;
   return HFX_OK;

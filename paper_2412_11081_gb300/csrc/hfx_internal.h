@@ -247,9 +247,29 @@ cudaError_t launch_t1_umma(const DevPlan& P, const MixPlan& X, const T1UPlan& U,
 //   3: bytes[i] != 0
 //   4: flag[i] itself (a count)
 // The scan writes out[i] (exclusive prefix, int64) and *total (device).
+// Device allocation hooks of a plan (hfx_options alloc / free; null = the
+// CUDA runtime).
+struct AllocHooks {
+  void* (*alloc)(size_t, void*, void*) = nullptr;
+  void (*free)(void*, size_t, void*, void*) = nullptr;
+  void* ctx = nullptr;
+  void* stream = nullptr;
+  cudaError_t get(void** p, size_t bytes) const {
+    if (!alloc) return cudaMalloc(p, bytes);
+    *p = alloc(bytes, stream, ctx);
+    return *p ? cudaSuccess : cudaErrorMemoryAllocation;
+  }
+  void put(void* p, size_t bytes) const {
+    if (!p) return;
+    if (free) free(p, bytes, stream, ctx);
+    else cudaFree(p);
+  }
+};
+
 struct ScanTmp {
   long long* buf = nullptr;
   size_t cap = 0;
+  AllocHooks mem;
 };
 cudaError_t scan_flags(const int* flag, const long long* size, const unsigned* mask,
                        const unsigned char* bytes, int mode, int n, long long* out,

@@ -768,11 +768,13 @@ cudaError_t scan_flags(const int* flag, const long long* size, const unsigned* m
   // Block totals plus the levels of the recursive scan fit in 2*nb + 64.
   const size_t need = 2 * (size_t)nb + 64;
   if (tmp.cap < need) {
-    if (tmp.buf) cudaFree(tmp.buf);
+    tmp.mem.put(tmp.buf, tmp.cap * sizeof(long long));
     tmp.buf = nullptr;
     tmp.cap = 0;
-    cudaError_t e = cudaMalloc(&tmp.buf, need * sizeof(long long));
+    void* p = nullptr;
+    cudaError_t e = tmp.mem.get(&p, need * sizeof(long long));
     if (e != cudaSuccess) return e;
+    tmp.buf = static_cast<long long*>(p);
     tmp.cap = need;
   }
   ++g_launches;

@@ -36,12 +36,16 @@ class HfxModel(ct.Structure):
                 ("d_index", _ip), ("d_offset", _llp), ("d_values", _dp)]
 
 
+ALLOC_FN = ct.CFUNCTYPE(ct.c_void_p, ct.c_size_t, ct.c_void_p, ct.c_void_p)
+FREE_FN = ct.CFUNCTYPE(None, ct.c_void_p, ct.c_size_t, ct.c_void_p, ct.c_void_p)
+
+
 class HfxOptions(ct.Structure):
     _fields_ = [("theta_C", ct.c_double), ("theta_dC", ct.c_double), ("theta_V", ct.c_double),
                 ("theta_dV", ct.c_double), ("theta_D", ct.c_double), ("theta_CS", ct.c_double),
                 ("precision", ct.c_int), ("terms", ct.c_int), ("skin", ct.c_double),
                 ("freeze_lists", ct.c_int), ("deterministic", ct.c_int), ("stream", ct.c_void_p),
-                ("device", ct.c_int)]
+                ("device", ct.c_int), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", ct.c_void_p)]
 
 
 class HfxTuneReport(ct.Structure):
@@ -135,7 +139,7 @@ class Plan:
 
     def __init__(self, w, *, precision: int = HFX_FP64, terms: int = 3, skin: float = 0.5,
                  freeze_lists: bool = False, stream: Optional[int] = None, device: int = 0,
-                 theta: Optional[dict] = None, aniso=None):
+                 theta: Optional[dict] = None, aniso=None, allocator: Optional[str] = None):
         self.lib = load_library()
         th = dict(w.theta) if theta is None else dict(theta)
         if stream is None:
@@ -143,6 +147,15 @@ class Plan:
         self.opts = default_options(theta_C=th["C"], theta_dC=th["dC"], theta_V=th["V"], theta_dV=th["dV"],
                                     theta_D=th["D"], theta_CS=th["CS"], precision=precision, terms=terms,
                                     skin=skin, freeze_lists=int(freeze_lists), stream=stream, device=device)
+        # allocator="torch": the plan's device memory comes from PyTorch's
+        # caching allocator (hfx_options alloc / free); the callbacks live
+        # as long as the plan
+        self._hooks = None
+        if allocator == "torch":
+            self._hooks = _torch_hooks(device)
+            self.opts.alloc, self.opts.free = self._hooks
+        elif allocator is not None:
+            raise ValueError("allocator must be None or 'torch'")
         self.n_atoms = int(np.asarray(w.species).shape[0])
         # keep every marshalled array alive for the duration of the create call
         self._keep = []
@@ -281,6 +294,22 @@ def lri_fit(A, B, dA=None, dB=None, device: int = 0):
                          ptr(X), ptr(dX) if grad else None, device)
     _check(lib, st, None)
     return (X, dX) if grad else X
+
+
+def _torch_hooks(device: int):
+    """hfx_options alloc / free over torch.cuda's caching allocator."""
+    import torch
+
+    def alloc(nbytes, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), device, int(stream or 0))
+        except RuntimeError:
+            return None
+
+    def free(ptr, nbytes, stream, ctx):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    return ALLOC_FN(alloc), FREE_FN(free)
 
 
 def _current_stream() -> int:
