@@ -302,8 +302,11 @@ def run_ours(args):
     pin_pos = [torch.tensor(g, dtype=torch.float64).pin_memory().numpy() for g in geoms]
     barrier()
     t0 = time.perf_counter()
+    lat = []   # per request: host positions in -> E, F, sigma back on the host (the call is synchronous)
     for k in range(args.steps):
+        tk = time.perf_counter()
         plan.evaluate(w.lattice, pin_pos[args.warmup + k])
+        lat.append(time.perf_counter() - tk)
     barrier()
     t_e2e = time.perf_counter() - t0
 
@@ -376,6 +379,9 @@ def run_ours(args):
                            "parallelism": f"replicas{world}" if world > 1 else "single",
                            "l2": "working set > L2 (block, Y and Z stores of several GB per step)"},
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "latency": {"p50_ms": float(np.percentile(lat, 50)) * 1e3, "p99_ms": float(np.percentile(lat, 99)) * 1e3,
+                            "requests": len(lat), "what": "one evaluation through the host entry point on an "
+                            "otherwise idle GPU, rank 0; a loaded request stream is reported by the serving loop"},
                 "gpu_launches": launches,
                 "roofline": roofline,
                 "cpu_baseline": cpu,
