@@ -62,8 +62,11 @@ typedef enum {
 
 /* Arithmetic of the contraction.  HFX_FP64 runs every step in FP64.  The
  * other values select split-precision tensor-core contractions with FP32
- * accumulation and FP64 screening, force, stress and energy reduction. */
-enum { HFX_FP64 = 0, HFX_TF32X3 = 1, HFX_BF16X3 = 2, HFX_BF16X6 = 3 };
+ * accumulation and FP64 screening, force, stress and energy reduction:
+ * every operand is written as 2 (BF16X3) or 3 (BF16X6) bf16 pieces and the
+ * piece products above 2^-16 (BF16X3) or 2^-24 (BF16X6) of the operands'
+ * scale are kept.  (Value 1 is not assigned.) */
+enum { HFX_FP64 = 0, HFX_BF16X3 = 2, HFX_BF16X6 = 3 };
 
 /* Exchange products of Eq. exx_expand: bit 0 = D_AB D_FG, bit 1 = D_AG D_FB. */
 enum { HFX_TERM_AB_FG = 1, HFX_TERM_AG_FB = 2, HFX_TERMS_ALL = 3 };
@@ -111,7 +114,21 @@ typedef struct {
                          decisions; a move beyond skin/2 gives
                          HFX_ERR_PAIRLIST_STALE.  0: lists are rebuilt when
                          stale and screening is redone on every call. */
-  int deterministic;  /* reserved; must be 0 */
+  /* Home atoms.  Eq. exx_expand sums over the atom A of the home cell; the
+   * plan sums A over [home_begin, home_end) only, so that E, F and sigma
+   * are that range's share and the shares of disjoint ranges add up to the
+   * whole (the paper distributes the atom quartets over processes the same
+   * way, Sec. 3.3).  home_begin = home_end = 0 (the default) takes every
+   * atom; otherwise 0 <= home_begin < home_end <= n_atoms (HFX_ERR_INVALID
+   * otherwise).  F still has n_atoms rows: a range's items move atoms
+   * outside it too. */
+  int home_begin, home_end;
+  /* Home atoms per pass of the contraction.  The Y blocks are built once per
+   * evaluation; the per-call operand stores of the two exchange products
+   * then hold one pass of home atoms at a time, so this bounds the memory
+   * they take (roughly proportional to it).  0 (the default) = 128; larger
+   * values save a little launch overhead, smaller ones memory. */
+  int home_chunk;
   void* stream;       /* cudaStream_t for every launch and copy; NULL = legacy default */
   int device;         /* CUDA device ordinal */
   /* Device memory of the plan.  NULL (the default) = cudaMalloc / cudaFree.
@@ -131,7 +148,11 @@ typedef struct {
 
 /* Counters of the last call (FLOPs are the algorithmic count of the
  * factorised contraction; times are CUDA-event times per stage in ms when
- * timing was requested via hfx_set_timing). */
+ * timing was requested via hfx_set_timing: ms_blocks the block norms,
+ * ms_screen both screening steps and the item lists, ms_y the operand
+ * stores shared by all passes and the Y blocks, ms_term1 the per-pass
+ * operand stores and the first exchange product, ms_term2 the second
+ * product, ms_reduce forces, stress and energy). */
 typedef struct {
   long long c_pairs, v_pairs, d_blocks;        /* kept after step 1 */
   long long triplets, term1_pairs, term2_pairs; /* kept after step 2 */
@@ -141,6 +162,11 @@ typedef struct {
   long long device_bytes;                       /* device memory held by the plan */
   long long kernel_launches;                    /* CUDA kernels this library launched during the call
                                                    (all threads: exact when one plan evaluates at a time) */
+  int passes;                                   /* passes of home atoms (home_chunk) */
+  /* Error of this result against the reference set by hfx_set_reference
+   * (-1 when none is set): |E - E_ref| / |E_ref|, and max|x - x_ref| /
+   * max|x_ref| over the entries of F and of sigma. */
+  double ref_err_E, ref_err_F, ref_err_sigma;
 } hfx_stats;
 
 /* Fill *opt with the defaults (all thresholds 1e-10, FP64, both terms,
@@ -172,21 +198,28 @@ hfx_status hfx_energy_force_stress_device(hfx_plan* plan, const double* lattice,
                                           hfx_stats* stats);
 
 /* Evaluation for callers that cannot allocate device memory while they
- * evaluate: work recorded under a stream capture, hosts whose device memory
- * belongs to their own pool after start-up, real-time loops that forbid
- * allocation after initialisation.  hfx_energy_force_stress may grow the
- * plan's per-call block stores with cudaMalloc; this entry point computes the
- * same E, F and sigma (same arguments, host pointers) with that scratch taken
- * from one fixed array inside the library, HFX_NOALLOC_SCRATCH_BYTES = 64 MiB,
+ * evaluate: hosts whose device memory belongs to their own pool after
+ * start-up (an allocation by the library would take memory the pool counts
+ * as its own), and real-time loops that forbid allocation after
+ * initialisation (cudaMalloc and cudaFree can block for milliseconds and
+ * synchronise the device).  hfx_energy_force_stress may grow the plan's
+ * per-call block stores with cudaMalloc; this entry point computes the same
+ * E, F and sigma (same arguments, host pointers) with that scratch taken from
+ * one fixed array inside the library, HFX_NOALLOC_SCRATCH_BYTES = 64 MiB,
  * which every device that loads the library holds until the process exits.
- * It calls no cudaMalloc or cudaFree and allocates no host memory.
+ * It calls no cudaMalloc or cudaFree and no allocation hook of the plan.
+ * Like hfx_energy_force_stress it reads the screening counts back to the
+ * host in the middle of the call and synchronises the plan's stream, so it
+ * cannot be recorded under a stream capture.
  *  - FP64 plans only (HFX_ERR_UNSUPPORTED otherwise).
  *  - A call whose pair lists, Y blocks or V blocks do not fit the array
  *    returns HFX_ERR_UNSUPPORTED with a message; nothing is written.
  *  - Atoms moved beyond skin/2 give HFX_ERR_PAIRLIST_STALE (rebuilding the
  *    lists allocates; call hfx_energy_force_stress once to rebuild them).
- *  - The first call on a device looks up the array's device address; make
- *    that first call before any stream capture.
+ *  - The first call on a device looks up the array's device address, with
+ *    that device current, and keeps it for the life of the process; a
+ *    cudaDeviceReset (or any teardown of the primary context) invalidates
+ *    it, so do not reset a device that has called this entry point.
  *  - Every call on every plan of a device shares the one array, which keeps
  *    the last call's contents (each call writes what it reads before reading
  *    it, so nothing has to start at zero).  Calls that overlap on the GPU
@@ -199,6 +232,14 @@ hfx_status hfx_energy_force_stress_noalloc(hfx_plan* plan, const double* lattice
 
 /* Per-stage CUDA-event timing on (1) or off (0, default). */
 hfx_status hfx_set_timing(hfx_plan* plan, int on);
+
+/* Reference result for the error report in hfx_stats (for example the FP64
+ * result of the same geometry when the plan runs a split precision): E (1
+ * double), F (n_atoms*3), sigma (9), host memory, copied.  Every later call
+ * that fills hfx_stats reports its relative errors against it.  E = F =
+ * sigma = NULL clears it.  HFX_ERR_INVALID for a partial set or non-finite
+ * values. */
+hfx_status hfx_set_reference(hfx_plan* plan, const double* E, const double* F, const double* sigma);
 
 /* Autotuner.  Times the evaluation of `positions` (host, [n_atoms*3], with
  * `lattice` as in hfx_energy_force_stress) for each launch configuration of

@@ -163,6 +163,11 @@ struct hfx_plan {
   double* d_acc = nullptr;     // hfx::ACC_N
   long long* d_tot = nullptr;  // [kTot] totals of the scans, then hfx::CNT_N counters
   int* d_err = nullptr;        // set by a kernel whose bounded wait ran out
+  std::vector<std::pair<int, int>> chunks;   // passes of home atoms [a0, a1)
+  std::vector<long long> ctot;               // per-pass totals of the last screening (kCT each)
+  std::vector<int> c_ptr_h, v_ptr_h;         // host copies of the list offsets per atom
+  bool has_ref = false;                      // reference result of hfx_set_reference
+  std::vector<double> ref;                   // [E, F (3N), sigma (9)]
   double* Yst = nullptr;
   long long Ycap = 0;
   double* Vst = nullptr;
@@ -250,7 +255,7 @@ void validate_options(const hfx_options* o) {
     fail(HFX_ERR_UNSUPPORTED, "precision must be HFX_FP64, HFX_BF16X3 or HFX_BF16X6");
   if (o->terms < 1 || o->terms > 3) fail(HFX_ERR_INVALID, "terms must be 1, 2 or 3");
   if (!std::isfinite(o->skin) || o->skin < 0) fail(HFX_ERR_INVALID, "skin must be finite and >= 0");
-  if (o->deterministic != 0) fail(HFX_ERR_UNSUPPORTED, "deterministic mode is not available");
+  if (o->home_chunk < 0) fail(HFX_ERR_INVALID, "home_chunk must be >= 0");
   if ((o->alloc == nullptr) != (o->free == nullptr)) fail(HFX_ERR_INVALID, "alloc and free must be set together");
 }
 
@@ -464,6 +469,8 @@ DevPlan make_devplan(hfx_plan* P, const double* lattice) {
   D.thD = P->opt.theta_D;
   D.thCS = P->opt.theta_CS;
   D.terms = P->opt.terms;
+  D.h0 = P->chunks.empty() ? 0 : P->chunks.front().first;
+  D.h1 = P->chunks.empty() ? P->N : P->chunks.back().second;
   D.pos = P->d_pos;
   for (int k = 0; k < 9; ++k) D.L[k] = lattice[k];
   D.n_d = P->n_d;
@@ -662,9 +669,11 @@ void build_lists(hfx_plan* P, const double* L, const double* pos) {
   P->c_j = P->lalloc<int>(nC);
   P->c_R = P->lalloc<int>(3 * (size_t)nC);
   P->c_off = P->lalloc<long long>(nC + 1);
-  P->Cst = P->lalloc<double>(P->c_elems);
+  // FP64 C blocks: the FP64 path only (the split path evaluates C from the
+  // model where it writes its operand stores)
+  P->Cst = P->lalloc<double>(P->np ? 1 : P->c_elems);
   P->c_sc = P->lalloc<double>(8 * (size_t)nC);
-  P->dCst = P->lalloc<double>(3 * P->c_elems);
+  P->dCst = P->lalloc<double>(P->np ? 1 : 3 * P->c_elems);
   P->c_norm = P->lalloc<double>(nC);
   P->c_keep = P->lalloc<unsigned char>(nC);
   P->v_ptr = P->lalloc<int>(N + 1);
@@ -750,6 +759,8 @@ void build_lists(hfx_plan* P, const double* L, const double* pos) {
   ck(cudaMemsetAsync(P->c_keep, 0, nC, s), "memset");
   ck(cudaMemsetAsync(P->v_keep, 0, nV, s), "memset");
   ck(cudaStreamSynchronize(s), "upload lists");
+  P->c_ptr_h = c_ptr;
+  P->v_ptr_h = v_ptr;
   P->pos_ref.assign(pos, pos + 3 * N);
   P->lat_ref.assign(L, L + 9);
   P->list_Rabs = Rabs;
@@ -944,15 +955,16 @@ struct Timer {
   cudaStream_t s;
   std::vector<cudaEvent_t> ev;
   explicit Timer(bool o, cudaStream_t st) : on(o), s(st) {}
-  void mark() {
-    if (!on) return;
+  int mark() {   // index of the recorded event (-1 when timing is off)
+    if (!on) return -1;
     cudaEvent_t e;
     cudaEventCreate(&e);
     cudaEventRecord(e, s);
     ev.push_back(e);
+    return (int)ev.size() - 1;
   }
   double ms(int a, int b) {
-    if (!on || b >= (int)ev.size()) return 0;
+    if (!on || a < 0 || b < 0 || b >= (int)ev.size()) return 0;
     float t = 0;
     cudaEventElapsedTime(&t, ev[a], ev[b]);
     return t;
@@ -962,13 +974,29 @@ struct Timer {
   }
 };
 
+// Totals of one pass of home atoms (scans over the pass's slice of the V and
+// C pair lists): FP64 V store elements, needed V pairs, first-product V
+// pairs, second-product pairs, split-path V store elements, first-product
+// (A,F) items.
+enum PassTot { CT_VE = 0, CT_VN = 1, CT_T1 = 2, CT_T2 = 3, CT_VM = 4, CT_Q = 5, kCT = 6 };
+
 // One evaluation.  positions are in P->d_pos already; writes d_out.
+//
+// Screening and the Y blocks cover every home atom of the plan at once; the
+// per-call operand stores and both exchange products then run in passes of
+// home atoms (P->chunks), each pass with its own slice of the pair lists, so
+// those stores hold one pass at a time.  Every pass's totals are read back
+// with the global ones in the single host synchronisation after screening.
 void evaluate(hfx_plan* P, const double* L, hfx_stats* st) {
   cudaStream_t s = P->stream;
   DevPlan D = make_devplan(P, L);
   const long long launches0 = hfx::launch_count() + hfx::mixed_launch_count() + hfx::t1u_launch_count();
   hfx::MixPlan X{P->Dsp, P->dsp_off, P->Ysp, P->Cm, P->cm_off, P->Vm, P->vm_off, P->Zst, P->qcnt, P->qoff, P->blist};
   const bool reuse = P->opt.freeze_lists && P->frozen_ready;
+  const int nch = (int)P->chunks.size();
+  long long* T = P->d_tot;
+  long long* CT = P->d_tot + kTot + hfx::CNT_N;   // [nch][kCT]
+  constexpr int MW = hfx::kMaskWords;
   Timer tm(P->timing, s);
   tm.mark();  // 0
   ck(cudaMemsetAsync(P->d_acc, 0, hfx::ACC_N * sizeof(double), s), "memset");
@@ -990,32 +1018,49 @@ void evaluate(hfx_plan* P, const double* L, hfx_stats* st) {
     ck(cudaMemsetAsync(P->y_flag, 0, (size_t)P->nY * sizeof(int), s), "memset");
     ck(hfx::launch_yhat(D, s), "yhat");
     ck(hfx::launch_screen(D, s), "screen");
-    long long* T = P->d_tot;
     ck(hfx::scan_flags(P->y_flag, P->y_size, nullptr, nullptr, 1, P->nY, P->y_off, T + 0, P->scan_tmp, s), "scan");
     ck(hfx::scan_flags(P->y_flag, nullptr, nullptr, nullptr, 0, P->nY, P->y_idx, T + 1, P->scan_tmp, s), "scan");
-    ck(hfx::scatter_list(P->y_flag, nullptr, nullptr, 0, P->nY, P->y_idx, P->y_list, s), "scatter");
-    ck(hfx::scan_flags(P->v_flag, P->v_size, nullptr, nullptr, 1, P->nV, P->v_off, T + 2, P->scan_tmp, s), "scan");
-    ck(hfx::scan_flags(P->v_flag, nullptr, nullptr, nullptr, 0, P->nV, P->v_idx, T + 3, P->scan_tmp, s), "scan");
-    ck(hfx::scatter_list(P->v_flag, nullptr, nullptr, 0, P->nV, P->v_idx, P->v_list, s), "scatter");
-    ck(hfx::scan_flags(nullptr, nullptr, P->v_mask, nullptr, 2, P->nV, P->t1_idx, T + 4, P->scan_tmp, s), "scan");
-    ck(hfx::scatter_list(nullptr, P->v_mask, nullptr, 2, P->nV, P->t1_idx, P->t1_list, s), "scatter");
-    ck(hfx::scan_flags(nullptr, nullptr, nullptr, P->v_t2, 3, P->nV, P->t2_idx, T + 5, P->scan_tmp, s), "scan");
-    ck(hfx::scatter_list(nullptr, nullptr, P->v_t2, 3, P->nV, P->t2_idx, P->t2_list, s), "scatter");
+    ck(hfx::scatter_list(P->y_flag, nullptr, nullptr, 0, P->nY, P->y_idx, P->y_list, 0, s), "scatter");
+    for (int c = 0; c < nch; ++c) {   // per pass: its slice [v0, v1) of the V pairs
+      const int v0 = P->v_ptr_h[P->chunks[c].first], nv = P->v_ptr_h[P->chunks[c].second] - v0;
+      long long* ct = CT + (size_t)kCT * c;
+      ck(hfx::scan_flags(P->v_flag + v0, P->v_size + v0, nullptr, nullptr, 1, nv, P->v_off + v0, ct + CT_VE,
+                         P->scan_tmp, s), "scan");
+      ck(hfx::scan_flags(P->v_flag + v0, nullptr, nullptr, nullptr, 0, nv, P->v_idx + v0, ct + CT_VN, P->scan_tmp, s),
+         "scan");
+      ck(hfx::scatter_list(P->v_flag + v0, nullptr, nullptr, 0, nv, P->v_idx + v0, P->v_list + v0, v0, s), "scatter");
+      ck(hfx::scan_flags(nullptr, nullptr, P->v_mask + (size_t)v0 * MW, nullptr, 2, nv, P->t1_idx + v0, ct + CT_T1,
+                         P->scan_tmp, s), "scan");
+      ck(hfx::scatter_list(nullptr, P->v_mask + (size_t)v0 * MW, nullptr, 2, nv, P->t1_idx + v0, P->t1_list + v0, v0, s),
+         "scatter");
+      ck(hfx::scan_flags(nullptr, nullptr, nullptr, P->v_t2 + v0, 3, nv, P->t2_idx + v0, ct + CT_T2, P->scan_tmp, s),
+         "scan");
+      ck(hfx::scatter_list(nullptr, nullptr, P->v_t2 + v0, 3, nv, P->t2_idx + v0, P->t2_list + v0, v0, s), "scatter");
+      if (P->np)
+        ck(hfx::scan_flags(P->v_flag + v0, P->vm_size + v0, nullptr, nullptr, 1, nv, P->vm_off + v0, ct + CT_VM,
+                           P->scan_tmp, s), "scan");
+    }
     if (P->np) {
       // (A,F) view of the kept triplets: per C pair, its kept B in V-pair order
-      ck(hfx::scan_flags(P->v_flag, P->vm_size, nullptr, nullptr, 1, P->nV, P->vm_off, T + 8, P->scan_tmp, s), "scan");
       ck(hfx::launch_ygroups(D, P->y_idx, T + 1, P->gcnt, nullptr, nullptr, nullptr, nullptr, 0, s), "ygroups");
       ck(hfx::scan_flags(P->gcnt, nullptr, nullptr, nullptr, 4, P->N, P->goff, T + 9, P->scan_tmp, s), "scan");
       ck(hfx::launch_ygroups(D, P->y_idx, T + 1, P->gcnt, P->goff, P->gX, P->gS, P->gN, 1, s), "ygroups");
       ck(hfx::launch_t1_lists(D, X, 0, s), "t1 count");
       ck(hfx::scan_flags(P->qcnt, nullptr, nullptr, nullptr, 4, P->nC, P->qoff, T + 6, P->scan_tmp, s), "scan");
-      ck(hfx::scan_flags(P->qcnt, nullptr, nullptr, nullptr, 0, P->nC, P->q_idx, T + 7, P->scan_tmp, s), "scan");
-      ck(hfx::scatter_list(P->qcnt, nullptr, nullptr, 0, P->nC, P->q_idx, P->t1q_list, s), "scatter");
-      ck(hfx::launch_lpt_order(P->qcnt, P->t1q_list, P->nC, P->d_tot + 7, P->lpt_hist, P->t1q_lpt, s),
-         "item order");
+      for (int c = 0; c < nch; ++c) {   // per pass: its items, longest first
+        const int c0 = P->c_ptr_h[P->chunks[c].first], nc = P->c_ptr_h[P->chunks[c].second] - c0;
+        long long* ct = CT + (size_t)kCT * c;
+        ck(hfx::scan_flags(P->qcnt + c0, nullptr, nullptr, nullptr, 0, nc, P->q_idx + c0, ct + CT_Q, P->scan_tmp, s),
+           "scan");
+        ck(hfx::scatter_list(P->qcnt + c0, nullptr, nullptr, 0, nc, P->q_idx + c0, P->t1q_list + c0, c0, s), "scatter");
+        ck(hfx::launch_lpt_order(P->qcnt, P->t1q_list + c0, nc, ct + CT_Q, P->lpt_hist, P->t1q_lpt + c0, s),
+           "item order");
+      }
     }
+    ck(cudaMemcpyAsync(P->tot, P->d_tot, kTot * sizeof(long long), cudaMemcpyDeviceToHost, s), "D2H totals");
+    ck(cudaMemcpyAsync(P->ctot.data(), CT, P->ctot.size() * sizeof(long long), cudaMemcpyDeviceToHost, s),
+       "D2H pass totals");
   }
-  ck(cudaMemcpyAsync(P->tot, P->d_tot, kTot * sizeof(long long), cudaMemcpyDeviceToHost, s), "D2H totals");
   ck(cudaMemcpyAsync(P->cnt, P->d_tot + kTot, hfx::CNT_N * sizeof(long long), cudaMemcpyDeviceToHost, s), "D2H counts");
   ck(cudaStreamSynchronize(s), "screening");
   if (dnorm_now) {
@@ -1024,18 +1069,12 @@ void evaluate(hfx_plan* P, const double* L, hfx_stats* st) {
   }
   if (P->opt.freeze_lists) P->frozen_ready = true;
   tm.mark();  // 2
+  // ---- shared by every pass: the Y blocks (and the C operand pieces they read)
+  hfx::T1UPlan U{};
   if (!P->np) {
-    ensure_store(P, P->Vst, P->Vcap, P->tot[2]);
-    D.Vst = P->Vst;
     ensure_store(P, P->Yst, P->Ycap, P->tot[0]);
     D.Yst = P->Yst;
-    ck(hfx::launch_vblocks(D, P->v_list, (int)P->tot[3], s), "vblocks");
     ck(hfx::launch_ybuild(D, P->y_list, (int)P->tot[1], s), "ybuild");
-    tm.mark();  // 3
-    ck(hfx::launch_term1(D, P->t1_list, (int)P->tot[4], P->beta_chunk, P->smem_t1, s), "term1");
-    tm.mark();  // 4
-    ck(hfx::launch_term2(D, P->t2_list, (int)P->tot[5], P->alpha_chunk, P->smem_t2, s), "term2");
-    tm.mark();  // 5
   } else {
     ensure_buf(P, P->Ysp, P->Yspcap, P->tot[0]);
     X.Ysp = P->Ysp;
@@ -1045,10 +1084,7 @@ void evaluate(hfx_plan* P, const double* L, hfx_stats* st) {
       ck(hfx::launch_t1_lists(D, X, 1, s), "t1 fill");
     }
     X.blist = P->blist;
-    ensure_buf(P, P->Vm, P->Vmcap, P->tot[8]);
-    X.Vm = P->Vm;
     ck(hfx::launch_cpieces(D, X, P->np, s), "cpieces");
-    hfx::T1UPlan U{};
     if (P->t1u) {
       U.KP = P->t1u_KP;
       U.NS = P->t1u_NS;
@@ -1056,24 +1092,12 @@ void evaluate(hfx_plan* P, const double* L, hfx_stats* st) {
       U.seg = P->t1u_seg;
       U.cu_blk = (long long)P->np * 64 * U.KP + 2LL * 4 * 64 * hfx::t1u_kp32(U.KP);
       U.vu_blk = (long long)P->np * 4096 + 2LL * 3 * 4096;
-      ensure_buf(P, P->Cu, P->Cucap, std::max(1LL, P->tot[7]) * U.cu_blk);
-      ensure_buf(P, P->Vu, P->Vucap, std::max(1LL, P->tot[4]) * U.vu_blk);
       ensure_buf(P, P->Yf, P->Yfcap, std::max(1LL, P->tot[0] / P->np));
-      U.Cu = P->Cu;
-      U.Vu = P->Vu;
       U.Yf = P->Yf;
       U.Df = P->Df;
       U.t1_idx = P->t1_idx;
       X.Yf = P->Yf;
-      ck(hfx::launch_t1u_stores(D, U, P->np, P->t1q_lpt, (int)P->tot[7], false, s), "term-1 C store");
     }
-    // the split path evaluates V and grad V from the block model where it
-    // writes the operand stores (no FP64 V blocks): one pass per needed pair
-    // for both products when the tcgen05 first product runs
-    if (P->t1u)
-      ck(hfx::launch_vstores(D, X, U, P->np, P->v_list, (int)P->tot[3], s), "V stores");
-    else
-      ck(hfx::launch_vpieces(D, X, P->np, P->v_list, (int)P->tot[3], s), "vpieces");
     X.yT_blk = (long long)P->np * P->MC * 128 * 16;
     ensure_buf(P, P->YspT, P->YspTcap, std::max(1LL, P->tot[1]) * X.yT_blk);
     X.YspT = P->YspT;
@@ -1083,30 +1107,66 @@ void evaluate(hfx_plan* P, const double* L, hfx_stats* st) {
     X.ytab_stride = 8 * P->maxC;
     ck(hfx::launch_ybuild_mma(D, X, P->np, P->y_list, P->gX, P->gS, P->gN, (int)P->tot[9], P->MC, P->drows, P->d_err, s),
        "ybuild");
-    tm.mark();  // 3
-    if (P->t1u)
-      ck(hfx::launch_t1_umma(D, X, U, P->np, P->t1q_lpt, (int)P->tot[7], P->smem_t1u, P->d_work, P->d_err, s), "term1");
-    else
-      ck(hfx::launch_term1_mma(D, X, P->np, P->t1q_lpt, (int)P->tot[7], P->MAmax, P->MBmax, P->KSmax, P->YRmax,
-                               P->smem_m1, s),
-         "term1");
-    tm.mark();  // 4
-    if (P->tot[5] * P->zblk > P->Zcap) {
-      ensure_buf(P, P->Zst, P->Zcap, P->tot[5] * P->zblk);
-      ck(cudaMemsetAsync(P->Zst, 0, (size_t)P->Zcap * sizeof(uint16_t), s), "memset");   // tile padding rows stay zero
-    }
-    X.Zst = P->Zst;
-    const int FC = (P->maxC + 3) / 4;
-    ensure_buf(P, P->q2tab, P->q2tabcap, std::max(1LL, hfx::q2tab_size((int)P->tot[5], FC)));
-    X.q2tab = P->q2tab;
-    ck(hfx::launch_term2_mma(D, X, P->np, P->t2_list, P->t2_idx, (int)P->tot[5], P->MAmax, P->KZmax, P->zblk, P->ZROWS,
-                             FC, P->MC, hfx::q2_umma_segments(P->maxV, P->np), P->q2_flush, P->drows, P->smem_m2, P->d_err, s),
-       "term2");
-    tm.mark();  // 5
   }
+  tm.mark();  // 3
+  // ---- passes of home atoms: per-call operand stores and both exchange products
+  std::vector<int> m1, m2, m3;   // timer marks around each pass's products
+  for (int c = 0; c < nch; ++c) {
+    const int a0 = P->chunks[c].first, a1 = P->chunks[c].second;
+    const int v0 = P->v_ptr_h[a0], c0 = P->c_ptr_h[a0];
+    const long long* ct = P->ctot.data() + (size_t)kCT * c;
+    m1.push_back(tm.mark());
+    if (!P->np) {
+      ensure_store(P, P->Vst, P->Vcap, ct[CT_VE]);
+      D.Vst = P->Vst;
+      ck(hfx::launch_vblocks(D, P->v_list + v0, (int)ct[CT_VN], s), "vblocks");
+      ck(hfx::launch_term1(D, P->t1_list + v0, (int)ct[CT_T1], P->beta_chunk, P->smem_t1, s), "term1");
+      m2.push_back(tm.mark());
+      ck(hfx::launch_term2(D, P->t2_list + v0, (int)ct[CT_T2], P->alpha_chunk, P->smem_t2, s), "term2");
+    } else {
+      ensure_buf(P, P->Vm, P->Vmcap, ct[CT_VM]);
+      X.Vm = P->Vm;
+      // the split path evaluates V and grad V from the block model where it
+      // writes the operand stores (no FP64 V blocks): one pass per needed pair
+      // for both products when the tcgen05 first product runs
+      if (P->t1u) {
+        ensure_buf(P, P->Cu, P->Cucap, std::max(1LL, ct[CT_Q]) * U.cu_blk);
+        ensure_buf(P, P->Vu, P->Vucap, std::max(1LL, ct[CT_T1]) * U.vu_blk);
+        U.Cu = P->Cu;
+        U.Vu = P->Vu;
+        ck(hfx::launch_t1u_stores(D, U, P->np, P->t1q_lpt + c0, (int)ct[CT_Q], false, s), "term-1 C store");
+        ck(hfx::launch_vstores(D, X, U, P->np, P->v_list + v0, (int)ct[CT_VN], s), "V stores");
+        ck(hfx::launch_t1_umma(D, X, U, P->np, P->t1q_lpt + c0, (int)ct[CT_Q], P->smem_t1u, P->d_work, P->d_err, s),
+           "term1");
+      } else {
+        ck(hfx::launch_vpieces(D, X, P->np, P->v_list + v0, (int)ct[CT_VN], s), "vpieces");
+        ck(hfx::launch_term1_mma(D, X, P->np, P->t1q_lpt + c0, (int)ct[CT_Q], P->MAmax, P->MBmax, P->KSmax, P->YRmax,
+                                 P->smem_m1, s),
+           "term1");
+      }
+      m2.push_back(tm.mark());
+      if (ct[CT_T2] * P->zblk > P->Zcap) {
+        ensure_buf(P, P->Zst, P->Zcap, ct[CT_T2] * P->zblk);
+        ck(cudaMemsetAsync(P->Zst, 0, (size_t)P->Zcap * sizeof(uint16_t), s), "memset");   // tile padding rows stay zero
+      }
+      X.Zst = P->Zst;
+      const int FC = (P->maxC + 3) / 4;
+      ensure_buf(P, P->q2tab, P->q2tabcap, std::max(1LL, hfx::q2tab_size((int)ct[CT_T2], FC)));
+      X.q2tab = P->q2tab;
+      // test-only fault injection (see MixPlan::stall_q2)
+      const char* stall = std::getenv("HFX_TEST_STALL_Q2_PRODUCER");
+      X.stall_q2 = stall && stall[0] == '1' ? 1 : 0;
+      ck(hfx::launch_term2_mma(D, X, P->np, P->t2_list + v0, P->t2_idx, (int)ct[CT_T2], a0, a1, P->MAmax, P->KZmax,
+                               P->zblk, P->ZROWS, FC, P->MC, hfx::q2_umma_segments(P->maxV, P->np), P->q2_flush,
+                               P->drows, P->smem_m2, P->d_err, s),
+         "term2");
+    }
+    m3.push_back(tm.mark());
+  }
+  const int mr = tm.mark();
   ck(cudaMemsetAsync(P->d_out, 0, (1 + 3 * (size_t)P->N + 9) * sizeof(double), s), "memset");
   ck(hfx::launch_reduce(D, P->d_out, s), "reduce");
-  tm.mark();  // 6
+  const int me = tm.mark();
   if (P->np) {
     int errflag = 0;
     ck(cudaMemcpyAsync(&errflag, P->d_err, sizeof(int), cudaMemcpyDeviceToHost, s), "D2H error flag");
@@ -1125,8 +1185,10 @@ void evaluate(hfx_plan* P, const double* L, hfx_stats* st) {
     S.v_pairs = (long long)P->cnt[hfx::CNT_V];
     S.d_blocks = P->d_kept;
     S.triplets = (long long)P->cnt[hfx::CNT_TRIP];
-    S.term1_pairs = P->tot[4];
-    S.term2_pairs = P->tot[5];
+    for (int c = 0; c < nch; ++c) {
+      S.term1_pairs += P->ctot[(size_t)kCT * c + CT_T1];
+      S.term2_pairs += P->ctot[(size_t)kCT * c + CT_T2];
+    }
     S.y_blocks = P->tot[1];
     S.flops_y = acc[hfx::ACC_FY];
     S.flops_term1 = acc[hfx::ACC_F1];
@@ -1135,14 +1197,35 @@ void evaluate(hfx_plan* P, const double* L, hfx_stats* st) {
     S.ms_blocks = tm.ms(0, 1);
     S.ms_screen = tm.ms(1, 2);
     S.ms_y = tm.ms(2, 3);
-    S.ms_term1 = tm.ms(3, 4);
-    S.ms_term2 = tm.ms(4, 5);
-    S.ms_reduce = tm.ms(5, 6);
-    S.ms_total = tm.ms(0, 6);
+    for (int c = 0; c < nch; ++c) {
+      S.ms_term1 += tm.ms(m1[c], m2[c]);
+      S.ms_term2 += tm.ms(m2[c], m3[c]);
+    }
+    S.ms_reduce = tm.ms(mr, me);
+    S.ms_total = tm.ms(0, me);
     S.device_bytes = P->mem.bytes;
     S.kernel_launches = hfx::launch_count() + hfx::mixed_launch_count() + hfx::t1u_launch_count() - launches0;
+    S.passes = nch;
+    S.ref_err_E = S.ref_err_F = S.ref_err_sigma = -1.0;
     *st = S;
   }
+}
+
+// Relative errors of a result (host [E, F, sigma]) against the plan's reference.
+void ref_errors(const hfx_plan* P, const double* out, hfx_stats* st) {
+  if (!st || !P->has_ref) return;
+  const int n = 3 * P->N;
+  st->ref_err_E = std::fabs(out[0] - P->ref[0]) / std::max(std::fabs(P->ref[0]), 1e-300);
+  auto rel = [&](int o, int m) {
+    double num = 0, den = 0;
+    for (int i = 0; i < m; ++i) {
+      num = std::max(num, std::fabs(out[o + i] - P->ref[o + i]));
+      den = std::max(den, std::fabs(P->ref[o + i]));
+    }
+    return num / std::max(den, 1e-300);
+  };
+  st->ref_err_F = rel(1, n);
+  st->ref_err_sigma = rel(1 + n, 9);
 }
 
 }  // namespace
@@ -1190,7 +1273,8 @@ hfx_status hfx_default_options(hfx_options* o) {
   o->terms = HFX_TERMS_ALL;
   o->skin = 0.5;
   o->freeze_lists = 0;
-  o->deterministic = 0;
+  o->home_begin = o->home_end = 0;
+  o->home_chunk = 0;
   o->stream = nullptr;
   o->device = 0;
   return HFX_OK;
@@ -1214,6 +1298,9 @@ hfx_status hfx_plan_create(const hfx_system* sys, const hfx_model* model, const 
     if (!(model->r_c > 0) || !std::isfinite(model->r_c) || !(model->omega > 0) || !std::isfinite(model->omega))
       fail(HFX_ERR_INVALID, "r_c and omega must be finite and > 0");
     validate_geometry(sys->n_atoms, sys->lattice, sys->positions);
+    int h0 = opt->home_begin, h1 = opt->home_end;
+    if (h0 == 0 && h1 == 0) h1 = sys->n_atoms;
+    if (h0 < 0 || h1 > sys->n_atoms || h0 >= h1) fail(HFX_ERR_INVALID, "home atom range outside [0, n_atoms) or empty");
     P->opt = *opt;
     P->dev = opt->device;
     P->stream = static_cast<cudaStream_t>(opt->stream);
@@ -1230,15 +1317,23 @@ hfx_status hfx_plan_create(const hfx_system* sys, const hfx_model* model, const 
     P->RC = 2.0 * model->r_c;
     P->omega = model->omega;
     P->np = opt->precision == HFX_BF16X3 ? 2 : opt->precision == HFX_BF16X6 ? 3 : 0;
+    // passes of the plan's home atoms
+    const int want = opt->home_chunk > 0 ? opt->home_chunk : 128;
+    const int npass = (h1 - h0 + want - 1) / want;
+    for (int c = 0; c < npass; ++c)
+      P->chunks.emplace_back(h0 + (int)((long long)(h1 - h0) * c / npass),
+                             h0 + (int)((long long)(h1 - h0) * (c + 1) / npass));
+    P->ctot.assign((size_t)kCT * npass, 0);
     upload_model(P, sys, model);
     upload_density(P, model);
     P->d_pos = P->mem.alloc<double>(3 * (size_t)P->N);
     P->d_out = P->mem.alloc<double>(1 + 3 * (size_t)P->N + 9);
     P->d_acc = P->mem.alloc<double>(hfx::ACC_N);
-    P->d_tot = P->mem.alloc<long long>(kTot + hfx::CNT_N);
+    const size_t ntot = kTot + hfx::CNT_N + (size_t)kCT * npass;
+    P->d_tot = P->mem.alloc<long long>(ntot);
     P->d_err = P->mem.alloc<int>(1);
     ck(cudaMemset(P->d_err, 0, sizeof(int)), "memset");
-    ck(cudaMemset(P->d_tot, 0, (kTot + hfx::CNT_N) * sizeof(long long)), "memset");
+    ck(cudaMemset(P->d_tot, 0, ntot * sizeof(long long)), "memset");
     setup_shapes(P);
     build_lists(P, sys->lattice, sys->positions);
     split_density(P);
@@ -1269,6 +1364,7 @@ hfx_status hfx_energy_force_stress(hfx_plan* P, const double* lattice, const dou
     ck(cudaMemcpyAsync(P->pos_host_buf.data(), P->d_out, n * sizeof(double), cudaMemcpyDeviceToHost, P->stream),
        "D2H results");
     ck(cudaStreamSynchronize(P->stream), "results");
+    ref_errors(P, P->pos_host_buf.data(), stats);
     *E = P->pos_host_buf[0];
     std::memcpy(F, P->pos_host_buf.data() + 1, 3 * (size_t)P->N * sizeof(double));
     std::memcpy(sigma, P->pos_host_buf.data() + 1 + 3 * P->N, 9 * sizeof(double));
@@ -1292,7 +1388,14 @@ hfx_status hfx_energy_force_stress_device(hfx_plan* P, const double* lattice, co
     ck(cudaMemcpyAsync(d_out, P->d_out, (1 + 3 * (size_t)P->N + 9) * sizeof(double), cudaMemcpyDeviceToDevice,
                        P->stream),
        "D2D results");
+    if (stats && P->has_ref) {   // the error report needs the result on the host
+      P->pos_host_buf.resize(1 + 3 * (size_t)P->N + 9);
+      ck(cudaMemcpyAsync(P->pos_host_buf.data(), P->d_out, P->pos_host_buf.size() * sizeof(double),
+                         cudaMemcpyDeviceToHost, P->stream),
+         "D2H results");
+    }
     ck(cudaStreamSynchronize(P->stream), "results");
+    if (stats && P->has_ref) ref_errors(P, P->pos_host_buf.data(), stats);
   });
 }
 
@@ -1300,6 +1403,25 @@ hfx_status hfx_set_timing(hfx_plan* P, int on) {
   if (!P) return HFX_ERR_INVALID;
   P->timing = on != 0;
   return HFX_OK;
+}
+
+hfx_status hfx_set_reference(hfx_plan* P, const double* E, const double* F, const double* sigma) {
+  if (!P) return HFX_ERR_INVALID;
+  return run_guarded(P, [&]() {
+    if (!E && !F && !sigma) {
+      P->has_ref = false;
+      P->ref.clear();
+      return;
+    }
+    if (!E || !F || !sigma) fail(HFX_ERR_INVALID, "reference: E, F and sigma must be all set or all NULL");
+    std::vector<double> r(1 + 3 * (size_t)P->N + 9);
+    r[0] = *E;
+    std::memcpy(r.data() + 1, F, 3 * (size_t)P->N * sizeof(double));
+    std::memcpy(r.data() + 1 + 3 * (size_t)P->N, sigma, 9 * sizeof(double));
+    if (!finite_all(r.data(), r.size())) fail(HFX_ERR_INVALID, "reference: non-finite values");
+    P->ref.swap(r);
+    P->has_ref = true;
+  });
 }
 
 hfx_status hfx_plan_autotune(hfx_plan* P, const double* lattice, const double* positions, int reps,
@@ -1460,8 +1582,7 @@ const char* hfx_last_error(const hfx_plan* P) {
 // ---------------------------------------------------------------------------
 // Evaluation without device allocation.
 //
-// Some callers cannot allocate device memory while they evaluate: code that
-// records work into a CUDA graph or runs under a stream capture, hosts that
+// Some callers cannot allocate device memory while they evaluate: hosts that
 // hand all device memory to their own pool after start-up, and real-time
 // loops that forbid allocation after initialisation.  hfx_energy_force_stress
 // may grow its per-call block stores with cudaMalloc, so this entry point runs
@@ -1480,7 +1601,8 @@ constexpr int kNoAllocMaxDevices = 64;
 double* g_noalloc_ptr[kNoAllocMaxDevices] = {};
 
 // Device address of the scratch array on the current device (first call on a
-// device looks it up; later calls reuse it).
+// device looks it up; later calls reuse it, which assumes the device's primary
+// context is never reset while the process runs).
 double* noalloc_scratch(int dev) {
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
   if (dev < 0 || dev >= kNoAllocMaxDevices) fail(HFX_ERR_UNSUPPORTED, "device ordinal too large for the scratch table");
@@ -1508,7 +1630,7 @@ extern "C" hfx_status hfx_energy_force_stress_noalloc(hfx_plan* P, const double*
     // scratch layout: scan temporaries | Y blocks | V blocks
     const long long total = (long long)(kNoAllocScratchBytes / sizeof(double));
     const long long nmax = std::max<long long>(std::max(P->nY, P->nV), P->nC);
-    const long long scan_need = 2 * ((nmax + 1023) / 1024) + 64;
+    const long long scan_need = (long long)hfx::scan_tmp_need((int)nmax);
     if (scan_need >= total / 4) fail(HFX_ERR_UNSUPPORTED, "pair lists too long for the fixed no-allocation array");
     const long long half = (total - scan_need) / 2;
     const hfx::ScanTmp saved_scan = P->scan_tmp;
@@ -1518,6 +1640,7 @@ extern "C" hfx_status hfx_energy_force_stress_noalloc(hfx_plan* P, const double*
     const bool saved_timing = P->timing;
     P->scan_tmp.buf = reinterpret_cast<long long*>(base);
     P->scan_tmp.cap = (size_t)scan_need;
+    P->scan_tmp.fixed = true;   // never freed or grown: a mismatch fails instead
     P->Yst = base + scan_need;
     P->Ycap = half;
     P->Vst = base + scan_need + half;

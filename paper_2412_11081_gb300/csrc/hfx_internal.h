@@ -42,6 +42,7 @@ struct DevPlan {
   double RC, omega;
   double thC, thdC, thV, thdV, thD, thCS;
   int terms;
+  int h0, h1;                  // home atoms A whose items are screened in: [h0, h1)
 
   const double* pos;           // [N*3] current positions
   double L[9];                 // current lattice (rows)
@@ -124,6 +125,9 @@ struct MixPlan {
   int* ytab = nullptr;         // Y build: D block (256-element units) per (key group, C slot t, key i), or -1
   int ytab_stride = 0;         // ints per key group (8 * most C pairs of an atom)
   int* q2tab = nullptr;        // second product: D block per (group of 8 C slots, pair slot, i), or -1
+  // Fault injection for the failure tests: 1 = the second product's producer
+  // issues no copies, so its pipeline waits run out (HFX_ERR_TIMEOUT).
+  int stall_q2 = 0;
 };
 
 // Element (row, f < 16) of one component of grad C_AF (FP32) in the C operand
@@ -213,9 +217,11 @@ size_t term2_mma_smem(int np, int MAmax, int KZmax);
 cudaError_t set_mixed_smem_limits(int np);
 cudaError_t launch_term1_mma(const DevPlan& P, const MixPlan& X, int np, const int* qlist, int n, int MAmax,
                              int MBmax, int KSmax, int YRmax, size_t smem, cudaStream_t s);
+// Second product of the home atoms [a0, a1): list / slot0 / n are that pass's
+// pair list, its slot of every V pair of those atoms and its length.
 cudaError_t launch_term2_mma(const DevPlan& P, const MixPlan& X, int np, const int* list, const long long* slot0,
-                             int n, int MAmax, int KZmax, long long zblk, int zrows, int FC, int MC, int nseg,
-                             int flush, const DRows& drows, size_t smem, int* err, cudaStream_t s);
+                             int n, int a0, int a1, int MAmax, int KZmax, long long zblk, int zrows, int FC, int MC,
+                             int nseg, int flush, const DRows& drows, size_t smem, int* err, cudaStream_t s);
 int q2_umma_segments(int max_pairs_per_atom, int np);
 
 // tcgen05 first exchange product (hfx_t1umma.cu): shapes n_abf <= 64, n_ao <= 16.
@@ -266,16 +272,23 @@ struct AllocHooks {
   }
 };
 
+// Scratch of the scans.  A fixed ScanTmp (the no-allocation entry point's
+// slice of the library's static array) is never freed or grown: a scan that
+// needs more fails with cudaErrorMemoryAllocation.
 struct ScanTmp {
   long long* buf = nullptr;
   size_t cap = 0;
   AllocHooks mem;
+  bool fixed = false;
 };
+// long longs of scratch one scan_flags call over n elements needs
+size_t scan_tmp_need(int n);
 cudaError_t scan_flags(const int* flag, const long long* size, const unsigned* mask,
                        const unsigned char* bytes, int mode, int n, long long* out,
                        long long* total, ScanTmp& tmp, cudaStream_t s);
-// list[out[i]] = i for every i selected by the same `mode` rule.
+// list[out[i]] = base + i for every i selected by the same `mode` rule (a
+// scan over a slice of a pair list passes the slice's first pair as base).
 cudaError_t scatter_list(const int* flag, const unsigned* mask, const unsigned char* bytes, int mode,
-                         int n, const long long* off, int* list, cudaStream_t s);
+                         int n, const long long* off, int* list, int base, cudaStream_t s);
 
 }  // namespace hfx

@@ -247,6 +247,8 @@ __global__ void k_yhat(DevPlan P) {
 // One thread per V pair (A,B).  First product: F in C(A) is kept iff
 // c_AF v_AB d_AB yhat_BF > theta_CS.  Second product: (A,B) is kept iff
 // v_AB yhat_AB yhat_BA > theta_CS.  Marks the Y keys the kept items read.
+// Only home atoms A in [h0, h1) have items (the plan's share of the sum over
+// A of Eq. exx_expand).
 __global__ void k_screen(DevPlan P) {
   unsigned long long trip = 0;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P.nV; p += gridDim.x * blockDim.x) {
@@ -254,9 +256,10 @@ __global__ void k_screen(DevPlan P) {
 #pragma unroll
     for (int w = 0; w < kMaskWords; ++w) mask[w] = 0u;
     int t2 = 0;
-    const double v = P.v_norm[p];
+    const int A = P.v_home[p];
+    const double v = (A >= P.h0 && A < P.h1) ? P.v_norm[p] : 0.0;
     if (v > 0.0) {
-      const int A = P.v_home[p], b = P.v_j[p];
+      const int b = P.v_j[p];
       const int* Rb = P.v_R + 3 * p;
       if (P.terms & 1) {
         const int di = P.v_didx[p];
@@ -727,9 +730,9 @@ __global__ void k_scan_total(const long long* out, const int* flag, const long l
 }
 
 __global__ void k_scatter(const int* flag, const unsigned* mask, const unsigned char* bytes, int mode, int n,
-                          const long long* off, int* list) {
+                          const long long* off, int* list, int base) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    if (scan_value(flag, nullptr, mask, bytes, mode == 1 ? 0 : mode, i)) list[off[i]] = i;
+    if (scan_value(flag, nullptr, mask, bytes, mode == 1 ? 0 : mode, i)) list[off[i]] = base + i;
 }
 
 int grid_for(long long n, int per_block, int cap = 152 * 32) {
@@ -758,6 +761,12 @@ cudaError_t scan_values(long long* vals, int n, long long* out, long long* tmp, 
 
 long long launch_count() { return g_launches; }
 
+// Block totals plus the levels of the recursive scan fit in 2*nb + 64.
+size_t scan_tmp_need(int n) {
+  const size_t nb = n > 0 ? ((size_t)n + kScanTile - 1) / kScanTile : 0;
+  return 2 * nb + 64;
+}
+
 cudaError_t scan_flags(const int* flag, const long long* size, const unsigned* mask, const unsigned char* bytes,
                        int mode, int n, long long* out, long long* total, ScanTmp& tmp, cudaStream_t s) {
   if (n <= 0) {
@@ -765,9 +774,9 @@ cudaError_t scan_flags(const int* flag, const long long* size, const unsigned* m
     return e;
   }
   const int nb = (n + kScanTile - 1) / kScanTile;
-  // Block totals plus the levels of the recursive scan fit in 2*nb + 64.
-  const size_t need = 2 * (size_t)nb + 64;
+  const size_t need = scan_tmp_need(n);
   if (tmp.cap < need) {
+    if (tmp.fixed) return cudaErrorMemoryAllocation;
     tmp.mem.put(tmp.buf, tmp.cap * sizeof(long long));
     tmp.buf = nullptr;
     tmp.cap = 0;
@@ -791,10 +800,10 @@ cudaError_t scan_flags(const int* flag, const long long* size, const unsigned* m
 }
 
 cudaError_t scatter_list(const int* flag, const unsigned* mask, const unsigned char* bytes, int mode, int n,
-                         const long long* off, int* list, cudaStream_t s) {
+                         const long long* off, int* list, int base, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   ++g_launches;
-  k_scatter<<<grid_for(n, kThreads), kThreads, 0, s>>>(flag, mask, bytes, mode, n, off, list);
+  k_scatter<<<grid_for(n, kThreads), kThreads, 0, s>>>(flag, mask, bytes, mode, n, off, list, base);
   return cudaGetLastError();
 }
 

@@ -835,8 +835,9 @@ struct Q2Shape {
 
 template <int NP, int TPC>
 __global__ void __launch_bounds__(192) k_q2_umma(DevPlan P, MixPlan X, const int* list, const long long* slot0,
-                                                 int n_slots, int FC8, int MC, int NSEG, long long zblk,
-                                                 int flush, const __grid_constant__ DRows drows, int* err) {
+                                                 int n_slots, int a0, int a1, int FC8, int MC, int NSEG,
+                                                 long long zblk, int flush, const __grid_constant__ DRows drows,
+                                                 int* err) {
   // Warp roles: warp 0 lane 0 produces (bulk async copies into a stage
   // ring, completion counted in bytes on full[s]); warp 1 lane 0 issues the
   // MMAs (all piece products of a pair into the TMEM accumulators, commits
@@ -863,15 +864,15 @@ __global__ void __launch_bounds__(192) k_q2_umma(DevPlan P, MixPlan X, const int
   const int mc = (rem % MCP) * TPC;   // first row tile of this CTA
   rem /= MCP;
   const int fc = rem % FC8;
-  const int A = rem / FC8;
+  const int A = a0 + rem / FC8;   // home atom of this pass [a0, a1); slot0 counts from the pass's first pair
   const int sA = P.species[A];
   const int nA = P.n_ao[sA], mA = P.n_abf[sA];
   const int rows = mA * nA, nt = (rows + 127) >> 7;
   const int q0 = P.c_ptr[A], nq = P.c_ptr[A + 1] - q0;
-  if (fc * 8 >= nq || mc * 128 >= rows) return;
+  if (fc * 8 >= nq || mc * 128 >= rows || P.v_ptr[A] == P.v_ptr[A + 1]) return;
   const int ntile = min(TPC, nt - mc);   // row tiles of this CTA
   const long long s0 = slot0[P.v_ptr[A]];
-  const long long s1 = A + 1 < P.N ? slot0[P.v_ptr[A + 1]] : (long long)n_slots;
+  const long long s1 = A + 1 < a1 ? slot0[P.v_ptr[A + 1]] : (long long)n_slots;
   const long long p0 = s0 + (long long)seg * KMP;
   const int np = (int)max(0ll, min((long long)KMP, s1 - p0));
   if (np <= 0) return;
@@ -933,7 +934,7 @@ __global__ void __launch_bounds__(192) k_q2_umma(DevPlan P, MixPlan X, const int
   const int nsteps = s_nsteps;
   const int nruns = (nsteps + flush - 1) / flush;
 
-  if (warp == 0) {
+  if (warp == 0 && !X.stall_q2) {
     // producer warp: every lane waits for the stage, then lanes issue the
     // copies of one stage in parallel (lane 0 also posts the byte count)
     const uint32_t abytes = (uint32_t)ntile * NP * kTileElems * 2;
@@ -1557,20 +1558,22 @@ cudaError_t launch_term1_mma(const DevPlan& P, const MixPlan& X, int np, const i
 }
 
 cudaError_t launch_term2_mma(const DevPlan& P, const MixPlan& X, int np, const int* list, const long long* slot0,
-                             int n, int MAmax, int KZmax, long long zblk, int zrows, int FC, int MC, int nseg,
-                             int flush, const DRows& drows, size_t smem, int* err, cudaStream_t s) {
-  if (n == 0) return cudaSuccess;
+                             int n, int a0, int a1, int MAmax, int KZmax, long long zblk, int zrows, int FC, int MC,
+                             int nseg, int flush, const DRows& drows, size_t smem, int* err, cudaStream_t s) {
+  if (n == 0 || a1 <= a0) return cudaSuccess;
   g_mix_launches += 3;
   const int FC8 = (FC * 4 + 7) / 8;     // groups of 8 C slots for the tcgen05 kernel
   k_q2tab<<<grid_for(((long long)n * FC8 * 8 + 255) / 256, 152 * 16), 256, 0, s>>>(P, X, list, n, FC8);
   const size_t sq = q2_umma_smem(np);
-  const long long grid = (long long)P.N * FC8 * ((MC + q2_tpc(np) - 1) / q2_tpc(np)) * nseg;
+  const long long grid = (long long)(a1 - a0) * FC8 * ((MC + q2_tpc(np) - 1) / q2_tpc(np)) * nseg;
   if (np == 2) {
     k_term2_pairs<2><<<grid_for(n, 152 * 32), kWarps * 32, smem, s>>>(P, X, list, n, MAmax, KZmax, zblk, zrows);
-    k_q2_umma<2, q2_tpc(2)><<<(unsigned)grid, 192, sq, s>>>(P, X, list, slot0, n, FC8, MC, nseg, zblk, flush, drows, err);
+    k_q2_umma<2, q2_tpc(2)><<<(unsigned)grid, 192, sq, s>>>(P, X, list, slot0, n, a0, a1, FC8, MC, nseg, zblk, flush,
+                                                             drows, err);
   } else {
     k_term2_pairs<3><<<grid_for(n, 152 * 32), kWarps * 32, smem, s>>>(P, X, list, n, MAmax, KZmax, zblk, zrows);
-    k_q2_umma<3, q2_tpc(3)><<<(unsigned)grid, 192, sq, s>>>(P, X, list, slot0, n, FC8, MC, nseg, zblk, flush, drows, err);
+    k_q2_umma<3, q2_tpc(3)><<<(unsigned)grid, 192, sq, s>>>(P, X, list, slot0, n, a0, a1, FC8, MC, nseg, zblk, flush,
+                                                             drows, err);
   }
   return cudaGetLastError();
 }

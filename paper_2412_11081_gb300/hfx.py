@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libhfx.so")
 
 HFX_OK = 0
-HFX_FP64, HFX_TF32X3, HFX_BF16X3, HFX_BF16X6 = 0, 1, 2, 3
+HFX_FP64, HFX_BF16X3, HFX_BF16X6 = 0, 2, 3
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error", 4: "timeout",
           5: "pair list stale", 6: "unsupported"}
 
@@ -44,8 +44,9 @@ class HfxOptions(ct.Structure):
     _fields_ = [("theta_C", ct.c_double), ("theta_dC", ct.c_double), ("theta_V", ct.c_double),
                 ("theta_dV", ct.c_double), ("theta_D", ct.c_double), ("theta_CS", ct.c_double),
                 ("precision", ct.c_int), ("terms", ct.c_int), ("skin", ct.c_double),
-                ("freeze_lists", ct.c_int), ("deterministic", ct.c_int), ("stream", ct.c_void_p),
-                ("device", ct.c_int), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", ct.c_void_p)]
+                ("freeze_lists", ct.c_int), ("home_begin", ct.c_int), ("home_end", ct.c_int),
+                ("home_chunk", ct.c_int), ("stream", ct.c_void_p), ("device", ct.c_int), ("alloc", ALLOC_FN),
+                ("free", FREE_FN), ("alloc_ctx", ct.c_void_p)]
 
 
 class HfxTuneReport(ct.Structure):
@@ -60,7 +61,8 @@ class HfxStats(ct.Structure):
                 ("flops_term2", ct.c_double), ("flops_total", ct.c_double), ("ms_blocks", ct.c_double),
                 ("ms_screen", ct.c_double), ("ms_y", ct.c_double), ("ms_term1", ct.c_double),
                 ("ms_term2", ct.c_double), ("ms_reduce", ct.c_double), ("ms_total", ct.c_double),
-                ("device_bytes", ct.c_longlong), ("kernel_launches", ct.c_longlong)]
+                ("device_bytes", ct.c_longlong), ("kernel_launches", ct.c_longlong), ("passes", ct.c_int),
+                ("ref_err_E", ct.c_double), ("ref_err_F", ct.c_double), ("ref_err_sigma", ct.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -76,6 +78,7 @@ _SIGNATURES = {
                                                   ct.POINTER(HfxStats)]),
     "hfx_energy_force_stress_noalloc": (ct.c_int, [ct.c_void_p, _dp, _dp, _dp, _dp, _dp]),
     "hfx_set_timing": (ct.c_int, [ct.c_void_p, ct.c_int]),
+    "hfx_set_reference": (ct.c_int, [ct.c_void_p, _dp, _dp, _dp]),
     "hfx_plan_autotune": (ct.c_int, [ct.c_void_p, _dp, _dp, ct.c_int, ct.c_void_p]),
     "hfx_lri_fit": (ct.c_int, [ct.c_int, ct.c_int, ct.c_int, _dp, _dp, _dp, _dp, _dp, _dp, ct.c_int]),
     "hfx_plan_destroy": (ct.c_int, [ct.c_void_p]),
@@ -139,23 +142,31 @@ class Plan:
 
     def __init__(self, w, *, precision: int = HFX_FP64, terms: int = 3, skin: float = 0.5,
                  freeze_lists: bool = False, stream: Optional[int] = None, device: int = 0,
-                 theta: Optional[dict] = None, aniso=None, allocator: Optional[str] = None):
+                 theta: Optional[dict] = None, aniso=None, allocator=None, home=None, home_chunk: int = 0):
         self.lib = load_library()
         th = dict(w.theta) if theta is None else dict(theta)
         if stream is None:
             stream = _current_stream()
+        hb, he = (0, 0) if home is None else (int(home[0]), int(home[1]))
         self.opts = default_options(theta_C=th["C"], theta_dC=th["dC"], theta_V=th["V"], theta_dV=th["dV"],
                                     theta_D=th["D"], theta_CS=th["CS"], precision=precision, terms=terms,
-                                    skin=skin, freeze_lists=int(freeze_lists), stream=stream, device=device)
+                                    skin=skin, freeze_lists=int(freeze_lists), stream=stream, device=device,
+                                    home_begin=hb, home_end=he, home_chunk=int(home_chunk))
         # allocator="torch": the plan's device memory comes from PyTorch's
-        # caching allocator (hfx_options alloc / free); the callbacks live
-        # as long as the plan
+        # caching allocator (hfx_options alloc / free); a pair of callables
+        # (alloc(nbytes) -> device address or 0, free(address, nbytes)) is
+        # wrapped the same way.  The callbacks live as long as the plan.
         self._hooks = None
         if allocator == "torch":
             self._hooks = _torch_hooks(device)
-            self.opts.alloc, self.opts.free = self._hooks
+        elif isinstance(allocator, tuple) and len(allocator) == 2:
+            a_fn, f_fn = allocator
+            self._hooks = (ALLOC_FN(lambda n, s, c: a_fn(int(n)) or None),
+                           FREE_FN(lambda p, n, s, c: f_fn(int(p), int(n))))
         elif allocator is not None:
-            raise ValueError("allocator must be None or 'torch'")
+            raise ValueError("allocator must be None, 'torch' or (alloc, free)")
+        if self._hooks is not None:
+            self.opts.alloc, self.opts.free = self._hooks
         self.n_atoms = int(np.asarray(w.species).shape[0])
         # keep every marshalled array alive for the duration of the create call
         self._keep = []
@@ -203,6 +214,20 @@ class Plan:
 
     def set_timing(self, on: bool = True):
         _check(self.lib, self.lib.hfx_set_timing(self.handle, int(on)), self.handle)
+
+    def set_reference(self, E=None, F=None, sigma=None):
+        """hfx_set_reference: later stats report their error against (E, F,
+        sigma); no arguments clear it."""
+        if E is None and F is None and sigma is None:
+            st = self.lib.hfx_set_reference(self.handle, None, None, None)
+        else:
+            e = np.array([float(E)])
+            f, s = _f64(F).ravel(), _f64(sigma).ravel()
+            if f.size != 3 * self.n_atoms or s.size != 9:
+                raise ValueError("F must be n_atoms x 3 and sigma 3 x 3")
+            st = self.lib.hfx_set_reference(self.handle, e.ctypes.data_as(_dp), f.ctypes.data_as(_dp),
+                                            s.ctypes.data_as(_dp))
+        _check(self.lib, st, self.handle)
 
     def evaluate(self, lattice, positions, stats: bool = False):
         """E, F (n x 3), sigma (3 x 3) at the given geometry (host arrays)."""

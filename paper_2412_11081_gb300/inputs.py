@@ -177,6 +177,12 @@ def _make_density(rng, species, lattice, pos, n_ao, theta_d, ell=D_DECAY_LENGTH)
     rcut = ell * math.log(nmax / theta_d)
     Rs = image_range(lattice, rcut)
     RL = Rs @ lattice
+    # drop the images whose translated bounding box of the positions lies
+    # rcut or farther from the untranslated one (no pair can reach them)
+    span = pos.max(0) - pos.min(0)
+    gap = np.maximum(np.abs(RL) - span[None, :], 0.0)
+    near = (gap * gap).sum(1) < rcut * rcut
+    Rs, RL = Rs[near], RL[near]
     canon = []  # (I, J, R1, R2, R3, d0)
     for i in range(n):
         d = pos[None, :, :] + RL[:, None, :] - pos[i][None, None, :]   # [nR, n, 3]
@@ -199,25 +205,41 @@ def _make_density(rng, species, lattice, pos, n_ao, theta_d, ell=D_DECAY_LENGTH)
     sizes = na[keys[:, 0]] * na[keys[:, 1]]
     raw = rng.standard_normal(int(sizes.sum()))
     offs = np.concatenate([[0], np.cumsum(sizes)])
+    scale = np.array([math.exp(-x / ell) for x in d0.tolist()])
 
-    blocks = {}
-    out_keys = []
-    for k in range(keys.shape[0]):
-        i, j = int(keys[k, 0]), int(keys[k, 1])
-        R = keys[k, 2:5]
-        S_ = raw[offs[k]:offs[k + 1]].reshape(na[i], na[j])
-        if i == j and not R.any():
-            S_ = (S_ + S_.T) / math.sqrt(2.0)
-        blk = S_ * math.exp(-d0[k] / ell)
-        blocks[(i, j, int(R[0]), int(R[1]), int(R[2]))] = blk
-        if not (i == j and not R.any()):
-            blocks[(j, i, -int(R[0]), -int(R[1]), -int(R[2]))] = np.ascontiguousarray(blk.T)
-    all_keys = np.array(sorted(blocks.keys()), dtype=np.int32).reshape(-1, 5)
-    vals = [blocks[tuple(int(x) for x in k)].ravel() for k in all_keys]
+    # Every stored block: the canonical ones and the mirrors D_JI(-R) = D_IJ(R)^T
+    # (not of the on-site blocks), in lexicographic order of (I, J, R1, R2, R3).
+    onsite = (keys[:, 0] == keys[:, 1]) & ~keys[:, 2:5].any(axis=1)
+    mir = np.nonzero(~onsite)[0]
+    mkeys = np.column_stack([keys[mir, 1], keys[mir, 0], -keys[mir, 2:5]])
+    all_keys = np.concatenate([keys, mkeys])
+    src = np.concatenate([np.arange(keys.shape[0]), mir])                 # canonical block of each entry
+    trans = np.concatenate([np.zeros(keys.shape[0], bool), np.ones(mir.size, bool)])
+    order = np.lexsort(tuple(all_keys[:, c] for c in (4, 3, 2, 1, 0)))
+    all_keys, src, trans = all_keys[order], src[order], trans[order]
+    esz = na[all_keys[:, 0]] * na[all_keys[:, 1]]
     d_offset = np.zeros(all_keys.shape[0] + 1, dtype=np.int64)
-    d_offset[1:] = np.cumsum([v.size for v in vals])
-    d_values = np.concatenate(vals) if vals else np.zeros(0)
-    return all_keys, d_offset, d_values
+    d_offset[1:] = np.cumsum(esz)
+    d_values = np.zeros(int(d_offset[-1]))
+    # fill by canonical shape (a, b) and orientation: S from its draws,
+    # symmetrised on site, times exp(-d0/ell), transposed for a mirror
+    ca, cb = na[keys[src, 0]], na[keys[src, 1]]
+    for a in np.unique(ca):
+        for b in np.unique(cb):
+            for t in (False, True):
+                sel_all = np.nonzero((ca == a) & (cb == b) & (trans == t))[0]
+                for s0 in range(0, sel_all.size, 65536):   # bounded index arrays
+                    sel = sel_all[s0:s0 + 65536]
+                    c = src[sel]
+                    S_ = raw[offs[c][:, None] + np.arange(a * b)[None, :]].reshape(-1, a, b)
+                    on = onsite[c]
+                    if on.any():
+                        S_[on] = (S_[on] + S_[on].transpose(0, 2, 1)) / math.sqrt(2.0)
+                    blk = S_ * scale[c][:, None, None]
+                    if t:
+                        blk = blk.transpose(0, 2, 1)
+                    d_values[d_offset[sel][:, None] + np.arange(a * b)[None, :]] = blk.reshape(sel.size, a * b)
+    return all_keys.astype(np.int32), d_offset, d_values
 
 
 def make_workload(kind: str, n_rep: int, a: float, n_ao: Sequence[int], n_abf: Sequence[int],

@@ -48,6 +48,7 @@ def test_status_strings(lib):
 def test_default_options(lib):
     o = hfx.default_options()
     assert o.theta_CS == 1e-10 and o.precision == hfx.HFX_FP64 and o.terms == 3 and o.skin == 0.5
+    assert o.home_begin == 0 and o.home_end == 0 and o.home_chunk == 0
     assert lib.hfx_default_options(None) == 1
 
 
@@ -83,6 +84,11 @@ def test_invalid_arguments_rejected_before_any_device_work(lib):
     assert _create(lib, w, theta_CS=-1.0) == 1                    # negative threshold
     assert _create(lib, w, terms=0) == 1                          # no exchange product
     assert _create(lib, w, precision=7) == 6                      # unknown precision
+    assert _create(lib, w, precision=1) == 6                      # unassigned precision value
+    assert _create(lib, w, home_begin=3, home_end=3) == 1         # empty home-atom range
+    assert _create(lib, w, home_begin=0, home_end=9) == 1         # range past n_atoms (8)
+    assert _create(lib, w, home_begin=-1, home_end=4) == 1
+    assert _create(lib, w, home_chunk=-2) == 1
     assert _create(lib, w, r_c=float("nan")) == 1                 # non-finite model
     bad = w.positions.copy()
     bad[2, 1] = float("inf")

@@ -2,18 +2,14 @@
 FP64 screening and reductions) against the FP64 CPU oracle.
 
 Error metric: max|x - x_ref| / max|x_ref| per output (|dE|/|E| for E).
-HFX_BF16X6 keeps every piece product down to 2^-24 of the operands;
-HFX_BF16X3 drops the products below 2^-16 of them.  Both must meet the
-1e-5 relative force/stress contract on the unperturbed cells here (BF16X3
-misses it on the two-species cell and on some jittered si64 geometries,
-see the tests below): in the tcgen05 first product U is
-built in FP32 from FP32 Y and D, so the 16-bit truncation of BF16X3 only
-touches the operands of the two tensor-core products, and the FP32
-accumulators are flushed to FP64 every 32 B (the remaining error is the
-sum of independent per-element rounding, measured at 4e-6 to 6e-6 on
-si64).  The warp-level MMA first product (HFX_T1_KERNEL=mma; it also takes
-the shapes the tcgen05 kernel does not: n_abf > 64) is held to 3e-5 at
-BF16X3 and checked against the tcgen05 one.
+Every case is held to the 1e-5 relative contract.  HFX_BF16X6 keeps every
+piece product down to 2^-24 of the operands and meets it everywhere.
+HFX_BF16X3 drops the products below 2^-16 of them: it meets the contract on
+the unperturbed cells, but not on the two-species cell (2.1e-5 in F from its
+second product) nor on every jittered si64 geometry (up to 1.8e-5 in sigma);
+those cases are marked as expected failures (strict: they must keep
+failing, so a change that brings BF16X3 within the contract shows up) and
+print the error they measure.
 """
 import json
 import os
@@ -27,8 +23,8 @@ from paper_2412_11081_gb300 import hfx, inputs
 pytestmark = pytest.mark.gpu
 HERE = os.path.dirname(os.path.abspath(__file__))
 SPLITS = [hfx.HFX_BF16X6, hfx.HFX_BF16X3]
-BOUND = {hfx.HFX_BF16X6: 1e-5, hfx.HFX_BF16X3: 1e-5}
-BOUND_MMA = {hfx.HFX_BF16X6: 1e-5, hfx.HFX_BF16X3: 3e-5}
+BOUND = 1e-5   # the relative force/stress/energy contract of the split precisions
+BF16X3_MISSES = pytest.mark.xfail(strict=True, reason="BF16X3 exceeds the 1e-5 contract here (two-piece operands)")
 
 
 def rel(a, ref):
@@ -55,7 +51,7 @@ def test_mixed_small_cells(case, prec):
     w = tiny_periodic() if case == "tiny" else inputs.diamond8()
     r = evaluate(w)
     E, F, S, st = run(w, prec)
-    b = BOUND[prec]
+    b = BOUND
     assert abs(E - r.E) <= b * abs(r.E)
     assert rel(F, r.F) <= b, rel(F, r.F)
     assert rel(S, r.sigma) <= b, rel(S, r.sigma)
@@ -73,20 +69,18 @@ def two_species_cell(seed=13):
     return inputs.cut_density(w, 4.5)
 
 
-@pytest.mark.parametrize("prec", SPLITS)
+@pytest.mark.parametrize("prec", [hfx.HFX_BF16X6, pytest.param(hfx.HFX_BF16X3, marks=BF16X3_MISSES)])
 def test_mixed_two_species_shapes(prec):
     """BF16X6 meets 1e-5 here too.  BF16X3 does not on this cell: its
     second product (R2 and Z from two-piece Y, the 2^-16 piece product
-    dropped) leaves 2.1e-5 in F on its own, the same with the warp-level and
-    the tcgen05 first product, so BF16X3 is held to 3e-5 on it."""
+    dropped) leaves about 2e-5 in F on its own."""
     w = two_species_cell()
     r = evaluate(w)
     E, F, S, st = run(w, prec)
-    b = 3e-5 if prec == hfx.HFX_BF16X3 else BOUND[prec]
-    assert abs(E - r.E) <= b * abs(r.E)
-    assert rel(F, r.F) <= b, rel(F, r.F)
-    assert rel(S, r.sigma) <= b, rel(S, r.sigma)
+    eE, eF, eS = abs(E - r.E) / abs(r.E), rel(F, r.F), rel(S, r.sigma)
+    print(f"two-species cell, precision {prec}: errE {eE:.2e} errF {eF:.2e} errS {eS:.2e}")
     assert st["triplets"] == r.counts["triplets"] and st["term2_pairs"] == r.counts["term2_pairs"]
+    assert eE <= BOUND and eF <= BOUND and eS <= BOUND
 
 
 @pytest.mark.parametrize("prec", SPLITS)
@@ -95,33 +89,34 @@ def test_mixed_si64_full_size(prec):
     ref = json.load(open(os.path.join(HERE, "golden", "si64_oracle.json")))
     w = inputs.si_supercell(2)
     E, F, S, st = run(w, prec)
-    b = BOUND[prec]
+    b = BOUND
     eF, eS, eE = rel(F, ref["F"]), rel(S, ref["sigma"]), abs(E - ref["E"]) / abs(ref["E"])
     print(f"precision {prec}: errE {eE:.2e} errF {eF:.2e} errS {eS:.2e}")
     assert eE <= b and eF <= b and eS <= b
     assert st["triplets"] == ref["counts"]["triplets"]
 
 
-@pytest.mark.parametrize("prec", [hfx.HFX_BF16X6, hfx.HFX_BF16X3])
+@pytest.mark.parametrize("prec", [hfx.HFX_BF16X6, pytest.param(hfx.HFX_BF16X3, marks=BF16X3_MISSES)])
 def test_split_precisions_on_jittered_si64_geometries(prec):
     """The first four geometries of the benchmark's jittered si64 sequence,
     against the FP64 GPU path (itself within 1e-10 of the oracle).  BF16X6
-    stays within 1e-5 on each.  BF16X3 reaches 1.75e-5 in sigma on some of
-    them (its two-piece operands leave 2^-16-level errors in both exchange
-    products), so it is held to 2.5e-5 here, and the benchmark takes it as
-    its headline only where it meets 1e-5 on these geometries."""
+    stays within 1e-5 on each.  BF16X3 reaches about 1.8e-5 in sigma on some
+    of them (its two-piece operands leave 2^-16-level errors in both
+    exchange products); the benchmark takes it as its headline only where it
+    meets 1e-5 on these geometries."""
     w = inputs.si_supercell(2)
     geoms = inputs.geometry_sequence(w, 4)
     with hfx.Plan(w, precision=hfx.HFX_FP64) as p0:
         refs = [p0.evaluate(w.lattice, g) for g in geoms]
+    worst = 0.0
     with hfx.Plan(w, precision=prec) as p:
         for k, g in enumerate(geoms):
             E, F, S = p.evaluate(w.lattice, g)
             E0, F0, S0 = refs[k]
             eE, eF, eS = abs(E - E0) / abs(E0), rel(F, F0), rel(S, S0)
             print(f"precision {prec} geometry {k}: errE {eE:.2e} errF {eF:.2e} errS {eS:.2e}")
-            b = 1e-5 if prec == hfx.HFX_BF16X6 else 2.5e-5
-            assert eE <= b and eF <= b and eS <= b, k
+            worst = max(worst, eE, eF, eS)
+    assert worst <= BOUND, worst
 
 
 def test_mixed_anisotropic_gradient_blocks():
@@ -150,19 +145,16 @@ def test_mixed_each_exchange_product_alone():
 @pytest.mark.parametrize("prec", SPLITS)
 def test_first_product_kernels_agree(prec, monkeypatch):
     """The tcgen05 first product and the warp-level MMA one (selected at plan
-    creation by HFX_T1_KERNEL) on the same cell: both within their bound of
-    the oracle, and within it of each other."""
+    creation by HFX_T1_KERNEL) on the same cell: both within the contract of
+    the oracle."""
     w = inputs.diamond8()
     r = evaluate(w)
-    out = {}
     for kern in ("umma", "mma"):
         monkeypatch.setenv("HFX_T1_KERNEL", kern)
-        out[kern] = run(w, prec)
-        b = BOUND[prec] if kern == "umma" else BOUND_MMA[prec]
-        E, F, S, _ = out[kern]
-        assert abs(E - r.E) <= b * abs(r.E) and rel(F, r.F) <= b and rel(S, r.sigma) <= b, kern
-    assert rel(out["umma"][1], out["mma"][1]) <= BOUND_MMA[prec]
-    assert rel(out["umma"][2], out["mma"][2]) <= BOUND_MMA[prec]
+        E, F, S, _ = run(w, prec)
+        eE, eF, eS = abs(E - r.E) / abs(r.E), rel(F, r.F), rel(S, r.sigma)
+        print(f"first product {kern}, precision {prec}: errE {eE:.2e} errF {eF:.2e} errS {eS:.2e}")
+        assert eE <= BOUND and eF <= BOUND and eS <= BOUND, kern
 
 
 def test_auxiliary_basis_beyond_tcgen05_kernel(monkeypatch):
@@ -202,4 +194,4 @@ def test_mixed_single_atom_cell_self_images_only(prec):
     r = evaluate(w)
     E, F, S, _ = run(w, prec)
     assert np.max(np.abs(F)) <= 1e-10 * abs(r.E)
-    assert abs(E - r.E) <= BOUND[prec] * abs(r.E) and rel(S, r.sigma) <= BOUND[prec]
+    assert abs(E - r.E) <= BOUND * abs(r.E) and rel(S, r.sigma) <= BOUND
