@@ -1,20 +1,26 @@
-"""Benchmark: HFX force+stress evaluations per second on the 64-atom Si-like
-supercell (2x2x2 diamond, n_ao 13, n_abf 50, r_c 3.7 A, thresholds 1e-10).
+"""Benchmark: HFX force+stress evaluations per second on the 1000-atom
+Si-like supercell (5x5x5 diamond, n_ao 13, n_abf 50, r_c 3.7 A, 3 % random
+strain, thresholds 1e-10), the configuration the mixed-precision target is
+quoted on.
 
-One step = one full evaluation of the hot path (block generation, two-step
-screening, Y build, both exchange products, force/stress/energy reduction)
-on a warm plan, at a new geometry (small seeded jitter within the pair-list
-skin, so every block, norm and screening decision is recomputed).  The
-headline precision (`--precision auto`, the default) is HFX_BF16X3 if its
-energy, force and stress errors against the FP64 GPU results of the first
-four geometries of the sequence are all within 1e-5 relative, else
-HFX_BF16X6; the other split and FP64 are reported beside it, each with its
-measured (largest) error.
+One step = one full evaluation of the hot path (block norms, two-step
+screening, Y build, both exchange products in passes of 128 home atoms,
+force/stress/energy reduction) on a warm plan, at a new geometry (small
+seeded jitter within the pair-list skin, so every block, norm and screening
+decision is recomputed).  The headline precision is HFX_BF16X6 (the split
+that meets the 1e-5 contract on every tested geometry; HFX_BF16X3 misses it
+on some, see tests/test_gpu_mixed.py); FP64 and BF16X3 are reported beside
+it, each with its error against the FP64 GPU result of the same geometry.
+Plans run one after another (FP64, the headline, the other split), each
+freed before the next, so that one holds the GPU's memory at a time.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+With N > 1 (torchrun, one rank per GPU) each rank's plan takes a contiguous
+range of home atoms and an all-reduce of E, F and sigma finishes each step
+(home-atom sharding; total work fixed, "scaling": "strong").
 `--impl reference` times the CPU oracle (the only reference that exists:
-the paper has no code) on a bounded sample of the same workload.
+the paper has no code) on bounded samples of the same per-atom work.
 Prints one JSON line on rank 0.
 """
 from __future__ import annotations
@@ -35,7 +41,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "HFX force+stress evals/s & %tensor roofline, mixed vs FP64 at 1e-5 rel; p99 latency"
 UNIT = "evals/s"
-WORKLOAD = "si64: 2x2x2 diamond supercell, 64 atoms, n_ao 13, n_abf 50, r_c 3.7 A, theta 1e-10"
+WORKLOAD_NAME = "si1000"
+N_ATOMS = 1000
+WORKLOAD = ("si1000: 5x5x5 diamond supercell, 1000 atoms, n_ao 13, n_abf 50, r_c 3.7 A, 3 % random strain, "
+            "theta 1e-10")
+SI64_TRIPLETS = 828423   # kept triplets of si64, the case the first product's DRAM traffic was scaled to
 
 
 def _env_rank():
@@ -52,13 +62,6 @@ def max_over_ranks(values, dist=None, device=None):
     t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return [float(x) for x in t]
-
-
-def job_rates(steps_per_rank, world, t_dev, t_e2e, dist=None, device=None):
-    """Whole-job throughput: the units all ranks processed over the slowest
-    rank's time, device-timed and end to end."""
-    t_max, t_e2e_max = max_over_ranks([t_dev, t_e2e], dist, device)
-    return world * steps_per_rank / t_max, world * steps_per_rank / t_e2e_max, t_max
 
 
 class ClockSampler:
@@ -165,56 +168,103 @@ def fp64_gemm_peak(torch, dev):
     return 2.0 * n ** 3 / best / 1e12
 
 
-def cpu_baseline(w, homes, reps=1):
-    """Time the oracle, as it stands, on `homes` home atoms of the workload.
-    Its work is a sum over home atoms, so evals/s = 1 / (t * N / k)."""
+def cpu_baseline_sample(name="si64"):
+    """Time the oracle, as it stands, on a bounded sample with the per-atom
+    work of the benchmark's workload: si64 has the same species, basis sizes,
+    thresholds and per-atom pair counts as si1000 (the lattice sums cover
+    every image, so the work per atom does not depend on the supercell).
+    One evaluation costs a per-structure part (the plan's D norms, then the
+    blocks, norms and Cauchy-Schwarz factors of every atom: OraclePlan and
+    evaluate(homes=[])) and a part per home atom (evaluate(homes=[k]) minus
+    evaluate(homes=[])).  The per-home part builds every Y block that home
+    atom's items read, blocks a full evaluation shares among home atoms, so
+    N times it overstates the oracle's time on a full evaluation."""
     from oracle import OraclePlan
+    from paper_2412_11081_gb300 import inputs
+    w = inputs.workload_by_name(name)
+    t0 = time.time()
     plan = OraclePlan(w)
-    t = time.time()
-    for _ in range(reps):
-        plan.evaluate(homes=list(range(homes)))
-    dt = (time.time() - t) / reps
-    per_eval = dt * w.n_atoms / homes
-    return {"value": 1.0 / per_eval, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{homes} of {w.n_atoms} home atoms of {w.name} ({dt:.1f} s), scaled by N/k; "
+    t_ctor = time.time() - t0
+    t1 = time.time()
+    plan.evaluate(homes=[])
+    t_pre = time.time() - t1
+    t2 = time.time()
+    plan.evaluate(homes=[0])
+    t_one = time.time() - t2
+    return {"n_atoms": w.n_atoms, "t_ctor": t_ctor, "t_pre": t_pre, "t_one": t_one, "wall": time.time() - t0}
+
+
+def oracle_rate(sample, n_atoms):
+    """Oracle evals/s on n_atoms atoms: the per-structure part scaled by
+    atoms plus n_atoms times one home atom's part."""
+    per_atom_pre = (sample["t_ctor"] + sample["t_pre"]) / sample["n_atoms"]
+    per_home = max(sample["t_one"] - sample["t_pre"], 0.0)
+    return 1.0 / (n_atoms * (per_atom_pre + per_home)), per_atom_pre, per_home
+
+
+def cpu_baseline(n_atoms):
+    s = cpu_baseline_sample()
+    rate, pa, ph = oracle_rate(s, n_atoms)
+    return {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"oracle on si64 (same per-atom shapes and pair counts as {WORKLOAD_NAME}): per-structure "
+                      f"part {s['t_ctor'] + s['t_pre']:.1f} s for 64 atoms, one home atom {ph:.1f} s; estimate for "
+                      f"{n_atoms} atoms = {n_atoms} x ({pa:.3f} + {ph:.2f}) s (each home atom's Y blocks counted "
+                      f"in full: an upper bound of a full evaluation's time); {s['wall']:.1f} s of CPU work; "
                       f"numpy/OpenBLAS threads = cores"}
 
 
 def run_reference(args):
+    """The oracle (the reference arm: the paper ships no code) on bounded
+    samples of the workload.  Step k evaluates home atom k of si64 (the same
+    per-atom work as si1000); the line's value is the oracle's evals/s on
+    si1000 from the per-structure part (timed once before the steps) plus
+    the mean per-home-atom time of the steps; ms_per_step is the measured
+    wall time of one step."""
     rank, world, _ = _env_rank()
     if rank != 0:
         return 0
-    from paper_2412_11081_gb300 import inputs
-    w = inputs.si_supercell(2)
     from oracle import OraclePlan
+    from paper_2412_11081_gb300 import inputs
+    w = inputs.workload_by_name("si64")
+    t0 = time.time()
     plan = OraclePlan(w)
-    homes = 1
-    for _ in range(args.warmup):
-        plan.evaluate(homes=[0])
+    t_ctor = time.time() - t0
+    t1 = time.time()
+    plan.evaluate(homes=[])
+    t_pre = time.time() - t1
+    for k in range(args.warmup):
+        plan.evaluate(homes=[k % w.n_atoms])
     times = []
     for k in range(args.steps):
         t = time.time()
         plan.evaluate(homes=[k % w.n_atoms])
         times.append(time.time() - t)
-    per_eval = statistics.mean(times) * w.n_atoms / homes
-    value = 1.0 / per_eval
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": per_eval * 1e3, "higher_is_better": True,
+    step = statistics.mean(times)
+    rate, pa, ph = oracle_rate({"n_atoms": w.n_atoms, "t_ctor": t_ctor, "t_pre": t_pre, "t_one": step}, N_ATOMS)
+    sample = (f"step k = home atom k of si64 (same per-atom shapes and pair counts as {WORKLOAD_NAME}); "
+              f"value = 1 / ({N_ATOMS} x ({pa:.3f} s per-structure part per atom + {ph:.2f} s per home atom)), "
+              f"the per-structure part ({t_ctor + t_pre:.1f} s for 64 atoms) timed once before the steps, the "
+              f"per-home part = mean step minus it; each home atom's Y blocks counted in full (an upper bound "
+              f"of a full evaluation's time)")
+    line = {"metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": WORKLOAD, "sample": "one home atom per step, scaled by 64"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": f"{homes} of 64 home atoms per step ({statistics.mean(times):.1f} s)"},
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
-def _time_device(plan, w, d_pos, d_out, first, steps, stream, torch):
+def _time_device(plan, w, d_pos, d_out, first, steps, stream, torch, reduce=None):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     for k in range(steps):
         plan.evaluate_device(w.lattice, d_pos[first + k].data_ptr(), d_out.data_ptr())
+        if reduce is not None:
+            reduce(d_out)
     ev1.record(stream)
     torch.cuda.synchronize()
     return ev0.elapsed_time(ev1) / 1e3
@@ -223,6 +273,10 @@ def _time_device(plan, w, d_pos, d_out, first, steps, stream, torch):
 def _rel(a, b):
     a, b = np.asarray(a, float), np.asarray(b, float)
     return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def _errs(got, ref):
+    return {"errE": abs(got[0] - ref[0]) / abs(ref[0]), "errF": _rel(got[1], ref[1]), "errS": _rel(got[2], ref[2])}
 
 
 def run_ours(args):
@@ -236,148 +290,165 @@ def run_ours(args):
         raise SystemExit("bench.py needs a CUDA GPU")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    from paper_2412_11081_gb300 import hfx, inputs
-    w = inputs.si_supercell(2)
+    from paper_2412_11081_gb300 import hfx, inputs, shard
+    w = inputs.workload_by_name(WORKLOAD_NAME)
     stream = torch.cuda.current_stream(dev)
     n = w.n_atoms
-    geoms = inputs.geometry_sequence(w, args.warmup + args.steps + 8)
+    home = shard.home_ranges(n, world)[rank] if world > 1 else None
+    geoms = inputs.geometry_sequence(w, args.warmup + args.steps + 4)
     d_pos = [torch.tensor(g, dtype=torch.float64, device=dev) for g in geoms]
     d_out = torch.zeros(1 + 3 * n + 9, dtype=torch.float64, device=dev)
+    PREC = {"bf16x6": hfx.HFX_BF16X6, "bf16x3": hfx.HFX_BF16X3, "fp64": hfx.HFX_FP64}
+    reduce = None
+    if dist is not None:
+        def reduce(t):   # the sum of the ranks' shares (home-atom sharding): the one exchange
+            dist.all_reduce(t, op=dist.ReduceOp.SUM)
 
     def barrier():
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    # ---- reference result of the same geometry on the FP64 GPU path (parity-tested
-    #      against the CPU oracle to 1e-10): the error of the mixed path is taken here
-    fp64 = hfx.Plan(w, precision=hfx.HFX_FP64, stream=stream.cuda_stream, device=local)
-    n_chk = 4   # geometries the split precisions are checked on
-    refs = [fp64.evaluate(w.lattice, geoms[k]) for k in range(n_chk)]
-    fp64_steps = max(1, min(2, args.steps))
-    fp64.evaluate_device(w.lattice, d_pos[1].data_ptr(), d_out.data_ptr())
+    def new_plan(name):
+        return hfx.Plan(w, precision=PREC[name], stream=stream.cuda_stream, device=local, home=home)
+
+    def whole(plan, k):
+        """E, F, sigma of geometry k (the shares summed over the ranks)."""
+        plan.evaluate_device(w.lattice, d_pos[k].data_ptr(), d_out.data_ptr())
+        if reduce is not None:
+            reduce(d_out)
+        v = d_out.cpu().numpy()
+        return float(v[0]), v[1:1 + 3 * n].reshape(n, 3).copy(), v[1 + 3 * n:].reshape(3, 3).copy()
+
+    # ---- the FP64 GPU path (parity-tested against the oracle to 1e-10) on the
+    #      first geometry: the reference of the split precisions' errors, and its rate
+    pl = new_plan("fp64")
+    pl.set_timing(True)
     barrier()
-    t_fp64 = _time_device(fp64, w, d_pos, d_out, 2, fp64_steps, stream, torch) / fp64_steps
-    fp64.close()
+    t = time.perf_counter()
+    ref = whole(pl, 0)
+    barrier()
+    t_fp64 = time.perf_counter() - t
+    pl.evaluate_device(w.lattice, d_pos[0].data_ptr(), d_out.data_ptr(), stats=True)
+    fp64_stats = pl.stats.as_dict()
+    pl.close()
 
-    variants = {}
-    for name, prec in (("bf16x6", hfx.HFX_BF16X6), ("bf16x3", hfx.HFX_BF16X3)):
-        pl = hfx.Plan(w, precision=prec, stream=stream.cuda_stream, device=local)
-        errs = []
-        for k in range(n_chk):
-            E, F, S = pl.evaluate(w.lattice, geoms[k])
-            ref = refs[k]
-            errs.append((abs(E - ref[0]) / abs(ref[0]), _rel(F, ref[1]), _rel(S, ref[2])))
-        variants[name] = dict(plan=pl, errE=max(e[0] for e in errs), errF=max(e[1] for e in errs),
-                              errS=max(e[2] for e in errs))
-    auto = args.precision == "auto"
-    if auto:
-        # BF16X3 runs half the piece products of BF16X6: it is the headline
-        # only if it meets the 1e-5 contract on every checked geometry
-        x3 = variants["bf16x3"]
-        args.precision = "bf16x3" if max(x3["errE"], x3["errF"], x3["errS"]) <= 1e-5 else "bf16x6"
-    plan = variants[args.precision]["plan"] if args.precision != "fp64" else \
-        hfx.Plan(w, precision=hfx.HFX_FP64, stream=stream.cuda_stream, device=local)
-    # the split plans pick their launch shapes with the library's autotuner
-    # (hfx_plan_autotune, untimed; the arithmetic does not change)
+    head = args.precision if args.precision != "auto" else "bf16x6"
+    # ---- headline precision
+    plan = new_plan(head)
+    head_err = _errs(whole(plan, 0), ref) if head != "fp64" else {"errE": 0.0, "errF": 0.0, "errS": 0.0}
     tuned = {}
-    if not args.no_autotune:
-        for name, v in variants.items():
-            tuned[name] = v["plan"].autotune(w.lattice, geoms[0], reps=3)
-
+    if head != "fp64" and not args.no_autotune:   # launch shapes by the library's autotuner (untimed)
+        tuned[head] = plan.autotune(w.lattice, geoms[1], reps=2)
     for k in range(args.warmup):
-        plan.evaluate_device(w.lattice, d_pos[k].data_ptr(), d_out.data_ptr(), stats=True)
+        plan.evaluate_device(w.lattice, d_pos[1 + k].data_ptr(), d_out.data_ptr(), stats=True)
+        if reduce is not None:
+            reduce(d_out)
     st = plan.stats.as_dict()
 
-    # ---- device-resident timing of the headline precision (value)
+    # device-resident timing (value)
     clocks = ClockSampler(local)
     clocks.start()
     barrier()
-    t_dev = _time_device(plan, w, d_pos, d_out, args.warmup, args.steps, stream, torch)
+    first = 1 + args.warmup
+    t_dev = _time_device(plan, w, d_pos, d_out, first, args.steps, stream, torch, reduce)
     barrier()
     ck = clocks.stop()
     launches = st["kernel_launches"] * args.steps
 
-    # ---- end-to-end through the host entry point (H2D positions, D2H results)
+    # end to end through the host entry point (H2D positions, D2H results)
     pin_pos = [torch.tensor(g, dtype=torch.float64).pin_memory().numpy() for g in geoms]
     barrier()
     t0 = time.perf_counter()
     lat = []   # per request: host positions in -> E, F, sigma back on the host (the call is synchronous)
     for k in range(args.steps):
         tk = time.perf_counter()
-        plan.evaluate(w.lattice, pin_pos[args.warmup + k])
+        E, F, S = plan.evaluate(w.lattice, pin_pos[first + k])
+        if reduce is not None:
+            v = torch.from_numpy(shard.pack(E, F, S)).to(dev)
+            reduce(v)
+            v.cpu()
         lat.append(time.perf_counter() - tk)
     barrier()
     t_e2e = time.perf_counter() - t0
 
-    # ---- the other split precision (secondary line items)
-    other = {}
-    for name, v in variants.items():
-        if name == args.precision:
-            continue
-        pl = v["plan"]
-        pl.evaluate_device(w.lattice, d_pos[0].data_ptr(), d_out.data_ptr())
-        tt = _time_device(pl, w, d_pos, d_out, args.warmup, min(args.steps, 5), stream, torch) / min(args.steps, 5)
-        other[name] = {"evals_per_s": 1.0 / tt, "errE": v["errE"], "errF": v["errF"], "errS": v["errS"]}
-
-    # ---- per-stage times (CUDA events on the plan's stream)
+    # per-stage and per-kernel times (CUDA events on the plan's stream)
     plan.set_timing(True)
-    stage = {k: [] for k in ("ms_blocks", "ms_screen", "ms_y", "ms_term1", "ms_term2", "ms_reduce")}
-    flops = None
+    keys = ("ms_blocks", "ms_screen", "ms_y", "ms_term1", "ms_term2", "ms_reduce", "ms_term1_kernel",
+            "ms_term2_kernel", "ms_total")
+    stage = {k: [] for k in keys}
     for k in range(min(3, args.steps)):
-        plan.evaluate_device(w.lattice, d_pos[k].data_ptr(), d_out.data_ptr(), stats=True)
+        plan.evaluate_device(w.lattice, d_pos[first + k].data_ptr(), d_out.data_ptr(), stats=True)
         flops = plan.stats.as_dict()
-        for key in stage:
+        for key in keys:
             stage[key].append(flops[key])
     plan.set_timing(False)
     stage_ms = {k: statistics.mean(v) for k, v in stage.items()}
+    plan.close()
 
-    value, e2e_value, t_max = job_rates(args.steps, world, t_dev, t_e2e, dist, dev)
+    # ---- the other split precision (secondary line item)
+    other = {}
+    for name in ("bf16x6", "bf16x3"):
+        if name == head:
+            continue
+        pl = new_plan(name)
+        e = _errs(whole(pl, 0), ref)
+        pl.evaluate_device(w.lattice, d_pos[1].data_ptr(), d_out.data_ptr())
+        m = min(args.steps, 3)
+        tt = _time_device(pl, w, d_pos, d_out, first, m, stream, torch, reduce) / m
+        pl.close()
+        other[name] = {"evals_per_s": 1.0 / tt, **e}
+
+    t_max, t_e2e_max = max_over_ranks([t_dev, t_e2e], dist, dev)
+    value = args.steps / t_max          # whole evaluations of the structure per second
+    e2e_value = args.steps / t_e2e_max
 
     if rank == 0:
         peaks = measured_peaks()
         fp64_peak = fp64_gemm_peak(torch, dev)
-        dom = max(("y", "term1", "term2"), key=lambda k: stage_ms["ms_" + k])
-        dom_flops = flops["flops_" + dom]
-        dom_ms = stage_ms["ms_" + dom]
-        achieved = dom_flops / (dom_ms / 1e3) / 1e12
-        kname = {"y": "k_ybuild", "term1": "k_term1", "term2": "k_term2"}[dom]
-        if args.precision != "fp64":
-            kname = {"y": "k_ybuild_umma", "term1": "k_t1_umma", "term2": "k_term2_pairs+k_q2_umma"}[dom]
-        if args.precision == "fp64":
-            roofline = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                        "frac": achieved / fp64_peak, "traffic": None,
+        # the dominant kernel: the first exchange product's contraction (one launch per pass)
+        kflops = flops["flops_term1"]
+        kms = stage_ms["ms_term1_kernel"]
+        passes = flops["passes"]
+        achieved = kflops / (kms / 1e3) / 1e12
+        if head == "fp64":
+            roofline = {"kernel": "k_term1", "bound": "alu", "achieved": achieved, "peak": fp64_peak,
+                        "unit": "TFLOP/s", "frac": achieved / fp64_peak, "traffic": None,
                         "peak_source": "FP64 cuBLAS DGEMM 4096^3 measured in this run (FP64 pipe)"}
         else:
             pk = peaks.get("bf16_tflops_sustained") or 1717.3
-            pieces = 6 if args.precision == "bf16x6" else 3
-            roofline = {"kernel": kname, "bound": "tensor", "achieved": achieved, "peak": pk,
-                        "unit": "TFLOP/s", "frac": achieved / pk,
-                        "traffic": t1_traffic(args.precision) if kname == "k_t1_umma" else None,
-                        "traffic_source": f"profiles/k_t1_umma_si8_{args.precision}.md: dram read+write of one si8 "
-                                          "launch, scaled to si64 by kept triplets (bytes per launch)",
+            pieces = 6 if head == "bf16x6" else 3
+            tr = t1_traffic(head)
+            # DRAM bytes per launch: the capture's bytes per kept triplet times one launch's kept triplets
+            traffic = tr / SI64_TRIPLETS * (flops["triplets"] / passes) if tr is not None else None
+            roofline = {"kernel": "k_t1_umma", "bound": "tensor", "achieved": achieved, "peak": pk,
+                        "unit": "TFLOP/s", "frac": achieved / pk, "traffic": traffic,
+                        "launches_per_step": passes,
+                        "per_launch": f"{kflops / passes / 1e12:.3f} TFLOP algorithmic ({flops['triplets'] // passes} "
+                                      f"kept triplets) in {kms / passes:.1f} ms",
+                        "traffic_source": f"profiles/k_t1_umma_si8_{head}.md: DRAM read+write per kept triplet of "
+                                          "the capture, times the kept triplets of one launch (one pass)",
                         "peak_source": "bf16 dense, sustained, of measured (MEASURED_PEAKS.json)",
                         "note": f"achieved counts algorithmic FLOPs only; the {pieces} bf16 piece products per "
                                 f"multiply and the 13->16 / 50->64 tile padding are not counted",
                         "tensor_issue_tflops": achieved * pieces}
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
-            cpu = cpu_baseline(w, homes=1)
-        h2d = 3 * n * 8 + 9 * 8
+            cpu = cpu_baseline(n)
+        h2d = 3 * n * 8
         d2h = (1 + 3 * n + 9) * 8
-        head = variants.get(args.precision, {})
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None,
-                "dtype": "bf16" if args.precision != "fp64" else "f64",
+                "scaling": "strong" if world > 1 else "weak", "vs_baseline": None,
+                "dtype": "bf16" if head != "fp64" else "f64",
                 "data": "synthetic",
-                "config": {"workload": WORKLOAD, "precision": args.precision,
-                           "headline_rule": "bf16x3 if max(errE, errF, errS) <= 1e-5 vs FP64 GPU on 4 geometries, else bf16x6"
-                           if auto else "fixed by --precision",
+                "config": {"workload": WORKLOAD, "precision": head,
                            "arithmetic": "bf16 pieces on tensor cores, fp32 accumulate, fp64 screening/reduction"
-                           if args.precision != "fp64" else "fp64",
-                           "parallelism": f"replicas{world}" if world > 1 else "single",
-                           "l2": "working set > L2 (block, Y and Z stores of several GB per step)"},
+                           if head != "fp64" else "fp64",
+                           "parallelism": f"home-atom shards x{world} + all-reduce of E, F, sigma" if world > 1
+                           else "single",
+                           "passes": passes,
+                           "l2": "working set > L2 (Y stores of over 100 GB and per-pass operand stores each step)"},
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "latency": {"p50_ms": float(np.percentile(lat, 50)) * 1e3, "p99_ms": float(np.percentile(lat, 99)) * 1e3,
                             "requests": len(lat), "what": "one evaluation through the host entry point on an "
@@ -386,23 +457,21 @@ def run_ours(args):
                 "roofline": roofline,
                 "cpu_baseline": cpu,
                 "clocks": ck,
-                "error_vs_fp64": {k: head.get(k) for k in ("errE", "errF", "errS")} if head else None,
-                "fp64": {"evals_per_s": 1.0 / t_fp64, "speedup_of_headline": value / world * t_fp64},
+                "error_vs_fp64": head_err,
+                "fp64": {"evals_per_s": 1.0 / t_fp64, "speedup_of_headline": value * t_fp64,
+                         "term1_kernel_tflops": fp64_stats["flops_term1"] / fp64_stats["ms_term1_kernel"] / 1e9
+                         if fp64_stats["ms_term1_kernel"] > 0 else None},
                 "other_precisions": other,
                 "stages_ms": stage_ms,
                 "autotune": tuned,
                 "gflop_per_eval": flops["flops_total"] / 1e9,
                 "achieved_tflops_total": flops["flops_total"] / (t_max / args.steps) / 1e12,
                 "counts": {k: flops[k] for k in ("c_pairs", "v_pairs", "triplets", "term1_pairs",
-                                                 "term2_pairs", "y_blocks", "device_bytes")},
+                                                 "term2_pairs", "y_blocks", "device_bytes", "passes")},
                 "peaks": {"hbm_gbs": peaks.get("hbm_gbs"), "bf16_tflops": peaks.get("bf16_tflops"),
                           "bf16_tflops_sustained": peaks.get("bf16_tflops_sustained"),
                           "fp64_dgemm_tflops": fp64_peak}}
         print(json.dumps(line), flush=True)
-    for v in variants.values():
-        v["plan"].close()
-    if args.precision == "fp64":
-        plan.close()
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
@@ -416,7 +485,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--precision", default="auto", choices=["auto", "bf16x6", "bf16x3", "fp64"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "bf16x6", "bf16x3", "fp64"],
+                    help="headline precision; auto = bf16x6")
     ap.add_argument("--no-autotune", action="store_true", help="keep the plans' initial launch shapes")
     args = ap.parse_args()
     if args.impl == "reference":

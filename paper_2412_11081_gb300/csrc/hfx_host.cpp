@@ -1110,7 +1110,7 @@ void evaluate(hfx_plan* P, const double* L, hfx_stats* st) {
   }
   tm.mark();  // 3
   // ---- passes of home atoms: per-call operand stores and both exchange products
-  std::vector<int> m1, m2, m3;   // timer marks around each pass's products
+  std::vector<int> m1, m2, m3, k1a, k1b, k2a;   // timer marks around each pass's stages and kernels
   for (int c = 0; c < nch; ++c) {
     const int a0 = P->chunks[c].first, a1 = P->chunks[c].second;
     const int v0 = P->v_ptr_h[a0], c0 = P->c_ptr_h[a0];
@@ -1120,8 +1120,11 @@ void evaluate(hfx_plan* P, const double* L, hfx_stats* st) {
       ensure_store(P, P->Vst, P->Vcap, ct[CT_VE]);
       D.Vst = P->Vst;
       ck(hfx::launch_vblocks(D, P->v_list + v0, (int)ct[CT_VN], s), "vblocks");
+      k1a.push_back(tm.mark());
       ck(hfx::launch_term1(D, P->t1_list + v0, (int)ct[CT_T1], P->beta_chunk, P->smem_t1, s), "term1");
-      m2.push_back(tm.mark());
+      k1b.push_back(tm.mark());
+      m2.push_back(k1b.back());
+      k2a.push_back(k1b.back());
       ck(hfx::launch_term2(D, P->t2_list + v0, (int)ct[CT_T2], P->alpha_chunk, P->smem_t2, s), "term2");
     } else {
       ensure_buf(P, P->Vm, P->Vmcap, ct[CT_VM]);
@@ -1136,15 +1139,18 @@ void evaluate(hfx_plan* P, const double* L, hfx_stats* st) {
         U.Vu = P->Vu;
         ck(hfx::launch_t1u_stores(D, U, P->np, P->t1q_lpt + c0, (int)ct[CT_Q], false, s), "term-1 C store");
         ck(hfx::launch_vstores(D, X, U, P->np, P->v_list + v0, (int)ct[CT_VN], s), "V stores");
+        k1a.push_back(tm.mark());
         ck(hfx::launch_t1_umma(D, X, U, P->np, P->t1q_lpt + c0, (int)ct[CT_Q], P->smem_t1u, P->d_work, P->d_err, s),
            "term1");
       } else {
         ck(hfx::launch_vpieces(D, X, P->np, P->v_list + v0, (int)ct[CT_VN], s), "vpieces");
+        k1a.push_back(tm.mark());
         ck(hfx::launch_term1_mma(D, X, P->np, P->t1q_lpt + c0, (int)ct[CT_Q], P->MAmax, P->MBmax, P->KSmax, P->YRmax,
                                  P->smem_m1, s),
            "term1");
       }
-      m2.push_back(tm.mark());
+      k1b.push_back(tm.mark());
+      m2.push_back(k1b.back());
       if (ct[CT_T2] * P->zblk > P->Zcap) {
         ensure_buf(P, P->Zst, P->Zcap, ct[CT_T2] * P->zblk);
         ck(cudaMemsetAsync(P->Zst, 0, (size_t)P->Zcap * sizeof(uint16_t), s), "memset");   // tile padding rows stay zero
@@ -1156,6 +1162,7 @@ void evaluate(hfx_plan* P, const double* L, hfx_stats* st) {
       // test-only fault injection (see MixPlan::stall_q2)
       const char* stall = std::getenv("HFX_TEST_STALL_Q2_PRODUCER");
       X.stall_q2 = stall && stall[0] == '1' ? 1 : 0;
+      k2a.push_back(tm.mark());
       ck(hfx::launch_term2_mma(D, X, P->np, P->t2_list + v0, P->t2_idx, (int)ct[CT_T2], a0, a1, P->MAmax, P->KZmax,
                                P->zblk, P->ZROWS, FC, P->MC, hfx::q2_umma_segments(P->maxV, P->np), P->q2_flush,
                                P->drows, P->smem_m2, P->d_err, s),
@@ -1200,6 +1207,8 @@ void evaluate(hfx_plan* P, const double* L, hfx_stats* st) {
     for (int c = 0; c < nch; ++c) {
       S.ms_term1 += tm.ms(m1[c], m2[c]);
       S.ms_term2 += tm.ms(m2[c], m3[c]);
+      S.ms_term1_kernel += tm.ms(k1a[c], k1b[c]);
+      S.ms_term2_kernel += tm.ms(k2a[c], m3[c]);
     }
     S.ms_reduce = tm.ms(mr, me);
     S.ms_total = tm.ms(0, me);

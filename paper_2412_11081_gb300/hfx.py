@@ -62,6 +62,7 @@ class HfxStats(ct.Structure):
                 ("ms_screen", ct.c_double), ("ms_y", ct.c_double), ("ms_term1", ct.c_double),
                 ("ms_term2", ct.c_double), ("ms_reduce", ct.c_double), ("ms_total", ct.c_double),
                 ("device_bytes", ct.c_longlong), ("kernel_launches", ct.c_longlong), ("passes", ct.c_int),
+                ("ms_term1_kernel", ct.c_double), ("ms_term2_kernel", ct.c_double),
                 ("ref_err_E", ct.c_double), ("ref_err_F", ct.c_double), ("ref_err_sigma", ct.c_double)]
 
     def as_dict(self):

@@ -48,8 +48,12 @@ SHAPES: Dict[str, Callable] = {
     "si8": lambda seed, strain: inputs.si_supercell(1, seed=seed, strain_amp=strain),
     "si64": lambda seed, strain: inputs.si_supercell(2, seed=seed, strain_amp=strain),
     "si216": lambda seed, strain: inputs.si_supercell(3, seed=seed, strain_amp=strain),
+    "si512": lambda seed, strain: inputs.si_supercell(4, seed=seed, strain_amp=strain),
+    "si1000": lambda seed, strain: inputs.si_supercell(5, seed=seed, strain_amp=strain),
     "perovskite5": lambda seed, strain: inputs.perovskite_supercell(1, seed=seed, strain_amp=strain),
     "perovskite40": lambda seed, strain: inputs.perovskite_supercell(2, seed=seed, strain_amp=strain),
+    "perovskite135": lambda seed, strain: inputs.perovskite_supercell(3, seed=seed, strain_amp=strain),
+    "perovskite320": lambda seed, strain: inputs.perovskite_supercell(4, seed=seed, strain_amp=strain),
 }
 
 
@@ -73,6 +77,7 @@ class Record:
     end: float
     plan_ms: float                # plan creation inside this request (first step only)
     result: Optional[tuple] = None
+    device: Optional[tuple] = None   # (start, end) of its GPU work in s on the server's device clock
 
     @property
     def latency(self) -> float:
@@ -149,6 +154,7 @@ class Server:
                         plan_ms = (time.perf_counter() - tp) * 1e3
                     plan = plans[s.sid]
                     res = plan.evaluate(s.workload.lattice, s.geoms[k])
+                    dev_iv = plan.last_device_interval() if hasattr(plan, "last_device_interval") else None
                 except Exception as e:   # a failed request ends the run with its message
                     with cond:
                         errors.append(f"structure {s.sid} step {k}: {e}")
@@ -156,7 +162,7 @@ class Server:
                     return
                 end = clock()
                 rec = Record(s.sid, s.shape, k, plan.precision, issued, start, end, plan_ms,
-                             res if self.keep_results else None)
+                             res if self.keep_results else None, dev_iv)
                 last = k + 1 == len(s.geoms)
                 if k == 0:
                     b = float(plan.device_bytes())
@@ -217,6 +223,27 @@ class Server:
                                    for sid in admitted_at}, "known_bytes": known}
 
 
+def device_overlap(records: List[Record]) -> Optional[dict]:
+    """Concurrency of the requests' GPU work, from their device intervals:
+    the sum of the intervals over the time the GPU had at least one request
+    in flight (1 = no overlap; k = k requests in flight on average while
+    busy)."""
+    iv = sorted(r.device for r in records if r.device is not None)
+    if not iv:
+        return None
+    union, cur_s, cur_e = 0.0, iv[0][0], iv[0][1]
+    for s, e in iv[1:]:
+        if s > cur_e:
+            union += cur_e - cur_s
+            cur_s, cur_e = s, e
+        else:
+            cur_e = max(cur_e, e)
+    union += cur_e - cur_s
+    total = sum(e - s for s, e in iv)
+    return {"busy_s": union, "sum_of_request_device_s": total, "mean_requests_in_flight": total / union
+            if union > 0 else 0.0, "first_start_s": iv[0][0], "last_end_s": max(e for _, e in iv)}
+
+
 def summarize(out: dict, structures: List[Structure]) -> dict:
     recs: List[Record] = out["records"]
     lat = np.array([r.latency for r in recs]) * 1e3
@@ -230,9 +257,16 @@ def summarize(out: dict, structures: List[Structure]) -> dict:
     waits = np.array(list(out["admission_wait"].values())) * 1e3 if out["admission_wait"] else np.zeros(1)
     span = out["makespan"]
     last_arrival = max(s.arrival for s in structures) if structures else 0.0
+    ov = device_overlap(recs)
+    served = {r.sid for r in recs}
     return {"requests": len(recs), "structures": len(structures), "rejected": len(out["rejected"]),
             "makespan_s": span, "last_arrival_s": last_arrival,
             "throughput_req_s": len(recs) / span if span > 0 else 0.0,
+            "device_overlap": ov,
+            # the arrival rate this mix of shapes can be served at: the served
+            # structures over the time the GPU was busy with them (above it the
+            # queue grows without bound)
+            "sustainable_structures_per_s": len(served) / ov["busy_s"] if ov and ov["busy_s"] > 0 else None,
             "p50_ms": float(np.percentile(lat, 50)) if lat.size else None,
             "p99_ms": float(np.percentile(lat, 99)) if lat.size else None,
             "admission_wait_ms_p50": float(np.percentile(waits, 50)),
@@ -281,6 +315,7 @@ class GpuBackend:
         self.precision = precision
         self.code = {"fp64": hfx.HFX_FP64, "bf16x3": hfx.HFX_BF16X3, "bf16x6": hfx.HFX_BF16X6}[precision]
         self.device = device
+        self.clock0 = _DeviceClock(torch, device)
 
     def estimate_bytes(self, s: Structure, known: Dict[str, float]) -> float:
         if s.shape in known:
@@ -296,19 +331,48 @@ class GpuBackend:
         if code != hfx.HFX_FP64 and max(s.workload.n_ao) > 16:
             code, name = hfx.HFX_FP64, "fp64 (n_ao > 16)"
         plan = hfx.Plan(s.workload, precision=code, stream=stream.cuda_stream, device=self.device)
-        return _GpuPlan(plan, stream, name)
+        return _GpuPlan(plan, stream, name, self.clock0)
+
+
+class _DeviceClock:
+    """A CUDA event recorded once on the device: the time origin of every
+    request's device interval (elapsed time between events of different
+    streams of one device is well defined)."""
+
+    def __init__(self, torch, device):
+        self.torch = torch
+        with torch.cuda.device(device):
+            self.e = torch.cuda.Event(enable_timing=True)
+            self.e.record(torch.cuda.current_stream(device))
+            self.e.synchronize()
+
+    def since(self, ev) -> float:
+        return self.e.elapsed_time(ev) / 1e3
 
 
 class _GpuPlan:
-    def __init__(self, plan, stream, precision):
+    def __init__(self, plan, stream, precision, clock0):
         self.plan, self.stream, self.precision = plan, stream, precision
         self._bytes = None
+        self._clock0 = clock0
+        self._iv = None
 
     def evaluate(self, lattice, positions):
+        torch = self._clock0.torch
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(self.stream)
         E, F, S = self.plan.evaluate(lattice, positions, stats=self._bytes is None)
+        e1.record(self.stream)
+        e1.synchronize()
+        self._iv = (self._clock0.since(e0), self._clock0.since(e1))
         if self._bytes is None:
             self._bytes = int(self.plan.stats.device_bytes)
         return E, F, S
+
+    def last_device_interval(self):
+        """(start, end) of the last evaluation's GPU work, in s on the device
+        clock shared by every plan of the backend."""
+        return self._iv
 
     def device_bytes(self) -> int:
         return self._bytes or 0

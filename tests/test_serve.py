@@ -139,6 +139,18 @@ def test_summary_percentiles_and_alone_vs_mix():
     assert serve.alone_vs_mix(be, st, out["records"], 5) == 0.0   # the stand-in is deterministic
 
 
+def test_device_overlap_from_request_intervals():
+    """Requests in flight on the GPU at once: the sum of their device
+    intervals over the union of them."""
+    rec = lambda a, b: serve.Record(0, "x", 0, "p", 0.0, 0.0, 0.0, 0.0, None, (a, b))
+    ov = serve.device_overlap([rec(0.0, 1.0), rec(0.5, 1.5), rec(2.0, 3.0), rec(2.2, 2.4)])
+    assert ov["busy_s"] == pytest.approx(2.5)
+    assert ov["sum_of_request_device_s"] == pytest.approx(3.2)
+    assert ov["mean_requests_in_flight"] == pytest.approx(3.2 / 2.5)
+    assert serve.device_overlap([rec(0.0, 1.0)])["mean_requests_in_flight"] == pytest.approx(1.0)
+    assert serve.device_overlap([]) is None
+
+
 def test_failed_request_ends_the_run_with_its_message():
     st = fake_stream(4, 500.0, 2)
 
@@ -168,3 +180,7 @@ def test_gpu_stream_alone_vs_mix():
     assert precs.get("si8", "bf16x6") == "bf16x6"
     assert precs.get("perovskite5", "fp64 (n_ao > 16)") == "fp64 (n_ao > 16)"
     assert serve.alone_vs_mix(be, st, out["records"], 6) <= 1e-12
+    summ = serve.summarize(out, st)
+    ov = summ["device_overlap"]
+    assert ov is not None and ov["busy_s"] > 0 and ov["mean_requests_in_flight"] >= 1.0 - 1e-9
+    assert summ["sustainable_structures_per_s"] > 0
