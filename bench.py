@@ -386,6 +386,25 @@ def run_ours(args):
     stage_ms = {k: statistics.mean(v) for k, v in stage.items()}
     plan.close()
 
+    # ---- graph replay (hfx_options.graph): frozen plans of the headline
+    #      precision with and without it, the same steps
+    graph_cmp = {}
+    if not args.no_graph:
+        m = min(args.steps, 3)
+        for use_graph in (False, True):
+            pl = hfx.Plan(w, precision=PREC[head], stream=stream.cuda_stream, device=local, home=home,
+                          freeze_lists=True, graph=use_graph)
+            for k in range(2):   # the first call fixes the decisions, the second records the graph
+                pl.evaluate_device(w.lattice, d_pos[1 + k].data_ptr(), d_out.data_ptr())
+            barrier()
+            tt = _time_device(pl, w, d_pos, d_out, first, m, stream, torch, reduce) / m
+            pl.evaluate_device(w.lattice, d_pos[first].data_ptr(), d_out.data_ptr(), stats=True)
+            graph_cmp["graph" if use_graph else "direct"] = {"ms_per_eval": tt * 1e3,
+                                                             "graph_replayed": pl.stats.graph_replayed}
+            pl.close()
+        graph_cmp["what"] = ("frozen plans (screening decisions of the first call kept), the headline precision, "
+                             f"{m} steps each: every kernel launched per call vs one CUDA graph launch per call")
+
     # ---- the other split precision (secondary line item)
     other = {}
     for name in ("bf16x6", "bf16x3"):
@@ -462,6 +481,7 @@ def run_ours(args):
                          "term1_kernel_tflops": fp64_stats["flops_term1"] / fp64_stats["ms_term1_kernel"] / 1e9
                          if fp64_stats["ms_term1_kernel"] > 0 else None},
                 "other_precisions": other,
+                "graph_replay": graph_cmp,
                 "stages_ms": stage_ms,
                 "autotune": tuned,
                 "gflop_per_eval": flops["flops_total"] / 1e9,
@@ -488,6 +508,7 @@ def main():
     ap.add_argument("--precision", default="auto", choices=["auto", "bf16x6", "bf16x3", "fp64"],
                     help="headline precision; auto = bf16x6")
     ap.add_argument("--no-autotune", action="store_true", help="keep the plans' initial launch shapes")
+    ap.add_argument("--no-graph", action="store_true", help="skip the frozen-plan graph replay comparison")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -129,6 +129,17 @@ typedef struct {
    * they take (roughly proportional to it).  0 (the default) = 128; larger
    * values save a little launch overhead, smaller ones memory. */
   int home_chunk;
+  /* 1: replay the evaluations of a frozen plan (freeze_lists = 1) from a
+   * CUDA graph.  Once the first call has fixed the screening decisions and
+   * sized every store, an evaluation is a fixed sequence of launches whose
+   * inputs (positions, lattice) sit in device memory: the second call
+   * records it (stream capture on a stream of the plan's own, since the
+   * plan's stream may be the legacy default stream) and every later call
+   * launches the graph on the plan's stream.
+   * Per-stage timing (hfx_set_timing) evaluates without the graph;
+   * hfx_plan_autotune records a new one.  0 (the default): launch every
+   * kernel on each call. */
+  int graph;
   void* stream;       /* cudaStream_t for every launch and copy; NULL = legacy default */
   int device;         /* CUDA device ordinal */
   /* Device memory of the plan.  NULL (the default) = cudaMalloc / cudaFree.
@@ -163,6 +174,11 @@ typedef struct {
   long long kernel_launches;                    /* CUDA kernels this library launched during the call
                                                    (all threads: exact when one plan evaluates at a time) */
   int passes;                                   /* passes of home atoms (home_chunk) */
+  int graph_replayed;                           /* 1 if the call launched the plan's CUDA graph */
+  /* CUDA-event times (ms, with timing on) of the contraction kernels alone,
+   * summed over the passes: the first product's kernel (ms_term1 without
+   * the per-pass operand stores) and the second product's kernels. */
+  double ms_term1_kernel, ms_term2_kernel;
   /* Error of this result against the reference set by hfx_set_reference
    * (-1 when none is set): |E - E_ref| / |E_ref|, and max|x - x_ref| /
    * max|x_ref| over the entries of F and of sigma. */
@@ -247,7 +263,10 @@ hfx_status hfx_set_reference(hfx_plan* plan, const double* E, const double* F, c
  * the plan's later calls.  Today that is the shape of the tcgen05 first
  * product's Y ring (rows f per slot and number of slots, bounded by shared
  * memory): the shapes of the block pairs decide which run length balances
- * the copy of Y rows against the U build.  Each candidate is timed as the
+ * the copy of Y rows against the U build; then, with the best shape, the
+ * order in which its items are handed out (longest first, so that the SMs
+ * finish together, or by home atom, so that items running at the same time
+ * share their V_AB and grad V_AB blocks in L2).  Each candidate is timed as the
  * median of `reps` >= 1 evaluations (CUDA events) after one warm-up.
  * `report` (nullable) receives the choice and both times.  Plans without a
  * tunable kernel (FP64, or the warp-level first product) return HFX_OK
@@ -258,6 +277,8 @@ typedef struct {
   int t1_slots;            /* chosen number of Y slots */
   double default_ms;       /* median evaluation time with the initial choice */
   double best_ms;          /* median evaluation time with the chosen one */
+  int t1_home_order;       /* chosen order of the first product's items: 0 = longest
+                              first, 1 = by home atom */
 } hfx_tune_report;
 hfx_status hfx_plan_autotune(hfx_plan* plan, const double* lattice, const double* positions, int reps,
                              hfx_tune_report* report);

@@ -159,6 +159,7 @@ struct hfx_plan {
 
   // per-call state
   double* d_pos = nullptr;
+  double* d_lat = nullptr;     // [9] lattice of the current call
   double* d_out = nullptr;     // [1 + 3N + 9]
   double* d_acc = nullptr;     // hfx::ACC_N
   long long* d_tot = nullptr;  // [kTot] totals of the scans, then hfx::CNT_N counters
@@ -197,6 +198,7 @@ struct hfx_plan {
   long long *qoff = nullptr, *q_idx = nullptr;
   int* t1q_list = nullptr;
   int* t1q_lpt = nullptr;      // the same items, longest (most kept B) first
+  bool t1_home_order = false;  // first-product items in home-atom order instead of longest first
   int q2_flush = 32;           // pairs per FP32 run of the second product's Q2 accumulator (128 for BF16X6)
   uint16_t* YspT = nullptr;    // transposed Y pieces (second product)
   long long YspTcap = 0;
@@ -229,6 +231,9 @@ struct hfx_plan {
 
   bool timing = false;
   bool noalloc_call = false;   // set only inside hfx_energy_force_stress_noalloc
+  cudaGraphExec_t gexec = nullptr;   // recorded evaluation of a frozen plan (hfx_options.graph)
+  cudaStream_t cap_stream = nullptr; // the stream it is recorded on (the legacy stream cannot be captured)
+  long long graph_launches = 0;      // kernels in it
   std::vector<double> pos_host_buf;
   hfx_stats last{};
 
@@ -256,6 +261,7 @@ void validate_options(const hfx_options* o) {
   if (o->terms < 1 || o->terms > 3) fail(HFX_ERR_INVALID, "terms must be 1, 2 or 3");
   if (!std::isfinite(o->skin) || o->skin < 0) fail(HFX_ERR_INVALID, "skin must be finite and >= 0");
   if (o->home_chunk < 0) fail(HFX_ERR_INVALID, "home_chunk must be >= 0");
+  if (o->graph != 0 && o->graph != 1) fail(HFX_ERR_INVALID, "graph must be 0 or 1");
   if ((o->alloc == nullptr) != (o->free == nullptr)) fail(HFX_ERR_INVALID, "alloc and free must be set together");
 }
 
@@ -472,7 +478,7 @@ DevPlan make_devplan(hfx_plan* P, const double* lattice) {
   D.h0 = P->chunks.empty() ? 0 : P->chunks.front().first;
   D.h1 = P->chunks.empty() ? P->N : P->chunks.back().second;
   D.pos = P->d_pos;
-  for (int k = 0; k < 9; ++k) D.L[k] = lattice[k];
+  D.L = P->d_lat;   // the entry points copy the call's lattice there first
   D.n_d = P->n_d;
   D.Dval = P->d_Dval;
   D.Doff = P->d_Doff;
@@ -987,10 +993,65 @@ enum PassTot { CT_VE = 0, CT_VN = 1, CT_T1 = 2, CT_T2 = 3, CT_VM = 4, CT_Q = 5, 
 // home atoms (P->chunks), each pass with its own slice of the pair lists, so
 // those stores hold one pass at a time.  Every pass's totals are read back
 // with the global ones in the single host synchronisation after screening.
+long long launches_so_far() { return hfx::launch_count() + hfx::mixed_launch_count() + hfx::t1u_launch_count(); }
+
+void evaluate_launches(hfx_plan* P, const double* L, hfx_stats* st, bool tail = true);
+void finish_evaluation(hfx_plan* P, hfx_stats* st, hfx_stats S, long long launches);
+
+// One evaluation.  positions are in P->d_pos already; writes d_out.
+//
+// A frozen plan with hfx_options.graph records its second evaluation (the
+// first one fixed the screening decisions and sized every store, so the
+// launches no longer depend on the host) into a CUDA graph and launches that
+// graph on later calls; the positions and the lattice are read from device
+// memory, written before the launch.
 void evaluate(hfx_plan* P, const double* L, hfx_stats* st) {
   cudaStream_t s = P->stream;
+  ck(cudaMemcpyAsync(P->d_lat, L, 9 * sizeof(double), cudaMemcpyHostToDevice, s), "H2D lattice");
+  const bool reuse = P->opt.freeze_lists && P->frozen_ready;
+  const bool graph = P->opt.graph && reuse && !P->timing && !P->noalloc_call;
+  if (!graph) {
+    evaluate_launches(P, L, st);
+    if (st) st->graph_replayed = 0;
+    return;
+  }
+  if (!P->gexec) {
+    // record on a stream of the plan's own (the plan's stream may be the
+    // legacy default stream, which cannot be captured); the graph is then
+    // launched on the plan's stream, after the lattice copy above
+    if (!P->cap_stream) ck(cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking), "capture stream");
+    cudaGraph_t g = nullptr;
+    const long long l0 = launches_so_far();
+    cudaStream_t own = P->stream;
+    P->stream = P->cap_stream;
+    ck(cudaStreamBeginCapture(P->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    try {
+      evaluate_launches(P, L, nullptr, false);
+    } catch (...) {
+      cudaStreamEndCapture(P->cap_stream, &g);
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      P->stream = own;
+      throw;
+    }
+    P->stream = own;
+    ck(cudaStreamEndCapture(P->cap_stream, &g), "end capture");
+    const cudaError_t e = cudaGraphInstantiate(&P->gexec, g, 0);
+    cudaGraphDestroy(g);
+    ck(e, "graph instantiate");
+    P->graph_launches = launches_so_far() - l0;
+  }
+  ck(cudaGraphLaunch(P->gexec, s), "graph launch");
+  finish_evaluation(P, st, hfx_stats{}, P->graph_launches);
+  if (st) st->graph_replayed = 1;
+}
+
+// The launches of one evaluation (see evaluate); with tail, also the
+// error-flag check and the stats.
+void evaluate_launches(hfx_plan* P, const double* L, hfx_stats* st, bool tail) {
+  cudaStream_t s = P->stream;
   DevPlan D = make_devplan(P, L);
-  const long long launches0 = hfx::launch_count() + hfx::mixed_launch_count() + hfx::t1u_launch_count();
+  const long long launches0 = launches_so_far();
   hfx::MixPlan X{P->Dsp, P->dsp_off, P->Ysp, P->Cm, P->cm_off, P->Vm, P->vm_off, P->Zst, P->qcnt, P->qoff, P->blist};
   const bool reuse = P->opt.freeze_lists && P->frozen_ready;
   const int nch = (int)P->chunks.size();
@@ -1060,9 +1121,12 @@ void evaluate(hfx_plan* P, const double* L, hfx_stats* st) {
     ck(cudaMemcpyAsync(P->tot, P->d_tot, kTot * sizeof(long long), cudaMemcpyDeviceToHost, s), "D2H totals");
     ck(cudaMemcpyAsync(P->ctot.data(), CT, P->ctot.size() * sizeof(long long), cudaMemcpyDeviceToHost, s),
        "D2H pass totals");
+    ck(cudaMemcpyAsync(P->cnt, P->d_tot + kTot, hfx::CNT_N * sizeof(long long), cudaMemcpyDeviceToHost, s),
+       "D2H counts");
+    ck(cudaStreamSynchronize(s), "screening");
   }
-  ck(cudaMemcpyAsync(P->cnt, P->d_tot + kTot, hfx::CNT_N * sizeof(long long), cudaMemcpyDeviceToHost, s), "D2H counts");
-  ck(cudaStreamSynchronize(s), "screening");
+  // (with frozen decisions the totals and counts of the first call stand, and
+  // nothing here waits for the device)
   if (dnorm_now) {
     P->d_kept = (long long)P->cnt[hfx::CNT_D];
     P->dnorm_done = true;
@@ -1111,6 +1175,10 @@ void evaluate(hfx_plan* P, const double* L, hfx_stats* st) {
   tm.mark();  // 3
   // ---- passes of home atoms: per-call operand stores and both exchange products
   std::vector<int> m1, m2, m3, k1a, k1b, k2a;   // timer marks around each pass's stages and kernels
+  // first-product items: longest first (the last ones handed out are short),
+  // or in home-atom order (items running at the same time share their V_AB,
+  // grad V_AB in L2); the autotuner picks
+  const int* t1items = P->t1_home_order ? P->t1q_list : P->t1q_lpt;
   for (int c = 0; c < nch; ++c) {
     const int a0 = P->chunks[c].first, a1 = P->chunks[c].second;
     const int v0 = P->v_ptr_h[a0], c0 = P->c_ptr_h[a0];
@@ -1137,15 +1205,15 @@ void evaluate(hfx_plan* P, const double* L, hfx_stats* st) {
         ensure_buf(P, P->Vu, P->Vucap, std::max(1LL, ct[CT_T1]) * U.vu_blk);
         U.Cu = P->Cu;
         U.Vu = P->Vu;
-        ck(hfx::launch_t1u_stores(D, U, P->np, P->t1q_lpt + c0, (int)ct[CT_Q], false, s), "term-1 C store");
+        ck(hfx::launch_t1u_stores(D, U, P->np, t1items + c0, (int)ct[CT_Q], false, s), "term-1 C store");
         ck(hfx::launch_vstores(D, X, U, P->np, P->v_list + v0, (int)ct[CT_VN], s), "V stores");
         k1a.push_back(tm.mark());
-        ck(hfx::launch_t1_umma(D, X, U, P->np, P->t1q_lpt + c0, (int)ct[CT_Q], P->smem_t1u, P->d_work, P->d_err, s),
+        ck(hfx::launch_t1_umma(D, X, U, P->np, t1items + c0, (int)ct[CT_Q], P->smem_t1u, P->d_work, P->d_err, s),
            "term1");
       } else {
         ck(hfx::launch_vpieces(D, X, P->np, P->v_list + v0, (int)ct[CT_VN], s), "vpieces");
         k1a.push_back(tm.mark());
-        ck(hfx::launch_term1_mma(D, X, P->np, P->t1q_lpt + c0, (int)ct[CT_Q], P->MAmax, P->MBmax, P->KSmax, P->YRmax,
+        ck(hfx::launch_term1_mma(D, X, P->np, t1items + c0, (int)ct[CT_Q], P->MAmax, P->MBmax, P->KSmax, P->YRmax,
                                  P->smem_m1, s),
            "term1");
       }
@@ -1174,33 +1242,10 @@ void evaluate(hfx_plan* P, const double* L, hfx_stats* st) {
   ck(cudaMemsetAsync(P->d_out, 0, (1 + 3 * (size_t)P->N + 9) * sizeof(double), s), "memset");
   ck(hfx::launch_reduce(D, P->d_out, s), "reduce");
   const int me = tm.mark();
-  if (P->np) {
-    int errflag = 0;
-    ck(cudaMemcpyAsync(&errflag, P->d_err, sizeof(int), cudaMemcpyDeviceToHost, s), "D2H error flag");
-    ck(cudaStreamSynchronize(s), "error flag");
-    if (errflag) {
-      ck(cudaMemsetAsync(P->d_err, 0, sizeof(int), s), "memset");
-      fail(HFX_ERR_TIMEOUT, "a tensor-core pipeline wait ran out (results discarded)");
-    }
-  }
+  if (!tail) return;   // recorded into a graph: the caller finishes after the launch
+  hfx_stats S{};
   if (st) {
-    double acc[hfx::ACC_N];
-    ck(cudaMemcpyAsync(acc, P->d_acc, sizeof(acc), cudaMemcpyDeviceToHost, s), "D2H acc");
-    ck(cudaStreamSynchronize(s), "stats");
-    hfx_stats S{};
-    S.c_pairs = (long long)P->cnt[hfx::CNT_C];
-    S.v_pairs = (long long)P->cnt[hfx::CNT_V];
-    S.d_blocks = P->d_kept;
-    S.triplets = (long long)P->cnt[hfx::CNT_TRIP];
-    for (int c = 0; c < nch; ++c) {
-      S.term1_pairs += P->ctot[(size_t)kCT * c + CT_T1];
-      S.term2_pairs += P->ctot[(size_t)kCT * c + CT_T2];
-    }
-    S.y_blocks = P->tot[1];
-    S.flops_y = acc[hfx::ACC_FY];
-    S.flops_term1 = acc[hfx::ACC_F1];
-    S.flops_term2 = acc[hfx::ACC_F2];
-    S.flops_total = S.flops_y + S.flops_term1 + S.flops_term2;
+    ck(cudaStreamSynchronize(s), "stats");   // the events are complete
     S.ms_blocks = tm.ms(0, 1);
     S.ms_screen = tm.ms(1, 2);
     S.ms_y = tm.ms(2, 3);
@@ -1212,12 +1257,48 @@ void evaluate(hfx_plan* P, const double* L, hfx_stats* st) {
     }
     S.ms_reduce = tm.ms(mr, me);
     S.ms_total = tm.ms(0, me);
-    S.device_bytes = P->mem.bytes;
-    S.kernel_launches = hfx::launch_count() + hfx::mixed_launch_count() + hfx::t1u_launch_count() - launches0;
-    S.passes = nch;
-    S.ref_err_E = S.ref_err_F = S.ref_err_sigma = -1.0;
-    *st = S;
   }
+  finish_evaluation(P, st, S, launches_so_far() - launches0);
+}
+
+// After the launches of an evaluation: the tensor-core pipelines' error flag
+// (split path) and the counters of hfx_stats (S carries the stage times).
+void finish_evaluation(hfx_plan* P, hfx_stats* st, hfx_stats S, long long launches) {
+  cudaStream_t s = P->stream;
+  if (P->np) {
+    int errflag = 0;
+    ck(cudaMemcpyAsync(&errflag, P->d_err, sizeof(int), cudaMemcpyDeviceToHost, s), "D2H error flag");
+    ck(cudaStreamSynchronize(s), "error flag");
+    if (errflag) {
+      ck(cudaMemsetAsync(P->d_err, 0, sizeof(int), s), "memset");
+      fail(HFX_ERR_TIMEOUT, "a tensor-core pipeline wait ran out (results discarded)");
+    }
+  }
+  if (!st) return;
+  double acc[hfx::ACC_N];
+  ck(cudaMemcpyAsync(acc, P->d_acc, sizeof(acc), cudaMemcpyDeviceToHost, s), "D2H acc");
+  ck(cudaStreamSynchronize(s), "stats");
+  const int nch = (int)P->chunks.size();
+  S.c_pairs = (long long)P->cnt[hfx::CNT_C];
+  S.v_pairs = (long long)P->cnt[hfx::CNT_V];
+  S.d_blocks = P->d_kept;
+  S.triplets = (long long)P->cnt[hfx::CNT_TRIP];
+  S.term1_pairs = S.term2_pairs = 0;
+  for (int c = 0; c < nch; ++c) {
+    S.term1_pairs += P->ctot[(size_t)kCT * c + CT_T1];
+    S.term2_pairs += P->ctot[(size_t)kCT * c + CT_T2];
+  }
+  S.y_blocks = P->tot[1];
+  S.flops_y = acc[hfx::ACC_FY];
+  S.flops_term1 = acc[hfx::ACC_F1];
+  S.flops_term2 = acc[hfx::ACC_F2];
+  S.flops_total = S.flops_y + S.flops_term1 + S.flops_term2;
+  S.device_bytes = P->mem.bytes;
+  S.kernel_launches = launches;
+  S.passes = nch;
+  S.graph_replayed = 0;
+  S.ref_err_E = S.ref_err_F = S.ref_err_sigma = -1.0;
+  *st = S;
 }
 
 // Relative errors of a result (host [E, F, sigma]) against the plan's reference.
@@ -1284,6 +1365,7 @@ hfx_status hfx_default_options(hfx_options* o) {
   o->freeze_lists = 0;
   o->home_begin = o->home_end = 0;
   o->home_chunk = 0;
+  o->graph = 0;
   o->stream = nullptr;
   o->device = 0;
   return HFX_OK;
@@ -1336,6 +1418,8 @@ hfx_status hfx_plan_create(const hfx_system* sys, const hfx_model* model, const 
     upload_model(P, sys, model);
     upload_density(P, model);
     P->d_pos = P->mem.alloc<double>(3 * (size_t)P->N);
+    P->d_lat = P->mem.alloc<double>(9);
+    ck(cudaMemcpy(P->d_lat, sys->lattice, 9 * sizeof(double), cudaMemcpyHostToDevice), "H2D lattice");
     P->d_out = P->mem.alloc<double>(1 + 3 * (size_t)P->N + 9);
     P->d_acc = P->mem.alloc<double>(hfx::ACC_N);
     const size_t ntot = kTot + hfx::CNT_N + (size_t)kCT * npass;
@@ -1439,6 +1523,7 @@ hfx_status hfx_plan_autotune(hfx_plan* P, const double* lattice, const double* p
   hfx_tune_report R{};
   R.t1_rows_per_slot = P->t1u_FS;
   R.t1_slots = P->t1u_NS;
+  R.t1_home_order = P->t1_home_order ? 1 : 0;
   if (!P->t1u) {
     if (report) *report = R;
     return HFX_OK;
@@ -1450,6 +1535,10 @@ hfx_status hfx_plan_autotune(hfx_plan* P, const double* lattice, const double* p
     P->t1u_FS = fs;
     P->t1u_NS = ns;
     P->smem_t1u = hfx::t1u_smem(P->np, P->t1u_KP, ns, fs);
+    if (P->gexec) {   // a recorded evaluation has the old launch shape
+      cudaGraphExecDestroy(P->gexec);
+      P->gexec = nullptr;
+    }
   };
   std::vector<double> F(3 * (size_t)P->N);
   double E = 0.0, sig[9];
@@ -1486,15 +1575,34 @@ hfx_status hfx_plan_autotune(hfx_plan* P, const double* lattice, const double* p
       best_ns = ns;
     }
   }
+  // the order of the items, with the best ring shape
+  const bool order0 = P->t1_home_order;
+  bool best_order = order0;
+  if (ok) {
+    use(best_fs, best_ns);
+    P->t1_home_order = !order0;
+    double ms = 0.0;
+    ok = time_it(ms);
+    if (ok) {
+      ++R.candidates;
+      if (ms < R.best_ms) {
+        R.best_ms = ms;
+        best_order = !order0;
+      }
+    }
+    P->t1_home_order = best_order;
+  }
   P->timing = timing0;
   if (!ok) {   // keep the initial choice
     use(fs0, ns0);
     P->smem_t1u = smem0;
+    P->t1_home_order = order0;
     return status;
   }
   use(best_fs, best_ns);
   R.t1_rows_per_slot = best_fs;
   R.t1_slots = best_ns;
+  R.t1_home_order = best_order ? 1 : 0;
   if (report) *report = R;
   return HFX_OK;
 }
@@ -1503,6 +1611,8 @@ hfx_status hfx_plan_destroy(hfx_plan* P) {
   if (!P) return HFX_OK;
   cudaSetDevice(P->dev);
   cudaStreamSynchronize(P->stream);
+  if (P->gexec) cudaGraphExecDestroy(P->gexec);
+  if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
   P->scan_tmp.mem.put(P->scan_tmp.buf, P->scan_tmp.cap * sizeof(long long));
   P->mem.free_all();
   delete P;

@@ -45,7 +45,7 @@ struct DevPlan {
   int h0, h1;                  // home atoms A whose items are screened in: [h0, h1)
 
   const double* pos;           // [N*3] current positions
-  double L[9];                 // current lattice (rows)
+  const double* L;             // [9] current lattice (rows), device memory (written before each evaluation)
 
   // density matrix
   long long n_d;

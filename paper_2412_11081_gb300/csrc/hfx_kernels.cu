@@ -648,7 +648,9 @@ __global__ void k_reduce_pairs(DevPlan P, double* F) {
 
 __global__ void k_finish(DevPlan P, double* out) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const double L[9] = {P.L[0], P.L[1], P.L[2], P.L[3], P.L[4], P.L[5], P.L[6], P.L[7], P.L[8]};
+  double L[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) L[k] = P.L[k];
   const double det = L[0] * (L[4] * L[8] - L[5] * L[7]) - L[1] * (L[3] * L[8] - L[5] * L[6]) +
                      L[2] * (L[3] * L[7] - L[4] * L[6]);
   const double vol = fabs(det);

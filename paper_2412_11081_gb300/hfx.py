@@ -45,13 +45,14 @@ class HfxOptions(ct.Structure):
                 ("theta_dV", ct.c_double), ("theta_D", ct.c_double), ("theta_CS", ct.c_double),
                 ("precision", ct.c_int), ("terms", ct.c_int), ("skin", ct.c_double),
                 ("freeze_lists", ct.c_int), ("home_begin", ct.c_int), ("home_end", ct.c_int),
-                ("home_chunk", ct.c_int), ("stream", ct.c_void_p), ("device", ct.c_int), ("alloc", ALLOC_FN),
+                ("home_chunk", ct.c_int), ("graph", ct.c_int), ("stream", ct.c_void_p), ("device", ct.c_int),
+                ("alloc", ALLOC_FN),
                 ("free", FREE_FN), ("alloc_ctx", ct.c_void_p)]
 
 
 class HfxTuneReport(ct.Structure):
     _fields_ = [("candidates", ct.c_int), ("t1_rows_per_slot", ct.c_int), ("t1_slots", ct.c_int),
-                ("default_ms", ct.c_double), ("best_ms", ct.c_double)]
+                ("default_ms", ct.c_double), ("best_ms", ct.c_double), ("t1_home_order", ct.c_int)]
 
 
 class HfxStats(ct.Structure):
@@ -62,6 +63,7 @@ class HfxStats(ct.Structure):
                 ("ms_screen", ct.c_double), ("ms_y", ct.c_double), ("ms_term1", ct.c_double),
                 ("ms_term2", ct.c_double), ("ms_reduce", ct.c_double), ("ms_total", ct.c_double),
                 ("device_bytes", ct.c_longlong), ("kernel_launches", ct.c_longlong), ("passes", ct.c_int),
+                ("graph_replayed", ct.c_int),
                 ("ms_term1_kernel", ct.c_double), ("ms_term2_kernel", ct.c_double),
                 ("ref_err_E", ct.c_double), ("ref_err_F", ct.c_double), ("ref_err_sigma", ct.c_double)]
 
@@ -143,7 +145,8 @@ class Plan:
 
     def __init__(self, w, *, precision: int = HFX_FP64, terms: int = 3, skin: float = 0.5,
                  freeze_lists: bool = False, stream: Optional[int] = None, device: int = 0,
-                 theta: Optional[dict] = None, aniso=None, allocator=None, home=None, home_chunk: int = 0):
+                 theta: Optional[dict] = None, aniso=None, allocator=None, home=None, home_chunk: int = 0,
+                 graph: bool = False):
         self.lib = load_library()
         th = dict(w.theta) if theta is None else dict(theta)
         if stream is None:
@@ -152,7 +155,7 @@ class Plan:
         self.opts = default_options(theta_C=th["C"], theta_dC=th["dC"], theta_V=th["V"], theta_dV=th["dV"],
                                     theta_D=th["D"], theta_CS=th["CS"], precision=precision, terms=terms,
                                     skin=skin, freeze_lists=int(freeze_lists), stream=stream, device=device,
-                                    home_begin=hb, home_end=he, home_chunk=int(home_chunk))
+                                    home_begin=hb, home_end=he, home_chunk=int(home_chunk), graph=int(graph))
         # allocator="torch": the plan's device memory comes from PyTorch's
         # caching allocator (hfx_options alloc / free); a pair of callables
         # (alloc(nbytes) -> device address or 0, free(address, nbytes)) is

@@ -31,6 +31,7 @@ def test_autotune_keeps_results_and_picks_the_fastest(case, prec):
         assert rep["candidates"] >= 2
         assert 0 < rep["best_ms"] <= rep["default_ms"]
         assert rep["t1_rows_per_slot"] >= 1 and rep["t1_slots"] >= 2
+        assert rep["t1_home_order"] in (0, 1)
         E1, F1, S1 = p.evaluate(w.lattice, w.positions)
     assert abs(E1 - E0) <= 1e-12 * abs(E0) and rel(F1, F0) <= 1e-12 and rel(S1, S0) <= 1e-12
 
