@@ -1,8 +1,8 @@
 """Build libhfx.so in-tree with nvcc for sm_103a (GB300).
 
-Four translation units compiled in parallel: the FP64 kernels, the
-split-precision kernels, the tcgen05 first-product kernel and the C++ host
-planner/ABI.  The result is written next to this file.
+Five translation units compiled in parallel: the FP64 kernels, the
+split-precision kernels, the tcgen05 first-product kernel, the split-precision
+kernels for wide blocks and the C++ host planner/ABI.  The result is written next to this file.
 """
 from __future__ import annotations
 
@@ -37,6 +37,8 @@ def build(verbose: bool = False) -> str:
                         "-c", os.path.join(CSRC, "hfx_mixed.cu")],
         "hfx_t1umma.o": [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", *inc,
                          "-c", os.path.join(CSRC, "hfx_t1umma.cu")],
+        "hfx_wide.o": [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", *inc,
+                       "-c", os.path.join(CSRC, "hfx_wide.cu")],
         "hfx_host.o": [nvcc, *ARCH, "-O2", "-std=c++17", "-Xcompiler", "-fPIC", *inc,
                        "-x", "cu", "-c", os.path.join(CSRC, "hfx_host.cpp")],
     }

@@ -228,6 +228,12 @@ struct hfx_plan {
   long long Yfcap = 0;
   float* Df = nullptr;
   int* d_work = nullptr;       // item counter of the tcgen05 first-product kernel
+  // split path for n_ao > 16 (hfx_wide.cu): FP64 C, V and D blocks, FP32 Y store
+  bool wide = false;
+  hfx::WideShapes ws{};
+  int wide_RB = 0;             // 64-row blocks of the largest Y block
+  float* Yw = nullptr;
+  long long Ywcap = 0;
 
   bool timing = false;
   bool noalloc_call = false;   // set only inside hfx_energy_force_stress_noalloc
@@ -654,7 +660,7 @@ void build_lists(hfx_plan* P, const double* L, const double* pos) {
     v_size[p] = 4ll * P->n_abf[P->species[v_home[p]]] * P->n_abf[P->species[v_j[p]]];
   for (int y = 0; y < nY; ++y) {
     const int sX = P->species[y_home[y]], sz = P->species[y_j[y]];
-    if (P->np)  // bf16 pieces of [alpha][z][rup16(n_ao(X))]
+    if (P->np && !P->wide)  // bf16 pieces of [alpha][z][rup16(n_ao(X))]
       y_size[y] = (long long)P->np * P->n_abf[sX] * P->n_ao[sz] * ((P->n_ao[sX] + 15) / 16 * 16);
     else
       y_size[y] = (long long)P->n_abf[sX] * P->n_ao[sX] * P->n_ao[sz];
@@ -675,11 +681,12 @@ void build_lists(hfx_plan* P, const double* L, const double* pos) {
   P->c_j = P->lalloc<int>(nC);
   P->c_R = P->lalloc<int>(3 * (size_t)nC);
   P->c_off = P->lalloc<long long>(nC + 1);
-  // FP64 C blocks: the FP64 path only (the split path evaluates C from the
-  // model where it writes its operand stores)
-  P->Cst = P->lalloc<double>(P->np ? 1 : P->c_elems);
+  // FP64 C blocks: the FP64 path and the wide split path only (the other
+  // split path evaluates C from the model where it writes its operand stores)
+  const bool fp64_c = !P->np || P->wide;
+  P->Cst = P->lalloc<double>(fp64_c ? P->c_elems : 1);
   P->c_sc = P->lalloc<double>(8 * (size_t)nC);
-  P->dCst = P->lalloc<double>(P->np ? 1 : 3 * P->c_elems);
+  P->dCst = P->lalloc<double>(fp64_c ? 3 * P->c_elems : 1);
   P->c_norm = P->lalloc<double>(nC);
   P->c_keep = P->lalloc<unsigned char>(nC);
   P->v_ptr = P->lalloc<int>(N + 1);
@@ -714,7 +721,14 @@ void build_lists(hfx_plan* P, const double* L, const double* pos) {
   P->y_list = P->lalloc<int>(nY);
   P->gC = P->lalloc<double>(3 * (size_t)nC);
   P->gV = P->lalloc<double>(3 * (size_t)nV);
-  if (P->np) {
+  if (P->np) {   // key groups of the Y build
+    P->gcnt = P->lalloc<int>(N);
+    P->goff = P->lalloc<long long>(N);
+    P->gX = P->lalloc<int>(nY);
+    P->gS = P->lalloc<int>(nY);
+    P->gN = P->lalloc<int>(nY);
+  }
+  if (P->np && !P->wide) {
     std::vector<long long> cm_off(nC + 1, 0), vm_size(nV);
     for (int p = 0; p < nC; ++p) {
       const int sA = P->species[c_home[p]], sj = P->species[c_j[p]];
@@ -733,11 +747,6 @@ void build_lists(hfx_plan* P, const double* L, const double* pos) {
     P->vm_size = P->lalloc<long long>(nV);
     upload(P->cm_off, cm_off, s);
     upload(P->vm_size, vm_size, s);
-    P->gcnt = P->lalloc<int>(N);
-    P->goff = P->lalloc<long long>(N);
-    P->gX = P->lalloc<int>(nY);
-    P->gS = P->lalloc<int>(nY);
-    P->gN = P->lalloc<int>(nY);
     P->qcnt = P->lalloc<int>(nC);
     P->qoff = P->lalloc<long long>(nC);
     P->q_idx = P->lalloc<long long>(nC);
@@ -821,6 +830,17 @@ void setup_shapes(hfx_plan* P) {
   P->alpha_chunk = (int)std::min<size_t>(maxABF, (limit - base2) / per1);
   P->smem_t2 = base2 + per1 * P->alpha_chunk;
   ck(hfx::set_kernel_smem_limits(), "smem attributes");
+  if (P->np && maxAO > 16) {
+    // n_ao beyond the 16-column tiles of the tensor-memory kernels: the wide kernels
+    P->wide = true;
+    P->ws = hfx::wide_shapes(P->np, maxABF, maxAO, limit);
+    if (!P->ws.ok) fail(HFX_ERR_UNSUPPORTED, "block shapes too large for the split-precision kernels");
+    int maxrows = 0;
+    for (int a = 0; a < P->S; ++a) maxrows = std::max(maxrows, P->n_abf[a] * P->n_ao[a]);
+    P->wide_RB = hfx::wide_ybuild_row_blocks(maxrows);
+    ck(hfx::set_wide_smem_limits(P->np), "smem attributes");
+    return;
+  }
   if (P->np) {
     auto r16 = [](int x) { return (x + 15) / 16 * 16; };
     int maxKAF = 0, zrows = 0;
@@ -890,7 +910,7 @@ void setup_shapes(hfx_plan* P) {
 
 // bf16 pieces of every D block (fixed for the plan)
 void split_density(hfx_plan* P) {
-  if (!P->np || P->n_d == 0) return;
+  if (!P->np || P->wide || P->n_d == 0) return;
   std::vector<long long> off(P->n_d + 1, 0);
   for (long long k = 0; k < P->n_d; ++k) {
     const int* r = &P->d_index[5 * k];
@@ -993,7 +1013,9 @@ enum PassTot { CT_VE = 0, CT_VN = 1, CT_T1 = 2, CT_T2 = 3, CT_VM = 4, CT_Q = 5, 
 // home atoms (P->chunks), each pass with its own slice of the pair lists, so
 // those stores hold one pass at a time.  Every pass's totals are read back
 // with the global ones in the single host synchronisation after screening.
-long long launches_so_far() { return hfx::launch_count() + hfx::mixed_launch_count() + hfx::t1u_launch_count(); }
+long long launches_so_far() {
+  return hfx::launch_count() + hfx::mixed_launch_count() + hfx::t1u_launch_count() + hfx::wide_launch_count();
+}
 
 void evaluate_launches(hfx_plan* P, const double* L, hfx_stats* st, bool tail = true);
 void finish_evaluation(hfx_plan* P, hfx_stats* st, hfx_stats S, long long launches);
@@ -1068,8 +1090,9 @@ void evaluate_launches(hfx_plan* P, const double* L, hfx_stats* st, bool tail) {
   const bool dnorm_now = !P->dnorm_done;
   if (dnorm_now) ck(hfx::launch_dnorm(D, s), "dnorm");
   // the split path evaluates C from the block model where it stores the
-  // operands; only the FP64 path writes the FP64 C blocks
-  if (P->np)
+  // operands; the FP64 path and the wide split path write the FP64 C blocks
+  const bool split = P->np && !P->wide;
+  if (split)
     ck(hfx::launch_cnorm(D, reuse ? 1 : 0, s), "cnorm");
   else
     ck(hfx::launch_cblocks(D, reuse ? 1 : 0, s), "cblocks");
@@ -1097,15 +1120,17 @@ void evaluate_launches(hfx_plan* P, const double* L, hfx_stats* st, bool tail) {
       ck(hfx::scan_flags(nullptr, nullptr, nullptr, P->v_t2 + v0, 3, nv, P->t2_idx + v0, ct + CT_T2, P->scan_tmp, s),
          "scan");
       ck(hfx::scatter_list(nullptr, nullptr, P->v_t2 + v0, 3, nv, P->t2_idx + v0, P->t2_list + v0, v0, s), "scatter");
-      if (P->np)
+      if (split)
         ck(hfx::scan_flags(P->v_flag + v0, P->vm_size + v0, nullptr, nullptr, 1, nv, P->vm_off + v0, ct + CT_VM,
                            P->scan_tmp, s), "scan");
     }
-    if (P->np) {
-      // (A,F) view of the kept triplets: per C pair, its kept B in V-pair order
+    if (P->np) {   // groups of up to 8 needed keys of one home atom (the Y build's CTAs)
       ck(hfx::launch_ygroups(D, P->y_idx, T + 1, P->gcnt, nullptr, nullptr, nullptr, nullptr, 0, s), "ygroups");
       ck(hfx::scan_flags(P->gcnt, nullptr, nullptr, nullptr, 4, P->N, P->goff, T + 9, P->scan_tmp, s), "scan");
       ck(hfx::launch_ygroups(D, P->y_idx, T + 1, P->gcnt, P->goff, P->gX, P->gS, P->gN, 1, s), "ygroups");
+    }
+    if (split) {
+      // (A,F) view of the kept triplets: per C pair, its kept B in V-pair order
       ck(hfx::launch_t1_lists(D, X, 0, s), "t1 count");
       ck(hfx::scan_flags(P->qcnt, nullptr, nullptr, nullptr, 4, P->nC, P->qoff, T + 6, P->scan_tmp, s), "scan");
       for (int c = 0; c < nch; ++c) {   // per pass: its items, longest first
@@ -1139,6 +1164,10 @@ void evaluate_launches(hfx_plan* P, const double* L, hfx_stats* st, bool tail) {
     ensure_store(P, P->Yst, P->Ycap, P->tot[0]);
     D.Yst = P->Yst;
     ck(hfx::launch_ybuild(D, P->y_list, (int)P->tot[1], s), "ybuild");
+  } else if (P->wide) {
+    ensure_buf(P, P->Yw, P->Ywcap, std::max(1LL, P->tot[0]));
+    ck(hfx::launch_ybuild_w(D, P->np, P->Yw, P->y_list, P->gX, P->gS, P->gN, (int)P->tot[9], P->wide_RB, s),
+       "ybuild");
   } else {
     ensure_buf(P, P->Ysp, P->Yspcap, P->tot[0]);
     X.Ysp = P->Ysp;
@@ -1184,16 +1213,22 @@ void evaluate_launches(hfx_plan* P, const double* L, hfx_stats* st, bool tail) {
     const int v0 = P->v_ptr_h[a0], c0 = P->c_ptr_h[a0];
     const long long* ct = P->ctot.data() + (size_t)kCT * c;
     m1.push_back(tm.mark());
-    if (!P->np) {
+    if (!split) {   // FP64 V blocks; the FP64 or the wide split kernels
       ensure_store(P, P->Vst, P->Vcap, ct[CT_VE]);
       D.Vst = P->Vst;
       ck(hfx::launch_vblocks(D, P->v_list + v0, (int)ct[CT_VN], s), "vblocks");
       k1a.push_back(tm.mark());
-      ck(hfx::launch_term1(D, P->t1_list + v0, (int)ct[CT_T1], P->beta_chunk, P->smem_t1, s), "term1");
+      if (P->wide)
+        ck(hfx::launch_term1_w(D, P->np, P->Yw, P->t1_list + v0, (int)ct[CT_T1], P->ws, s), "term1");
+      else
+        ck(hfx::launch_term1(D, P->t1_list + v0, (int)ct[CT_T1], P->beta_chunk, P->smem_t1, s), "term1");
       k1b.push_back(tm.mark());
       m2.push_back(k1b.back());
       k2a.push_back(k1b.back());
-      ck(hfx::launch_term2(D, P->t2_list + v0, (int)ct[CT_T2], P->alpha_chunk, P->smem_t2, s), "term2");
+      if (P->wide)
+        ck(hfx::launch_term2_w(D, P->np, P->Yw, P->t2_list + v0, (int)ct[CT_T2], P->ws, s), "term2");
+      else
+        ck(hfx::launch_term2(D, P->t2_list + v0, (int)ct[CT_T2], P->alpha_chunk, P->smem_t2, s), "term2");
     } else {
       ensure_buf(P, P->Vm, P->Vmcap, ct[CT_VM]);
       X.Vm = P->Vm;

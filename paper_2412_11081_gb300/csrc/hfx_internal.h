@@ -246,6 +246,28 @@ cudaError_t launch_t1u_stores(const DevPlan& P, const T1UPlan& U, int np, const 
 cudaError_t launch_t1_umma(const DevPlan& P, const MixPlan& X, const T1UPlan& U, int np, const int* qlist, int n,
                            size_t smem, int* work, int* err, cudaStream_t s);
 
+// Split-precision kernels for n_ao up to 32 and n_abf up to 128 (hfx_wide.cu):
+// warp-level MMAs on bf16 pieces staged from the FP64 C, V and D blocks and
+// an FP32 Y store (offsets y_off, layout [alpha][x][z] as the FP64 store).
+struct WideShapes {
+  int MA = 0, MB = 0;          // n_abf rounded up to 16
+  int KZ = 0;                  // n_ao rounded up to 16
+  int t1_da = 0, t1_KC = 0;    // first product: a per range, columns (a, f) per range (rounded to 16)
+  int t2_da = 0, t2_KC = 0, t2_ZR = 0;   // second product: a per range, columns (a, b), Z rows
+  size_t smem_t1 = 0, smem_t2 = 0;
+  bool ok = false;             // every shape fits the kernels' shared memory and tiles
+};
+long long wide_launch_count();
+WideShapes wide_shapes(int np, int maxABF, int maxAO, size_t limit);
+int wide_ybuild_row_blocks(int max_rows);
+cudaError_t set_wide_smem_limits(int np);
+cudaError_t launch_ybuild_w(const DevPlan& P, int np, float* Yw, const int* ylist, const int* gX, const int* gS,
+                            const int* gN, int ngroups, int RB, cudaStream_t s);
+cudaError_t launch_term1_w(const DevPlan& P, int np, const float* Yw, const int* list, int n, const WideShapes& w,
+                           cudaStream_t s);
+cudaError_t launch_term2_w(const DevPlan& P, int np, const float* Yw, const int* list, int n, const WideShapes& w,
+                           cudaStream_t s);
+
 // Exclusive scan helpers.  `mode` selects what is summed per element i:
 //   0: flag[i] != 0 (int32 flags)
 //   1: flag[i] != 0 ? size[i] : 0

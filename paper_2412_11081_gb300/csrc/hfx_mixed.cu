@@ -70,71 +70,6 @@ __device__ void block_sum_n(double (&v)[NV], double* red) {
   __syncthreads();
 }
 
-__device__ __forceinline__ uint32_t pack2(uint16_t lo, uint16_t hi) { return (uint32_t)lo | ((uint32_t)hi << 16); }
-
-__device__ __forceinline__ void mma16816(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-  asm(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-// All piece products (i, j) with i + j < NP, smallest first.
-template <int NP>
-__device__ __forceinline__ void mma_split(float (&c)[4], const uint32_t (&a)[NP][4], const uint32_t (&b)[NP][2]) {
-  if (NP == 3) {
-    mma16816(c, a[1], b[1]);
-    mma16816(c, a[0], b[2]);
-    mma16816(c, a[2], b[0]);
-  }
-  if (NP >= 2) {
-    mma16816(c, a[0], b[1]);
-    mma16816(c, a[1], b[0]);
-  }
-  mma16816(c, a[0], b[0]);
-}
-
-// Two independent accumulators with their product chains interleaved, so the
-// dependent MMAs of one tile overlap the other's.
-template <int NP>
-__device__ __forceinline__ void mma_split2(float (&c0)[4], const uint32_t (&a0)[NP][4], const uint32_t (&b0)[NP][2],
-                                           float (&c1)[4], const uint32_t (&a1)[NP][4], const uint32_t (&b1)[NP][2]) {
-  if (NP == 3) {
-    mma16816(c0, a0[1], b0[1]);
-    mma16816(c1, a1[1], b1[1]);
-    mma16816(c0, a0[0], b0[2]);
-    mma16816(c1, a1[0], b1[2]);
-    mma16816(c0, a0[2], b0[0]);
-    mma16816(c1, a1[2], b1[0]);
-  }
-  if (NP >= 2) {
-    mma16816(c0, a0[0], b0[1]);
-    mma16816(c1, a1[0], b1[1]);
-    mma16816(c0, a0[1], b0[0]);
-    mma16816(c1, a1[1], b1[0]);
-  }
-  mma16816(c0, a0[0], b0[0]);
-  mma16816(c1, a1[0], b1[0]);
-}
-
-__device__ __forceinline__ void ldm_x4(uint32_t (&r)[4], const void* p) {
-  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(a));
-}
-
-__device__ __forceinline__ void ldm_x2(uint32_t (&r)[2], const void* p) {
-  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
-  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n" : "=r"(r[0]), "=r"(r[1]) : "r"(a));
-}
-
-__device__ __forceinline__ void ldm_x2_trans(uint32_t (&r)[2], const void* p) {
-  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
-  asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];\n" : "=r"(r[0]), "=r"(r[1]) : "r"(a));
-}
-
 // ------------------------------------------------------------------ D split
 // D block k (n_ao(I) x n_ao(J)) -> NP bf16 planes of rup16(n_ao(I)) x rup16(n_ao(J)), zero padded.
 template <int NP>
