@@ -232,8 +232,13 @@ struct hfx_plan {
   bool wide = false;
   hfx::WideShapes ws{};
   int wide_RB = 0;             // 64-row blocks of the largest Y block
+  int wide_maxrows = 0;        // most rows (alpha, a) of a C block
   float* Yw = nullptr;
   long long Ywcap = 0;
+  uint16_t* Zw = nullptr;      // Z^{AB} of one pass's second-product pairs (bf16 pieces)
+  long long Zwcap = 0;
+  uint16_t* Dw = nullptr;      // bf16 pieces of every D block (fixed for the plan)
+  long long* dw_off = nullptr;
 
   bool timing = false;
   bool noalloc_call = false;   // set only inside hfx_energy_force_stress_noalloc
@@ -838,6 +843,7 @@ void setup_shapes(hfx_plan* P) {
     int maxrows = 0;
     for (int a = 0; a < P->S; ++a) maxrows = std::max(maxrows, P->n_abf[a] * P->n_ao[a]);
     P->wide_RB = hfx::wide_ybuild_row_blocks(maxrows);
+    P->wide_maxrows = maxrows;
     ck(hfx::set_wide_smem_limits(P->np), "smem attributes");
     return;
   }
@@ -910,7 +916,22 @@ void setup_shapes(hfx_plan* P) {
 
 // bf16 pieces of every D block (fixed for the plan)
 void split_density(hfx_plan* P) {
-  if (!P->np || P->wide || P->n_d == 0) return;
+  if (!P->np || P->n_d == 0) return;
+  if (P->wide) {   // NP planes of rup16(n_ao(I)) x rup16(n_ao(J)) per D block, row-major
+    std::vector<long long> off(P->n_d + 1, 0);
+    for (long long k = 0; k < P->n_d; ++k) {
+      const int* r = &P->d_index[5 * k];
+      const long long a = (P->n_ao[P->species[r[0]]] + 15) / 16 * 16, b = (P->n_ao[P->species[r[1]]] + 15) / 16 * 16;
+      off[k + 1] = off[k] + (long long)P->np * a * b;
+    }
+    P->dw_off = P->mem.alloc<long long>(P->n_d + 1);
+    P->Dw = P->mem.alloc<uint16_t>(off[P->n_d]);
+    upload(P->dw_off, off, P->stream);
+    DevPlan D = make_devplan(P, P->lat_ref.data());
+    ck(hfx::launch_dsplit_w(D, P->np, P->Dw, P->dw_off, P->stream), "D pieces");
+    ck(cudaStreamSynchronize(P->stream), "D pieces");
+    return;
+  }
   std::vector<long long> off(P->n_d + 1, 0);
   for (long long k = 0; k < P->n_d; ++k) {
     const int* r = &P->d_index[5 * k];
@@ -1225,9 +1246,13 @@ void evaluate_launches(hfx_plan* P, const double* L, hfx_stats* st, bool tail) {
       k1b.push_back(tm.mark());
       m2.push_back(k1b.back());
       k2a.push_back(k1b.back());
-      if (P->wide)
-        ck(hfx::launch_term2_w(D, P->np, P->Yw, P->t2_list + v0, (int)ct[CT_T2], P->ws, s), "term2");
-      else
+      if (P->wide) {
+        ensure_buf(P, P->Zw, P->Zwcap,
+                   std::max(1LL, ct[CT_T2]) * P->np * hfx::wide_zplane(P->wide_maxrows, P->ws.KZ));
+        ck(hfx::launch_term2_w(D, P->np, P->Yw, P->Zw, P->Dw, P->dw_off, P->t2_list + v0, P->t2_idx, (int)ct[CT_T2],
+                               a0, a1, P->wide_maxrows, P->maxC, P->ws, s),
+           "term2");
+      } else
         ck(hfx::launch_term2(D, P->t2_list + v0, (int)ct[CT_T2], P->alpha_chunk, P->smem_t2, s), "term2");
     } else {
       ensure_buf(P, P->Vm, P->Vmcap, ct[CT_VM]);

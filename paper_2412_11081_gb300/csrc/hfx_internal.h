@@ -253,8 +253,8 @@ struct WideShapes {
   int MA = 0, MB = 0;          // n_abf rounded up to 16
   int KZ = 0;                  // n_ao rounded up to 16
   int t1_da = 0, t1_KC = 0;    // first product: a per range, columns (a, f) per range (rounded to 16)
-  int t2_da = 0, t2_KC = 0, t2_ZR = 0;   // second product: a per range, columns (a, b), Z rows
-  size_t smem_t1 = 0, smem_t2 = 0;
+  int t2_da = 0, t2_KC = 0;    // second product: a per range, columns (a, b) per range
+  size_t smem_t1 = 0, smem_t2 = 0, smem_q2 = 0;
   bool ok = false;             // every shape fits the kernels' shared memory and tiles
 };
 long long wide_launch_count();
@@ -265,8 +265,16 @@ cudaError_t launch_ybuild_w(const DevPlan& P, int np, float* Yw, const int* ylis
                             const int* gN, int ngroups, int RB, cudaStream_t s);
 cudaError_t launch_term1_w(const DevPlan& P, int np, const float* Yw, const int* list, int n, const WideShapes& w,
                            cudaStream_t s);
-cudaError_t launch_term2_w(const DevPlan& P, int np, const float* Yw, const int* list, int n, const WideShapes& w,
-                           cudaStream_t s);
+// elements per bf16 piece plane of one pair slot of the Z store (rows (alpha, a), row stride KZ)
+long long wide_zplane(int max_rows, int KZ);
+// bf16 pieces of every D block (fixed for the plan): NP planes of
+// rup16(n_ao(I)) x rup16(n_ao(J)) at Dw + dw_off[k] (multiples of 256)
+cudaError_t launch_dsplit_w(const DevPlan& P, int np, uint16_t* Dw, const long long* dw_off, cudaStream_t s);
+// Second product of the home atoms [a0, a1): k_term2_w over the pass's pair
+// list (E, g^V and the Z piece store), then k_q2_w (grad C); slot0 as launch_term2_mma.
+cudaError_t launch_term2_w(const DevPlan& P, int np, const float* Yw, uint16_t* Zw, const uint16_t* Dw,
+                           const long long* dw_off, const int* list, const long long* slot0, int n, int a0, int a1,
+                           int max_rows, int max_c, const WideShapes& w, cudaStream_t s);
 
 // Exclusive scan helpers.  `mode` selects what is summed per element i:
 //   0: flag[i] != 0 (int32 flags)

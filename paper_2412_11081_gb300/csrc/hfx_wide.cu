@@ -19,8 +19,9 @@
 //                 Q  = V_AB . U     (dotted with grad C_AF at once)
 //   k_term2_w   per kept (A,B) of the second product, over ranges of a:
 //                 R2 += Y^{AB} . Y^{BA}   (K = (a, b))
-//                 Z   = V_AB . Y^{BA}     (rows (alpha, a), shared memory)
-//                 per C pair (A,F):  Q2 = Z . D_FB^T, dotted with grad C_AF
+//                 Z   = V_AB . Y^{BA}     (rows (alpha, a), to a bf16 piece store)
+//   k_q2_w      per (A, 128 rows (alpha, a), 8 C pairs (A,F)):
+//                 Q2 = sum_B Z^{AB} . D_FB^T, dotted with grad C_AF
 // (Eq. exx_expand by the distributive law; Eq. Fexx1 for the gradients.)
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -42,6 +43,15 @@ constexpr int kFlushF = 4;       // F per FP32 run of R in the first product
 std::atomic<long long> g_wide_launches{0};
 
 __device__ __forceinline__ int rup8(int x) { return (x + 7) & ~7; }
+
+// 16-byte asynchronous copies global -> shared (both 16-byte aligned)
+__device__ __forceinline__ void cpa16(void* sdst, const void* gsrc) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(a), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cpa_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 // piece pp of (x0, x1) packed as one 32-bit word, x0 in the low half
 template <int NP>
@@ -124,6 +134,24 @@ __device__ __forceinline__ void gemm_pair_kn(float (&acc)[2][4], const uint16_t*
       ldm_x2_trans(b1[pp], Bs + pp * pb + (long long)(k0 + (lane & 15)) * SB + nt1 * 8);
     }
     mma_split2<NP>(acc[0], af, b0, acc[1], af, b1);
+  }
+}
+
+// ------------------------------------------------------------------ D pieces
+// D block k (fixed for the plan) -> NP bf16 planes of rup16(n_ao(I)) x
+// rup16(n_ao(J)), row-major, zero padded, at Dw + dw_off[k].
+template <int NP>
+__global__ void k_dsplit_w(DevPlan P, uint16_t* Dw, const long long* dw_off) {
+  for (long long k = blockIdx.x; k < P.n_d; k += gridDim.x) {
+    const int I = P.Didx[5 * k], J = P.Didx[5 * k + 1];
+    const int na = P.n_ao[P.species[I]], nb = P.n_ao[P.species[J]];
+    const int pa = rup16(na), pb = rup16(nb);
+    const double* src = P.Dval + P.Doff[k];
+    uint16_t* out = Dw + dw_off[k];
+    for (int e = threadIdx.x; e < pa * pb; e += blockDim.x) {
+      const int a = e / pb, b = e - a * pb;
+      put_pieces<NP>(out, (long long)pa * pb, e, (a < na && b < nb) ? (float)src[a * nb + b] : 0.f);
+    }
   }
 }
 
@@ -498,63 +526,57 @@ __global__ void __launch_bounds__(kWThreads) k_term1_w(DevPlan P, const float* _
 }
 
 // ------------------------------------------------------------------ term 2
-// Shared memory (bf16 planes):
-//   Vs[NP][MA][MB + 8]          V_AB
-//   Ya[NP][MA][KC + 8]          Y^{AB} columns (a, b), a in the current range
-//   Yb[NP][MB][KC + 8]          Y^{BA} as [beta][(a, b)], same columns
-//   Zs[NP][ZR][KZ + 8]          Z rows (alpha, a - a0), columns b (KZ = rup16 max n_ao)
-//   gF[3 * kMaxCPerAtom]        FP64 grad C partials per C slot of A
-//   fdi[kMaxCPerAtom]           D_FB block per C slot of A (or -1)
+// k_term2_w, one CTA per kept (A,B) pair (slot s of the pass's list); shared
+// memory (bf16 planes):
+//   Vs[NP][MA][MB + 8]   V_AB
+//   Ya[NP][MA][KC + 8]   Y^{AB} columns (a, b), a in the current range
+//   Yb[NP][MB][KC + 8]   Y^{BA} as [beta][(a, b)], same columns
+// R2 gives E and g^V; Z = V_AB . Y^{BA} goes to the Z store of slot s as NP
+// bf16 planes of rows (alpha, a), columns b (row stride KZ, columns
+// n_ao(B) .. rup16(n_ao(B)) - 1 zero), for k_q2_w.
 struct T2W {
-  int MA, MB, KC, da, ZR, KZ;
+  int MA, MB, KC, da, KZ;
+  long long zplane;    // elements per piece plane of a slot (most rows x KZ)
 };
 
-__host__ __device__ inline size_t term2w_smem(int np, int MA, int MB, int KC, int ZR, int KZ) {
-  return (size_t)np * 2 *
-             ((size_t)MA * (MB + 8) + (size_t)MA * (KC + 8) + (size_t)MB * (KC + 8) + (size_t)ZR * (KZ + 8)) +
-         (size_t)3 * kMaxCPerAtom * sizeof(double) + (size_t)kMaxCPerAtom * sizeof(int);
+__host__ __device__ inline size_t term2w_smem(int np, int MA, int MB, int KC) {
+  return (size_t)np * 2 * ((size_t)MA * (MB + 8) + (size_t)MA * (KC + 8) + (size_t)MB * (KC + 8));
 }
 
 template <int NP>
-__global__ void __launch_bounds__(kWThreads) k_term2_w(DevPlan P, const float* __restrict__ Yw, const int* list,
-                                                       int n_list, T2W S) {
+__global__ void __launch_bounds__(kWThreads) k_term2_w(DevPlan P, const float* __restrict__ Yw, uint16_t* __restrict__ Zw,
+                                                       const int* list, int n_list, T2W S) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[4 * kWarpsW];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gid = lane >> 2, tig = lane & 3;
   const int MA = S.MA, MB = S.MB;
-  const int SV = MB + 8, SK = S.KC + 8, SZ = S.KZ + 8;
-  const long long pV = (long long)MA * SV, pA = (long long)MA * SK, pB = (long long)MB * SK, pZ = (long long)S.ZR * SZ;
-  double* gF = reinterpret_cast<double*>(smem);
-  int* fdi = reinterpret_cast<int*>(gF + 3 * kMaxCPerAtom);
-  uint16_t* Vs = reinterpret_cast<uint16_t*>(fdi + kMaxCPerAtom);
+  const int SV = MB + 8, SK = S.KC + 8;
+  const long long pV = (long long)MA * SV, pA = (long long)MA * SK, pB = (long long)MB * SK;
+  uint16_t* Vs = reinterpret_cast<uint16_t*>(smem);
   uint16_t* Ya = Vs + NP * pV;
   uint16_t* Yb = Ya + NP * pA;
-  uint16_t* Zs = Yb + NP * pB;
   for (int kk = blockIdx.x; kk < n_list; kk += gridDim.x) {
     const int p = list[kk];
     const int A = P.v_home[p], b = P.v_j[p];
     const int* Rb = P.v_R + 3 * p;
     const int sA = P.species[A], sB = P.species[b];
     const int nA = P.n_ao[sA], nB = P.n_ao[sB], mA = P.n_abf[sA], mB = P.n_abf[sB];
-    const int MAp = rup16(mA), MBp = rup16(mB), KB = rup16(nB);
+    const int MAp = rup16(mA), MBp = rup16(mB);
     const int y1 = ylut_get(P, A, b, Rb[0], Rb[1], Rb[2]);
     const int y2 = ylut_get(P, b, A, -Rb[0], -Rb[1], -Rb[2]);
     const float* Yab = Yw + P.y_off[y1];   // [alpha][a][b]
     const float* Yba = Yw + P.y_off[y2];   // [beta][b][a]
     const double* V = P.Vst + P.v_off[p];
     const int nvb = mA * mB, nab = nA * nB;
-    const int q0 = P.c_ptr[A], nq = P.c_ptr[A + 1] - q0;
+    uint16_t* Z = Zw + (long long)kk * NP * S.zplane;   // NP planes [(alpha, a)][KZ]
     __syncthreads();   // previous pair done with every buffer
-    for (int t = threadIdx.x; t < nq; t += blockDim.x) {
-      const int q = q0 + t;
-      int di = -1;
-      if (P.c_keep[q]) {
-        const int* Rf = P.c_R + 3 * q;
-        di = dlut_get(P, P.c_j[q], b, Rb[0] - Rf[0], Rb[1] - Rf[1], Rb[2] - Rf[2]);
-        if (di >= 0 && P.Dkept[di] == 0.0) di = -1;
+    {   // zero columns n_ao(B) .. rup16(n_ao(B)) - 1 (K padding of k_q2_w)
+      const int pad = rup16(nB) - nB;
+      for (int e = threadIdx.x; e < mA * nA * pad; e += blockDim.x) {
+        const int r = e / pad, c = nB + (e - r * pad);
+#pragma unroll
+        for (int pp = 0; pp < NP; ++pp) Z[pp * S.zplane + (long long)r * S.KZ + c] = 0;
       }
-      fdi[t] = di;
-      gF[3 * t] = gF[3 * t + 1] = gF[3 * t + 2] = 0.0;
     }
     for (int e = threadIdx.x; e < MA * SV; e += blockDim.x) {
       const int al = e / SV, be = e - al * SV;
@@ -572,12 +594,10 @@ __global__ void __launch_bounds__(kWThreads) k_term2_w(DevPlan P, const float* _
       for (int h = 0; h < 2; ++h)
 #pragma unroll
         for (int c = 0; c < 4; ++c) racc[i][h][c] = 0.f;
-    double fl = 4.0 * mA * mB * nA * nB;
     for (int a0 = 0; a0 < nA; a0 += S.da) {
       const int dA = min(S.da, nA - a0);
       const int dcols = dA * nB, KCc = rup16(dcols);
-      const int zrows = mA * S.da;
-      __syncthreads();   // the previous range is done with Ya, Yb and Zs
+      __syncthreads();   // the previous range is done with Ya and Yb
       for (int e = threadIdx.x; e < mA * KCc; e += blockDim.x) {
         const int al = e / KCc, c = e - al * KCc;
         put_pieces<NP>(Ya, pA, al * SK + c, c < dcols ? Yab[(long long)al * nab + a0 * nB + c] : 0.f);
@@ -591,12 +611,6 @@ __global__ void __launch_bounds__(kWThreads) k_term2_w(DevPlan P, const float* _
         }
         put_pieces<NP>(Yb, pB, be * SK + c, v);
       }
-      // Z columns b past n_ao(B) stay zero up to the 16-column step (K of Q2)
-      for (int e = threadIdx.x; e < zrows * (KB - nB); e += blockDim.x) {
-        const int r = e / (KB - nB), c = nB + (e - r * (KB - nB));
-#pragma unroll
-        for (int pp = 0; pp < NP; ++pp) Zs[pp * pZ + (long long)r * SZ + c] = 0;
-      }
       __syncthreads();
       // R2 += Y^{AB} . Y^{BA} (M = alpha, N = beta, K = (a, b) of the range)
 #pragma unroll
@@ -606,7 +620,7 @@ __global__ void __launch_bounds__(kWThreads) k_term2_w(DevPlan P, const float* _
         const int mt = pr / rt.NTP, nt0 = 2 * (pr - mt * rt.NTP);
         gemm_pair_kk<NP>(racc[i], Ya, pA, SK, Yb, pB, SK, mt, nt0, nt0 + 1 < rt.NT, KCc);
       }
-      // Z = V_AB . Y^{BA} (M = alpha, N = (a, b), K = beta) -> Zs rows (alpha, a - a0)
+      // Z = V_AB . Y^{BA} (M = alpha, N = (a, b), K = beta) -> Z store rows (alpha, a)
       {
         const int NTZ = rup8(dcols) >> 3, NPZ = (NTZ + 1) >> 1;
         const int npairs = (MAp >> 4) * NPZ;
@@ -622,86 +636,10 @@ __global__ void __launch_bounds__(kWThreads) k_term2_w(DevPlan P, const float* _
               const int n = (nt0 + h) * 8 + 2 * tig + (c & 1);
               if (al < mA && n < dcols && nt0 + h < NTZ) {
                 const int a = n / nB, bb = n - a * nB;
-                put_pieces<NP>(Zs, pZ, (al * S.da + a) * SZ + bb, acc[h][c]);
+                put_pieces<NP>(Z, S.zplane, (int)(((long long)al * nA + a0 + a) * S.KZ + bb), acc[h][c]);
               }
             }
         }
-      }
-      __syncthreads();   // Zs complete
-      // per C pair (A,F) with D_FB kept: Q2[(alpha, a)][f] = sum_b Z[(alpha, a)][b] D_FB[f][b]
-      const int MTZ = (zrows + 15) >> 4;
-      for (int t = 0; t < nq; ++t) {
-        const int di = fdi[t];
-        if (di < 0) continue;
-        const int q = q0 + t;
-        const int nF = P.n_ao[P.species[P.c_j[q]]];
-        const double* Dfb = P.Dval + P.Doff[di];   // [f][b]
-        const double* dC = P.dCst + 3 * P.c_off[q];
-        const long long nc = (long long)mA * nA * nF;
-        const int NTF = rup8(nF) >> 3;
-        float gq[3] = {0.f, 0.f, 0.f};
-        if (warp < MTZ) {
-          // B fragments of D_FB (K = b, N = f), this warp's for every m tile
-          uint32_t bfr[4][2][NP][2];
-#pragma unroll
-          for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-            for (int ks = 0; ks < 2; ++ks)
-#pragma unroll
-              for (int h = 0; h < 2; ++h) {
-                const int ff = nt * 8 + gid, kc = ks * 16 + 2 * tig + (h ? 8 : 0);
-                const bool in = nt < NTF && ff < nF;
-                const float x0 = (in && kc < nB) ? (float)Dfb[ff * nB + kc] : 0.f;
-                const float x1 = (in && kc + 1 < nB) ? (float)Dfb[ff * nB + kc + 1] : 0.f;
-                uint32_t w[NP];
-                split_pair<NP>(x0, x1, w);
-#pragma unroll
-                for (int pp = 0; pp < NP; ++pp) bfr[nt][ks][pp][h] = w[pp];
-              }
-          for (int mt = warp; mt < MTZ; mt += kWarpsW) {
-            float acc[4][4];
-#pragma unroll
-            for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-              for (int c = 0; c < 4; ++c) acc[nt][c] = 0.f;
-#pragma unroll
-            for (int ks = 0; ks < 2; ++ks) {
-              if (ks * 16 >= KB) break;
-              uint32_t af[NP][4];
-#pragma unroll
-              for (int pp = 0; pp < NP; ++pp)
-                ldm_x4(af[pp], Zs + pp * pZ + (long long)(mt * 16 + (lane & 15)) * SZ + ks * 16 + ((lane >> 4) << 3));
-#pragma unroll
-              for (int nt = 0; nt < 4; ++nt) {
-                if (nt >= NTF) break;
-                mma_split<NP>(acc[nt], af, bfr[nt][ks]);
-              }
-            }
-#pragma unroll
-            for (int nt = 0; nt < 4; ++nt) {
-              if (nt >= NTF) break;
-#pragma unroll
-              for (int c = 0; c < 4; ++c) {
-                const int r = mt * 16 + gid + ((c & 2) ? 8 : 0);
-                const int ff = nt * 8 + 2 * tig + (c & 1);
-                const int al = r / S.da, a = a0 + (r - al * S.da);
-                if (r < zrows && a < a0 + dA && ff < nF) {
-                  const long long ci = ((long long)al * nA + a) * nF + ff;
-                  const float v = acc[nt][c];
-                  gq[0] = fmaf((float)dC[ci], v, gq[0]);
-                  gq[1] = fmaf((float)dC[nc + ci], v, gq[1]);
-                  gq[2] = fmaf((float)dC[2 * nc + ci], v, gq[2]);
-                }
-              }
-            }
-          }
-        }
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const float w = warp_sum_f(gq[c]);
-          if (lane == 0 && w != 0.f) atomicAdd(&gF[3 * t + c], (double)w);
-        }
-        if (a0 == 0 && threadIdx.x == 0) fl += 2.0 * mA * nA * nB * nF;
       }
     }
     // E and g^V from R2
@@ -732,23 +670,237 @@ __global__ void __launch_bounds__(kWThreads) k_term2_w(DevPlan P, const float* _
 #pragma unroll
       for (int c = 0; c < 4; ++c) ev[c] = (double)evf[c];
     }
-    block_sum_w<4>(ev, red);   // also orders the gF additions before the flush below
-    for (int t = threadIdx.x; t < nq; t += blockDim.x) {
-      if (gF[3 * t] != 0.0 || gF[3 * t + 1] != 0.0 || gF[3 * t + 2] != 0.0) {
-        const int q = q0 + t;
-        atomicAdd(&P.gC[3 * q + 0], -2.0 * gF[3 * t + 0]);
-        atomicAdd(&P.gC[3 * q + 1], -2.0 * gF[3 * t + 1]);
-        atomicAdd(&P.gC[3 * q + 2], -2.0 * gF[3 * t + 2]);
-      }
-    }
+    block_sum_w<4>(ev, red);
     if (threadIdx.x == 0) {
       atomicAdd(&P.acc[ACC_E], -ev[0]);
       atomicAdd(&P.gV[3 * p + 0], -ev[1]);
       atomicAdd(&P.gV[3 * p + 1], -ev[2]);
       atomicAdd(&P.gV[3 * p + 2], -ev[3]);
-      atomicAdd(&P.acc[ACC_F2], fl);
+      atomicAdd(&P.acc[ACC_F2], 4.0 * mA * mB * nA * nB);
     }
   }
+}
+
+// k_q2_w: CTA = (home atom A of the pass, 128 rows (alpha, a), group of 8 C
+// slots F of A).  Q2^{AF}[(alpha, a)][f] = sum_B sum_b Z^{AB}[(alpha, a)][b]
+// D_FB[f][b] over the pairs (A,B) of the second product (one K step of
+// rup16(n_ao(B)) per pair), the eight F side by side in the columns (32 per
+// slot); every kQ2Run pairs the FP32 run is dotted with grad C_AF into FP64.
+// Warp w: rows 16 (w & 7) .. + 15 of the block, slots 4 (w >> 3) .. + 3.
+// Operands arrive by cp.async from the Z piece store and the D piece store,
+// two steps in flight:
+//   As[2][NP][128][KZ + 8]     Z rows, columns b
+//   Bs[2][NP][8 * 32][KZ + 8]  D_FB rows (slot, f), columns b
+constexpr int kQ2Threads = 512;
+constexpr int kQ2Rows = 128;
+constexpr int kQ2Slots = 8;
+constexpr int kQ2Seg = 256;   // pairs per segment of D-block metadata
+constexpr int kQ2Run = 64;    // pairs per FP32 run
+
+__host__ __device__ inline size_t q2w_smem(int np, int KZ) {
+  return (size_t)2 * np * 2 * (size_t)(kQ2Rows + kQ2Slots * 32) * (KZ + 8);
+}
+
+template <int NP>
+__global__ void __launch_bounds__(kQ2Threads, 1) k_q2_w(DevPlan P, const uint16_t* __restrict__ Zw, long long zplane,
+                                                        int KZ, const uint16_t* __restrict__ Dw,
+                                                        const long long* __restrict__ dw_off, const int* list,
+                                                        const long long* slot0, int n_slots, int a0, int a1, int RBQ,
+                                                        int SG) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int m_dw[kQ2Seg][kQ2Slots];   // D piece block of (pair, slot) in 256-element units, or -1
+  __shared__ int m_step[kQ2Seg];
+  __shared__ int s_nsteps;
+  __shared__ int s_q[kQ2Slots], s_nf[kQ2Slots];
+  __shared__ double s_ev[kQ2Threads / 32][4][3];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gid = lane >> 2, tig = lane & 3;
+  const int mt = warp & 7, sh = warp >> 3;
+  const int SZ = KZ + 8;
+  const long long pA = (long long)kQ2Rows * SZ, pB = (long long)kQ2Slots * 32 * SZ;
+  uint16_t* As0 = reinterpret_cast<uint16_t*>(smem);
+  uint16_t* Bs0 = As0 + 2 * NP * pA;
+  const int per_atom = RBQ * SG;
+  const int A = a0 + blockIdx.x / per_atom;
+  const int rem = blockIdx.x - (A - a0) * per_atom, rb = rem / SG, sg = rem - rb * SG;
+  if (A >= a1) return;
+  const int sA = P.species[A], mA = P.n_abf[sA], nA = P.n_ao[sA];
+  const int rows = mA * nA, row0 = rb * kQ2Rows;
+  const int q0 = P.c_ptr[A], nq = P.c_ptr[A + 1] - q0;
+  if (row0 >= rows || kQ2Slots * sg >= nq) return;
+  if (threadIdx.x < kQ2Slots) {
+    const int t = kQ2Slots * sg + threadIdx.x;
+    const int q = (t < nq && P.c_keep[q0 + t]) ? q0 + t : -1;
+    s_q[threadIdx.x] = q;
+    s_nf[threadIdx.x] = q >= 0 ? P.n_ao[P.species[P.c_j[q]]] : 0;
+  }
+  for (int e = threadIdx.x; e < (kQ2Threads / 32) * 12; e += blockDim.x) (&s_ev[0][0][0])[e] = 0.0;
+  __syncthreads();
+  bool any = false;
+#pragma unroll
+  for (int i = 0; i < kQ2Slots; ++i) any = any || s_q[i] >= 0;
+  if (!any) return;
+  int nf4[4];
+  bool live4[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    nf4[i] = s_nf[4 * sh + i];
+    live4[i] = s_q[4 * sh + i] >= 0;
+  }
+  const long long s0 = slot0[P.v_ptr[A]];
+  const long long s1 = A + 1 < a1 ? slot0[P.v_ptr[A + 1]] : (long long)n_slots;
+  float acc[4][4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[i][nt][c] = 0.f;
+  // dot of the FP32 run with grad C_AF (FP32 products, FP64 sums per warp), then the run restarts
+  auto flush = [&]() {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (!live4[i]) continue;
+      const int nF = nf4[i];
+      const double* dC = P.dCst + 3 * P.c_off[s_q[4 * sh + i]];
+      const long long nc = (long long)rows * nF;
+      float g[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) {
+        if (nt * 8 >= nF) break;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int r = row0 + mt * 16 + gid + ((c & 2) ? 8 : 0);
+          const int ff = nt * 8 + 2 * tig + (c & 1);
+          if (r < rows && ff < nF) {
+            const long long ci = (long long)r * nF + ff;
+            const float v = acc[i][nt][c];
+            g[0] = fmaf((float)dC[ci], v, g[0]);
+            g[1] = fmaf((float)dC[nc + ci], v, g[1]);
+            g[2] = fmaf((float)dC[2 * nc + ci], v, g[2]);
+          }
+          acc[i][nt][c] = 0.f;
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float w = warp_sum_f(g[c]);
+        if (lane == 0) s_ev[warp][i][c] += (double)w;
+      }
+    }
+  };
+  double fl = 0.0;
+  int run = 0;
+  for (long long sb = s0; sb < s1; sb += kQ2Seg) {
+    const int nseg = (int)min((long long)kQ2Seg, s1 - sb);
+    __syncthreads();   // the previous segment is done with the metadata
+    for (int e = threadIdx.x; e < nseg * kQ2Slots; e += blockDim.x) {
+      const int j = e / kQ2Slots, i = e - j * kQ2Slots;
+      const int q = s_q[i];
+      int dw = -1;
+      if (q >= 0) {
+        const int pr = list[sb + j];
+        const int* Rb = P.v_R + 3 * pr;
+        const int* Rf = P.c_R + 3 * q;
+        const int di = dlut_get(P, P.c_j[q], P.v_j[pr], Rb[0] - Rf[0], Rb[1] - Rf[1], Rb[2] - Rf[2]);
+        if (di >= 0 && P.Dkept[di] != 0.0) dw = (int)(dw_off[di] >> 8);
+      }
+      m_dw[j][i] = dw;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int n = 0;
+      for (int j = 0; j < nseg; ++j) {
+        bool k = false;
+#pragma unroll
+        for (int i = 0; i < kQ2Slots; ++i) k = k || m_dw[j][i] >= 0;
+        if (k) m_step[n++] = j;
+      }
+      s_nsteps = n;
+    }
+    __syncthreads();
+    const int nsteps = s_nsteps;
+    // copies of step k into buffer k & 1: Z rows of the block, D_FB of every live slot
+    auto issue = [&](int k) {
+      const int j = m_step[k];
+      const long long slot = sb + j;
+      const int nB = P.n_ao[P.species[P.v_j[list[slot]]]], KB = rup16(nB), ch = KB >> 3;
+      const uint16_t* Z = Zw + slot * NP * zplane + (long long)row0 * KZ;
+      uint16_t* As = As0 + (k & 1) * NP * pA;
+      uint16_t* Bs = Bs0 + (k & 1) * NP * pB;
+      const int zr = min(kQ2Rows, rows - row0);
+      for (int e = threadIdx.x; e < NP * zr * ch; e += blockDim.x) {
+        const int pp = e / (zr * ch), rr = e - pp * zr * ch, r = rr / ch, c = rr - r * ch;
+        cpa16(As + pp * pA + r * SZ + 8 * c, Z + pp * zplane + (long long)r * KZ + 8 * c);
+      }
+      for (int i = 0; i < kQ2Slots; ++i) {
+        const int dw = m_dw[j][i];
+        if (dw < 0) continue;
+        const int pf = rup16(s_nf[i]);
+        const uint16_t* Dg = Dw + ((long long)dw << 8);
+        const long long dplane = (long long)pf * KB;
+        for (int e = threadIdx.x; e < NP * pf * ch; e += blockDim.x) {
+          const int pp = e / (pf * ch), rr = e - pp * pf * ch, f = rr / ch, c = rr - f * ch;
+          cpa16(Bs + pp * pB + (i * 32 + f) * SZ + 8 * c, Dg + pp * dplane + (long long)f * KB + 8 * c);
+        }
+      }
+    };
+    if (nsteps > 0) issue(0);
+    cpa_commit();
+    for (int k = 0; k < nsteps; ++k) {
+      if (k + 1 < nsteps) issue(k + 1);
+      cpa_commit();
+      cpa_wait<1>();
+      __syncthreads();   // step k's operands are in shared memory
+      const int j = m_step[k];
+      const int nB = P.n_ao[P.species[P.v_j[list[sb + j]]]], KB = rup16(nB);
+      const uint16_t* As = As0 + (k & 1) * NP * pA;
+      const uint16_t* Bs = Bs0 + (k & 1) * NP * pB;
+      bool on[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) on[i] = m_dw[j][4 * sh + i] >= 0;
+      for (int ks = 0; ks < KB; ks += 16) {
+        uint32_t af[NP][4];
+#pragma unroll
+        for (int pp = 0; pp < NP; ++pp)
+          ldm_x4(af[pp], As + pp * pA + (mt * 16 + (lane & 15)) * SZ + ks + ((lane >> 4) << 3));
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          if (!on[i]) continue;
+#pragma unroll
+          for (int nt = 0; nt < 4; ++nt) {
+            if (nt * 8 >= nf4[i]) break;
+            uint32_t bf[NP][2];
+#pragma unroll
+            for (int pp = 0; pp < NP; ++pp)
+              ldm_x2(bf[pp], Bs + pp * pB + ((4 * sh + i) * 32 + nt * 8 + (lane & 7)) * SZ + ks +
+                                 (((lane >> 3) & 1) << 3));
+            mma_split<NP>(acc[i][nt], af, bf);
+          }
+        }
+      }
+      if (rb == 0 && threadIdx.x == 0)
+        for (int i = 0; i < kQ2Slots; ++i)
+          if (m_dw[j][i] >= 0) fl += 2.0 * mA * nA * nB * s_nf[i];
+      if (++run == kQ2Run) {
+        flush();
+        run = 0;
+      }
+      __syncthreads();   // buffer k & 1 is free for step k + 2
+    }
+    cpa_wait<0>();
+  }
+  flush();
+  __syncthreads();
+  if (threadIdx.x < kQ2Slots * 3) {
+    const int i = threadIdx.x / 3, c = threadIdx.x - 3 * i;
+    const int q = s_q[i];
+    if (q >= 0) {
+      double v = 0.0;
+      for (int w = 0; w < 8; ++w) v += s_ev[(i >> 2) * 8 + w][i & 3][c];
+      atomicAdd(&P.gC[3 * q + c], -2.0 * v);
+    }
+  }
+  if (threadIdx.x == 0 && fl != 0.0) atomicAdd(&P.acc[ACC_F2], fl);
 }
 
 int grid_cap(long long n, int cap) { return (int)(n < cap ? (n > 0 ? n : 1) : cap); }
@@ -774,17 +926,17 @@ WideShapes wide_shapes(int np, int maxABF, int maxAO, size_t limit) {
   }
   for (int da : {8, 4, 2, 1}) {
     const int KC = (da * maxAO + 15) / 16 * 16;
-    const int ZR = (maxABF * da + 15) / 16 * 16;
-    if (term2w_smem(np, w.MA, w.MB, KC, ZR, w.KZ) <= limit) {
+    if (term2w_smem(np, w.MA, w.MB, KC) <= limit) {
       w.t2_da = da;
       w.t2_KC = KC;
-      w.t2_ZR = ZR;
-      w.smem_t2 = term2w_smem(np, w.MA, w.MB, KC, ZR, w.KZ);
+      w.smem_t2 = term2w_smem(np, w.MA, w.MB, KC);
       break;
     }
   }
+  w.smem_q2 = q2w_smem(np, w.KZ);
   // R tiles: (MA / 16) x (MB / 16) pairs over the 8 warps, kRPairs each
-  w.ok = w.t1_da > 0 && w.t2_da > 0 && (w.MA / 16) * (w.MB / 16) <= kWarpsW * kRPairs && maxAO <= 32;
+  w.ok = w.t1_da > 0 && w.t2_da > 0 && w.smem_q2 <= limit && (w.MA / 16) * (w.MB / 16) <= kWarpsW * kRPairs &&
+         maxAO <= 32;
   return w;
 }
 
@@ -798,10 +950,12 @@ cudaError_t set_wide_smem_limits(int np) {
     one((const void*)k_ybuild_w<2>);
     one((const void*)k_term1_w<2>);
     one((const void*)k_term2_w<2>);
+    one((const void*)k_q2_w<2>);
   } else {
     one((const void*)k_ybuild_w<3>);
     one((const void*)k_term1_w<3>);
     one((const void*)k_term2_w<3>);
+    one((const void*)k_q2_w<3>);
   }
   return e;
 }
@@ -828,13 +982,37 @@ cudaError_t launch_term1_w(const DevPlan& P, int np, const float* Yw, const int*
   return cudaGetLastError();
 }
 
-cudaError_t launch_term2_w(const DevPlan& P, int np, const float* Yw, const int* list, int n, const WideShapes& w,
-                           cudaStream_t s) {
+long long wide_zplane(int max_rows, int KZ) { return (long long)max_rows * KZ; }
+
+cudaError_t launch_dsplit_w(const DevPlan& P, int np, uint16_t* Dw, const long long* dw_off, cudaStream_t s) {
+  if (P.n_d <= 0) return cudaSuccess;
+  const int grid = grid_cap(P.n_d, 1 << 16);
+  if (np == 2) k_dsplit_w<2><<<grid, 256, 0, s>>>(P, Dw, dw_off);
+  else k_dsplit_w<3><<<grid, 256, 0, s>>>(P, Dw, dw_off);
+  ++g_wide_launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_term2_w(const DevPlan& P, int np, const float* Yw, uint16_t* Zw, const uint16_t* Dw,
+                           const long long* dw_off, const int* list, const long long* slot0, int n, int a0, int a1,
+                           int max_rows, int max_c, const WideShapes& w, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  const T2W S{w.MA, w.MB, w.t2_KC, w.t2_da, w.t2_ZR, w.KZ};
+  const T2W S{w.MA, w.MB, w.t2_KC, w.t2_da, w.KZ, wide_zplane(max_rows, w.KZ)};
   const int grid = grid_cap(n, 1 << 20);
-  if (np == 2) k_term2_w<2><<<grid, kWThreads, w.smem_t2, s>>>(P, Yw, list, n, S);
-  else k_term2_w<3><<<grid, kWThreads, w.smem_t2, s>>>(P, Yw, list, n, S);
+  if (np == 2) k_term2_w<2><<<grid, kWThreads, w.smem_t2, s>>>(P, Yw, Zw, list, n, S);
+  else k_term2_w<3><<<grid, kWThreads, w.smem_t2, s>>>(P, Yw, Zw, list, n, S);
+  ++g_wide_launches;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int RBQ = (max_rows + kQ2Rows - 1) / kQ2Rows, SG = (max_c + kQ2Slots - 1) / kQ2Slots;
+  const long long qgrid = (long long)(a1 - a0) * RBQ * SG;
+  if (qgrid <= 0) return cudaSuccess;
+  if (np == 2)
+    k_q2_w<2><<<(unsigned)qgrid, kQ2Threads, w.smem_q2, s>>>(P, Zw, S.zplane, w.KZ, Dw, dw_off, list, slot0, n, a0, a1,
+                                                             RBQ, SG);
+  else
+    k_q2_w<3><<<(unsigned)qgrid, kQ2Threads, w.smem_q2, s>>>(P, Zw, S.zplane, w.KZ, Dw, dw_off, list, slot0, n, a0, a1,
+                                                             RBQ, SG);
   ++g_wide_launches;
   return cudaGetLastError();
 }

@@ -24,6 +24,8 @@ CELLS = {
     "si216": lambda: inputs.si_supercell(3),
     "si1000": lambda: inputs.workload_by_name("si1000"),
     "perovskite": lambda: inputs.perovskite_supercell(1),
+    "perovskite40": lambda: inputs.perovskite_supercell(2),
+    "perovskite135": lambda: inputs.perovskite_supercell(3),
     "perovskite320": lambda: inputs.workload_by_name("perovskite320"),
     "perovskite1080": lambda: inputs.workload_by_name("perovskite1080"),
 }
