@@ -279,6 +279,46 @@ def _errs(got, ref):
     return {"errE": abs(got[0] - ref[0]) / abs(ref[0]), "errF": _rel(got[1], ref[1]), "errS": _rel(got[2], ref[2])}
 
 
+PEROVSKITE = ("perovskite320: 4x4x4 CsSnI3-shaped cubic perovskite, 320 atoms, n_ao 18/13/13, n_abf 75/60/60 "
+              "(Cs/Sn/I), r_c 4.2 A, jittered, theta 1e-10")
+
+
+def perovskite_line(torch, dev, stream, local, steps=3):
+    """The 320-atom three-species perovskite in BF16X6 (the split kernels for
+    n_ao > 16) against the FP64 GPU path on the same GB300: rate of each,
+    the errors of the split result on the first geometry, per-stage times."""
+    from paper_2412_11081_gb300 import hfx, inputs
+    w = inputs.workload_by_name("perovskite320")
+    n = w.n_atoms
+    geoms = inputs.geometry_sequence(w, steps + 3, seed=23)
+    d_pos = [torch.tensor(g, dtype=torch.float64, device=dev) for g in geoms]
+    d_out = torch.zeros(1 + 3 * n + 9, dtype=torch.float64, device=dev)
+
+    def result(plan, k):
+        plan.evaluate_device(w.lattice, d_pos[k].data_ptr(), d_out.data_ptr())
+        v = d_out.cpu().numpy()
+        return float(v[0]), v[1:1 + 3 * n].reshape(n, 3).copy(), v[1 + 3 * n:].reshape(3, 3).copy()
+
+    out = {"workload": PEROVSKITE, "precision": "bf16x6"}
+    with hfx.Plan(w, precision=hfx.HFX_FP64, stream=stream.cuda_stream, device=local) as p:
+        ref = result(p, 0)
+        out["fp64_evals_per_s"] = 1.0 / _time_device(p, w, d_pos, d_out, 1, 1, stream, torch)
+    with hfx.Plan(w, precision=hfx.HFX_BF16X6, stream=stream.cuda_stream, device=local) as p:
+        out.update(_errs(result(p, 0), ref))
+        p.evaluate_device(w.lattice, d_pos[1].data_ptr(), d_out.data_ptr())
+        t = _time_device(p, w, d_pos, d_out, 2, steps, stream, torch) / steps
+        out["evals_per_s"] = 1.0 / t
+        out["speedup_over_fp64"] = out["evals_per_s"] / out["fp64_evals_per_s"]
+        p.set_timing(True)
+        p.evaluate_device(w.lattice, d_pos[2].data_ptr(), d_out.data_ptr(), stats=True)
+        st = p.stats.as_dict()
+        out["stages_ms"] = {k: st[k] for k in ("ms_blocks", "ms_screen", "ms_y", "ms_term1", "ms_term2", "ms_total")}
+        out["gflop_per_eval"] = st["flops_total"] / 1e9
+        out["achieved_tflops"] = st["flops_total"] / t / 1e12
+        out["kernels"] = "k_ybuild_w, k_term1_w, k_term2_w, k_q2_w (warp-level MMAs on bf16 pieces, n_ao up to 32)"
+    return out
+
+
 def run_ours(args):
     import torch
     rank, world, local = _env_rank()
@@ -454,6 +494,9 @@ def run_ours(args):
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
             cpu = cpu_baseline(n)
+        perov = None
+        if world == 1 and not args.no_perovskite:
+            perov = perovskite_line(torch, dev, stream, local)
         h2d = 3 * n * 8
         d2h = (1 + 3 * n + 9) * 8
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -481,6 +524,7 @@ def run_ours(args):
                          "term1_kernel_tflops": fp64_stats["flops_term1"] / fp64_stats["ms_term1_kernel"] / 1e9
                          if fp64_stats["ms_term1_kernel"] > 0 else None},
                 "other_precisions": other,
+                "perovskite320": perov,
                 "graph_replay": graph_cmp,
                 "stages_ms": stage_ms,
                 "autotune": tuned,
@@ -509,6 +553,7 @@ def main():
                     help="headline precision; auto = bf16x6")
     ap.add_argument("--no-autotune", action="store_true", help="keep the plans' initial launch shapes")
     ap.add_argument("--no-graph", action="store_true", help="skip the frozen-plan graph replay comparison")
+    ap.add_argument("--no-perovskite", action="store_true", help="skip the 320-atom perovskite line (BF16X6 vs FP64)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -233,8 +233,8 @@ struct hfx_plan {
   hfx::WideShapes ws{};
   int wide_RB = 0;             // 64-row blocks of the largest Y block
   int wide_maxrows = 0;        // most rows (alpha, a) of a C block
-  float* Yw = nullptr;
-  long long Ywcap = 0;
+  uint16_t* Cw = nullptr;      // C pieces of every C pair (written per call)
+  long long* cw_off = nullptr;
   uint16_t* Zw = nullptr;      // Z^{AB} of one pass's second-product pairs (bf16 pieces)
   long long Zwcap = 0;
   uint16_t* Dw = nullptr;      // bf16 pieces of every D block (fixed for the plan)
@@ -665,7 +665,7 @@ void build_lists(hfx_plan* P, const double* L, const double* pos) {
     v_size[p] = 4ll * P->n_abf[P->species[v_home[p]]] * P->n_abf[P->species[v_j[p]]];
   for (int y = 0; y < nY; ++y) {
     const int sX = P->species[y_home[y]], sz = P->species[y_j[y]];
-    if (P->np && !P->wide)  // bf16 pieces of [alpha][z][rup16(n_ao(X))]
+    if (P->np)  // bf16 pieces of [alpha][z][rup16(n_ao(X))]
       y_size[y] = (long long)P->np * P->n_abf[sX] * P->n_ao[sz] * ((P->n_ao[sX] + 15) / 16 * 16);
     else
       y_size[y] = (long long)P->n_abf[sX] * P->n_ao[sX] * P->n_ao[sz];
@@ -726,6 +726,16 @@ void build_lists(hfx_plan* P, const double* L, const double* pos) {
   P->y_list = P->lalloc<int>(nY);
   P->gC = P->lalloc<double>(3 * (size_t)nC);
   P->gV = P->lalloc<double>(3 * (size_t)nV);
+  if (P->wide) {   // C pieces (per call, every C pair)
+    std::vector<long long> cw_off(nC + 1, 0);
+    for (int p = 0; p < nC; ++p) {
+      const int sA = P->species[c_home[p]], sj = P->species[c_j[p]];
+      cw_off[p + 1] = cw_off[p] + hfx::wide_cpieces_size(P->np, P->n_abf[sA], P->n_ao[sA], P->n_ao[sj]);
+    }
+    P->cw_off = P->lalloc<long long>(nC + 1);
+    P->Cw = P->lalloc<uint16_t>(std::max(1LL, cw_off[nC]));
+    upload(P->cw_off, cw_off, s);
+  }
   if (P->np) {   // key groups of the Y build
     P->gcnt = P->lalloc<int>(N);
     P->goff = P->lalloc<long long>(N);
@@ -1186,8 +1196,10 @@ void evaluate_launches(hfx_plan* P, const double* L, hfx_stats* st, bool tail) {
     D.Yst = P->Yst;
     ck(hfx::launch_ybuild(D, P->y_list, (int)P->tot[1], s), "ybuild");
   } else if (P->wide) {
-    ensure_buf(P, P->Yw, P->Ywcap, std::max(1LL, P->tot[0]));
-    ck(hfx::launch_ybuild_w(D, P->np, P->Yw, P->y_list, P->gX, P->gS, P->gN, (int)P->tot[9], P->wide_RB, s),
+    ensure_buf(P, P->Ysp, P->Yspcap, std::max(1LL, P->tot[0]));
+    ck(hfx::launch_cpieces_w(D, P->np, P->Cw, P->cw_off, s), "C pieces");
+    ck(hfx::launch_ybuild_w(D, P->np, P->Ysp, P->Cw, P->cw_off, P->Dw, P->dw_off, P->y_list, P->gX, P->gS, P->gN,
+                            (int)P->tot[9], P->wide_RB, s),
        "ybuild");
   } else {
     ensure_buf(P, P->Ysp, P->Yspcap, P->tot[0]);
@@ -1240,7 +1252,9 @@ void evaluate_launches(hfx_plan* P, const double* L, hfx_stats* st, bool tail) {
       ck(hfx::launch_vblocks(D, P->v_list + v0, (int)ct[CT_VN], s), "vblocks");
       k1a.push_back(tm.mark());
       if (P->wide)
-        ck(hfx::launch_term1_w(D, P->np, P->Yw, P->t1_list + v0, (int)ct[CT_T1], P->ws, s), "term1");
+        ck(hfx::launch_term1_w(D, P->np, P->Ysp, P->Cw, P->cw_off, P->Dw, P->dw_off, P->t1_list + v0,
+                               (int)ct[CT_T1], P->ws, s),
+           "term1");
       else
         ck(hfx::launch_term1(D, P->t1_list + v0, (int)ct[CT_T1], P->beta_chunk, P->smem_t1, s), "term1");
       k1b.push_back(tm.mark());
@@ -1249,7 +1263,7 @@ void evaluate_launches(hfx_plan* P, const double* L, hfx_stats* st, bool tail) {
       if (P->wide) {
         ensure_buf(P, P->Zw, P->Zwcap,
                    std::max(1LL, ct[CT_T2]) * P->np * hfx::wide_zplane(P->wide_maxrows, P->ws.KZ));
-        ck(hfx::launch_term2_w(D, P->np, P->Yw, P->Zw, P->Dw, P->dw_off, P->t2_list + v0, P->t2_idx, (int)ct[CT_T2],
+        ck(hfx::launch_term2_w(D, P->np, P->Ysp, P->Zw, P->Dw, P->dw_off, P->t2_list + v0, P->t2_idx, (int)ct[CT_T2],
                                a0, a1, P->wide_maxrows, P->maxC, P->ws, s),
            "term2");
       } else

@@ -247,8 +247,9 @@ cudaError_t launch_t1_umma(const DevPlan& P, const MixPlan& X, const T1UPlan& U,
                            size_t smem, int* work, int* err, cudaStream_t s);
 
 // Split-precision kernels for n_ao up to 32 and n_abf up to 128 (hfx_wide.cu):
-// warp-level MMAs on bf16 pieces staged from the FP64 C, V and D blocks and
-// an FP32 Y store (offsets y_off, layout [alpha][x][z] as the FP64 store).
+// warp-level MMAs on bf16 pieces copied from piece stores of D (plan), C (per
+// call, from the FP64 blocks), Y (the Y build; offsets y_off, the split
+// path's layout [alpha][z][rup16(n_ao(X))]) and Z (per pass); V and grad V FP64.
 struct WideShapes {
   int MA = 0, MB = 0;          // n_abf rounded up to 16
   int KZ = 0;                  // n_ao rounded up to 16
@@ -261,9 +262,14 @@ long long wide_launch_count();
 WideShapes wide_shapes(int np, int maxABF, int maxAO, size_t limit);
 int wide_ybuild_row_blocks(int max_rows);
 cudaError_t set_wide_smem_limits(int np);
-cudaError_t launch_ybuild_w(const DevPlan& P, int np, float* Yw, const int* ylist, const int* gX, const int* gS,
-                            const int* gN, int ngroups, int RB, cudaStream_t s);
-cudaError_t launch_term1_w(const DevPlan& P, int np, const float* Yw, const int* list, int n, const WideShapes& w,
+// C pieces: per kept C pair, NP planes [alpha][rup8(n_ao(A) n_ao(F))] at Cw + cw_off[q]
+long long wide_cpieces_size(int np, int n_abf, int n_ao_a, int n_ao_f);
+cudaError_t launch_cpieces_w(const DevPlan& P, int np, uint16_t* Cw, const long long* cw_off, cudaStream_t s);
+cudaError_t launch_ybuild_w(const DevPlan& P, int np, uint16_t* Yp, const uint16_t* Cw, const long long* cw_off,
+                            const uint16_t* Dw, const long long* dw_off, const int* ylist, const int* gX,
+                            const int* gS, const int* gN, int ngroups, int RB, cudaStream_t s);
+cudaError_t launch_term1_w(const DevPlan& P, int np, const uint16_t* Yp, const uint16_t* Cw, const long long* cw_off,
+                           const uint16_t* Dw, const long long* dw_off, const int* list, int n, const WideShapes& w,
                            cudaStream_t s);
 // elements per bf16 piece plane of one pair slot of the Z store (rows (alpha, a), row stride KZ)
 long long wide_zplane(int max_rows, int KZ);
@@ -272,7 +278,7 @@ long long wide_zplane(int max_rows, int KZ);
 cudaError_t launch_dsplit_w(const DevPlan& P, int np, uint16_t* Dw, const long long* dw_off, cudaStream_t s);
 // Second product of the home atoms [a0, a1): k_term2_w over the pass's pair
 // list (E, g^V and the Z piece store), then k_q2_w (grad C); slot0 as launch_term2_mma.
-cudaError_t launch_term2_w(const DevPlan& P, int np, const float* Yw, uint16_t* Zw, const uint16_t* Dw,
+cudaError_t launch_term2_w(const DevPlan& P, int np, const uint16_t* Yp, uint16_t* Zw, const uint16_t* Dw,
                            const long long* dw_off, const int* list, const long long* slot0, int n, int a0, int a1,
                            int max_rows, int max_c, const WideShapes& w, cudaStream_t s);
 

@@ -5,9 +5,14 @@
 // Same factorisation and the same bf16 piece products as hfx_mixed.cu (NP
 // pieces per operand, the products (i, j) with i + j < NP, FP32 accumulation
 // in warp-level MMAs, FP64 screening, gradients and reductions), organised
-// like the FP64 kernels of hfx_kernels.cu so that any n_ao and n_abf fit:
-// operands are the FP64 blocks (C, grad C, V, grad V, D) and an FP32 store of
-// the Y blocks, split into bf16 pieces where they are staged in shared memory.
+// like the FP64 kernels of hfx_kernels.cu so that any n_ao and n_abf fit.
+// Operands are split into bf16 pieces once, into stores that the kernels copy
+// from:
+//   D pieces   per D block, NP planes [rup16(n_ao(I))][rup16(n_ao(J))]   (plan)
+//   C pieces   per C pair, NP planes [alpha][rup8(n_ao(A) n_ao(F))]        (per call)
+//   Y pieces   per needed key (X; Z), NP planes [alpha][z][rup16(n_ao(X))] (Y build)
+//   Z pieces   per second-product pair, NP planes [(alpha, a)][KZ]        (per pass)
+// V and grad V stay FP64 (one pair per CTA reads them once).
 //
 //   k_ybuild_w  Y^{XZ}[alpha][x][z] = sum_W sum_w C_XW[alpha][x][w] D_WZ[w][z]
 //               per group of up to 8 keys (X; Z) of one home atom X and 64 rows
@@ -19,7 +24,7 @@
 //                 Q  = V_AB . U     (dotted with grad C_AF at once)
 //   k_term2_w   per kept (A,B) of the second product, over ranges of a:
 //                 R2 += Y^{AB} . Y^{BA}   (K = (a, b))
-//                 Z   = V_AB . Y^{BA}     (rows (alpha, a), to a bf16 piece store)
+//                 Z   = V_AB . Y^{BA}     (rows (alpha, a), to the Z pieces)
 //   k_q2_w      per (A, 128 rows (alpha, a), 8 C pairs (A,F)):
 //                 Q2 = sum_B Z^{AB} . D_FB^T, dotted with grad C_AF
 // (Eq. exx_expand by the distributive law; Eq. Fexx1 for the gradients.)
@@ -155,6 +160,27 @@ __global__ void k_dsplit_w(DevPlan P, uint16_t* Dw, const long long* dw_off) {
   }
 }
 
+// ------------------------------------------------------------------ C pieces
+// Kept C pair q (evaluated this call, FP64) -> NP bf16 planes of
+// [alpha][rup8(n_ao(A) n_ao(F))] (columns (a, f) as in the FP64 block, zero
+// padded) at Cw + cw_off[q].
+__host__ __device__ inline int cw_cols(int nA, int nF) { return (nA * nF + 7) & ~7; }
+
+template <int NP>
+__global__ void k_cpieces_w(DevPlan P, uint16_t* Cw, const long long* cw_off) {
+  for (int q = blockIdx.x; q < P.nC; q += gridDim.x) {
+    if (!P.c_keep[q]) continue;
+    const int sA = P.species[P.c_home[q]], sF = P.species[P.c_j[q]];
+    const int mA = P.n_abf[sA], naf = P.n_ao[sA] * P.n_ao[sF], CW = cw_cols(P.n_ao[sA], P.n_ao[sF]);
+    const double* src = P.Cst + P.c_off[q];
+    uint16_t* out = Cw + cw_off[q];
+    for (int e = threadIdx.x; e < mA * CW; e += blockDim.x) {
+      const int al = e / CW, c = e - al * CW;
+      put_pieces<NP>(out, (long long)mA * CW, e, c < naf ? (float)src[(long long)al * naf + c] : 0.f);
+    }
+  }
+}
+
 // ------------------------------------------------------------------ Y build
 // CTA = (key group g, 64-row block rb).  Warp w: rows 16 (w & 3) of the block,
 // keys 4 (w >> 2) .. + 3 of the group, all z of each key (n_ao(Z) <= 32: four
@@ -166,12 +192,15 @@ constexpr int kYS = 24;
 size_t ybuild_w_smem(int np) { return (size_t)np * (kYRows + 256) * kYS * sizeof(uint16_t); }
 
 template <int NP>
-__global__ void __launch_bounds__(kWThreads) k_ybuild_w(DevPlan P, float* __restrict__ Yw, const int* ylist,
-                                                        const int* gX, const int* gS, const int* gN, int RB) {
+__global__ void __launch_bounds__(kWThreads) k_ybuild_w(DevPlan P, uint16_t* __restrict__ Yp,
+                                                        const uint16_t* __restrict__ Cw, const long long* cw_off,
+                                                        const uint16_t* __restrict__ Dw, const long long* dw_off,
+                                                        const int* ylist, const int* gX, const int* gS, const int* gN,
+                                                        int RB) {
   extern __shared__ __align__(16) unsigned char smem[];
   uint16_t* As = reinterpret_cast<uint16_t*>(smem);   // [NP][64][kYS]
   uint16_t* Bs = As + NP * kYRows * kYS;              // [NP][256][kYS]
-  __shared__ int m_di[kMaxCPerAtom][8];
+  __shared__ int m_dw[kMaxCPerAtom][8];   // D piece block of (C pair t, key i) in 256-element units, or -1
   __shared__ int m_step[2 * kMaxCPerAtom];
   __shared__ int s_key[8], s_zat[8], s_nz[8];
   __shared__ int s_nsteps;
@@ -179,7 +208,7 @@ __global__ void __launch_bounds__(kWThreads) k_ybuild_w(DevPlan P, float* __rest
   const int g = blockIdx.x / RB, rb = blockIdx.x - g * RB;
   const int Xa = gX[g], kstart = gS[g], nk = gN[g];
   const int sX = P.species[Xa];
-  const int mX = P.n_abf[sX], nX = P.n_ao[sX];
+  const int mX = P.n_abf[sX], nX = P.n_ao[sX], KX = rup16(nX);
   const int rows = mX * nX;
   const int row0 = rb * kYRows;
   if (row0 >= rows) return;
@@ -192,18 +221,17 @@ __global__ void __launch_bounds__(kWThreads) k_ybuild_w(DevPlan P, float* __rest
     s_nz[i] = key >= 0 ? P.n_ao[P.species[P.y_j[key]]] : 0;
   }
   __syncthreads();
-  // D block of every (kept C pair t, key i), or -1
   for (int e = threadIdx.x; e < nq * 8; e += blockDim.x) {
     const int t = e >> 3, i = e & 7;
     const int q = q0 + t;
-    int di = -1;
+    int dw = -1;
     if (s_key[i] >= 0 && P.c_keep[q]) {
       const int* Rw = P.c_R + 3 * q;
       const int* Rz = P.y_R + 3 * s_key[i];
-      di = dlut_get(P, P.c_j[q], s_zat[i], Rz[0] - Rw[0], Rz[1] - Rw[1], Rz[2] - Rw[2]);
-      if (di >= 0 && P.Dkept[di] == 0.0) di = -1;
+      const int di = dlut_get(P, P.c_j[q], s_zat[i], Rz[0] - Rw[0], Rz[1] - Rw[1], Rz[2] - Rw[2]);
+      if (di >= 0 && P.Dkept[di] != 0.0) dw = (int)(dw_off[di] >> 8);
     }
-    m_di[t][i] = di;
+    m_dw[t][i] = dw;
   }
   __syncthreads();
   if (threadIdx.x == 0) {   // K steps: (kept C pair with a D block among the keys, 16-column step)
@@ -213,7 +241,7 @@ __global__ void __launch_bounds__(kWThreads) k_ybuild_w(DevPlan P, float* __rest
       bool any = false;
       const int nW = P.n_ao[P.species[P.c_j[q0 + t]]];
       for (int i = 0; i < 8; ++i)
-        if (m_di[t][i] >= 0) {
+        if (m_dw[t][i] >= 0) {
           any = true;
           fl += 2.0 * rows * s_nz[i] * nW;
         }
@@ -240,21 +268,30 @@ __global__ void __launch_bounds__(kWThreads) k_ybuild_w(DevPlan P, float* __rest
   for (int k = 0; k < nsteps; ++k) {
     const int t = m_step[k] >> 8, k0 = m_step[k] & 255;
     const int q = q0 + t;
-    const int nW = P.n_ao[P.species[P.c_j[q]]];
-    const double* C = P.Cst + P.c_off[q];
+    const int nW = P.n_ao[P.species[P.c_j[q]]], pw = rup16(nW);
+    const int CW = cw_cols(nX, nW);
+    const uint16_t* C = Cw + cw_off[q];   // NP planes [alpha][(x, w)]
+    const long long cplane = (long long)mX * CW;
     __syncthreads();   // previous step's fragments read
     for (int e = threadIdx.x; e < kYRows * 16; e += blockDim.x) {
       const int r = e >> 4, c = e & 15;
       const int row = row0 + r, w = k0 + c;
-      put_pieces<NP>(As, pA, r * kYS + c, (row < rows && w < nW) ? (float)C[(long long)row * nW + w] : 0.f);
+      const bool in = row < rows && w < nW;
+      const int al = row / nX, x = row - al * nX;
+      const long long o = (long long)al * CW + x * nW + w;
+#pragma unroll
+      for (int pp = 0; pp < NP; ++pp) As[pp * pA + r * kYS + c] = in ? C[pp * cplane + o] : (uint16_t)0;
     }
     for (int e = threadIdx.x; e < 256 * 16; e += blockDim.x) {
       const int rz = e >> 4, c = e & 15;
       const int i = rz >> 5, z = rz & 31, w = k0 + c;
-      const int di = m_di[t][i];
-      float v = 0.f;
-      if (di >= 0 && w < nW && z < s_nz[i]) v = (float)P.Dval[P.Doff[di] + (long long)w * s_nz[i] + z];
-      put_pieces<NP>(Bs, pB, rz * kYS + c, v);
+      const int dw = m_dw[t][i];
+      const int pz = rup16(s_nz[i]);
+      const bool in = dw >= 0 && w < pw && z < pz;
+      const uint16_t* Dg = Dw + ((long long)(in ? dw : 0) << 8);
+#pragma unroll
+      for (int pp = 0; pp < NP; ++pp)
+        Bs[pp * pB + rz * kYS + c] = in ? Dg[(long long)pp * pw * pz + w * pz + z] : (uint16_t)0;
     }
     __syncthreads();
     uint32_t af[NP][4];
@@ -263,7 +300,7 @@ __global__ void __launch_bounds__(kWThreads) k_ybuild_w(DevPlan P, float* __rest
 #pragma unroll
     for (int ii = 0; ii < 4; ++ii) {
       const int i = 4 * kh + ii;
-      if (m_di[t][i] < 0) continue;
+      if (m_dw[t][i] < 0) continue;
 #pragma unroll
       for (int nt = 0; nt < 4; ++nt) {
         if (nt * 8 >= nz4[ii]) break;
@@ -275,20 +312,31 @@ __global__ void __launch_bounds__(kWThreads) k_ybuild_w(DevPlan P, float* __rest
       }
     }
   }
-  // Y (FP32) [alpha][x][z] = row (alpha, x), column z
+  // Y pieces [alpha][z][x] (x padded to rup16(n_ao(X)) with zeros, written
+  // with the row x = n_ao(X) - 1)
 #pragma unroll
   for (int ii = 0; ii < 4; ++ii) {
     const int key = s_key[4 * kh + ii];
     if (key < 0) continue;
-    float* Y = Yw + P.y_off[key];
+    const int nZ = nz4[ii];
+    uint16_t* Y = Yp + P.y_off[key];
+    const long long plane = (long long)mX * nZ * KX;
 #pragma unroll
     for (int nt = 0; nt < 4; ++nt) {
-      if (nt * 8 >= nz4[ii]) break;
+      if (nt * 8 >= nZ) break;
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         const int row = row0 + mt * 16 + gid + ((c & 2) ? 8 : 0);
         const int z = nt * 8 + 2 * tig + (c & 1);
-        if (row < rows && z < nz4[ii]) Y[(long long)row * nz4[ii] + z] = acc[ii][nt][c];
+        if (row < rows && z < nZ) {
+          const int al = row / nX, x = row - al * nX;
+          const long long o = ((long long)al * nZ + z) * KX;
+          put_pieces<NP>(Y, plane, (int)(o + x), acc[ii][nt][c]);
+          if (x == nX - 1)
+            for (int xp = nX; xp < KX; ++xp)
+#pragma unroll
+              for (int pp = 0; pp < NP; ++pp) Y[pp * plane + o + xp] = 0;
+        }
       }
     }
   }
@@ -298,7 +346,7 @@ __global__ void __launch_bounds__(kWThreads) k_ybuild_w(DevPlan P, float* __rest
 // Shared memory (bf16 planes; strides are multiples of 8 elements with an
 // odd count of 16-byte chunks, so that ldmatrix rows hit distinct banks):
 //   Vs[NP][MA][MB + 8]   V_AB (rows alpha, columns beta; zero padded)
-//   Ds[NP][40][40]       D_AB (rows a, columns b; zero padded)
+//   Ds[NP][48][40]       D_AB (rows a, columns b; zero padded; 16 rows from any a0 < 32)
 //   Cs[NP][MA][KC + 8]   C_AF columns (a, f) of the current range of a
 //   Us[NP][MB][KC + 8]   U of the same columns (rows beta)
 struct T1W {
@@ -306,12 +354,14 @@ struct T1W {
 };
 
 __host__ __device__ inline size_t term1w_smem(int np, int MA, int MB, int KC) {
-  return (size_t)np * 2 * ((size_t)MA * (MB + 8) + 40 * 40 + (size_t)MA * (KC + 8) + (size_t)MB * (KC + 8));
+  return (size_t)np * 2 * ((size_t)MA * (MB + 8) + 48 * 40 + (size_t)MA * (KC + 8) + (size_t)MB * (KC + 8));
 }
 
 template <int NP>
-__global__ void __launch_bounds__(kWThreads) k_term1_w(DevPlan P, const float* __restrict__ Yw, const int* list,
-                                                       int n_list, T1W S) {
+__global__ void __launch_bounds__(kWThreads) k_term1_w(DevPlan P, const uint16_t* __restrict__ Yp,
+                                                       const uint16_t* __restrict__ Cw, const long long* cw_off,
+                                                       const uint16_t* __restrict__ Dw, const long long* dw_off,
+                                                       const int* list, int n_list, T1W S) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[4 * kWarpsW];
   __shared__ double s_g[3];
@@ -319,7 +369,7 @@ __global__ void __launch_bounds__(kWThreads) k_term1_w(DevPlan P, const float* _
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gid = lane >> 2, tig = lane & 3;
   const int MA = S.MA, MB = S.MB;
   const int SV = MB + 8, SD = 40, SK = S.KC + 8;
-  const long long pV = (long long)MA * SV, pD = 40 * SD, pC = (long long)MA * SK, pU = (long long)MB * SK;
+  const long long pV = (long long)MA * SV, pD = 48 * SD, pC = (long long)MA * SK, pU = (long long)MB * SK;
   uint16_t* Vs = reinterpret_cast<uint16_t*>(smem);
   uint16_t* Ds = Vs + NP * pV;
   uint16_t* Cs = Ds + NP * pD;
@@ -333,7 +383,8 @@ __global__ void __launch_bounds__(kWThreads) k_term1_w(DevPlan P, const float* _
     const int MAp = rup16(mA), MBp = rup16(mB), KB = rup16(nB);
     const double* V = P.Vst + P.v_off[p];
     const int nvb = mA * mB;
-    const double* Dg = P.Dval + P.Doff[P.v_didx[p]];
+    const int pa = rup16(nA);
+    const uint16_t* Dg = Dw + dw_off[P.v_didx[p]];   // D_AB pieces [pa][KB]
     __syncthreads();   // previous pair done with every buffer
     if (threadIdx.x == 0) {
       s_g[0] = s_g[1] = s_g[2] = 0.0;
@@ -343,9 +394,11 @@ __global__ void __launch_bounds__(kWThreads) k_term1_w(DevPlan P, const float* _
       const int al = e / SV, be = e - al * SV;
       put_pieces<NP>(Vs, pV, e, (al < mA && be < mB) ? (float)V[al * mB + be] : 0.f);
     }
-    for (int e = threadIdx.x; e < 40 * SD; e += blockDim.x) {
+    for (int e = threadIdx.x; e < 48 * SD; e += blockDim.x) {
       const int a = e / SD, bb = e - a * SD;
-      put_pieces<NP>(Ds, pD, e, (a < nA && bb < nB) ? (float)Dg[a * nB + bb] : 0.f);
+      const bool in = a < pa && bb < KB;
+#pragma unroll
+      for (int pp = 0; pp < NP; ++pp) Ds[pp * pD + e] = in ? Dg[(long long)pp * pa * KB + a * KB + bb] : (uint16_t)0;
     }
     // U rows beyond n_abf(B) stay zero (they meet the zero V columns in Q)
     for (int e = threadIdx.x; e < (MB - mB) * SK; e += blockDim.x)
@@ -401,8 +454,11 @@ __global__ void __launch_bounds__(kWThreads) k_term1_w(DevPlan P, const float* _
         const int* Rf = P.c_R + 3 * q;
         const int nF = P.n_ao[P.species[f]];
         const int yc = ylut_get(P, b, f, Rf[0] - Rb[0], Rf[1] - Rb[1], Rf[2] - Rb[2]);
-        const float* Y = Yw + P.y_off[yc];             // [beta][b][f]
-        const double* C = P.Cst + P.c_off[q];           // [alpha][a][f]
+        const uint16_t* Y = Yp + P.y_off[yc];          // NP planes [beta][f][KB] (b padded)
+        const long long yplane = (long long)mB * nF * KB;
+        const int CW = cw_cols(nA, nF);
+        const uint16_t* C = Cw + cw_off[q];             // NP planes [alpha][(a, f)] (row length CW)
+        const long long cplane = (long long)mA * CW;
         const double* dC = P.dCst + 3 * P.c_off[q];
         const long long nc = (long long)mA * nA * nF;
         const int rowsU = mB * nF;
@@ -419,9 +475,30 @@ __global__ void __launch_bounds__(kWThreads) k_term1_w(DevPlan P, const float* _
           }
           if (threadIdx.x == 0) s_q = q;
           // C_AF columns (a, f), a in [a0, a0 + dA): contiguous in each row alpha
-          for (int e = threadIdx.x; e < mA * KCc; e += blockDim.x) {
-            const int al = e / KCc, c = e - al * KCc;
-            put_pieces<NP>(Cs, pC, al * SK + c, c < dcols ? (float)C[(long long)al * nA * nF + a0 * nF + c] : 0.f);
+          // of the C pieces; 16-byte copies where the range starts on a
+          // 16-byte boundary (a range of 8 a: it ends on one too, or at the
+          // row's zero padding), else element copies
+          const int c0 = a0 * nF;
+          if ((c0 & 7) == 0 && ((dcols & 7) == 0 || a0 + dA == nA)) {
+            const int nch = (dcols + 7) >> 3;
+            for (int e = threadIdx.x; e < NP * mA * nch; e += blockDim.x) {
+              const int pp = e / (mA * nch), rr = e - pp * mA * nch, al = rr / nch, c = rr - al * nch;
+              cpa16(Cs + pp * pC + al * SK + 8 * c, C + pp * cplane + (long long)al * CW + c0 + 8 * c);
+            }
+            const int cz = nch * 8;
+            for (int e = threadIdx.x; e < mA * (KCc - cz); e += blockDim.x) {
+              const int al = e / (KCc - cz), c = cz + (e - al * (KCc - cz));
+#pragma unroll
+              for (int pp = 0; pp < NP; ++pp) Cs[pp * pC + al * SK + c] = 0;
+            }
+            cpa_commit();
+          } else {
+            for (int e = threadIdx.x; e < mA * KCc; e += blockDim.x) {
+              const int al = e / KCc, c = e - al * KCc;
+#pragma unroll
+              for (int pp = 0; pp < NP; ++pp)
+                Cs[pp * pC + al * SK + c] = c < dcols ? C[pp * cplane + (long long)al * CW + c0 + c] : (uint16_t)0;
+            }
           }
           // U columns past the range stay zero up to the 16-column step
           for (int e = threadIdx.x; e < mB * (KCc - dcols); e += blockDim.x) {
@@ -429,41 +506,46 @@ __global__ void __launch_bounds__(kWThreads) k_term1_w(DevPlan P, const float* _
 #pragma unroll
             for (int pp = 0; pp < NP; ++pp) Us[pp * pU + (long long)be * SK + c] = 0;
           }
-          // U[(beta, f)][a] = sum_b Y[beta][b][f] D_AB[a][b]: rows (beta, f), one tile of 8 a
-          for (int mt = warp; mt * 16 < rowsU; mt += kWarpsW) {
-            float acc[4] = {0.f, 0.f, 0.f, 0.f};
-            const int r0 = mt * 16 + gid, r1 = r0 + 8;
-            const int be0 = r0 / nF, f0 = r0 - be0 * nF, be1 = r1 / nF, f1 = r1 - be1 * nF;
-            for (int k0 = 0; k0 < KB; k0 += 16) {
-              uint32_t af[NP][4], bf[NP][2];
+          // U^T[a][(beta, f)] = sum_b D_AB[a][b] Y^{BF}[beta][b][f]: rows a0 .. a0 + 15 of D_AB
+          // (the A fragments, kept for the range), columns (beta, f) eight at a
+          // time from the Y pieces (rows (beta, f), K = b); rows a >= a0 + dA unused
+          {
+            uint32_t af[2][NP][4];
 #pragma unroll
-              for (int h = 0; h < 4; ++h) {
-                const bool hi = h & 1;
-                const int r = hi ? r1 : r0, be = hi ? be1 : be0, ff = hi ? f1 : f0;
-                const int kc = k0 + 2 * tig + ((h & 2) ? 8 : 0);
-                const bool in = r < rowsU;
-                const float x0 = (in && kc < nB) ? Y[((long long)be * nB + kc) * nF + ff] : 0.f;
-                const float x1 = (in && kc + 1 < nB) ? Y[((long long)be * nB + kc + 1) * nF + ff] : 0.f;
-                uint32_t w[NP];
-                split_pair<NP>(x0, x1, w);
-#pragma unroll
-                for (int pp = 0; pp < NP; ++pp) af[pp][h] = w[pp];
-              }
+            for (int ks = 0; ks < 2; ++ks)
 #pragma unroll
               for (int pp = 0; pp < NP; ++pp)
-                ldm_x2(bf[pp], Ds + pp * pD + (a0 + (lane & 7)) * SD + k0 + (((lane >> 3) & 1) << 3));
-              mma_split<NP>(acc, af, bf);
-            }
+                ldm_x4(af[ks][pp], Ds + pp * pD + (a0 + (lane & 15)) * SD + ks * 16 + ((lane >> 4) << 3));
+            for (int nt = warp; nt * 8 < rowsU; nt += kWarpsW) {
+              float acc[4] = {0.f, 0.f, 0.f, 0.f};
+              const int rn = nt * 8 + gid;
+              const bool in = rn < rowsU;
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-              const int r = (c & 2) ? r1 : r0;
-              const int al = 2 * tig + (c & 1);
-              if (r < rowsU && al < dA) {
-                const int be = (c & 2) ? be1 : be0, ff = (c & 2) ? f1 : f0;
-                put_pieces<NP>(Us, pU, be * SK + al * nF + ff, acc[c]);
+              for (int ks = 0; ks < 2; ++ks) {
+                if (ks * 16 >= KB) break;
+                uint32_t bf[NP][2];
+#pragma unroll
+                for (int pp = 0; pp < NP; ++pp) {
+                  const uint16_t* yr = Y + pp * yplane + (long long)rn * KB + ks * 16 + 2 * tig;
+                  bf[pp][0] = in ? *reinterpret_cast<const uint32_t*>(yr) : 0u;
+                  bf[pp][1] = in ? *reinterpret_cast<const uint32_t*>(yr + 8) : 0u;
+                }
+                mma_split<NP>(acc, af[ks], bf);
+              }
+              // acc[0], acc[1]: row a0 + gid, columns (beta, f) = nt * 8 + 2 tig, + 1
+              if (gid < dA) {
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                  const int r = nt * 8 + 2 * tig + c;
+                  if (r < rowsU) {
+                    const int be = r / nF, ff = r - be * nF;
+                    put_pieces<NP>(Us, pU, be * SK + gid * nF + ff, acc[c]);
+                  }
+                }
               }
             }
           }
+          cpa_wait<0>();
           __syncthreads();   // Cs and Us complete
           // R += C_AF . U^T (M = alpha, N = beta, K = this range's columns)
 #pragma unroll
@@ -544,8 +626,8 @@ __host__ __device__ inline size_t term2w_smem(int np, int MA, int MB, int KC) {
 }
 
 template <int NP>
-__global__ void __launch_bounds__(kWThreads) k_term2_w(DevPlan P, const float* __restrict__ Yw, uint16_t* __restrict__ Zw,
-                                                       const int* list, int n_list, T2W S) {
+__global__ void __launch_bounds__(kWThreads) k_term2_w(DevPlan P, const uint16_t* __restrict__ Yp,
+                                                       uint16_t* __restrict__ Zw, const int* list, int n_list, T2W S) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[4 * kWarpsW];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gid = lane >> 2, tig = lane & 3;
@@ -564,10 +646,12 @@ __global__ void __launch_bounds__(kWThreads) k_term2_w(DevPlan P, const float* _
     const int MAp = rup16(mA), MBp = rup16(mB);
     const int y1 = ylut_get(P, A, b, Rb[0], Rb[1], Rb[2]);
     const int y2 = ylut_get(P, b, A, -Rb[0], -Rb[1], -Rb[2]);
-    const float* Yab = Yw + P.y_off[y1];   // [alpha][a][b]
-    const float* Yba = Yw + P.y_off[y2];   // [beta][b][a]
+    const int KA = rup16(nA), KB = rup16(nB);
+    const uint16_t* Yab = Yp + P.y_off[y1];   // Y^{AB} pieces [alpha][b][a] (a padded to KA)
+    const uint16_t* Yba = Yp + P.y_off[y2];   // Y^{BA} pieces [beta][a][b] (b padded to KB)
+    const long long plA = (long long)mA * nB * KA, plB = (long long)mB * nA * KB;
     const double* V = P.Vst + P.v_off[p];
-    const int nvb = mA * mB, nab = nA * nB;
+    const int nvb = mA * mB;
     uint16_t* Z = Zw + (long long)kk * NP * S.zplane;   // NP planes [(alpha, a)][KZ]
     __syncthreads();   // previous pair done with every buffer
     {   // zero columns n_ao(B) .. rup16(n_ao(B)) - 1 (K padding of k_q2_w)
@@ -598,18 +682,41 @@ __global__ void __launch_bounds__(kWThreads) k_term2_w(DevPlan P, const float* _
       const int dA = min(S.da, nA - a0);
       const int dcols = dA * nB, KCc = rup16(dcols);
       __syncthreads();   // the previous range is done with Ya and Yb
-      for (int e = threadIdx.x; e < mA * KCc; e += blockDim.x) {
+      // columns c = (b, a - a0): Y^{AB} rows (alpha, b) hold a contiguously,
+      // Y^{BA} rows (beta, a) hold b contiguously; both are read as 16-byte
+      // vectors (a0 and the row lengths are multiples of 8)
+      for (int e = threadIdx.x; e < mA * KCc; e += blockDim.x) {   // padding columns
         const int al = e / KCc, c = e - al * KCc;
-        put_pieces<NP>(Ya, pA, al * SK + c, c < dcols ? Yab[(long long)al * nab + a0 * nB + c] : 0.f);
+        if (c >= dcols)
+#pragma unroll
+          for (int pp = 0; pp < NP; ++pp) Ya[pp * pA + al * SK + c] = 0;
       }
       for (int e = threadIdx.x; e < mB * KCc; e += blockDim.x) {
         const int be = e / KCc, c = e - be * KCc;
-        float v = 0.f;
-        if (c < dcols) {
-          const int al = c / nB, bb = c - al * nB;
-          v = Yba[(long long)be * nab + bb * nA + a0 + al];
+        if (c >= dcols)
+#pragma unroll
+          for (int pp = 0; pp < NP; ++pp) Yb[pp * pB + be * SK + c] = 0;
+      }
+      for (int e = threadIdx.x; e < NP * mA * nB; e += blockDim.x) {   // Y^{AB}: the dA a of a row
+        const int pp = e / (mA * nB), r = e - pp * mA * nB, al = r / nB, bb = r - al * nB;
+        const uint16_t* src = Yab + pp * plA + ((long long)al * nB + bb) * KA + a0;
+        uint16_t* d = Ya + pp * pA + al * SK + bb * dA;
+        if ((a0 & 7) == 0) {   // a0 + 8 <= rup8(n_ao(A)) <= the row length: one 16-byte vector
+          const uint4 v = *reinterpret_cast<const uint4*>(src);
+          const uint16_t* h = reinterpret_cast<const uint16_t*>(&v);
+          for (int j = 0; j < dA; ++j) d[j] = h[j];
+        } else {
+          for (int j = 0; j < dA; ++j) d[j] = src[j];
         }
-        put_pieces<NP>(Yb, pB, be * SK + c, v);
+      }
+      const int nbc = (nB + 7) >> 3;
+      for (int e = threadIdx.x; e < NP * mB * dA * nbc; e += blockDim.x) {   // Y^{BA}: 8 b at once
+        const int pp = e / (mB * dA * nbc), r = e - pp * mB * dA * nbc;
+        const int be = r / (dA * nbc), r2 = r - be * dA * nbc, a = r2 / nbc, bc = r2 - a * nbc;
+        const uint4 v = *reinterpret_cast<const uint4*>(Yba + pp * plB + ((long long)be * nA + a0 + a) * KB + 8 * bc);
+        const uint16_t* h = reinterpret_cast<const uint16_t*>(&v);
+        uint16_t* d = Yb + pp * pB + be * SK + a;
+        for (int j = 0; j < 8 && 8 * bc + j < nB; ++j) d[(8 * bc + j) * dA] = h[j];
       }
       __syncthreads();
       // R2 += Y^{AB} . Y^{BA} (M = alpha, N = beta, K = (a, b) of the range)
@@ -635,7 +742,7 @@ __global__ void __launch_bounds__(kWThreads) k_term2_w(DevPlan P, const float* _
               const int al = mt * 16 + gid + ((c & 2) ? 8 : 0);
               const int n = (nt0 + h) * 8 + 2 * tig + (c & 1);
               if (al < mA && n < dcols && nt0 + h < NTZ) {
-                const int a = n / nB, bb = n - a * nB;
+                const int bb = n / dA, a = n - bb * dA;
                 put_pieces<NP>(Z, S.zplane, (int)(((long long)al * nA + a0 + a) * S.KZ + bb), acc[h][c]);
               }
             }
@@ -960,24 +1067,41 @@ cudaError_t set_wide_smem_limits(int np) {
   return e;
 }
 
-cudaError_t launch_ybuild_w(const DevPlan& P, int np, float* Yw, const int* ylist, const int* gX, const int* gS,
-                            const int* gN, int ngroups, int RB, cudaStream_t s) {
-  if (ngroups <= 0) return cudaSuccess;
-  const long long grid = (long long)ngroups * RB;
-  const size_t smem = ybuild_w_smem(np);
-  if (np == 2) k_ybuild_w<2><<<(unsigned)grid, kWThreads, smem, s>>>(P, Yw, ylist, gX, gS, gN, RB);
-  else k_ybuild_w<3><<<(unsigned)grid, kWThreads, smem, s>>>(P, Yw, ylist, gX, gS, gN, RB);
+cudaError_t launch_cpieces_w(const DevPlan& P, int np, uint16_t* Cw, const long long* cw_off, cudaStream_t s) {
+  if (P.nC <= 0) return cudaSuccess;
+  const int grid = grid_cap(P.nC, 1 << 16);
+  if (np == 2) k_cpieces_w<2><<<grid, 256, 0, s>>>(P, Cw, cw_off);
+  else k_cpieces_w<3><<<grid, 256, 0, s>>>(P, Cw, cw_off);
   ++g_wide_launches;
   return cudaGetLastError();
 }
 
-cudaError_t launch_term1_w(const DevPlan& P, int np, const float* Yw, const int* list, int n, const WideShapes& w,
+long long wide_cpieces_size(int np, int n_abf, int n_ao_a, int n_ao_f) {
+  return (long long)np * n_abf * cw_cols(n_ao_a, n_ao_f);
+}
+
+cudaError_t launch_ybuild_w(const DevPlan& P, int np, uint16_t* Yp, const uint16_t* Cw, const long long* cw_off,
+                            const uint16_t* Dw, const long long* dw_off, const int* ylist, const int* gX,
+                            const int* gS, const int* gN, int ngroups, int RB, cudaStream_t s) {
+  if (ngroups <= 0) return cudaSuccess;
+  const long long grid = (long long)ngroups * RB;
+  const size_t smem = ybuild_w_smem(np);
+  if (np == 2)
+    k_ybuild_w<2><<<(unsigned)grid, kWThreads, smem, s>>>(P, Yp, Cw, cw_off, Dw, dw_off, ylist, gX, gS, gN, RB);
+  else
+    k_ybuild_w<3><<<(unsigned)grid, kWThreads, smem, s>>>(P, Yp, Cw, cw_off, Dw, dw_off, ylist, gX, gS, gN, RB);
+  ++g_wide_launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_term1_w(const DevPlan& P, int np, const uint16_t* Yp, const uint16_t* Cw, const long long* cw_off,
+                           const uint16_t* Dw, const long long* dw_off, const int* list, int n, const WideShapes& w,
                            cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   const T1W S{w.MA, w.MB, w.t1_KC, w.t1_da};
   const int grid = grid_cap(n, 1 << 20);
-  if (np == 2) k_term1_w<2><<<grid, kWThreads, w.smem_t1, s>>>(P, Yw, list, n, S);
-  else k_term1_w<3><<<grid, kWThreads, w.smem_t1, s>>>(P, Yw, list, n, S);
+  if (np == 2) k_term1_w<2><<<grid, kWThreads, w.smem_t1, s>>>(P, Yp, Cw, cw_off, Dw, dw_off, list, n, S);
+  else k_term1_w<3><<<grid, kWThreads, w.smem_t1, s>>>(P, Yp, Cw, cw_off, Dw, dw_off, list, n, S);
   ++g_wide_launches;
   return cudaGetLastError();
 }
@@ -993,14 +1117,14 @@ cudaError_t launch_dsplit_w(const DevPlan& P, int np, uint16_t* Dw, const long l
   return cudaGetLastError();
 }
 
-cudaError_t launch_term2_w(const DevPlan& P, int np, const float* Yw, uint16_t* Zw, const uint16_t* Dw,
+cudaError_t launch_term2_w(const DevPlan& P, int np, const uint16_t* Yp, uint16_t* Zw, const uint16_t* Dw,
                            const long long* dw_off, const int* list, const long long* slot0, int n, int a0, int a1,
                            int max_rows, int max_c, const WideShapes& w, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   const T2W S{w.MA, w.MB, w.t2_KC, w.t2_da, w.KZ, wide_zplane(max_rows, w.KZ)};
   const int grid = grid_cap(n, 1 << 20);
-  if (np == 2) k_term2_w<2><<<grid, kWThreads, w.smem_t2, s>>>(P, Yw, Zw, list, n, S);
-  else k_term2_w<3><<<grid, kWThreads, w.smem_t2, s>>>(P, Yw, Zw, list, n, S);
+  if (np == 2) k_term2_w<2><<<grid, kWThreads, w.smem_t2, s>>>(P, Yp, Zw, list, n, S);
+  else k_term2_w<3><<<grid, kWThreads, w.smem_t2, s>>>(P, Yp, Zw, list, n, S);
   ++g_wide_launches;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

@@ -301,8 +301,9 @@ def alone_vs_mix(backend, structures: List[Structure], records: List[Record], n_
 
 
 class GpuBackend:
-    """Plans through the C ABI, one CUDA stream per plan.  Shapes the split
-    path rejects (n_ao > 16) run on the FP64 path and say so."""
+    """Plans through the C ABI, one CUDA stream per plan, every shape in the
+    requested precision (shapes with n_ao > 16, the perovskite Cs blocks, take
+    the library's wide split-precision kernels)."""
 
     # device bytes per atom before any plan of a shape has been measured
     # (si64: 139 MB per atom in FP64, 367 MB with BF16X6); refined online
@@ -321,15 +322,12 @@ class GpuBackend:
         if s.shape in known:
             return known[s.shape]
         n = len(s.workload.species)
-        prec = self.precision if max(s.workload.n_ao) <= 16 else "fp64"
-        return n * self.DEFAULT_BYTES_PER_ATOM[prec]
+        return n * self.DEFAULT_BYTES_PER_ATOM[self.precision]
 
     def create(self, s: Structure):
         torch, hfx = self.torch, self.hfx
         stream = torch.cuda.Stream(device=self.device)
         code, name = self.code, self.precision
-        if code != hfx.HFX_FP64 and max(s.workload.n_ao) > 16:
-            code, name = hfx.HFX_FP64, "fp64 (n_ao > 16)"
         plan = hfx.Plan(s.workload, precision=code, stream=stream.cuda_stream, device=self.device)
         return _GpuPlan(plan, stream, name, self.clock0)
 

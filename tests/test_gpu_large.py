@@ -7,8 +7,9 @@ share of a range of home atoms [B, E) (the sum over the home atom A of
 Eq. exx_expand restricted to it); the GPU plan here takes the same range
 (hfx_options home_begin / home_end) on the full structure, so every block,
 pair list, Y block and screening decision is that of the full cell.  The
-1000-atom Si-like cell is also evaluated whole, in BF16X6 against FP64 on
-the GPU, where the same plan shapes as the benchmark's run (8 passes).
+1000-atom Si-like cell and the 320-atom perovskite are also evaluated whole,
+in BF16X6 against FP64 on the GPU (the Si cell in the benchmark's 8 passes;
+the perovskite on the split kernels for n_ao > 16).
 """
 import json
 import os
@@ -42,7 +43,8 @@ def workload(name):
 
 
 CASES = [("si1000", 0, 4, hfx.HFX_FP64, 1e-10), ("si1000", 0, 4, hfx.HFX_BF16X6, 1e-5),
-         ("perovskite320", 0, 10, hfx.HFX_FP64, 1e-10), ("perovskite1080", 0, 5, hfx.HFX_FP64, 1e-10)]
+         ("perovskite320", 0, 10, hfx.HFX_FP64, 1e-10), ("perovskite320", 0, 10, hfx.HFX_BF16X6, 1e-5),
+         ("perovskite1080", 0, 5, hfx.HFX_FP64, 1e-10), ("perovskite1080", 0, 5, hfx.HFX_BF16X6, 1e-5)]
 
 
 @pytest.mark.parametrize("name,b,e,prec,tol", CASES)
@@ -78,3 +80,18 @@ def test_si1000_whole_cell_bf16x6_against_fp64():
     for (E, F, S), tol in ((ref, 1e-9), (got, 1e-6)):
         assert np.max(np.abs(F.sum(0))) <= 1e-9 * np.max(np.abs(F))
         assert np.max(np.abs(S - S.T)) <= tol * np.max(np.abs(S))
+
+
+def test_perovskite320_whole_cell_bf16x6_against_fp64():
+    """Every home atom of the CsSnI3-shaped 4x4x4 cell (Cs n_ao 18, n_abf 75):
+    the split result within 1e-5 of the FP64 GPU result, sum F = 0."""
+    w = workload("perovskite320")
+    with hfx.Plan(w, precision=hfx.HFX_FP64) as p:
+        ref = p.evaluate(w.lattice, w.positions)
+    with hfx.Plan(w, precision=hfx.HFX_BF16X6) as p:
+        got = p.evaluate(w.lattice, w.positions)
+    er = errs(got, ref)
+    print(f"perovskite320 BF16X6 vs FP64: errE {er[0]:.2e} errF {er[1]:.2e} errS {er[2]:.2e}")
+    assert max(er) <= 1e-5, er
+    F = got[1]
+    assert np.max(np.abs(F.sum(0))) <= 1e-9 * np.max(np.abs(F))
