@@ -228,6 +228,11 @@ struct hfx_plan {
   long long Yfcap = 0;
   float* Df = nullptr;
   int* d_work = nullptr;       // item counter of the tcgen05 first-product kernel
+  // tcgen05 R2 / Z of the second product (same shapes): core-matrix Y stores, V store per pair slot
+  bool t2u = false;
+  size_t smem_t2u = 0;
+  uint16_t* Vz = nullptr;
+  long long Vzcap = 0;
   // split path for n_ao > 16 (hfx_wide.cu): FP64 C, V and D blocks, FP32 Y store
   bool wide = false;
   hfx::WideShapes ws{};
@@ -665,7 +670,9 @@ void build_lists(hfx_plan* P, const double* L, const double* pos) {
     v_size[p] = 4ll * P->n_abf[P->species[v_home[p]]] * P->n_abf[P->species[v_j[p]]];
   for (int y = 0; y < nY; ++y) {
     const int sX = P->species[y_home[y]], sz = P->species[y_j[y]];
-    if (P->np)  // bf16 pieces of [alpha][z][rup16(n_ao(X))]
+    if (P->t2u)  // bf16 pieces of 64 rows alpha x (z, x) columns in core-matrix order
+      y_size[y] = (long long)P->np * 64 * 16 * P->n_ao[sz];
+    else if (P->np)  // bf16 pieces of [alpha][z][rup16(n_ao(X))]
       y_size[y] = (long long)P->np * P->n_abf[sX] * P->n_ao[sz] * ((P->n_ao[sX] + 15) / 16 * 16);
     else
       y_size[y] = (long long)P->n_abf[sX] * P->n_ao[sX] * P->n_ao[sz];
@@ -909,6 +916,13 @@ void setup_shapes(hfx_plan* P) {
         const char* sg = std::getenv("HFX_T1_SEG");
         P->t1u_seg = sg ? std::max(1, std::atoi(sg)) : (P->np == 3 ? 128 : 32);
         ck(hfx::t1u_set_smem(P->np), "smem attributes");
+        // the second product's R2 and Z on tcgen05 as well (HFX_T2_KERNEL=mma keeps the warp-level kernel)
+        const char* t2k = std::getenv("HFX_T2_KERNEL");
+        P->smem_t2u = hfx::t2u_smem(P->np, maxAO);
+        if (!(t2k && std::string(t2k) == "mma") && P->smem_t2u <= limit) {
+          P->t2u = true;
+          ck(hfx::t2u_set_smem(P->np), "smem attributes");
+        }
       }
     }
     if (!P->t1u) {
@@ -1202,8 +1216,13 @@ void evaluate_launches(hfx_plan* P, const double* L, hfx_stats* st, bool tail) {
                             (int)P->tot[9], P->wide_RB, s),
        "ybuild");
   } else {
+    // the core-matrix Y stores' rows past n_abf are never written: zero them
+    // once per allocation so that they hold finite values
+    const long long ycap0 = P->Yspcap;
     ensure_buf(P, P->Ysp, P->Yspcap, P->tot[0]);
+    if (P->t2u && P->Yspcap != ycap0) ck(cudaMemsetAsync(P->Ysp, 0, P->Yspcap * sizeof(uint16_t), s), "memset");
     X.Ysp = P->Ysp;
+    X.ycm = P->t2u ? 1 : 0;
     if (!reuse) {
       ensure_buf(P, P->blist, P->blist_cap, P->tot[6]);
       X.blist = P->blist;
@@ -1224,8 +1243,10 @@ void evaluate_launches(hfx_plan* P, const double* L, hfx_stats* st, bool tail) {
       U.t1_idx = P->t1_idx;
       X.Yf = P->Yf;
     }
-    X.yT_blk = (long long)P->np * P->MC * 128 * 16;
+    X.yT_blk = P->t2u ? (long long)P->np * 64 * P->t1u_KP : (long long)P->np * P->MC * 128 * 16;
+    const long long tcap0 = P->YspTcap;
     ensure_buf(P, P->YspT, P->YspTcap, std::max(1LL, P->tot[1]) * X.yT_blk);
+    if (P->t2u && P->YspTcap != tcap0) ck(cudaMemsetAsync(P->YspT, 0, P->YspTcap * sizeof(uint16_t), s), "memset");
     X.YspT = P->YspT;
     X.y_idx = P->y_idx;
     ensure_buf(P, P->ytab, P->ytabcap, std::max(1LL, hfx::ytab_size((int)P->tot[9], P->maxC)));
@@ -1275,6 +1296,12 @@ void evaluate_launches(hfx_plan* P, const double* L, hfx_stats* st, bool tail) {
       // writes the operand stores (no FP64 V blocks): one pass per needed pair
       // for both products when the tcgen05 first product runs
       if (P->t1u) {
+        if (P->t2u) {   // the tcgen05 R2 / Z kernel's V store, written by the V store kernel below
+          X.vz_blk = (long long)P->np * 4096 + 2LL * 4 * 4096;
+          ensure_buf(P, P->Vz, P->Vzcap, std::max(1LL, ct[CT_T2]) * X.vz_blk);
+          X.Vz = P->Vz;
+          X.t2_slot = P->t2_idx;
+        }
         ensure_buf(P, P->Cu, P->Cucap, std::max(1LL, ct[CT_Q]) * U.cu_blk);
         ensure_buf(P, P->Vu, P->Vucap, std::max(1LL, ct[CT_T1]) * U.vu_blk);
         U.Cu = P->Cu;
@@ -1305,9 +1332,12 @@ void evaluate_launches(hfx_plan* P, const double* L, hfx_stats* st, bool tail) {
       const char* stall = std::getenv("HFX_TEST_STALL_Q2_PRODUCER");
       X.stall_q2 = stall && stall[0] == '1' ? 1 : 0;
       k2a.push_back(tm.mark());
+      if (P->t2u)
+        ck(hfx::launch_t2_umma(D, X, P->np, P->t2_list + v0, (int)ct[CT_T2], P->zblk, P->smem_t2u, P->d_err, s),
+           "term2 R2 and Z");
       ck(hfx::launch_term2_mma(D, X, P->np, P->t2_list + v0, P->t2_idx, (int)ct[CT_T2], a0, a1, P->MAmax, P->KZmax,
                                P->zblk, P->ZROWS, FC, P->MC, hfx::q2_umma_segments(P->maxV, P->np), P->q2_flush,
-                               P->drows, P->smem_m2, P->d_err, s),
+                               P->drows, P->smem_m2, P->d_err, s, P->t2u),
          "term2");
     }
     m3.push_back(tm.mark());

@@ -128,6 +128,17 @@ struct MixPlan {
   // Fault injection for the failure tests: 1 = the second product's producer
   // issues no copies, so its pipeline waits run out (HFX_ERR_TIMEOUT).
   int stall_q2 = 0;
+  // tcgen05 R2 / Z kernel (k_t2_umma): with ycm the Y build writes Ysp and
+  // YspT per key as NP planes of 64 rows alpha x K columns in the tensor
+  // cores' core-matrix order (Ysp: K = (z, x), 16 n_ao(Z) columns; YspT:
+  // K = (x, z), 16 n_ao(X) columns; rows past n_abf(X) are left as they are:
+  // finite, never read into a kept result); Vz holds per second-product pair
+  // slot NP pieces of V [alpha 64][beta 64] in core-matrix order, then V and
+  // grad V as four FP32 planes of 64 x 64 in epilogue load order.
+  int ycm = 0;
+  uint16_t* Vz = nullptr;
+  long long vz_blk = 0;
+  const long long* t2_slot = nullptr;   // V pair -> its slot in the pass's second-product list
 };
 
 // Element (row, f < 16) of one component of grad C_AF (FP32) in the C operand
@@ -221,8 +232,17 @@ cudaError_t launch_term1_mma(const DevPlan& P, const MixPlan& X, int np, const i
 // pair list, its slot of every V pair of those atoms and its length.
 cudaError_t launch_term2_mma(const DevPlan& P, const MixPlan& X, int np, const int* list, const long long* slot0,
                              int n, int a0, int a1, int MAmax, int KZmax, long long zblk, int zrows, int FC, int MC,
-                             int nseg, int flush, const DRows& drows, size_t smem, int* err, cudaStream_t s);
+                             int nseg, int flush, const DRows& drows, size_t smem, int* err, cudaStream_t s,
+                             bool pairs_done = false);
 int q2_umma_segments(int max_pairs_per_atom, int np);
+// R2 and Z of the pass's second-product pairs on tcgen05 (hfx_t1umma.cu),
+// shapes n_abf <= 64, n_ao <= 16, with X.ycm and X.Vz set: E, g^V and the Z
+// store that k_q2_umma reads (launch_term2_mma with pairs_done then skips
+// its warp-level R2 / Z kernel).
+size_t t2u_smem(int np, int max_ao);
+cudaError_t t2u_set_smem(int np);
+cudaError_t launch_t2_umma(const DevPlan& P, const MixPlan& X, int np, const int* list, int n, long long zblk,
+                           size_t smem, int* err, cudaStream_t s);
 
 // tcgen05 first exchange product (hfx_t1umma.cu): shapes n_abf <= 64, n_ao <= 16.
 long long t1u_launch_count();

@@ -50,6 +50,13 @@ std::atomic<long long> g_mix_launches{0};
 // (128-row tiles) use it, so a tile is copied to shared memory as one block.
 __device__ __forceinline__ int tix(int r, int c) { return ((r >> 3) << 7) + ((c >> 3) << 6) + ((r & 7) << 3) + (c & 7); }
 
+// Element (row r, column k) of a tile of K columns (K a multiple of 8) in the
+// tensor cores' K-major core-matrix order: 8-row groups of K / 8 core matrices
+// (8 rows x 16 bytes each), the core matrices of a group consecutive.
+__device__ __forceinline__ long long cmx(int r, int k, int K) {
+  return (long long)(r >> 3) * 8 * K + ((k >> 3) << 6) + ((r & 7) << 3) + (k & 7);
+}
+
 // Block sum of NV doubles (all threads get the sums).  red: >= 32*NV doubles.
 template <int NV>
 __device__ void block_sum_n(double (&v)[NV], double* red) {
@@ -1188,11 +1195,26 @@ __global__ void __launch_bounds__(192) k_ybuild_umma(DevPlan P, MixPlan X, const
         const int nZ = P.n_ao[P.species[zat[i]]];
         uint16_t* Yo = X.Ysp + P.y_off[ykey[i]];
         float* Yf = X.Yf ? X.Yf + P.y_off[ykey[i]] / NP : nullptr;
-        const long long plane = (long long)mX * nZ * 16;
+        const bool cm = X.ycm != 0;   // Ysp rows alpha (64), K = (z, x) in core-matrix order
+        const int KZc = 16 * nZ;
+        const long long plane = cm ? 64LL * KZc : (long long)mX * nZ * 16;
         const float* eh = ep + h * 16;
         // bf16 pieces: chunk (alpha, z, half) holds x = 8 half .. 8 half + 7
+        // (core-matrix order: consecutive threads take consecutive alpha, whose
+        // chunks are 16 bytes apart)
         for (int c = et; c < nal * nZ * 2; c += 128) {
-          const int hf = c & 1, az = c >> 1, al = alF + az / nZ, zz = az - (az / nZ) * nZ;
+          int hf, al, zz;
+          if (cm) {
+            const int r2 = c / nal;
+            al = alF + (c - r2 * nal);
+            hf = r2 & 1;
+            zz = r2 >> 1;
+          } else {
+            const int az = c >> 1;
+            hf = c & 1;
+            al = alF + az / nZ;
+            zz = az - (az / nZ) * nZ;
+          }
           const int rl = al * nX - row0 + 8 * hf;
           float f0[4], f1[4];
 #pragma unroll
@@ -1203,7 +1225,7 @@ __global__ void __launch_bounds__(192) k_ybuild_umma(DevPlan P, MixPlan X, const
           uint2 p0[NP], p1[NP];
           split4<NP>(f0, p0);
           split4<NP>(f1, p1);
-          uint16_t* yo = Yo + ((long long)al * nZ + zz) * 16 + 8 * hf;
+          uint16_t* yo = Yo + (cm ? cmx(al, zz * 16 + 8 * hf, KZc) : ((long long)al * nZ + zz) * 16 + 8 * hf);
 #pragma unroll
           for (int pp = 0; pp < NP; ++pp)
             *reinterpret_cast<uint4*>(yo + pp * plane) = make_uint4(p0[pp].x, p0[pp].y, p1[pp].x, p1[pp].y);
@@ -1229,10 +1251,25 @@ __global__ void __launch_bounds__(192) k_ybuild_umma(DevPlan P, MixPlan X, const
         // with the 16 z of key i (z >= n_ao(Z) zero); every row of the tile
         // is this CTA's own
         if (X.YspT) {
-          uint16_t* yt = X.YspT + X.y_idx[ykey[i]] * X.yT_blk + (long long)row0 * 16;
-          const long long tplane = X.yT_blk / NP;
-          for (int c = et; c < (rend - row0) * 2; c += 128) {
-            const int rl = c >> 1, hz = c & 1;
+          // row-major tiles [(alpha, x)][16 z], or (ycm) rows alpha (64), K = (x, z) in core-matrix order
+          uint16_t* ytb = X.YspT + X.y_idx[ykey[i]] * X.yT_blk;
+          uint16_t* yt = ytb + (long long)row0 * 16;
+          const long long tplane = cm ? 64LL * 16 * nX : X.yT_blk / NP;
+          // (core-matrix order: consecutive threads take consecutive alpha of one
+          // (x, half), whose chunks are 16 bytes apart; rows outside the tile skipped)
+          const int nala = alB - alA + 1;
+          const int nct = cm ? nala * nX * 2 : (rend - row0) * 2;
+          for (int c = et; c < nct; c += 128) {
+            int rl, hz;
+            if (cm) {
+              const int r2 = c / nala, al = alA + (c - r2 * nala), x = r2 >> 1;
+              hz = r2 & 1;
+              rl = al * nX + x - row0;
+              if (rl < 0 || row0 + rl >= rend) continue;
+            } else {
+              rl = c >> 1;
+              hz = c & 1;
+            }
             float f0[4], f1[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -1242,9 +1279,14 @@ __global__ void __launch_bounds__(192) k_ybuild_umma(DevPlan P, MixPlan X, const
             uint2 p0[NP], p1[NP];
             split4<NP>(f0, p0);
             split4<NP>(f1, p1);
+            uint16_t* dst = yt + rl * 16 + 8 * hz;
+            if (cm) {
+              const int r = row0 + rl, al = r / nX, x = r - al * nX;
+              dst = ytb + cmx(al, x * 16 + 8 * hz, 16 * nX);
+            }
 #pragma unroll
             for (int pp = 0; pp < NP; ++pp)
-              *reinterpret_cast<uint4*>(yt + pp * tplane + rl * 16 + 8 * hz) = make_uint4(p0[pp].x, p0[pp].y, p1[pp].x, p1[pp].y);
+              *reinterpret_cast<uint4*>(dst + pp * tplane) = make_uint4(p0[pp].x, p0[pp].y, p1[pp].x, p1[pp].y);
           }
         }
         // alphas shared with a neighbouring row tile
@@ -1258,16 +1300,16 @@ __global__ void __launch_bounds__(192) k_ybuild_umma(DevPlan P, MixPlan X, const
             const float y = eh[(r - row0) * 33 + zz];
             uint16_t pc[NP];
             split_f<NP>(y, pc);
-            const long long o = ((long long)al * nZ + zz) * 16;
+            const long long o = cm ? cmx(al, zz * 16, KZc) : ((long long)al * nZ + zz) * 16;   // + x (x < 16)
             const int sw = 2 * ((al >> 1) & 1);
             float* yr = Yf ? Yf + ((long long)zz * mX + al) * 16 : nullptr;
 #pragma unroll
-            for (int pp = 0; pp < NP; ++pp) Yo[pp * plane + o + x] = pc[pp];
+            for (int pp = 0; pp < NP; ++pp) Yo[pp * plane + o + (cm ? ((x >> 3) << 6) + (x & 7) : x)] = pc[pp];
             if (yr) yr[(((x >> 2) ^ sw) << 2) + (x & 3)] = y;
             if (x == nX - 1)
               for (int xp = nX; xp < 16; ++xp) {
 #pragma unroll
-                for (int pp = 0; pp < NP; ++pp) Yo[pp * plane + o + xp] = 0;
+                for (int pp = 0; pp < NP; ++pp) Yo[pp * plane + o + (cm ? ((xp >> 3) << 6) + (xp & 7) : xp)] = 0;
                 if (yr) yr[(((xp >> 2) ^ sw) << 2) + (xp & 3)] = 0.f;
               }
           }
@@ -1494,19 +1536,22 @@ cudaError_t launch_term1_mma(const DevPlan& P, const MixPlan& X, int np, const i
 
 cudaError_t launch_term2_mma(const DevPlan& P, const MixPlan& X, int np, const int* list, const long long* slot0,
                              int n, int a0, int a1, int MAmax, int KZmax, long long zblk, int zrows, int FC, int MC,
-                             int nseg, int flush, const DRows& drows, size_t smem, int* err, cudaStream_t s) {
+                             int nseg, int flush, const DRows& drows, size_t smem, int* err, cudaStream_t s,
+                             bool pairs_done) {
   if (n == 0 || a1 <= a0) return cudaSuccess;
-  g_mix_launches += 3;
+  g_mix_launches += pairs_done ? 2 : 3;
   const int FC8 = (FC * 4 + 7) / 8;     // groups of 8 C slots for the tcgen05 kernel
   k_q2tab<<<grid_for(((long long)n * FC8 * 8 + 255) / 256, 152 * 16), 256, 0, s>>>(P, X, list, n, FC8);
   const size_t sq = q2_umma_smem(np);
   const long long grid = (long long)(a1 - a0) * FC8 * ((MC + q2_tpc(np) - 1) / q2_tpc(np)) * nseg;
   if (np == 2) {
-    k_term2_pairs<2><<<grid_for(n, 152 * 32), kWarps * 32, smem, s>>>(P, X, list, n, MAmax, KZmax, zblk, zrows);
+    if (!pairs_done)
+      k_term2_pairs<2><<<grid_for(n, 152 * 32), kWarps * 32, smem, s>>>(P, X, list, n, MAmax, KZmax, zblk, zrows);
     k_q2_umma<2, q2_tpc(2)><<<(unsigned)grid, 192, sq, s>>>(P, X, list, slot0, n, a0, a1, FC8, MC, nseg, zblk, flush,
                                                              drows, err);
   } else {
-    k_term2_pairs<3><<<grid_for(n, 152 * 32), kWarps * 32, smem, s>>>(P, X, list, n, MAmax, KZmax, zblk, zrows);
+    if (!pairs_done)
+      k_term2_pairs<3><<<grid_for(n, 152 * 32), kWarps * 32, smem, s>>>(P, X, list, n, MAmax, KZmax, zblk, zrows);
     k_q2_umma<3, q2_tpc(3)><<<(unsigned)grid, 192, sq, s>>>(P, X, list, slot0, n, a0, a1, FC8, MC, nseg, zblk, flush,
                                                              drows, err);
   }

@@ -133,7 +133,9 @@ __global__ void k_t1u_cstore(DevPlan P, T1UPlan U, const int* list, int n) {
 //   [alpha][rup16(n_abf(B))] and V, grad V in FP32 [4][n_abf(A) n_abf(B)];
 //   for the pairs of the first product (any bit of v_mask), the tcgen05
 //   store U.Vu at t1_idx[p]: NP pieces [alpha 64][beta 64] in core-matrix
-//   order and grad V in three planes in epilogue load order (ep_at).
+//   order and grad V in three planes in epilogue load order (ep_at);
+//   for the pairs of the second product (v_t2), with X.Vz set, the store of
+//   k_t2_umma at t2_slot[p]: the same pieces and V, grad V in four planes.
 // Outputs are written in storage order, four elements per thread.
 constexpr int kVStoreSmem = 4 * 64 * 64 * 4;
 
@@ -175,30 +177,38 @@ __global__ void k_vstores(DevPlan P, MixPlan X, T1UPlan U, const int* list, int 
     bool t1 = false;
 #pragma unroll
     for (int w = 0; w < kMaskWords; ++w) t1 = t1 || P.v_mask[(long long)p * kMaskWords + w] != 0u;
-    if (!U.Vu || !t1) continue;
-    uint16_t* vu = U.Vu + U.t1_idx[p] * U.vu_blk;
-    for (int t4 = threadIdx.x; t4 < 1024; t4 += blockDim.x) {   // core-matrix order, 4 columns per thread
-      const int t = 4 * t4;
-      const int al = ((t >> 9) << 3) + ((t >> 3) & 7), be = (((t >> 6) & 7) << 3) + (t & 7);
-      float x[4];
+    // the tcgen05 stores: the first product's (U.Vu, per first-product pair:
+    // pieces and the three grad V planes) and the second product's (X.Vz, per
+    // second-product pair: pieces and the four planes V, grad V)
+    for (int st = 0; st < 2; ++st) {
+      uint16_t* vu = nullptr;
+      if (st == 0 && U.Vu && t1) vu = U.Vu + U.t1_idx[p] * U.vu_blk;
+      if (st == 1 && X.Vz && P.v_t2[p]) vu = X.Vz + X.t2_slot[p] * X.vz_blk;
+      if (!vu) continue;
+      for (int t4 = threadIdx.x; t4 < 1024; t4 += blockDim.x) {   // core-matrix order, 4 columns per thread
+        const int t = 4 * t4;
+        const int al = ((t >> 9) << 3) + ((t >> 3) & 7), be = (((t >> 6) & 7) << 3) + (t & 7);
+        float x[4];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) x[j] = (al < mA && be + j < mB) ? vsm[al * mB + be + j] : 0.f;
-      uint2 pc[NP];
-      split4<NP>(x, pc);
+        for (int j = 0; j < 4; ++j) x[j] = (al < mA && be + j < mB) ? vsm[al * mB + be + j] : 0.f;
+        uint2 pc[NP];
+        split4<NP>(x, pc);
 #pragma unroll
-      for (int pp = 0; pp < NP; ++pp) *reinterpret_cast<uint2*>(vu + pp * 4096 + t) = pc[pp];
-    }
-    float* pl = reinterpret_cast<float*>(vu + NP * 4096);
-    for (int w4 = threadIdx.x; w4 < 3 * 1024; w4 += blockDim.x) {   // grad V, epilogue load order
-      const int c = w4 >> 10;
-      int al, be;
-      ep_at(4 * (w4 & 1023), al, be);
-      float4 o;
-      o.x = (al < mA && be < mB) ? vsm[(c + 1) * nv + al * mB + be] : 0.f;
-      o.y = (al < mA && be + 1 < mB) ? vsm[(c + 1) * nv + al * mB + be + 1] : 0.f;
-      o.z = (al < mA && be + 2 < mB) ? vsm[(c + 1) * nv + al * mB + be + 2] : 0.f;
-      o.w = (al < mA && be + 3 < mB) ? vsm[(c + 1) * nv + al * mB + be + 3] : 0.f;
-      *reinterpret_cast<float4*>(pl + 4 * w4) = o;
+        for (int pp = 0; pp < NP; ++pp) *reinterpret_cast<uint2*>(vu + pp * 4096 + t) = pc[pp];
+      }
+      float* pl = reinterpret_cast<float*>(vu + NP * 4096);
+      const int c0 = st == 0 ? 1 : 0;   // first plane: grad V (first product) or V (second)
+      for (int w4 = threadIdx.x; w4 < (4 - c0) * 1024; w4 += blockDim.x) {   // epilogue load order
+        const int c = c0 + (w4 >> 10);
+        int al, be;
+        ep_at(4 * (w4 & 1023), al, be);
+        float4 o;
+        o.x = (al < mA && be < mB) ? vsm[c * nv + al * mB + be] : 0.f;
+        o.y = (al < mA && be + 1 < mB) ? vsm[c * nv + al * mB + be + 1] : 0.f;
+        o.z = (al < mA && be + 2 < mB) ? vsm[c * nv + al * mB + be + 2] : 0.f;
+        o.w = (al < mA && be + 3 < mB) ? vsm[c * nv + al * mB + be + 3] : 0.f;
+        *reinterpret_cast<float4*>(pl + 4 * w4) = o;
+      }
     }
   }
 }
@@ -948,6 +958,282 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (tid == 0 && s_abort) atomicExch(err, 1);
 }
 
+// ------------------------------------------------------------------ R2 and Z
+// Second exchange product on the tensor cores, per kept pair (A,B) of the
+// pass (slot kk of its list), shapes n_abf <= 64, n_ao <= 16:
+//   R2 = Y^{AB} . (Y^{BA})^T (M = 64 alpha, N = 64 beta, K = (a, b)) -> E = -<V, R2>, g^V = -<grad V, R2>
+//   Z  = V_AB . Y^{BA}       (M = 64 alpha, N = (a, b), K = beta)    -> the Z store read by k_q2_umma
+// Both Y operands come whole from the Y build's core-matrix stores (X.ycm):
+// Y^{AB} from YspT (rows alpha, K = (a, b)), Y^{BA} from Ysp (rows beta,
+// K = (a, b)); Y^{BA} serves R2 as a K-major and Z as an MN-major operand.
+// V pieces and FP32 V, grad V from X.Vz.  CTA c takes the pairs c, c + grid,
+// ...  Warp 0 lane 0 copies (bulk), warp 1 owns tensor memory and its lane 0
+// issues the MMAs, warps 2-5 (one per tensor-memory lane quarter) are the
+// epilogue.  R2 is double-buffered in tensor memory, Z single-buffered;
+// Y^{AB} is released after R2, Y^{BA} and V after Z, so the next pair's
+// Y^{AB} lands while Z runs.  Every wait is bounded (1 s); a timeout sets the
+// error flag and every role stops.
+constexpr int kT2Threads = 192;
+constexpr int kT2RCol = 256;   // tensor-memory column of the first R2 accumulator (Z at column 0)
+
+template <int NP>
+__global__ void __launch_bounds__(kT2Threads, 1)
+    k_t2_umma(DevPlan P, MixPlan X, const int* list, int n_list, int KKmax, long long zblk, int* err) {
+  constexpr int NPROD = NP * (NP + 1) / 2;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  uint16_t* Ya = reinterpret_cast<uint16_t*>(smem_raw);   // [NP][64][KK]
+  uint16_t* Yb = Ya + (size_t)NP * 64 * KKmax;            // [NP][64][KK]
+  uint16_t* Vs = Yb + (size_t)NP * 64 * KKmax;            // [NP][64][64]
+  __shared__ __align__(8) uint64_t b_af, b_ae, b_bf, b_be, b_rf[2], b_re[2], b_zf, b_ze, b_done;
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_abort;
+  volatile int* abort_flag = &s_abort;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  auto sa = [](const void* p) { return (uint32_t)__cvta_generic_to_shared(p); };
+  const uint32_t mAf = sa(&b_af), mAe = sa(&b_ae), mBf = sa(&b_bf), mBe = sa(&b_be), rf = sa(b_rf), re = sa(b_re),
+                 zf = sa(&b_zf), ze = sa(&b_ze), mdone = sa(&b_done);
+  if (tid == 0) {
+    s_abort = 0;
+    mbar_init(mAf, 1);
+    mbar_init(mAe, 1);
+    mbar_init(mBf, 1);
+    mbar_init(mBe, 1);
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(rf + 8 * s, 1);
+      mbar_init(re + 8 * s, 4);
+    }
+    mbar_init(zf, 1);
+    mbar_init(ze, 4);
+    mbar_init(mdone, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(sa(&tmem_base)), "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t T = tmem_base;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------- producer
+    if (lane == 0) {
+      uint32_t na = 0, nb = 0;   // copies issued into Ya and into Yb / V
+      for (int kk = blockIdx.x; kk < n_list && !aborted(abort_flag); kk += gridDim.x) {
+        const int p = list[kk];
+        const int A = P.v_home[p], b = P.v_j[p];
+        const int* Rb = P.v_R + 3 * p;
+        const int KK = 16 * P.n_ao[P.species[A]];
+        const int y1 = ylut_get(P, A, b, Rb[0], Rb[1], Rb[2]);
+        const int y2 = ylut_get(P, b, A, -Rb[0], -Rb[1], -Rb[2]);
+        if (y1 < 0 || y2 < 0) {   // a kept pair always has both Y blocks
+          *abort_flag = 1;
+          break;
+        }
+        const uint32_t ybytes = (uint32_t)NP * 64u * (uint32_t)KK * 2u;
+        if (na >= 1 && !mbar_wait(mAe, (na - 1) & 1)) {
+          *abort_flag = 1;
+          break;
+        }
+        mbar_expect_tx(mAf, ybytes);
+        bulk_g2s(sa(Ya), X.YspT + X.y_idx[y1] * X.yT_blk, ybytes, mAf);
+        ++na;
+        if (nb >= 1 && !mbar_wait(mBe, (nb - 1) & 1)) {
+          *abort_flag = 1;
+          break;
+        }
+        mbar_expect_tx(mBf, ybytes + (uint32_t)NP * 8192u);
+        bulk_g2s(sa(Yb), X.Ysp + P.y_off[y2], ybytes, mBf);
+        bulk_g2s(sa(Vs), X.Vz + (long long)kk * X.vz_blk, (uint32_t)NP * 8192u, mBf);
+        ++nb;
+      }
+      // copies in flight land before the CTA leaves
+      if (na) mbar_wait(mAf, (na - 1) & 1);
+      if (nb) mbar_wait(mBf, (nb - 1) & 1);
+    }
+  } else if (warp == 1) {
+    // ----------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      const uint32_t idR = idesc_bf16(64, 64, 0);
+      uint32_t i = 0;
+      bool ok = true;
+      for (int kk = blockIdx.x; kk < n_list && ok; kk += gridDim.x, ++i) {
+        if (aborted(abort_flag)) {
+          ok = false;
+          break;
+        }
+        const int nA = P.n_ao[P.species[P.v_home[list[kk]]]];
+        const int KK = 16 * nA;
+        const uint32_t PB = 64u * (uint32_t)KK * 2u;   // bytes of one piece of Y^{AB} or Y^{BA}
+        const uint32_t rowg = 16u * (uint32_t)KK;      // bytes between 8-row groups
+        const uint64_t dA = sdesc2(sa(Ya), 128, rowg), dBK = sdesc2(sa(Yb), 128, rowg);
+        const uint64_t dV = sdesc2(sa(Vs), 128, 1024), dBM = sdesc2(sa(Yb), rowg, 128);
+        const uint32_t idZ = idesc_bf16(64, KK, 1);
+        const int rbuf = i & 1;
+        ok = mbar_wait(mAf, i & 1) && mbar_wait(mBf, i & 1) && (i < 2 || mbar_wait(re + 8 * rbuf, ((i >> 1) - 1) & 1));
+        if (!ok) break;
+        tc_fence_after();
+        // R2: one a (16 columns, 256 bytes) per k step, every piece product
+        const uint32_t tR = T + kT2RCol + 64u * rbuf;
+        for (int a = 0; a < nA; ++a) {
+          const uint64_t o = 16u * (uint32_t)a;
+          int k = 0;
+#pragma unroll
+          for (int sum = NP - 1; sum >= 0; --sum)
+#pragma unroll
+            for (int ia = 0; ia <= sum; ++ia, ++k)
+              umma_bf16(tR, dA + ((uint64_t)(ia * PB) >> 4) + o, dBK + ((uint64_t)((sum - ia) * PB) >> 4) + o, idR,
+                        (a > 0 || k > 0) ? 1u : 0u);
+        }
+        umma_commit(mAe);
+        umma_commit(rf + 8 * rbuf);
+        ok = i < 1 || mbar_wait(ze, (i - 1) & 1);
+        if (!ok) break;
+        tc_fence_after();
+        // Z: K = beta in four steps of 16 (V: 256 bytes; Y^{BA} MN-major: two 8-row groups)
+        for (int kb = 0; kb < 4; ++kb) {
+          int k = 0;
+#pragma unroll
+          for (int sum = NP - 1; sum >= 0; --sum)
+#pragma unroll
+            for (int ia = 0; ia <= sum; ++ia, ++k)
+              umma_bf16(T, dV + ((uint64_t)(ia * 8192) >> 4) + 16u * kb,
+                        dBM + ((uint64_t)((sum - ia) * PB) >> 4) + ((uint64_t)(2 * rowg * kb) >> 4), idZ,
+                        (kb > 0 || k > 0) ? 1u : 0u);
+        }
+        (void)NPROD;
+        umma_commit(mBe);
+        umma_commit(zf);
+      }
+      if (!ok) *abort_flag = 1;
+      // every MMA issued has completed before tensor memory is freed
+      umma_commit(mdone);
+      mbar_wait(mdone, 0);
+    }
+  } else {
+    // ------------------------------------------------------------- epilogue
+    const int qd = warp & 3;                   // tensor-memory lane quarter
+    const int alpha = qd * 16 + (lane & 15);   // accumulator row held by this thread
+    const int half = lane >> 4;                // columns [0,16) or [16,32) of a 32-column load
+    const uint32_t tl = T + ((uint32_t)(qd * 32) << 16);
+    uint32_t i = 0;
+    bool ok = true;
+    double fl = 0.0;
+    for (int kk = blockIdx.x; kk < n_list && ok; kk += gridDim.x, ++i) {
+      ok = __all_sync(0xffffffffu, !aborted(abort_flag)) != 0;
+      if (!ok) break;
+      const int p = list[kk];
+      const int sA = P.species[P.v_home[p]], sB = P.species[P.v_j[p]];
+      const int nA = P.n_ao[sA], nB = P.n_ao[sB], mA = P.n_abf[sA], mB = P.n_abf[sB];
+      const int KK = 16 * nA;
+      const int rbuf = i & 1;
+      // ---- R2 -> E, g^V (the V, grad V rows of the first 32 columns are
+      // fetched before the wait; they do not depend on R2)
+      const float4* V4 = reinterpret_cast<const float4*>(X.Vz + (long long)kk * X.vz_blk + NP * 4096) + qd * 32 + lane;
+      float ev[4] = {0.f, 0.f, 0.f, 0.f};
+      float4 w[4][4];
+      if (alpha < mA && 16 * half < mB)
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+          for (int t4 = 0; t4 < 4; ++t4) w[c][t4] = V4[c * 1024 + t4 * 128];
+      ok = wait_all(rf + 8 * rbuf, (i >> 1) & 1);
+      tc_fence_after();
+      if (ok) {
+        for (int c0 = 0; c0 < 64; c0 += 32) {
+          if (c0 >= mB) break;
+          const bool act = alpha < mA && c0 + 16 * half < mB;
+          if (c0 > 0 && act)
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+#pragma unroll
+              for (int t4 = 0; t4 < 4; ++t4) w[c][t4] = V4[c * 1024 + 512 + t4 * 128];
+          uint32_t v[32];
+          tmem_ld32(tl + kT2RCol + 64u * rbuf + c0, v);
+          float x[16];
+#pragma unroll
+          for (int t = 0; t < 16; ++t) {
+            const float hi = __shfl_sync(0xffffffffu, __uint_as_float(v[16 + t]), lane & 15);
+            x[t] = half ? hi : __uint_as_float(v[t]);
+          }
+          if (act) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              float s = 0.f;
+#pragma unroll
+              for (int t4 = 0; t4 < 4; ++t4) {
+                s = fmaf(w[c][t4].x, x[4 * t4], s);
+                s = fmaf(w[c][t4].y, x[4 * t4 + 1], s);
+                s = fmaf(w[c][t4].z, x[4 * t4 + 2], s);
+                s = fmaf(w[c][t4].w, x[4 * t4 + 3], s);
+              }
+              ev[c] += s;
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(re + 8 * rbuf);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) ev[c] = warp_sum_f(ev[c]);
+      if (lane == 0 && ok) {
+        if (ev[0] != 0.f) atomicAdd(&P.acc[ACC_E], -(double)ev[0]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          if (ev[c + 1] != 0.f) atomicAdd(&P.gV[3 * p + c], -(double)ev[c + 1]);
+      }
+      // ---- Z -> the Z store: NP planes of 128-row tiles of rows (alpha, a),
+      // 16 columns b each, in the core-matrix order of tix; a thread writes
+      // the 16 b of one (alpha, a) as two 16-byte chunks per piece
+      ok = ok && wait_all(zf, i & 1);
+      tc_fence_after();
+      if (ok) {
+        uint16_t* Zo = X.Zst + (long long)kk * zblk;
+        for (int c0 = 0; c0 < KK; c0 += 32) {
+          uint32_t v[32];
+          tmem_ld32(tl + c0, v);
+          float x[16];
+#pragma unroll
+          for (int t = 0; t < 16; ++t) {
+            const float hi = __shfl_sync(0xffffffffu, __uint_as_float(v[16 + t]), lane & 15);
+            x[t] = half ? hi : __uint_as_float(v[t]);
+          }
+          const int a = (c0 >> 4) + half;
+          if (alpha < mA && a < nA) {
+            const int r = alpha * nA + a;
+            uint16_t* d = Zo + (long long)(r >> 7) * NP * 2048 + (((r & 127) >> 3) << 7) + ((r & 7) << 3);
+#pragma unroll
+            for (int hb = 0; hb < 2; ++hb) {
+              const float x0[4] = {x[8 * hb], x[8 * hb + 1], x[8 * hb + 2], x[8 * hb + 3]};
+              const float x1[4] = {x[8 * hb + 4], x[8 * hb + 5], x[8 * hb + 6], x[8 * hb + 7]};
+              uint2 p0[NP], p1[NP];
+              split4<NP>(x0, p0);
+              split4<NP>(x1, p1);
+#pragma unroll
+              for (int pp = 0; pp < NP; ++pp)
+                *reinterpret_cast<uint4*>(d + pp * 2048 + 64 * hb) = make_uint4(p0[pp].x, p0[pp].y, p1[pp].x, p1[pp].y);
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(ze);
+      if (warp == 2 && lane == 0) fl += 4.0 * mA * mB * nA * nB;
+    }
+    if (!ok) *abort_flag = 1;
+    if (warp == 2 && lane == 0 && fl != 0.0) atomicAdd(&P.acc[ACC_F2], fl);
+  }
+  // ------------------------------------------------------------------ teardown
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(T), "r"(512));
+  if (tid == 0 && s_abort) atomicExch(err, 1);
+}
+
 int num_sms() {
   static const int n = [] {
     int dev = 0, v = 0;
@@ -1018,6 +1304,23 @@ cudaError_t launch_vstores(const DevPlan& P, const MixPlan& X, const T1UPlan& U,
   const int g = n < 152 * 3 ? n : 152 * 3;
   if (np == 2) k_vstores<2><<<g, 256, kVStoreSmem, s>>>(P, X, U, list, n);
   else k_vstores<3><<<g, 256, kVStoreSmem, s>>>(P, X, U, list, n);
+  return cudaGetLastError();
+}
+
+size_t t2u_smem(int np, int max_ao) { return (size_t)np * (2 * 64 * 16 * (size_t)max_ao * 2 + 8192); }
+
+cudaError_t t2u_set_smem(int np) {
+  return allow_max_dynamic_smem(np == 2 ? (const void*)k_t2_umma<2> : (const void*)k_t2_umma<3>);
+}
+
+cudaError_t launch_t2_umma(const DevPlan& P, const MixPlan& X, int np, const int* list, int n, long long zblk,
+                           size_t smem, int* err, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  ++g_t1u_launches;
+  const int grid = n < num_sms() ? n : num_sms();
+  const int KKmax = (int)(smem / np - 8192) / (2 * 64 * 2);   // 16 x the largest n_ao
+  if (np == 2) k_t2_umma<2><<<grid, kT2Threads, smem, s>>>(P, X, list, n, KKmax, zblk, err);
+  else k_t2_umma<3><<<grid, kT2Threads, smem, s>>>(P, X, list, n, KKmax, zblk, err);
   return cudaGetLastError();
 }
 
