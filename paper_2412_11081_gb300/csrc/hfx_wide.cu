@@ -43,7 +43,6 @@ using namespace dev;
 
 constexpr int kWThreads = 256;   // 8 warps per CTA
 constexpr int kWarpsW = kWThreads / 32;
-constexpr int kRPairs = 8;       // (alpha, beta) tile pairs of R per warp (n_abf <= 128)
 constexpr int kFlushF = 4;       // F per FP32 run of R in the first product
 std::atomic<long long> g_wide_launches{0};
 
@@ -77,7 +76,7 @@ __device__ __forceinline__ void put_pieces(uint16_t* base, long long plane, int 
   for (int pp = 0; pp < NP; ++pp) base[pp * plane + e] = pc[pp];
 }
 
-template <int NV>
+template <int NV, int NW = kWarpsW>
 __device__ void block_sum_w(double (&v)[NV], double* red) {
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
 #pragma unroll
@@ -85,16 +84,22 @@ __device__ void block_sum_w(double (&v)[NV], double* red) {
   __syncthreads();
   if (l == 0)
 #pragma unroll
-    for (int i = 0; i < NV; ++i) red[i * kWarpsW + w] = v[i];
+    for (int i = 0; i < NV; ++i) red[i * NW + w] = v[i];
   __syncthreads();
 #pragma unroll
   for (int i = 0; i < NV; ++i) {
     double t = 0.0;
-    for (int k = 0; k < kWarpsW; ++k) t += red[i * kWarpsW + k];
+    for (int k = 0; k < NW; ++k) t += red[i * NW + k];
     v[i] = t;
   }
   __syncthreads();
 }
+
+// Warps per CTA of the two product kernels (one CTA per SM, bound by shared
+// memory) and the R tile pairs each warp keeps: NW * RP >= 64 pairs covers
+// n_abf <= 128.
+constexpr int kPW = 16;
+constexpr int kPRP = 64 / kPW;
 
 // R (M = alpha tiles, N = beta tiles) as pairs of beta tiles; pair k of warp w
 // is pair index w + 8 k of the MT x ceil(NT / 2) pairs.
@@ -161,9 +166,11 @@ __global__ void k_dsplit_w(DevPlan P, uint16_t* Dw, const long long* dw_off) {
 }
 
 // ------------------------------------------------------------------ C pieces
-// Kept C pair q (evaluated this call, FP64) -> NP bf16 planes of
-// [alpha][rup8(n_ao(A) n_ao(F))] (columns (a, f) as in the FP64 block, zero
-// padded) at Cw + cw_off[q].
+// Kept C pair q (evaluated this call, FP64) -> at Cw + cw_off[q]: NP bf16
+// planes of [alpha][rup8(n_ao(A) n_ao(F))] (columns (a, f) as in the FP64
+// block, zero padded; the first product's layout), then NP planes of
+// [(alpha, a)][rup16(n_ao(F))] (the Y build's A operand: every row starts on
+// a 16-byte boundary).
 __host__ __device__ inline int cw_cols(int nA, int nF) { return (nA * nF + 7) & ~7; }
 
 template <int NP>
@@ -171,12 +178,18 @@ __global__ void k_cpieces_w(DevPlan P, uint16_t* Cw, const long long* cw_off) {
   for (int q = blockIdx.x; q < P.nC; q += gridDim.x) {
     if (!P.c_keep[q]) continue;
     const int sA = P.species[P.c_home[q]], sF = P.species[P.c_j[q]];
-    const int mA = P.n_abf[sA], naf = P.n_ao[sA] * P.n_ao[sF], CW = cw_cols(P.n_ao[sA], P.n_ao[sF]);
+    const int mA = P.n_abf[sA], nA = P.n_ao[sA], nF = P.n_ao[sF];
+    const int naf = nA * nF, CW = cw_cols(nA, nF), KW = rup16(nF);
     const double* src = P.Cst + P.c_off[q];
     uint16_t* out = Cw + cw_off[q];
     for (int e = threadIdx.x; e < mA * CW; e += blockDim.x) {
       const int al = e / CW, c = e - al * CW;
       put_pieces<NP>(out, (long long)mA * CW, e, c < naf ? (float)src[(long long)al * naf + c] : 0.f);
+    }
+    uint16_t* cy = out + (long long)NP * mA * CW;
+    for (int e = threadIdx.x; e < mA * nA * KW; e += blockDim.x) {
+      const int r = e / KW, c = e - r * KW;
+      put_pieces<NP>(cy, (long long)mA * nA * KW, e, c < nF ? (float)src[(long long)r * nF + c] : 0.f);
     }
   }
 }
@@ -184,12 +197,14 @@ __global__ void k_cpieces_w(DevPlan P, uint16_t* Cw, const long long* cw_off) {
 // ------------------------------------------------------------------ Y build
 // CTA = (key group g, 64-row block rb).  Warp w: rows 16 (w & 3) of the block,
 // keys 4 (w >> 2) .. + 3 of the group, all z of each key (n_ao(Z) <= 32: four
-// column tiles).  Per K step (one kept C pair t, 16 columns w of it):
-//   As[NP][64][24]       C_XW rows (alpha, x), columns w
-//   Bs[NP][8 * 32][24]   D_{W Z_i}[w][z] as rows (i, z), columns w
+// column tiles).  K steps: 16 columns w of one kept C pair (X, W) with a D
+// block among the keys, two steps in flight (16-byte asynchronous copies):
+//   As[2][NP][64][24]          C_XW rows (alpha, x), columns w (the padded C pieces)
+//   Bs[2][NP][16][8 * 32 + 8]  D_{W Z_i} rows w, columns (i, z) (the D pieces)
 constexpr int kYRows = 64;
-constexpr int kYS = 24;
-size_t ybuild_w_smem(int np) { return (size_t)np * (kYRows + 256) * kYS * sizeof(uint16_t); }
+constexpr int kYSA = 24;
+constexpr int kYSB = 8 * 32 + 8;
+size_t ybuild_w_smem(int np) { return (size_t)2 * np * (kYRows * kYSA + 16 * kYSB) * sizeof(uint16_t); }
 
 template <int NP>
 __global__ void __launch_bounds__(kWThreads) k_ybuild_w(DevPlan P, uint16_t* __restrict__ Yp,
@@ -198,8 +213,9 @@ __global__ void __launch_bounds__(kWThreads) k_ybuild_w(DevPlan P, uint16_t* __r
                                                         const int* ylist, const int* gX, const int* gS, const int* gN,
                                                         int RB) {
   extern __shared__ __align__(16) unsigned char smem[];
-  uint16_t* As = reinterpret_cast<uint16_t*>(smem);   // [NP][64][kYS]
-  uint16_t* Bs = As + NP * kYRows * kYS;              // [NP][256][kYS]
+  constexpr long long pA = kYRows * kYSA, pB = 16 * kYSB;
+  uint16_t* As0 = reinterpret_cast<uint16_t*>(smem);   // [2][NP][64][kYSA]
+  uint16_t* Bs0 = As0 + 2 * NP * pA;                   // [2][NP][16][kYSB]
   __shared__ int m_dw[kMaxCPerAtom][8];   // D piece block of (C pair t, key i) in 256-element units, or -1
   __shared__ int m_step[2 * kMaxCPerAtom];
   __shared__ int s_key[8], s_zat[8], s_nz[8];
@@ -264,39 +280,46 @@ __global__ void __launch_bounds__(kWThreads) k_ybuild_w(DevPlan P, uint16_t* __r
     for (int j = 0; j < 4; ++j)
 #pragma unroll
       for (int c = 0; c < 4; ++c) acc[i][j][c] = 0.f;
-  constexpr long long pA = kYRows * kYS, pB = 256 * kYS;
-  for (int k = 0; k < nsteps; ++k) {
+  // copies of step k into buffer k & 1 (rows past the block and columns past
+  // the keys' D blocks are not copied: they only meet discarded results)
+  auto issue = [&](int k) {
     const int t = m_step[k] >> 8, k0 = m_step[k] & 255;
     const int q = q0 + t;
     const int nW = P.n_ao[P.species[P.c_j[q]]], pw = rup16(nW);
-    const int CW = cw_cols(nX, nW);
-    const uint16_t* C = Cw + cw_off[q];   // NP planes [alpha][(x, w)]
-    const long long cplane = (long long)mX * CW;
-    __syncthreads();   // previous step's fragments read
-    for (int e = threadIdx.x; e < kYRows * 16; e += blockDim.x) {
-      const int r = e >> 4, c = e & 15;
-      const int row = row0 + r, w = k0 + c;
-      const bool in = row < rows && w < nW;
-      const int al = row / nX, x = row - al * nX;
-      const long long o = (long long)al * CW + x * nW + w;
-#pragma unroll
-      for (int pp = 0; pp < NP; ++pp) As[pp * pA + r * kYS + c] = in ? C[pp * cplane + o] : (uint16_t)0;
+    const uint16_t* Cy = Cw + cw_off[q] + (long long)NP * mX * cw_cols(nX, nW);   // [(alpha, x)][pw]
+    const long long cplane = (long long)rows * pw;
+    uint16_t* As = As0 + (k & 1) * NP * pA;
+    uint16_t* Bs = Bs0 + (k & 1) * NP * pB;
+    const int nr = min(kYRows, rows - row0);
+    for (int e = threadIdx.x; e < NP * nr * 2; e += blockDim.x) {
+      const int pp = e / (nr * 2), rr = e - pp * nr * 2, r = rr >> 1, h = rr & 1;
+      cpa16(As + pp * pA + r * kYSA + 8 * h, Cy + pp * cplane + (long long)(row0 + r) * pw + k0 + 8 * h);
     }
-    for (int e = threadIdx.x; e < 256 * 16; e += blockDim.x) {
-      const int rz = e >> 4, c = e & 15;
-      const int i = rz >> 5, z = rz & 31, w = k0 + c;
+    for (int i = 0; i < 8; ++i) {
       const int dw = m_dw[t][i];
-      const int pz = rup16(s_nz[i]);
-      const bool in = dw >= 0 && w < pw && z < pz;
-      const uint16_t* Dg = Dw + ((long long)(in ? dw : 0) << 8);
-#pragma unroll
-      for (int pp = 0; pp < NP; ++pp)
-        Bs[pp * pB + rz * kYS + c] = in ? Dg[(long long)pp * pw * pz + w * pz + z] : (uint16_t)0;
+      if (dw < 0) continue;
+      const int pz = rup16(s_nz[i]), ch = pz >> 3;
+      const uint16_t* Dg = Dw + ((long long)dw << 8) + (long long)k0 * pz;   // rows w of D_{W Z_i} pieces [pw][pz]
+      const long long dplane = (long long)pw * pz;
+      for (int e = threadIdx.x; e < NP * 16 * ch; e += blockDim.x) {
+        const int pp = e / (16 * ch), rr = e - pp * 16 * ch, w = rr / ch, c = rr - w * ch;
+        cpa16(Bs + pp * pB + w * kYSB + i * 32 + 8 * c, Dg + pp * dplane + (long long)w * pz + 8 * c);
+      }
     }
-    __syncthreads();
+  };
+  if (nsteps > 0) issue(0);
+  cpa_commit();
+  for (int k = 0; k < nsteps; ++k) {
+    if (k + 1 < nsteps) issue(k + 1);
+    cpa_commit();
+    cpa_wait<1>();
+    __syncthreads();   // step k's operands are in shared memory
+    const int t = m_step[k] >> 8;
+    const uint16_t* As = As0 + (k & 1) * NP * pA;
+    const uint16_t* Bs = Bs0 + (k & 1) * NP * pB;
     uint32_t af[NP][4];
 #pragma unroll
-    for (int pp = 0; pp < NP; ++pp) ldm_x4(af[pp], As + pp * pA + (mt * 16 + (lane & 15)) * kYS + ((lane >> 4) << 3));
+    for (int pp = 0; pp < NP; ++pp) ldm_x4(af[pp], As + pp * pA + (mt * 16 + (lane & 15)) * kYSA + ((lane >> 4) << 3));
 #pragma unroll
     for (int ii = 0; ii < 4; ++ii) {
       const int i = 4 * kh + ii;
@@ -306,12 +329,13 @@ __global__ void __launch_bounds__(kWThreads) k_ybuild_w(DevPlan P, uint16_t* __r
         if (nt * 8 >= nz4[ii]) break;
         uint32_t bf[NP][2];
 #pragma unroll
-        for (int pp = 0; pp < NP; ++pp)
-          ldm_x2(bf[pp], Bs + pp * pB + (i * 32 + nt * 8 + (lane & 7)) * kYS + (((lane >> 3) & 1) << 3));
+        for (int pp = 0; pp < NP; ++pp) ldm_x2_trans(bf[pp], Bs + pp * pB + (lane & 15) * kYSB + i * 32 + nt * 8);
         mma_split<NP>(acc[ii][nt], af, bf);
       }
     }
+    __syncthreads();   // buffer k & 1 is free for step k + 2
   }
+  cpa_wait<0>();
   // Y pieces [alpha][z][x] (x padded to rup16(n_ao(X)) with zeros, written
   // with the row x = n_ao(X) - 1)
 #pragma unroll
@@ -358,12 +382,12 @@ __host__ __device__ inline size_t term1w_smem(int np, int MA, int MB, int KC) {
 }
 
 template <int NP>
-__global__ void __launch_bounds__(kWThreads) k_term1_w(DevPlan P, const uint16_t* __restrict__ Yp,
+__global__ void __launch_bounds__(kPW * 32, 1) k_term1_w(DevPlan P, const uint16_t* __restrict__ Yp,
                                                        const uint16_t* __restrict__ Cw, const long long* cw_off,
                                                        const uint16_t* __restrict__ Dw, const long long* dw_off,
                                                        const int* list, int n_list, T1W S) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ double red[4 * kWarpsW];
+  __shared__ double red[4 * kPW];
   __shared__ double s_g[3];
   __shared__ int s_q;   // C pair whose grad C partials are in s_g
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gid = lane >> 2, tig = lane & 3;
@@ -405,9 +429,9 @@ __global__ void __launch_bounds__(kWThreads) k_term1_w(DevPlan P, const uint16_t
 #pragma unroll
       for (int pp = 0; pp < NP; ++pp) Us[pp * pU + (long long)mB * SK + e] = 0;
     const RTiles rt(MAp, MBp);
-    float racc[kRPairs][2][4];
+    float racc[kPRP][2][4];
 #pragma unroll
-    for (int i = 0; i < kRPairs; ++i)
+    for (int i = 0; i < kPRP; ++i)
 #pragma unroll
       for (int h = 0; h < 2; ++h)
 #pragma unroll
@@ -417,8 +441,8 @@ __global__ void __launch_bounds__(kWThreads) k_term1_w(DevPlan P, const uint16_t
     auto flush_r = [&]() {
       float evf[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-      for (int i = 0; i < kRPairs; ++i) {
-        const int pr = warp + kWarpsW * i;
+      for (int i = 0; i < kPRP; ++i) {
+        const int pr = warp + kPW * i;
         if (pr >= rt.count()) break;
         const int mt = pr / rt.NTP, nt0 = 2 * (pr - mt * rt.NTP);
 #pragma unroll
@@ -516,7 +540,7 @@ __global__ void __launch_bounds__(kWThreads) k_term1_w(DevPlan P, const uint16_t
 #pragma unroll
               for (int pp = 0; pp < NP; ++pp)
                 ldm_x4(af[ks][pp], Ds + pp * pD + (a0 + (lane & 15)) * SD + ks * 16 + ((lane >> 4) << 3));
-            for (int nt = warp; nt * 8 < rowsU; nt += kWarpsW) {
+            for (int nt = warp; nt * 8 < rowsU; nt += kPW) {
               float acc[4] = {0.f, 0.f, 0.f, 0.f};
               const int rn = nt * 8 + gid;
               const bool in = rn < rowsU;
@@ -549,8 +573,8 @@ __global__ void __launch_bounds__(kWThreads) k_term1_w(DevPlan P, const uint16_t
           __syncthreads();   // Cs and Us complete
           // R += C_AF . U^T (M = alpha, N = beta, K = this range's columns)
 #pragma unroll
-          for (int i = 0; i < kRPairs; ++i) {
-            const int pr = warp + kWarpsW * i;
+          for (int i = 0; i < kPRP; ++i) {
+            const int pr = warp + kPW * i;
             if (pr >= rt.count()) break;
             const int mt = pr / rt.NTP, nt0 = 2 * (pr - mt * rt.NTP);
             gemm_pair_kk<NP>(racc[i], Cs, pC, SK, Us, pU, SK, mt, nt0, nt0 + 1 < rt.NT, KCc);
@@ -559,7 +583,7 @@ __global__ void __launch_bounds__(kWThreads) k_term1_w(DevPlan P, const uint16_t
           {
             const int NTQ = rup8(dcols) >> 3, NPQ = (NTQ + 1) >> 1;
             const int npairs = (MAp >> 4) * NPQ;
-            for (int pr = warp; pr < npairs; pr += kWarpsW) {
+            for (int pr = warp; pr < npairs; pr += kPW) {
               const int mt = pr / NPQ, nt0 = 2 * (pr - mt * NPQ);
               float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
               gemm_pair_kn<NP>(acc, Vs, pV, SV, Us, pU, SK, mt, nt0, nt0 + 1 < NTQ, MBp);
@@ -591,7 +615,7 @@ __global__ void __launch_bounds__(kWThreads) k_term1_w(DevPlan P, const uint16_t
       }
     }
     flush_r();
-    block_sum_w<4>(ev, red);   // also orders the s_g additions before the flush below
+    block_sum_w<4, kPW>(ev, red);   // also orders the s_g additions before the flush below
     if (threadIdx.x == 0) {
       if (s_q >= 0) {
         atomicAdd(&P.gC[3 * s_q + 0], -2.0 * s_g[0]);
@@ -626,10 +650,10 @@ __host__ __device__ inline size_t term2w_smem(int np, int MA, int MB, int KC) {
 }
 
 template <int NP>
-__global__ void __launch_bounds__(kWThreads) k_term2_w(DevPlan P, const uint16_t* __restrict__ Yp,
+__global__ void __launch_bounds__(kPW * 32, 1) k_term2_w(DevPlan P, const uint16_t* __restrict__ Yp,
                                                        uint16_t* __restrict__ Zw, const int* list, int n_list, T2W S) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ double red[4 * kWarpsW];
+  __shared__ double red[4 * kPW];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gid = lane >> 2, tig = lane & 3;
   const int MA = S.MA, MB = S.MB;
   const int SV = MB + 8, SK = S.KC + 8;
@@ -671,9 +695,9 @@ __global__ void __launch_bounds__(kWThreads) k_term2_w(DevPlan P, const uint16_t
 #pragma unroll
       for (int pp = 0; pp < NP; ++pp) Yb[pp * pB + (long long)mB * SK + e] = 0;
     const RTiles rt(MAp, MBp);
-    float racc[kRPairs][2][4];
+    float racc[kPRP][2][4];
 #pragma unroll
-    for (int i = 0; i < kRPairs; ++i)
+    for (int i = 0; i < kPRP; ++i)
 #pragma unroll
       for (int h = 0; h < 2; ++h)
 #pragma unroll
@@ -721,8 +745,8 @@ __global__ void __launch_bounds__(kWThreads) k_term2_w(DevPlan P, const uint16_t
       __syncthreads();
       // R2 += Y^{AB} . Y^{BA} (M = alpha, N = beta, K = (a, b) of the range)
 #pragma unroll
-      for (int i = 0; i < kRPairs; ++i) {
-        const int pr = warp + kWarpsW * i;
+      for (int i = 0; i < kPRP; ++i) {
+        const int pr = warp + kPW * i;
         if (pr >= rt.count()) break;
         const int mt = pr / rt.NTP, nt0 = 2 * (pr - mt * rt.NTP);
         gemm_pair_kk<NP>(racc[i], Ya, pA, SK, Yb, pB, SK, mt, nt0, nt0 + 1 < rt.NT, KCc);
@@ -731,7 +755,7 @@ __global__ void __launch_bounds__(kWThreads) k_term2_w(DevPlan P, const uint16_t
       {
         const int NTZ = rup8(dcols) >> 3, NPZ = (NTZ + 1) >> 1;
         const int npairs = (MAp >> 4) * NPZ;
-        for (int pr = warp; pr < npairs; pr += kWarpsW) {
+        for (int pr = warp; pr < npairs; pr += kPW) {
           const int mt = pr / NPZ, nt0 = 2 * (pr - mt * NPZ);
           float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
           gemm_pair_kn<NP>(acc, Vs, pV, SV, Yb, pB, SK, mt, nt0, nt0 + 1 < NTZ, MBp);
@@ -754,8 +778,8 @@ __global__ void __launch_bounds__(kWThreads) k_term2_w(DevPlan P, const uint16_t
     {
       float evf[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-      for (int i = 0; i < kRPairs; ++i) {
-        const int pr = warp + kWarpsW * i;
+      for (int i = 0; i < kPRP; ++i) {
+        const int pr = warp + kPW * i;
         if (pr >= rt.count()) break;
         const int mt = pr / rt.NTP, nt0 = 2 * (pr - mt * rt.NTP);
 #pragma unroll
@@ -777,7 +801,7 @@ __global__ void __launch_bounds__(kWThreads) k_term2_w(DevPlan P, const uint16_t
 #pragma unroll
       for (int c = 0; c < 4; ++c) ev[c] = (double)evf[c];
     }
-    block_sum_w<4>(ev, red);
+    block_sum_w<4, kPW>(ev, red);
     if (threadIdx.x == 0) {
       atomicAdd(&P.acc[ACC_E], -ev[0]);
       atomicAdd(&P.gV[3 * p + 0], -ev[1]);
@@ -1041,8 +1065,8 @@ WideShapes wide_shapes(int np, int maxABF, int maxAO, size_t limit) {
     }
   }
   w.smem_q2 = q2w_smem(np, w.KZ);
-  // R tiles: (MA / 16) x (MB / 16) pairs over the 8 warps, kRPairs each
-  w.ok = w.t1_da > 0 && w.t2_da > 0 && w.smem_q2 <= limit && (w.MA / 16) * (w.MB / 16) <= kWarpsW * kRPairs &&
+  // R tiles: (MA / 16) x (MB / 16) pairs over the warps, kPRP each
+  w.ok = w.t1_da > 0 && w.t2_da > 0 && w.smem_q2 <= limit && (w.MA / 16) * (w.MB / 16) <= kPW * kPRP &&
          maxAO <= 32;
   return w;
 }
@@ -1077,7 +1101,7 @@ cudaError_t launch_cpieces_w(const DevPlan& P, int np, uint16_t* Cw, const long 
 }
 
 long long wide_cpieces_size(int np, int n_abf, int n_ao_a, int n_ao_f) {
-  return (long long)np * n_abf * cw_cols(n_ao_a, n_ao_f);
+  return (long long)np * n_abf * (cw_cols(n_ao_a, n_ao_f) + n_ao_a * ((n_ao_f + 15) / 16 * 16));
 }
 
 cudaError_t launch_ybuild_w(const DevPlan& P, int np, uint16_t* Yp, const uint16_t* Cw, const long long* cw_off,
@@ -1100,8 +1124,8 @@ cudaError_t launch_term1_w(const DevPlan& P, int np, const uint16_t* Yp, const u
   if (n <= 0) return cudaSuccess;
   const T1W S{w.MA, w.MB, w.t1_KC, w.t1_da};
   const int grid = grid_cap(n, 1 << 20);
-  if (np == 2) k_term1_w<2><<<grid, kWThreads, w.smem_t1, s>>>(P, Yp, Cw, cw_off, Dw, dw_off, list, n, S);
-  else k_term1_w<3><<<grid, kWThreads, w.smem_t1, s>>>(P, Yp, Cw, cw_off, Dw, dw_off, list, n, S);
+  if (np == 2) k_term1_w<2><<<grid, kPW * 32, w.smem_t1, s>>>(P, Yp, Cw, cw_off, Dw, dw_off, list, n, S);
+  else k_term1_w<3><<<grid, kPW * 32, w.smem_t1, s>>>(P, Yp, Cw, cw_off, Dw, dw_off, list, n, S);
   ++g_wide_launches;
   return cudaGetLastError();
 }
@@ -1123,8 +1147,8 @@ cudaError_t launch_term2_w(const DevPlan& P, int np, const uint16_t* Yp, uint16_
   if (n <= 0) return cudaSuccess;
   const T2W S{w.MA, w.MB, w.t2_KC, w.t2_da, w.KZ, wide_zplane(max_rows, w.KZ)};
   const int grid = grid_cap(n, 1 << 20);
-  if (np == 2) k_term2_w<2><<<grid, kWThreads, w.smem_t2, s>>>(P, Yp, Zw, list, n, S);
-  else k_term2_w<3><<<grid, kWThreads, w.smem_t2, s>>>(P, Yp, Zw, list, n, S);
+  if (np == 2) k_term2_w<2><<<grid, kPW * 32, w.smem_t2, s>>>(P, Yp, Zw, list, n, S);
+  else k_term2_w<3><<<grid, kPW * 32, w.smem_t2, s>>>(P, Yp, Zw, list, n, S);
   ++g_wide_launches;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
