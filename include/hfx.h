@@ -266,7 +266,10 @@ hfx_status hfx_set_reference(hfx_plan* plan, const double* E, const double* F, c
  * the copy of Y rows against the U build; then, with the best shape, the
  * order in which its items are handed out (longest first, so that the SMs
  * finish together, or by home atom, so that items running at the same time
- * share their V_AB and grad V_AB blocks in L2).  Each candidate is timed as the
+ * share their V_AB and grad V_AB blocks in L2); then the 128-row tiles per
+ * CTA of the tcgen05 Y build and of the Q2 GEMM (two tiles share each K
+ * step's D blocks; one tile runs more pipeline stages and two accumulators),
+ * each kept if it is faster.  Each candidate is timed as the
  * median of `reps` >= 1 evaluations (CUDA events) after one warm-up.
  * `report` (nullable) receives the choice and both times.  Plans without a
  * tunable kernel (FP64, or the warp-level first product) return HFX_OK
@@ -279,6 +282,8 @@ typedef struct {
   double best_ms;          /* median evaluation time with the chosen one */
   int t1_home_order;       /* chosen order of the first product's items: 0 = longest
                               first, 1 = by home atom */
+  int y_tiles_per_cta;     /* chosen 128-row tiles per CTA of the tcgen05 Y build (1 or 2) */
+  int q2_tiles_per_cta;    /* chosen 128-row tiles per CTA of the tcgen05 Q2 GEMM (1 or 2) */
 } hfx_tune_report;
 hfx_status hfx_plan_autotune(hfx_plan* plan, const double* lattice, const double* positions, int reps,
                              hfx_tune_report* report);

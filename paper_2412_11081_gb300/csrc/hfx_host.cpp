@@ -199,6 +199,7 @@ struct hfx_plan {
   int* t1q_list = nullptr;
   int* t1q_lpt = nullptr;      // the same items, longest (most kept B) first
   bool t1_home_order = false;  // first-product items in home-atom order instead of longest first
+  int ybtpc = 2, q2tpc = 2;    // 128-row tiles per CTA of the tcgen05 Y build and Q2 GEMM (autotuner)
   int q2_flush = 32;           // pairs per FP32 run of the second product's Q2 accumulator (128 for BF16X6)
   uint16_t* YspT = nullptr;    // transposed Y pieces (second product)
   long long YspTcap = 0;
@@ -932,6 +933,12 @@ void setup_shapes(hfx_plan* P) {
     }
     if (P->smem_m2 > limit || maxAO > 16)
       fail(HFX_ERR_UNSUPPORTED, "block shapes too large for the split-precision kernels");
+    // 128-row tiles per CTA of the tcgen05 Y build and Q2 GEMM (the autotuner
+    // may change them; HFX_Y_TILES / HFX_Q2_TILES = 1 or 2 set the initial choice)
+    const char* yt = std::getenv("HFX_Y_TILES");
+    const char* qt = std::getenv("HFX_Q2_TILES");
+    P->ybtpc = yt && std::atoi(yt) == 1 ? 1 : 2;
+    P->q2tpc = qt && std::atoi(qt) == 1 ? 1 : 2;
     const char* qf = std::getenv("HFX_Q2_FLUSH");
     P->q2_flush = qf ? std::max(1, std::atoi(qf)) : (P->np == 3 ? 128 : 32);   // as t1u_seg
     ck(hfx::set_mixed_smem_limits(P->np), "smem attributes");
@@ -1223,6 +1230,8 @@ void evaluate_launches(hfx_plan* P, const double* L, hfx_stats* st, bool tail) {
     if (P->t2u && P->Yspcap != ycap0) ck(cudaMemsetAsync(P->Ysp, 0, P->Yspcap * sizeof(uint16_t), s), "memset");
     X.Ysp = P->Ysp;
     X.ycm = P->t2u ? 1 : 0;
+    X.ybtpc = P->ybtpc;
+    X.q2tpc = P->q2tpc;
     if (!reuse) {
       ensure_buf(P, P->blist, P->blist_cap, P->tot[6]);
       X.blist = P->blist;
@@ -1336,7 +1345,7 @@ void evaluate_launches(hfx_plan* P, const double* L, hfx_stats* st, bool tail) {
         ck(hfx::launch_t2_umma(D, X, P->np, P->t2_list + v0, (int)ct[CT_T2], P->zblk, P->smem_t2u, P->d_err, s),
            "term2 R2 and Z");
       ck(hfx::launch_term2_mma(D, X, P->np, P->t2_list + v0, P->t2_idx, (int)ct[CT_T2], a0, a1, P->MAmax, P->KZmax,
-                               P->zblk, P->ZROWS, FC, P->MC, hfx::q2_umma_segments(P->maxV, P->np), P->q2_flush,
+                               P->zblk, P->ZROWS, FC, P->MC, hfx::q2_umma_segments(P->maxV, P->np, P->q2tpc), P->q2_flush,
                                P->drows, P->smem_m2, P->d_err, s, P->t2u),
          "term2");
     }
@@ -1628,6 +1637,8 @@ hfx_status hfx_plan_autotune(hfx_plan* P, const double* lattice, const double* p
   R.t1_rows_per_slot = P->t1u_FS;
   R.t1_slots = P->t1u_NS;
   R.t1_home_order = P->t1_home_order ? 1 : 0;
+  R.y_tiles_per_cta = P->ybtpc;
+  R.q2_tiles_per_cta = P->q2tpc;
   if (!P->t1u) {
     if (report) *report = R;
     return HFX_OK;
@@ -1696,17 +1707,38 @@ hfx_status hfx_plan_autotune(hfx_plan* P, const double* lattice, const double* p
     }
     P->t1_home_order = best_order;
   }
+  // then the row tiles per CTA of the Y build and of the Q2 GEMM, one at a time
+  const int yb0 = P->ybtpc, q20 = P->q2tpc;
+  for (int which = 0; which < 2 && ok; ++which) {
+    int& knob = which == 0 ? P->ybtpc : P->q2tpc;
+    const int keep = knob;
+    knob = 3 - keep;   // 1 <-> 2
+    if (P->gexec) {
+      cudaGraphExecDestroy(P->gexec);
+      P->gexec = nullptr;
+    }
+    double ms = 0.0;
+    ok = time_it(ms);
+    if (!ok) break;
+    ++R.candidates;
+    if (ms < R.best_ms) R.best_ms = ms;
+    else knob = keep;
+  }
   P->timing = timing0;
   if (!ok) {   // keep the initial choice
     use(fs0, ns0);
     P->smem_t1u = smem0;
     P->t1_home_order = order0;
+    P->ybtpc = yb0;
+    P->q2tpc = q20;
     return status;
   }
   use(best_fs, best_ns);
   R.t1_rows_per_slot = best_fs;
   R.t1_slots = best_ns;
   R.t1_home_order = best_order ? 1 : 0;
+  R.y_tiles_per_cta = P->ybtpc;
+  R.q2_tiles_per_cta = P->q2tpc;
   if (report) *report = R;
   return HFX_OK;
 }

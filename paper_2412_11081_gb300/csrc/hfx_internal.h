@@ -139,6 +139,11 @@ struct MixPlan {
   uint16_t* Vz = nullptr;
   long long vz_blk = 0;
   const long long* t2_slot = nullptr;   // V pair -> its slot in the pass's second-product list
+  // 128-row tiles per CTA of the tcgen05 Y build and Q2 GEMM (1 or 2; the
+  // autotuner's choice): two tiles share each K step's D blocks, one tile
+  // runs more stages and two accumulators
+  int ybtpc = 2;
+  int q2tpc = 2;
 };
 
 // Element (row, f < 16) of one component of grad C_AF (FP32) in the C operand
@@ -234,7 +239,7 @@ cudaError_t launch_term2_mma(const DevPlan& P, const MixPlan& X, int np, const i
                              int n, int a0, int a1, int MAmax, int KZmax, long long zblk, int zrows, int FC, int MC,
                              int nseg, int flush, const DRows& drows, size_t smem, int* err, cudaStream_t s,
                              bool pairs_done = false);
-int q2_umma_segments(int max_pairs_per_atom, int np);
+int q2_umma_segments(int max_pairs_per_atom, int np, int tpc);
 // R2 and Z of the pass's second-product pairs on tcgen05 (hfx_t1umma.cu),
 // shapes n_abf <= 64, n_ao <= 16, with X.ycm and X.Vz set: E, g^V and the Z
 // store that k_q2_umma reads (launch_term2_mma with pairs_done then skips

@@ -1020,7 +1020,6 @@ __global__ void __launch_bounds__(192) k_q2_umma(DevPlan P, MixPlan X, const int
 // bf16 pieces and writes the Y store ([alpha][z][16], x padding zeroed).
 // TPC row tiles of 128 rows per CTA share each K step's D blocks (one
 // accumulator of 128 columns per tile).
-__host__ __device__ constexpr int yb_tpc(int) { return 2; }
 // stages of the Y build's ring: 4, or 2 for two six-product tiles (so that
 // two CTAs still fit an SM)
 __host__ __device__ constexpr int yb_stages(int np, int tpc) { return tpc == 2 && np == 3 ? 2 : umma::kStages; }
@@ -1414,19 +1413,16 @@ __global__ void k_q2tab(DevPlan P, MixPlan X, const int* list, int n_slots, int 
   if ((threadIdx.x & 31) == 0 && fl != 0.0) atomicAdd(&P.acc[ACC_F2], fl);
 }
 
-size_t ybuild_umma_smem(int np) {
-  return (size_t)(yb_tpc(np) + 1) * yb_stages(np, yb_tpc(np)) * np * umma::kTileElems * sizeof(uint16_t) +
+size_t ybuild_umma_smem(int np, int tpc) {
+  return (size_t)(tpc + 1) * yb_stages(np, tpc) * np * umma::kTileElems * sizeof(uint16_t) +
          (size_t)kMaxCPerAtom * 8 * sizeof(int);
 }
 
-// row tiles per CTA of the Q2 GEMM
-constexpr int q2_tpc(int np) { return 2; }
-
-size_t q2_umma_smem(int np) {
-  const int tpc = q2_tpc(np);
-  const int ks = np == 2 ? Q2Shape<2, 2>::kS : Q2Shape<3, 2>::kS;
-  const int kmp = Q2Shape<2, 2>::kMP;
-  if (tpc == 2) return (size_t)ks * 3 * np * umma::kTileElems * sizeof(uint16_t) + (size_t)kmp * 8 * sizeof(int);
+size_t q2_umma_smem(int np, int tpc) {
+  if (tpc == 2) {
+    const int ks = np == 2 ? Q2Shape<2, 2>::kS : Q2Shape<3, 2>::kS;
+    return (size_t)ks * 3 * np * umma::kTileElems * sizeof(uint16_t) + (size_t)Q2Shape<2, 2>::kMP * 8 * sizeof(int);
+  }
   return (size_t)2 * Q2Shape<2, 1>::kS * np * umma::kTileElems * sizeof(uint16_t) +
          (size_t)Q2Shape<2, 1>::kMP * 8 * sizeof(int);
 }
@@ -1443,8 +1439,8 @@ long long mixed_launch_count() { return g_mix_launches; }
 long long ytab_size(int ngroups, int maxC) { return (long long)ngroups * 8 * maxC; }
 long long q2tab_size(int n_slots, int FC) { return (long long)n_slots * ((FC * 4 + 7) / 8) * 8; }
 
-int q2_umma_segments(int max_pairs_per_atom, int np) {
-  const int kmp = q2_tpc(np) == 2 ? Q2Shape<2, 2>::kMP : Q2Shape<2, 1>::kMP;
+int q2_umma_segments(int max_pairs_per_atom, int np, int tpc) {
+  const int kmp = tpc == 2 ? Q2Shape<2, 2>::kMP : Q2Shape<2, 1>::kMP;
   return (max_pairs_per_atom + kmp - 1) / kmp;
 }
 
@@ -1486,11 +1482,13 @@ cudaError_t launch_ybuild_mma(const DevPlan& P, const MixPlan& X, int np, const 
   g_mix_launches += 2;
   k_ytab<<<grid_for(((long long)ngroups * X.ytab_stride + 255) / 256, 152 * 16), 256, 0, s>>>(P, X, ylist, gX, gS, gN,
                                                                                           ngroups);
-  const long long grid = (long long)ngroups * ((MC + yb_tpc(np) - 1) / yb_tpc(np));
-  if (np == 2)
-    k_ybuild_umma<2, yb_tpc(2)><<<(unsigned)grid, 192, ybuild_umma_smem(2), s>>>(P, X, ylist, gX, gS, gN, MC, drows, err);
-  else
-    k_ybuild_umma<3, yb_tpc(3)><<<(unsigned)grid, 192, ybuild_umma_smem(3), s>>>(P, X, ylist, gX, gS, gN, MC, drows, err);
+  const int tpc = X.ybtpc == 1 ? 1 : 2;
+  const long long grid = (long long)ngroups * ((MC + tpc - 1) / tpc);
+  const size_t sm = ybuild_umma_smem(np, tpc);
+  if (np == 2 && tpc == 2) k_ybuild_umma<2, 2><<<(unsigned)grid, 192, sm, s>>>(P, X, ylist, gX, gS, gN, MC, drows, err);
+  else if (np == 2) k_ybuild_umma<2, 1><<<(unsigned)grid, 192, sm, s>>>(P, X, ylist, gX, gS, gN, MC, drows, err);
+  else if (tpc == 2) k_ybuild_umma<3, 2><<<(unsigned)grid, 192, sm, s>>>(P, X, ylist, gX, gS, gN, MC, drows, err);
+  else k_ybuild_umma<3, 1><<<(unsigned)grid, 192, sm, s>>>(P, X, ylist, gX, gS, gN, MC, drows, err);
   return cudaGetLastError();
 }
 
@@ -1511,9 +1509,11 @@ size_t term2_mma_smem(int np, int MAmax, int KZmax) {
 }
 
 cudaError_t set_mixed_smem_limits(int np) {
-  const void* f[4] = {
-      np == 2 ? (const void*)k_ybuild_umma<2, yb_tpc(2)> : (const void*)k_ybuild_umma<3, yb_tpc(3)>,
-      np == 2 ? (const void*)k_q2_umma<2, q2_tpc(2)> : (const void*)k_q2_umma<3, q2_tpc(3)>,
+  const void* f[6] = {
+      np == 2 ? (const void*)k_ybuild_umma<2, 2> : (const void*)k_ybuild_umma<3, 2>,
+      np == 2 ? (const void*)k_ybuild_umma<2, 1> : (const void*)k_ybuild_umma<3, 1>,
+      np == 2 ? (const void*)k_q2_umma<2, 2> : (const void*)k_q2_umma<3, 2>,
+      np == 2 ? (const void*)k_q2_umma<2, 1> : (const void*)k_q2_umma<3, 1>,
       np == 2 ? (const void*)k_term1_mma<2> : (const void*)k_term1_mma<3>,
       np == 2 ? (const void*)k_term2_pairs<2> : (const void*)k_term2_pairs<3>};
   for (const void* k : f) {
@@ -1542,18 +1542,27 @@ cudaError_t launch_term2_mma(const DevPlan& P, const MixPlan& X, int np, const i
   g_mix_launches += pairs_done ? 2 : 3;
   const int FC8 = (FC * 4 + 7) / 8;     // groups of 8 C slots for the tcgen05 kernel
   k_q2tab<<<grid_for(((long long)n * FC8 * 8 + 255) / 256, 152 * 16), 256, 0, s>>>(P, X, list, n, FC8);
-  const size_t sq = q2_umma_smem(np);
-  const long long grid = (long long)(a1 - a0) * FC8 * ((MC + q2_tpc(np) - 1) / q2_tpc(np)) * nseg;
+  const int tpc = X.q2tpc == 1 ? 1 : 2;
+  const size_t sq = q2_umma_smem(np, tpc);
+  const long long grid = (long long)(a1 - a0) * FC8 * ((MC + tpc - 1) / tpc) * nseg;
   if (np == 2) {
     if (!pairs_done)
       k_term2_pairs<2><<<grid_for(n, 152 * 32), kWarps * 32, smem, s>>>(P, X, list, n, MAmax, KZmax, zblk, zrows);
-    k_q2_umma<2, q2_tpc(2)><<<(unsigned)grid, 192, sq, s>>>(P, X, list, slot0, n, a0, a1, FC8, MC, nseg, zblk, flush,
-                                                             drows, err);
+    if (tpc == 2)
+      k_q2_umma<2, 2><<<(unsigned)grid, 192, sq, s>>>(P, X, list, slot0, n, a0, a1, FC8, MC, nseg, zblk, flush, drows,
+                                                      err);
+    else
+      k_q2_umma<2, 1><<<(unsigned)grid, 192, sq, s>>>(P, X, list, slot0, n, a0, a1, FC8, MC, nseg, zblk, flush, drows,
+                                                      err);
   } else {
     if (!pairs_done)
       k_term2_pairs<3><<<grid_for(n, 152 * 32), kWarps * 32, smem, s>>>(P, X, list, n, MAmax, KZmax, zblk, zrows);
-    k_q2_umma<3, q2_tpc(3)><<<(unsigned)grid, 192, sq, s>>>(P, X, list, slot0, n, a0, a1, FC8, MC, nseg, zblk, flush,
-                                                             drows, err);
+    if (tpc == 2)
+      k_q2_umma<3, 2><<<(unsigned)grid, 192, sq, s>>>(P, X, list, slot0, n, a0, a1, FC8, MC, nseg, zblk, flush, drows,
+                                                      err);
+    else
+      k_q2_umma<3, 1><<<(unsigned)grid, 192, sq, s>>>(P, X, list, slot0, n, a0, a1, FC8, MC, nseg, zblk, flush, drows,
+                                                      err);
   }
   return cudaGetLastError();
 }

@@ -52,7 +52,8 @@ class HfxOptions(ct.Structure):
 
 class HfxTuneReport(ct.Structure):
     _fields_ = [("candidates", ct.c_int), ("t1_rows_per_slot", ct.c_int), ("t1_slots", ct.c_int),
-                ("default_ms", ct.c_double), ("best_ms", ct.c_double), ("t1_home_order", ct.c_int)]
+                ("default_ms", ct.c_double), ("best_ms", ct.c_double), ("t1_home_order", ct.c_int),
+                ("y_tiles_per_cta", ct.c_int), ("q2_tiles_per_cta", ct.c_int)]
 
 
 class HfxStats(ct.Structure):
