@@ -1299,7 +1299,7 @@ void evaluate_launches(hfx_plan* P, const double* L, hfx_stats* st, bool tail) {
       } else
         ck(hfx::launch_term2(D, P->t2_list + v0, (int)ct[CT_T2], P->alpha_chunk, P->smem_t2, s), "term2");
     } else {
-      ensure_buf(P, P->Vm, P->Vmcap, ct[CT_VM]);
+      if (!P->t2u) ensure_buf(P, P->Vm, P->Vmcap, ct[CT_VM]);   // read by the warp-level kernels only
       X.Vm = P->Vm;
       // the split path evaluates V and grad V from the block model where it
       // writes the operand stores (no FP64 V blocks): one pass per needed pair

@@ -129,8 +129,9 @@ __global__ void k_t1u_cstore(DevPlan P, T1UPlan U, const int* list, int n) {
 
 // Every needed V pair p = list[k], in one pass: V and grad V evaluated once
 // from the block model into shared memory (FP32), then
-//   the second product's store X.Vm at vm_off[p]: NP bf16 planes
-//   [alpha][rup16(n_abf(B))] and V, grad V in FP32 [4][n_abf(A) n_abf(B)];
+//   the warp-level second product's store X.Vm at vm_off[p] (unless X.Vz is
+//   set): NP bf16 planes [alpha][rup16(n_abf(B))] and V, grad V in FP32
+//   [4][n_abf(A) n_abf(B)];
 //   for the pairs of the first product (any bit of v_mask), the tcgen05
 //   store U.Vu at t1_idx[p]: NP pieces [alpha 64][beta 64] in core-matrix
 //   order and grad V in three planes in epilogue load order (ep_at);
@@ -159,20 +160,23 @@ __global__ void k_vstores(DevPlan P, MixPlan X, T1UPlan U, const int* list, int 
       vsm[3 * nv + e] = m * g2;
     }
     __syncthreads();
-    // second-product store
-    uint16_t* out = X.Vm + X.vm_off[p];
-    for (int e4 = threadIdx.x; e4 < mA * MB / 4; e4 += blockDim.x) {
-      const int e = 4 * e4, al = e / MB, be = e - al * MB;
-      float x[4];
+    // second-product store of the warp-level R2 / Z kernel (none with the
+    // tcgen05 one, X.Vz: nothing reads it then)
+    if (!X.Vz) {
+      uint16_t* out = X.Vm + X.vm_off[p];
+      for (int e4 = threadIdx.x; e4 < mA * MB / 4; e4 += blockDim.x) {
+        const int e = 4 * e4, al = e / MB, be = e - al * MB;
+        float x[4];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) x[j] = be + j < mB ? vsm[al * mB + be + j] : 0.f;
-      uint2 pc[NP];
-      split4<NP>(x, pc);
+        for (int j = 0; j < 4; ++j) x[j] = be + j < mB ? vsm[al * mB + be + j] : 0.f;
+        uint2 pc[NP];
+        split4<NP>(x, pc);
 #pragma unroll
-      for (int pp = 0; pp < NP; ++pp) *reinterpret_cast<uint2*>(out + (long long)pp * mA * MB + e) = pc[pp];
+        for (int pp = 0; pp < NP; ++pp) *reinterpret_cast<uint2*>(out + (long long)pp * mA * MB + e) = pc[pp];
+      }
+      float* v32 = reinterpret_cast<float*>(out + (long long)NP * mA * MB);
+      for (int e = threadIdx.x; e < 4 * nv; e += blockDim.x) v32[e] = vsm[e];
     }
-    float* v32 = reinterpret_cast<float*>(out + (long long)NP * mA * MB);
-    for (int e = threadIdx.x; e < 4 * nv; e += blockDim.x) v32[e] = vsm[e];
     // first-product store
     bool t1 = false;
 #pragma unroll
