@@ -155,6 +155,20 @@ typedef struct {
   void* (*alloc)(size_t bytes, void* stream, void* ctx);
   void (*free)(void* ptr, size_t bytes, void* stream, void* ctx);
   void* alloc_ctx;
+  /* 1: a deterministic reduction (Sec. 2, the sums of Eq. Fexx1 and Eq.
+   * stress over pairs).  Every sum that several CTAs add to (E, the virial,
+   * the per-pair gradients g^C and g^V, and F) is kept as an exact 128-bit
+   * fixed-point integer in units of 2^-64 instead of an FP64 atomic sum,
+   * and rounded to FP64 once at the end.  Integer sums do not depend on
+   * the order of the additions, and every contribution is computed in a
+   * fixed order inside its CTA, so E, F and sigma are bit-identical from
+   * run to run, for any launch shape the autotuner picks and any split into
+   * passes of home atoms (results differ from the FP64 atomic sums by
+   * their rounding, about 1e-15 relative).  Costs 16 bytes per pair
+   * gradient component and atom force component of device memory and two
+   * integer atomics per addition.  0 (the default): FP64 atomic sums,
+   * repeatable to rounding order (about 1e-15). */
+  int deterministic;
 } hfx_options;
 
 /* Counters of the last call (FLOPs are the algorithmic count of the

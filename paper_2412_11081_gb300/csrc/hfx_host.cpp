@@ -155,6 +155,8 @@ struct hfx_plan {
   long long *y_off = nullptr, *y_size = nullptr, *y_idx = nullptr;
   int* y_list = nullptr;
   double *gC = nullptr, *gV = nullptr;
+  unsigned long long* fx = nullptr;   // deterministic plans: exact cells of gC, gV, E and the virial, F
+  size_t fx_words = 0;
   long long c_elems = 0;
 
   // per-call state
@@ -546,6 +548,12 @@ DevPlan make_devplan(hfx_plan* P, const double* lattice) {
   D.gC = P->gC;
   D.gV = P->gV;
   D.acc = P->d_acc;
+  if (P->fx) {   // [gC 3 nC][gV 3 nV][E, virial 10][F 3N] cells of two words
+    D.fxC = P->fx;
+    D.fxV = D.fxC + 2 * 3 * (size_t)P->nC;
+    D.fxA = D.fxV + 2 * 3 * (size_t)P->nV;
+    D.fxF = D.fxA + 2 * 10;
+  }
   D.cnt = reinterpret_cast<unsigned long long*>(P->d_tot + kTot);
   return D;
 }
@@ -734,6 +742,10 @@ void build_lists(hfx_plan* P, const double* L, const double* pos) {
   P->y_list = P->lalloc<int>(nY);
   P->gC = P->lalloc<double>(3 * (size_t)nC);
   P->gV = P->lalloc<double>(3 * (size_t)nV);
+  if (P->opt.deterministic) {
+    P->fx_words = 2 * (3 * (size_t)nC + 3 * (size_t)nV + 10 + 3 * (size_t)N);
+    P->fx = P->lalloc<unsigned long long>(P->fx_words);
+  }
   if (P->wide) {   // C pieces (per call, every C pair)
     std::vector<long long> cw_off(nC + 1, 0);
     for (int p = 0; p < nC; ++p) {
@@ -1138,6 +1150,7 @@ void evaluate_launches(hfx_plan* P, const double* L, hfx_stats* st, bool tail) {
   ck(cudaMemsetAsync(P->d_tot + kTot, 0, hfx::CNT_N * sizeof(long long), s), "memset");
   ck(cudaMemsetAsync(P->gC, 0, 3 * (size_t)P->nC * sizeof(double), s), "memset");
   ck(cudaMemsetAsync(P->gV, 0, 3 * (size_t)P->nV * sizeof(double), s), "memset");
+  if (P->fx) ck(cudaMemsetAsync(P->fx, 0, P->fx_words * sizeof(unsigned long long), s), "memset");
   // D is fixed for the plan: its norms and step-1 decisions are taken once
   const bool dnorm_now = !P->dnorm_done;
   if (dnorm_now) ck(hfx::launch_dnorm(D, s), "dnorm");
@@ -1479,6 +1492,7 @@ hfx_status hfx_default_options(hfx_options* o) {
   o->home_begin = o->home_end = 0;
   o->home_chunk = 0;
   o->graph = 0;
+  o->deterministic = 0;
   o->stream = nullptr;
   o->device = 0;
   return HFX_OK;

@@ -103,6 +103,13 @@ struct DevPlan {
   double* gV;                  // [nV*3]
   double* acc;                 // [0] E, [1..9] virial sum g (x) d, [10] flops y, [11] t1, [12] t2
   unsigned long long* cnt;     // [0] c kept, [1] v kept, [2] d kept, [3] triplets
+  // deterministic plans: exact fixed-point cells (hfx_accum.cuh) of gC, gV,
+  // E and the virial (fxA: E, then the nine virial components) and F, in
+  // place of the FP64 atomics; all nullptr otherwise
+  unsigned long long* fxC;
+  unsigned long long* fxV;
+  unsigned long long* fxA;
+  unsigned long long* fxF;
 };
 
 // Extra state of the split-precision path.

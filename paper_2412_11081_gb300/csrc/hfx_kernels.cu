@@ -22,6 +22,7 @@
 #include <cmath>
 #include <cstdio>
 
+#include "hfx_accum.cuh"
 #include "hfx_internal.h"
 #include "hfx_model.cuh"
 
@@ -448,9 +449,9 @@ __global__ void k_term1(DevPlan P, const int* list, int n_list, int BC) {
         g1 = block_sum(g1, red);
         g2 = block_sum(g2, red);
         if (threadIdx.x == 0) {
-          atomicAdd(&P.gC[3 * q + 0], -2.0 * g0);
-          atomicAdd(&P.gC[3 * q + 1], -2.0 * g1);
-          atomicAdd(&P.gC[3 * q + 2], -2.0 * g2);
+          dev::add_gC(P, 3 * q + 0, -2.0 * g0);
+          dev::add_gC(P, 3 * q + 1, -2.0 * g1);
+          dev::add_gC(P, 3 * q + 2, -2.0 * g2);
           fl += 2.0 * mB * nA * nB * nF + 4.0 * mA * mB * nA * nF;
         }
       }
@@ -472,10 +473,10 @@ __global__ void k_term1(DevPlan P, const int* list, int n_list, int BC) {
     h1 = block_sum(h1, red);
     h2 = block_sum(h2, red);
     if (threadIdx.x == 0) {
-      atomicAdd(&P.acc[ACC_E], -e0);
-      atomicAdd(&P.gV[3 * p + 0], -h0);
-      atomicAdd(&P.gV[3 * p + 1], -h1);
-      atomicAdd(&P.gV[3 * p + 2], -h2);
+      dev::add_E(P, -e0);
+      dev::add_gV(P, 3 * p + 0, -h0);
+      dev::add_gV(P, 3 * p + 1, -h1);
+      dev::add_gV(P, 3 * p + 2, -h2);
       atomicAdd(&P.acc[ACC_F1], fl);
     }
   }
@@ -519,10 +520,10 @@ __global__ void k_term2(DevPlan P, const int* list, int n_list, int AC) {
     h1 = block_sum(h1, red);
     h2 = block_sum(h2, red);
     if (threadIdx.x == 0) {
-      atomicAdd(&P.acc[ACC_E], -e0);
-      atomicAdd(&P.gV[3 * p + 0], -h0);
-      atomicAdd(&P.gV[3 * p + 1], -h1);
-      atomicAdd(&P.gV[3 * p + 2], -h2);
+      dev::add_E(P, -e0);
+      dev::add_gV(P, 3 * p + 0, -h0);
+      dev::add_gV(P, 3 * p + 1, -h1);
+      dev::add_gV(P, 3 * p + 2, -h2);
     }
     const int q0 = P.c_ptr[A], nq = P.c_ptr[A + 1] - q0;
     double* Zc = sm;                         // AC*nA*nB
@@ -588,9 +589,9 @@ __global__ void k_term2(DevPlan P, const int* list, int n_list, int AC) {
     for (int t = threadIdx.x; t < nq; t += blockDim.x) {
       if (gF[3 * t] != 0.0 || gF[3 * t + 1] != 0.0 || gF[3 * t + 2] != 0.0) {
         const int q = q0 + t;
-        atomicAdd(&P.gC[3 * q + 0], -2.0 * gF[3 * t + 0]);
-        atomicAdd(&P.gC[3 * q + 1], -2.0 * gF[3 * t + 1]);
-        atomicAdd(&P.gC[3 * q + 2], -2.0 * gF[3 * t + 2]);
+        dev::add_gC(P, 3 * q + 0, -2.0 * gF[3 * t + 0]);
+        dev::add_gC(P, 3 * q + 1, -2.0 * gF[3 * t + 1]);
+        dev::add_gC(P, 3 * q + 2, -2.0 * gF[3 * t + 2]);
       }
     }
     if (threadIdx.x == 0) atomicAdd(&P.acc[ACC_F2], fl);
@@ -614,25 +615,30 @@ __global__ void k_reduce_pairs(DevPlan P, double* F) {
       A = P.c_home[t];
       j = P.c_j[t];
       R = P.c_R + 3 * t;
-      g[0] = P.gC[3 * t];
-      g[1] = P.gC[3 * t + 1];
-      g[2] = P.gC[3 * t + 2];
+      g[0] = dev::get_gC(P, 3LL * t);
+      g[1] = dev::get_gC(P, 3LL * t + 1);
+      g[2] = dev::get_gC(P, 3LL * t + 2);
     } else {
       const int p = t - P.nC;
       A = P.v_home[p];
       j = P.v_j[p];
       R = P.v_R + 3 * p;
-      g[0] = P.gV[3 * p];
-      g[1] = P.gV[3 * p + 1];
-      g[2] = P.gV[3 * p + 2];
+      g[0] = dev::get_gV(P, 3LL * p);
+      g[1] = dev::get_gV(P, 3LL * p + 1);
+      g[2] = dev::get_gV(P, 3LL * p + 2);
     }
     if (g[0] == 0.0 && g[1] == 0.0 && g[2] == 0.0) continue;
     double d[3];
     pair_vector(P, A, j, R, d);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      atomicAdd(&F[3 * A + c], g[c]);
-      atomicAdd(&F[3 * j + c], -g[c]);
+      if (P.fxF) {   // deterministic plan: exact cells, written to F by k_finish
+        dev::fx_add(P.fxF + 2 * (3 * A + c), g[c]);
+        dev::fx_add(P.fxF + 2 * (3 * j + c), -g[c]);
+      } else {
+        atomicAdd(&F[3 * A + c], g[c]);
+        atomicAdd(&F[3 * j + c], -g[c]);
+      }
     }
 #pragma unroll
     for (int a = 0; a < 3; ++a)
@@ -642,11 +648,13 @@ __global__ void k_reduce_pairs(DevPlan P, double* F) {
 #pragma unroll
   for (int c = 0; c < 9; ++c) {
     const double s = block_sum(w[c], red);
-    if (threadIdx.x == 0 && s != 0.0) atomicAdd(&P.acc[ACC_W + c], s);
+    if (threadIdx.x == 0 && s != 0.0) dev::add_W(P, c, s);
   }
 }
 
 __global__ void k_finish(DevPlan P, double* out) {
+  if (P.fxF)
+    for (int i = threadIdx.x; i < 3 * P.N; i += blockDim.x) out[1 + i] = dev::fx_get(P.fxF + 2 * i);
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double L[9];
 #pragma unroll
@@ -654,9 +662,9 @@ __global__ void k_finish(DevPlan P, double* out) {
   const double det = L[0] * (L[4] * L[8] - L[5] * L[7]) - L[1] * (L[3] * L[8] - L[5] * L[6]) +
                      L[2] * (L[3] * L[7] - L[4] * L[6]);
   const double vol = fabs(det);
-  out[0] = P.acc[ACC_E];
+  out[0] = dev::get_E(P);
   double* sig = out + 1 + 3 * P.N;
-  for (int c = 0; c < 9; ++c) sig[c] = -P.acc[ACC_W + c] / vol;
+  for (int c = 0; c < 9; ++c) sig[c] = -dev::get_W(P, c) / vol;
 }
 
 // ---------------------------------------------------------------- scans

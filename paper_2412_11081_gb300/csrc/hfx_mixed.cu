@@ -29,6 +29,7 @@
 #include <atomic>
 #include <cstdint>
 
+#include "hfx_accum.cuh"
 #include "hfx_device.cuh"
 #include "hfx_model.cuh"
 
@@ -323,9 +324,9 @@ __global__ void __launch_bounds__(kWarps1 * 32) k_term1_mma(DevPlan P, MixPlan X
         __syncthreads();   // staged V (and Y) visible; previous B done with Us and sacc
         if (threadIdx.x == 0) {
           if (sprev >= 0) {
-            atomicAdd(&P.gV[3 * sprev + 0], -sacc[1]);
-            atomicAdd(&P.gV[3 * sprev + 1], -sacc[2]);
-            atomicAdd(&P.gV[3 * sprev + 2], -sacc[3]);
+            dev::add_gV(P, 3 * sprev + 0, -sacc[1]);
+            dev::add_gV(P, 3 * sprev + 1, -sacc[2]);
+            dev::add_gV(P, 3 * sprev + 2, -sacc[3]);
           }
           sacc[1] = sacc[2] = sacc[3] = 0.0;
           sprev = p;
@@ -452,7 +453,12 @@ __global__ void __launch_bounds__(kWarps1 * 32) k_term1_mma(DevPlan P, MixPlan X
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
           const float w = warp_sum_f(evf[c]);
-          if (lane == 0) atomicAdd(&sacc[c], (double)w);
+          if (lane == 0) {
+            if (P.fxC)   // deterministic plan: straight into the exact cells
+              (c == 0) ? dev::add_E(P, -(double)w) : dev::add_gV(P, 3 * p + c - 1, -(double)w);
+            else
+              atomicAdd(&sacc[c], (double)w);
+          }
         }
         // Q += V_AB . U (M = alpha, N = (a,f), K = beta).  Warp -> one alpha tile
         // and the (a,f) tiles nt = w0 + i * wpm; tiles i, i + 1 interleaved.
@@ -515,15 +521,15 @@ __global__ void __launch_bounds__(kWarps1 * 32) k_term1_mma(DevPlan P, MixPlan X
     }
     block_sum_n<3>(g, red);   // once per (A,F) item; also orders sacc
     if (threadIdx.x == 0) {
-      atomicAdd(&P.gC[3 * q + 0], -2.0 * g[0]);
-      atomicAdd(&P.gC[3 * q + 1], -2.0 * g[1]);
-      atomicAdd(&P.gC[3 * q + 2], -2.0 * g[2]);
+      dev::add_gC(P, 3 * q + 0, -2.0 * g[0]);
+      dev::add_gC(P, 3 * q + 1, -2.0 * g[1]);
+      dev::add_gC(P, 3 * q + 2, -2.0 * g[2]);
       if (sprev >= 0) {
-        atomicAdd(&P.gV[3 * sprev + 0], -sacc[1]);
-        atomicAdd(&P.gV[3 * sprev + 1], -sacc[2]);
-        atomicAdd(&P.gV[3 * sprev + 2], -sacc[3]);
+        dev::add_gV(P, 3 * sprev + 0, -sacc[1]);
+        dev::add_gV(P, 3 * sprev + 1, -sacc[2]);
+        dev::add_gV(P, 3 * sprev + 2, -sacc[3]);
       }
-      atomicAdd(&P.acc[ACC_E], -sacc[0]);
+      dev::add_E(P, -sacc[0]);
       atomicAdd(&P.acc[ACC_F1], (double)fl);
     }
   }
@@ -698,10 +704,10 @@ __global__ void __launch_bounds__(kWarps * 32) k_term2_pairs(DevPlan P, MixPlan 
     }
     block_sum_n<4>(ev, red);
     if (threadIdx.x == 0) {
-      atomicAdd(&P.acc[ACC_E], -ev[0]);
-      atomicAdd(&P.gV[3 * p + 0], -ev[1]);
-      atomicAdd(&P.gV[3 * p + 1], -ev[2]);
-      atomicAdd(&P.gV[3 * p + 2], -ev[3]);
+      dev::add_E(P, -ev[0]);
+      dev::add_gV(P, 3 * p + 0, -ev[1]);
+      dev::add_gV(P, 3 * p + 1, -ev[2]);
+      dev::add_gV(P, 3 * p + 2, -ev[3]);
       atomicAdd(&P.acc[ACC_F2], 4.0 * mA * mB * nA * nB);
     }
   }
@@ -997,7 +1003,10 @@ __global__ void __launch_bounds__(192) k_q2_umma(DevPlan P, MixPlan X, const int
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const double w = warp_sum_d(gd[i][c]);
-        if (lane == 0 && w != 0.0) atomicAdd(&sg[i][c], w);
+        if (lane == 0 && w != 0.0) {
+          if (P.fxC) dev::add_gC(P, 3 * qf[i] + c, -2.0 * w);   // deterministic plan: straight into the exact cell
+          else atomicAdd(&sg[i][c], w);
+        }
       }
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -1006,7 +1015,7 @@ __global__ void __launch_bounds__(192) k_q2_umma(DevPlan P, MixPlan X, const int
   if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(256));
   if (tid < 24) {
     const int i = tid / 3, c = tid % 3;
-    if (qf[i] >= 0 && sg[i][c] != 0.0) atomicAdd(&P.gC[3 * qf[i] + c], -2.0 * sg[i][c]);
+    if (qf[i] >= 0 && sg[i][c] != 0.0) dev::add_gC(P, 3 * qf[i] + c, -2.0 * sg[i][c]);
   }
   if (tid == 0 && s_abort) atomicExch(err, 1);
 }

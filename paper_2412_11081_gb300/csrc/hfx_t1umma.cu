@@ -33,6 +33,7 @@
 #include <atomic>
 #include <mutex>
 
+#include "hfx_accum.cuh"
 #include "hfx_device.cuh"
 #include "hfx_model.cuh"
 
@@ -709,7 +710,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (lane == 0 && ok)
 #pragma unroll
             for (int c = 0; c < 3; ++c)
-              if (gv[c] != 0.f) atomicAdd(&P.gV[3 * p + c], -(double)gv[c]);
+              if (gv[c] != 0.f) dev::add_gV(P, 3 * p + c, -(double)gv[c]);
           if (ew == 0 && lane == 0) fl += 2.0 * mB * nA * nB * nF + 4.0 * mA * mB * nA * nF;
           ++rb;
           // ---- end of a run: Q -> E, g^C
@@ -763,10 +764,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
       for (int c = 0; c < 3; ++c) g_it[c] = warp_sum_d(g_it[c]);
       if (lane == 0 && ok) {
-        if (e_it != 0.0) atomicAdd(&P.acc[ACC_E], -e_it);
+        if (e_it != 0.0) dev::add_E(P, -e_it);
 #pragma unroll
         for (int c = 0; c < 3; ++c)
-          if (g_it[c] != 0.0) atomicAdd(&P.gC[3 * q + c], -2.0 * g_it[c]);
+          if (g_it[c] != 0.0) dev::add_gC(P, 3 * q + c, -2.0 * g_it[c]);
       }
     }
     if (!ok) *abort_flag = 1;
@@ -1183,10 +1184,10 @@ __global__ void __launch_bounds__(kT2Threads, 1)
 #pragma unroll
       for (int c = 0; c < 4; ++c) ev[c] = warp_sum_f(ev[c]);
       if (lane == 0 && ok) {
-        if (ev[0] != 0.f) atomicAdd(&P.acc[ACC_E], -(double)ev[0]);
+        if (ev[0] != 0.f) dev::add_E(P, -(double)ev[0]);
 #pragma unroll
         for (int c = 0; c < 3; ++c)
-          if (ev[c + 1] != 0.f) atomicAdd(&P.gV[3 * p + c], -(double)ev[c + 1]);
+          if (ev[c + 1] != 0.f) dev::add_gV(P, 3 * p + c, -(double)ev[c + 1]);
       }
       // ---- Z -> the Z store: NP planes of 128-row tiles of rows (alpha, a),
       // 16 columns b each, in the core-matrix order of tix; a thread writes

@@ -34,6 +34,7 @@
 #include <atomic>
 #include <cstdint>
 
+#include "hfx_accum.cuh"
 #include "hfx_device.cuh"
 
 namespace hfx {
@@ -492,9 +493,9 @@ __global__ void __launch_bounds__(kPW * 32, 1) k_term1_w(DevPlan P, const uint16
           const int dcols = dA * nF, KCc = rup16(dcols);
           __syncthreads();   // the previous range's products are done with Cs and Us
           if (threadIdx.x == 0 && s_q >= 0 && s_q != q) {   // grad C partials of the previous F
-            atomicAdd(&P.gC[3 * s_q + 0], -2.0 * s_g[0]);
-            atomicAdd(&P.gC[3 * s_q + 1], -2.0 * s_g[1]);
-            atomicAdd(&P.gC[3 * s_q + 2], -2.0 * s_g[2]);
+            dev::add_gC(P, 3 * s_q + 0, -2.0 * s_g[0]);
+            dev::add_gC(P, 3 * s_q + 1, -2.0 * s_g[1]);
+            dev::add_gC(P, 3 * s_q + 2, -2.0 * s_g[2]);
             s_g[0] = s_g[1] = s_g[2] = 0.0;
           }
           if (threadIdx.x == 0) s_q = q;
@@ -608,7 +609,10 @@ __global__ void __launch_bounds__(kPW * 32, 1) k_term1_w(DevPlan P, const uint16
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           const float w = warp_sum_f(gq[c]);
-          if (lane == 0) atomicAdd(&s_g[c], (double)w);
+          if (lane == 0) {
+            if (P.fxC) dev::add_gC(P, 3 * q + c, -2.0 * (double)w);   // deterministic plan: straight into the exact cell
+            else atomicAdd(&s_g[c], (double)w);
+          }
         }
         fl += 2.0 * mB * nA * nB * nF + 4.0 * mA * mB * nA * nF;
         if (++nf % kFlushF == 0) flush_r();
@@ -618,14 +622,14 @@ __global__ void __launch_bounds__(kPW * 32, 1) k_term1_w(DevPlan P, const uint16
     block_sum_w<4, kPW>(ev, red);   // also orders the s_g additions before the flush below
     if (threadIdx.x == 0) {
       if (s_q >= 0) {
-        atomicAdd(&P.gC[3 * s_q + 0], -2.0 * s_g[0]);
-        atomicAdd(&P.gC[3 * s_q + 1], -2.0 * s_g[1]);
-        atomicAdd(&P.gC[3 * s_q + 2], -2.0 * s_g[2]);
+        dev::add_gC(P, 3 * s_q + 0, -2.0 * s_g[0]);
+        dev::add_gC(P, 3 * s_q + 1, -2.0 * s_g[1]);
+        dev::add_gC(P, 3 * s_q + 2, -2.0 * s_g[2]);
       }
-      atomicAdd(&P.acc[ACC_E], -ev[0]);
-      atomicAdd(&P.gV[3 * p + 0], -ev[1]);
-      atomicAdd(&P.gV[3 * p + 1], -ev[2]);
-      atomicAdd(&P.gV[3 * p + 2], -ev[3]);
+      dev::add_E(P, -ev[0]);
+      dev::add_gV(P, 3 * p + 0, -ev[1]);
+      dev::add_gV(P, 3 * p + 1, -ev[2]);
+      dev::add_gV(P, 3 * p + 2, -ev[3]);
       atomicAdd(&P.acc[ACC_F1], fl);
     }
   }
@@ -803,10 +807,10 @@ __global__ void __launch_bounds__(kPW * 32, 1) k_term2_w(DevPlan P, const uint16
     }
     block_sum_w<4, kPW>(ev, red);
     if (threadIdx.x == 0) {
-      atomicAdd(&P.acc[ACC_E], -ev[0]);
-      atomicAdd(&P.gV[3 * p + 0], -ev[1]);
-      atomicAdd(&P.gV[3 * p + 1], -ev[2]);
-      atomicAdd(&P.gV[3 * p + 2], -ev[3]);
+      dev::add_E(P, -ev[0]);
+      dev::add_gV(P, 3 * p + 0, -ev[1]);
+      dev::add_gV(P, 3 * p + 1, -ev[2]);
+      dev::add_gV(P, 3 * p + 2, -ev[3]);
       atomicAdd(&P.acc[ACC_F2], 4.0 * mA * mB * nA * nB);
     }
   }
@@ -1028,7 +1032,7 @@ __global__ void __launch_bounds__(kQ2Threads, 1) k_q2_w(DevPlan P, const uint16_
     if (q >= 0) {
       double v = 0.0;
       for (int w = 0; w < 8; ++w) v += s_ev[(i >> 2) * 8 + w][i & 3][c];
-      atomicAdd(&P.gC[3 * q + c], -2.0 * v);
+      dev::add_gC(P, 3 * q + c, -2.0 * v);
     }
   }
   if (threadIdx.x == 0 && fl != 0.0) atomicAdd(&P.acc[ACC_F2], fl);

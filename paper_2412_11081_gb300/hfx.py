@@ -47,7 +47,7 @@ class HfxOptions(ct.Structure):
                 ("freeze_lists", ct.c_int), ("home_begin", ct.c_int), ("home_end", ct.c_int),
                 ("home_chunk", ct.c_int), ("graph", ct.c_int), ("stream", ct.c_void_p), ("device", ct.c_int),
                 ("alloc", ALLOC_FN),
-                ("free", FREE_FN), ("alloc_ctx", ct.c_void_p)]
+                ("free", FREE_FN), ("alloc_ctx", ct.c_void_p), ("deterministic", ct.c_int)]
 
 
 class HfxTuneReport(ct.Structure):
@@ -147,7 +147,7 @@ class Plan:
     def __init__(self, w, *, precision: int = HFX_FP64, terms: int = 3, skin: float = 0.5,
                  freeze_lists: bool = False, stream: Optional[int] = None, device: int = 0,
                  theta: Optional[dict] = None, aniso=None, allocator=None, home=None, home_chunk: int = 0,
-                 graph: bool = False):
+                 graph: bool = False, deterministic: bool = False):
         self.lib = load_library()
         th = dict(w.theta) if theta is None else dict(theta)
         if stream is None:
@@ -156,7 +156,8 @@ class Plan:
         self.opts = default_options(theta_C=th["C"], theta_dC=th["dC"], theta_V=th["V"], theta_dV=th["dV"],
                                     theta_D=th["D"], theta_CS=th["CS"], precision=precision, terms=terms,
                                     skin=skin, freeze_lists=int(freeze_lists), stream=stream, device=device,
-                                    home_begin=hb, home_end=he, home_chunk=int(home_chunk), graph=int(graph))
+                                    home_begin=hb, home_end=he, home_chunk=int(home_chunk), graph=int(graph),
+                                    deterministic=int(deterministic))
         # allocator="torch": the plan's device memory comes from PyTorch's
         # caching allocator (hfx_options alloc / free); a pair of callables
         # (alloc(nbytes) -> device address or 0, free(address, nbytes)) is
