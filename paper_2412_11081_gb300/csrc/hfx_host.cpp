@@ -590,24 +590,93 @@ void build_lists(hfx_plan* P, const double* L, const double* pos) {
   B[6] = (L[1] * L[5] - L[2] * L[4]) / det;
   B[7] = (L[2] * L[3] - L[0] * L[5]) / det;
   B[8] = (L[0] * L[4] - L[1] * L[3]) / det;
-  int nm[3];
+  // Candidates by a cell list over the wrapped fractional coordinates:
+  // atom i sits at w_i = pos_i - L k_i with k_i = floor(s_i), s_i = B pos_i;
+  // cells are at least max(rmax / 8, 1 A) wide (n_k per axis, the D reach
+  // makes rmax ~30 A on the Si cells); atom A searches the cells within
+  // +-m_k of its own, where m_k = ceil(n_k rmax |b_k|) covers
+  // every fractional separation |ds_k| <= rmax |b_k| of two points within
+  // rmax.  A visited cell c (unwrapped) is cell c mod n of image floor(c / n)
+  // in wrapped coordinates, i.e. image R = floor(c / n) - k_j + k_A of the
+  // original positions; each (j, R) is visited at most once.  The inclusion
+  // test below is the direct one on the original positions, and each atom's
+  // candidates are sorted by (j, R), so the lists do not depend on the
+  // binning.
+  int ncell[3], mc[3];
+  double bnorm[3];
   for (int k = 0; k < 3; ++k) {
-    const double bn = std::sqrt(B[3 * k] * B[3 * k] + B[3 * k + 1] * B[3 * k + 1] + B[3 * k + 2] * B[3 * k + 2]);
-    nm[k] = (int)std::ceil(rmax * bn) + 1;
-    if (nm[k] > 200) fail(HFX_ERR_UNSUPPORTED, "pair range spans too many images");
+    bnorm[k] = std::sqrt(B[3 * k] * B[3 * k] + B[3 * k + 1] * B[3 * k + 1] + B[3 * k + 2] * B[3 * k + 2]);
+    const double width = 1.0 / bnorm[k];   // distance between the lattice planes of axis k
+    ncell[k] = std::max(1, std::min(256, (int)std::floor(width / std::max(0.125 * rmax, 1.0))));
+    mc[k] = (int)std::ceil(ncell[k] * rmax * bnorm[k]);
+    if (mc[k] > 200 * ncell[k]) fail(HFX_ERR_UNSUPPORTED, "pair range spans too many images");
   }
+  std::vector<int> kimg(3 * (size_t)N), cell_of(N);
+  const int nct = ncell[0] * ncell[1] * ncell[2];
+  std::vector<int> cell_ptr(nct + 1, 0), cell_atoms(N);
+  std::vector<double> wpos(3 * (size_t)N);
+  for (int i = 0; i < N; ++i) {
+    int ci[3];
+    for (int k = 0; k < 3; ++k) {
+      const double sk = B[3 * k] * pos[3 * i] + B[3 * k + 1] * pos[3 * i + 1] + B[3 * k + 2] * pos[3 * i + 2];
+      const double fk = std::floor(sk);
+      kimg[3 * i + k] = (int)fk;
+      ci[k] = std::min(ncell[k] - 1, std::max(0, (int)std::floor((sk - fk) * ncell[k])));
+    }
+    for (int k = 0; k < 3; ++k)
+      wpos[3 * i + k] = pos[3 * i + k] - (kimg[3 * i] * L[k] + kimg[3 * i + 1] * L[3 + k] + kimg[3 * i + 2] * L[6 + k]);
+    cell_of[i] = (ci[0] * ncell[1] + ci[1]) * ncell[2] + ci[2];
+    ++cell_ptr[cell_of[i] + 1];
+  }
+  for (int c = 0; c < nct; ++c) cell_ptr[c + 1] += cell_ptr[c];
+  {
+    std::vector<int> fill(cell_ptr.begin(), cell_ptr.end() - 1);
+    for (int i = 0; i < N; ++i) cell_atoms[fill[cell_of[i]]++] = i;
+  }
+  auto floordiv = [](int a, int n) { return a >= 0 ? a / n : -((-a + n - 1) / n); };
+  struct Cand {
+    int j, a, b, c;
+  };
+  std::vector<Cand> cand;
   std::vector<int> c_ptr(N + 1, 0), v_ptr(N + 1, 0), y_ptr(N + 1, 0);
   std::vector<int> c_home, c_j, c_R, v_home, v_j, v_R, y_home, y_j, y_R;
   int HY[3] = {0, 0, 0};
   double Rabs = 0;
+  const double rmax2 = (rmax * 1.0001 + 1e-9) * (rmax * 1.0001 + 1e-9);
   for (int A = 0; A < N; ++A) {
     c_ptr[A] = (int)c_j.size();
     v_ptr[A] = (int)v_j.size();
     y_ptr[A] = (int)y_j.size();
-    for (int j = 0; j < N; ++j)
-      for (int a = -nm[0]; a <= nm[0]; ++a)
-        for (int b = -nm[1]; b <= nm[1]; ++b)
-          for (int c = -nm[2]; c <= nm[2]; ++c) {
+    const int cA = cell_of[A];
+    const int cA0 = cA / (ncell[1] * ncell[2]), cA1 = (cA / ncell[2]) % ncell[1], cA2 = cA % ncell[2];
+    cand.clear();
+    for (int d0 = -mc[0]; d0 <= mc[0]; ++d0)
+      for (int d1 = -mc[1]; d1 <= mc[1]; ++d1)
+        for (int d2 = -mc[2]; d2 <= mc[2]; ++d2) {
+          const int u0 = cA0 + d0, u1 = cA1 + d1, u2 = cA2 + d2;
+          const int W0 = floordiv(u0, ncell[0]), W1 = floordiv(u1, ncell[1]), W2 = floordiv(u2, ncell[2]);
+          const int cw = ((u0 - W0 * ncell[0]) * ncell[1] + (u1 - W1 * ncell[1])) * ncell[2] + (u2 - W2 * ncell[2]);
+          for (int t = cell_ptr[cw]; t < cell_ptr[cw + 1]; ++t) {
+            const int j = cell_atoms[t];
+            double e2 = 0;   // loose prefilter in wrapped coordinates
+            for (int k = 0; k < 3; ++k) {
+              const double dv = wpos[3 * j + k] + W0 * L[k] + W1 * L[3 + k] + W2 * L[6 + k] - wpos[3 * A + k];
+              e2 += dv * dv;
+            }
+            if (e2 > rmax2) continue;
+            cand.push_back({j, W0 - kimg[3 * j] + kimg[3 * A], W1 - kimg[3 * j + 1] + kimg[3 * A + 1],
+                            W2 - kimg[3 * j + 2] + kimg[3 * A + 2]});
+          }
+        }
+    std::sort(cand.begin(), cand.end(), [](const Cand& x, const Cand& y) {
+      if (x.j != y.j) return x.j < y.j;
+      if (x.a != y.a) return x.a < y.a;
+      if (x.b != y.b) return x.b < y.b;
+      return x.c < y.c;
+    });
+    for (const Cand& q : cand) {
+      const int j = q.j, a = q.a, b = q.b, c = q.c;
+      {
             double d2 = 0;
             for (int k = 0; k < 3; ++k) {
               const double dv = (pos[3 * j + k] + (a * L[k] + b * L[3 + k] + c * L[6 + k])) - pos[3 * A + k];
@@ -635,7 +704,8 @@ void build_lists(hfx_plan* P, const double* L, const double* pos) {
               HY[1] = std::max(HY[1], std::abs(b));
               HY[2] = std::max(HY[2], std::abs(c));
             }
-          }
+      }
+    }
     if ((int)c_j.size() - c_ptr[A] > hfx::kMaxCPerAtom)
       fail(HFX_ERR_UNSUPPORTED, "more than 256 C-pair candidates on one atom");
   }

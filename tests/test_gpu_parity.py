@@ -206,3 +206,40 @@ def test_nonfinite_positions_rejected():
         # the plan stays usable after a rejected call
         E, F, S = p.evaluate(w.lattice, w.positions)
         assert np.isfinite(E)
+
+
+def _thin_cell(seed):
+    """Three atoms of two species in a long, sheared cell: several pair-list
+    cells along the long axis, one or two across, and pairs many images away."""
+    rng = np.random.default_rng(seed)
+    L = np.array([[3.0, 0.0, 0.0], [0.9, 2.8, 0.0], [-0.6, 0.7, 11.0]])
+    frac = np.array([[0.02, 0.97, 0.01], [0.51, 0.48, 0.35], [0.96, 0.03, 0.93]])
+    pos = frac @ L + rng.normal(0, 0.05, (3, 3))
+    w = inputs.tiny_model([2, 3], [3, 4], [0, 1, 1], L, pos, r_c=1.35, seed=seed)
+    return inputs.cut_density(w, 3.6)
+
+
+def _sheared_cell(seed):
+    """Three atoms near the faces of a strongly sheared cell."""
+    rng = np.random.default_rng(seed)
+    L = np.eye(3) * rng.uniform(2.6, 3.6, 3)
+    off = ~np.eye(3, dtype=bool)
+    L[off] = rng.uniform(-1.2, 1.2, 6)
+    frac = np.array([[0.01, 0.02, 0.99], [0.98, 0.97, 0.03], [0.5, 0.01, 0.5]])
+    w = inputs.tiny_model([2, 3], [3, 4], [0, 1, 1], L, frac @ L, r_c=1.3, seed=seed)
+    return inputs.cut_density(w, 3.4)
+
+
+@pytest.mark.parametrize("make,seed", [(_thin_cell, 1), (_thin_cell, 2), (_sheared_cell, 3), (_sheared_cell, 4)])
+def test_pair_lists_on_thin_and_sheared_cells(make, seed):
+    """The pair lists come from a cell list over wrapped fractional
+    coordinates; on cells whose axes get different cell counts, with atoms at
+    the faces and pairs across many images, the kept counts and the result
+    must still be the oracle's."""
+    w = make(seed)
+    r = evaluate(w, Options.from_theta(w.theta))
+    g = gpu_eval(w)
+    st = g[3]
+    for k in ("c_pairs", "triplets", "term1_pairs", "term2_pairs", "y_blocks"):
+        assert st[k] == r.counts[k], (k, st[k], r.counts[k])
+    assert_parity(g, r)
