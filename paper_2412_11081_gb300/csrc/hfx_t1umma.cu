@@ -5,6 +5,7 @@
 // product of Eq. exx_expand, factorised through Y^{BF} = sum_W C_BW D_WF:
 //   U_B[beta][(f,a)] = sum_b Y^{BF}[f][beta][b] D_AB[a][b]   (CUDA cores, FP32)
 //   R_B = C_AF . U_B^T        (M = alpha, N = beta, K = (f,a))  -> g^V_AB = -<grad V_AB, R_B>
+//                             (two U pieces per instruction, N = 128: R is the sum of two 64-column blocks)
 //   Q  += V_AB . U_B          (M = alpha, N = (f,a), K = beta)  -> E = -<C_AF, Q>, g^C_AF = -2 <grad C_AF, Q>
 // (E through Q: <V_AB, C U^T> = <C, V_AB U>, so the per-B epilogue carries
 // only the three gradient planes of V.)
@@ -51,6 +52,7 @@ constexpr int kItemRing = 4;
 constexpr int kItemReaders = 3 + kNE + kNU;   // Y, R issuer, Q issuer, epilogue warps, U warps
 constexpr int kMaxNS = 16;
 constexpr int kRCol = 256;   // tensor-memory column of the first R accumulator (Q sits at column 0)
+constexpr int kRCols = 128;  // columns of one R accumulator: two 64-column blocks, R = block 0 + block 1
 
 __device__ __forceinline__ bool aborted(const volatile int* f) { return *f != 0; }
 
@@ -498,22 +500,30 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else if (warp == kWarpM) {
     // ------------------------------------------------------------ R issuer
-    // R_B = C_AF . U_B^T (M = 64 alpha, N = 64 beta, K = (f,a), one f per k
-    // step), every piece product, into one of two accumulators.  Descriptors
-    // of the products are formed once; a k step adds 16 (256 bytes).
-    const uint32_t idR = idesc_bf16(64, 64, 0);
+    // R_B = C_AF . U_B^T (M = 64 alpha, N = beta, K = (f,a), one f per k
+    // step) into one of two accumulators of kRCols columns.  A U piece
+    // plane is 64 rows, i.e. eight 8-row groups, after the previous one, so
+    // pieces 0 and 1 together are one N = 128 operand: block 0 (columns
+    // 0-63) collects the products with U_0 (and U_2), block 1 those with U_1,
+    // and R = block 0 + block 1.  BF16X6: C0 [U0;U1], C0 U2, C1 [U0;U1]
+    // (C1 U1 comes with it), C2 U0; BF16X3: C0 [U0;U1], C1 U0.  Descriptors
+    // are formed once; a k step adds 16 (256 bytes).
+    constexpr int NR = NP == 3 ? 4 : 2;   // MMAs per k step
+    const uint32_t idR128 = idesc_bf16(64, 128, 0), idR64 = idesc_bf16(64, 64, 0);
     const uint32_t rowg = 16u * KP;   // bytes between 8-row groups of C and U
     const uint64_t dC = sdesc2(sa(Cs), 128, rowg), dUR = sdesc2(sa(Us), 128, rowg);
-    uint64_t pa[NPROD], pb[NPROD];
+    uint64_t pa[NR], pb[NR];
+    uint32_t pid[NR];
     {
-      int k = 0;
+      const int ca[4] = {0, 0, 1, 2}, ub[4] = {0, 2, 0, 0}, wide[4] = {1, 0, 1, 0};   // BF16X6
+      const int ca2[2] = {0, 1}, ub2[2] = {0, 0}, wide2[2] = {1, 0};                  // BF16X3
 #pragma unroll
-      for (int sum = NP - 1; sum >= 0; --sum)
-#pragma unroll
-        for (int ia = 0; ia <= sum; ++ia, ++k) {
-          pa[k] = dC + ((uint64_t)(ia * CPB) >> 4);
-          pb[k] = dUR + ((uint64_t)((sum - ia) * CPB) >> 4);
-        }
+      for (int k = 0; k < NR; ++k) {
+        const int c = NP == 3 ? ca[k] : ca2[k], u = NP == 3 ? ub[k] : ub2[k], w = NP == 3 ? wide[k] : wide2[k];
+        pa[k] = dC + ((uint64_t)(c * CPB) >> 4);
+        pb[k] = dUR + ((uint64_t)(u * CPB) >> 4);
+        pid[k] = w ? idR128 : idR64;
+      }
     }
     uint32_t rb = 0, it = 0, ik = 0;
     bool ok = true;
@@ -529,7 +539,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             break;
           }
           const int rbuf = rb & 1;
-          const uint32_t dR = T + kRCol + 64u * rbuf;
+          const uint32_t dR = T + kRCol + (uint32_t)kRCols * rbuf;
           if (rb >= 2) ok = mbar_wait(re + 8 * rbuf, ((rb >> 1) - 1) & 1);
           for (int c = 0; c < 2 && ok; ++c) {
             ok = mbar_wait(uf + 8 * c, rb & 1);
@@ -539,7 +549,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int f = f0; f < f1; ++f) {
               const uint64_t o = 16u * (uint32_t)f;
 #pragma unroll
-              for (int k = 0; k < NPROD; ++k) umma_bf16(dR, pa[k] + o, pb[k] + o, idR, (f > 0 || k > 0) ? 1u : 0u);
+              for (int k = 0; k < NR; ++k) umma_bf16(dR, pa[k] + o, pb[k] + o, pid[k], (f > 0 || k > 0) ? 1u : 0u);
             }
             umma_commit(ue + 8 * c);
             if (c == 1) umma_commit(rf + 8 * rbuf);
@@ -678,26 +688,30 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int c = 0; c < 3; ++c)
 #pragma unroll
                   for (int t4 = 0; t4 < 4; ++t4) w[c][t4] = dV4[c * 1024 + 512 + t4 * 128];
-              uint32_t v[32];
-              tmem_ld32(tl + kRCol + 64u * rbuf + c0, v);
-              float x[16];
+              // R = block 0 + block 1: each block dotted in turn (the dots are linear in R)
+#pragma unroll 1
+              for (int blk = 0; blk < 2; ++blk) {
+                uint32_t v[32];
+                tmem_ld32(tl + kRCol + (uint32_t)kRCols * rbuf + 64u * blk + c0, v);
+                float x[16];
 #pragma unroll
-              for (int t = 0; t < 16; ++t) {
-                const float hi = __shfl_sync(0xffffffffu, __uint_as_float(v[16 + t]), lane & 15);
-                x[t] = half ? hi : __uint_as_float(v[t]);
-              }
-              if (act) {
+                for (int t = 0; t < 16; ++t) {
+                  const float hi = __shfl_sync(0xffffffffu, __uint_as_float(v[16 + t]), lane & 15);
+                  x[t] = half ? hi : __uint_as_float(v[t]);
+                }
+                if (act) {
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                  float s = 0.f;
+                  for (int c = 0; c < 3; ++c) {
+                    float s = 0.f;
 #pragma unroll
-                  for (int t4 = 0; t4 < 4; ++t4) {
-                    s = fmaf(w[c][t4].x, x[4 * t4], s);
-                    s = fmaf(w[c][t4].y, x[4 * t4 + 1], s);
-                    s = fmaf(w[c][t4].z, x[4 * t4 + 2], s);
-                    s = fmaf(w[c][t4].w, x[4 * t4 + 3], s);
+                    for (int t4 = 0; t4 < 4; ++t4) {
+                      s = fmaf(w[c][t4].x, x[4 * t4], s);
+                      s = fmaf(w[c][t4].y, x[4 * t4 + 1], s);
+                      s = fmaf(w[c][t4].z, x[4 * t4 + 2], s);
+                      s = fmaf(w[c][t4].w, x[4 * t4 + 3], s);
+                    }
+                    gv[c] += s;
                   }
-                  gv[c] += s;
                 }
               }
             }
