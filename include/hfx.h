@@ -297,7 +297,8 @@ typedef struct {
   int t1_home_order;       /* chosen order of the first product's items: 0 = longest
                               first, 1 = by home atom */
   int y_tiles_per_cta;     /* chosen 128-row tiles per CTA of the tcgen05 Y build (1 or 2) */
-  int q2_tiles_per_cta;    /* chosen 128-row tiles per CTA of the tcgen05 Q2 GEMM (1 or 2) */
+  int q2_tiles_per_cta;    /* chosen shape of the tcgen05 Q2 GEMM: 1 or 2 row tiles of 128 per CTA,
+                              or 3 = two tiles, one CTA per SM with a deeper copy pipeline */
 } hfx_tune_report;
 hfx_status hfx_plan_autotune(hfx_plan* plan, const double* lattice, const double* positions, int reps,
                              hfx_tune_report* report);

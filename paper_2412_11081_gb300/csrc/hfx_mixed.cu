@@ -773,15 +773,19 @@ __device__ __forceinline__ void stage_d(int lane, uint16_t* stB, const int* md, 
 // of 2 NP for one, in 3 stages (2 with NP = 3, so that two CTAs still fit an
 // SM), one accumulator per tile (no double buffer; two CTAs per SM overlap
 // one's epilogue with the other's MMAs) and 512 pairs of metadata; TPC = 1
-// keeps 4 stages and two accumulators.
-template <int NP, int TPC>
+// keeps 4 stages and two accumulators.  DEEP = 1 (with TPC = 2) runs one
+// CTA per SM instead: 5 stages (6 with NP = 2) to cover the copies' latency
+// and two accumulators per tile (all 512 tensor-memory columns), so the
+// epilogue of one run overlaps the next run's MMAs within the CTA.
+template <int NP, int TPC, int DEEP = 0>
 struct Q2Shape {
-  static constexpr int kS = TPC == 2 ? (NP == 2 ? 3 : 2) : umma::kStages;   // stages
+  static constexpr int kS = DEEP ? (NP == 2 ? 6 : 5) : TPC == 2 ? (NP == 2 ? 3 : 2) : umma::kStages;   // stages
   static constexpr int kMP = TPC == 2 ? 512 : umma::kMetaPairs;    // pairs per CTA segment
-  static constexpr int kNB = TPC == 2 ? 1 : 2;                     // accumulator buffers
+  static constexpr int kNB = TPC == 2 && !DEEP ? 1 : 2;            // accumulator buffers
+  static constexpr int kCols = kNB * TPC * 128;                    // tensor-memory columns
 };
 
-template <int NP, int TPC>
+template <int NP, int TPC, int DEEP>
 __global__ void __launch_bounds__(192) k_q2_umma(DevPlan P, MixPlan X, const int* list, const long long* slot0,
                                                  int n_slots, int a0, int a1, int FC8, int MC, int NSEG,
                                                  long long zblk, int flush, const __grid_constant__ DRows drows,
@@ -793,7 +797,8 @@ __global__ void __launch_bounds__(192) k_q2_umma(DevPlan P, MixPlan X, const int
   // the accumulators (each its 32-lane quarter of tensor memory) and dot
   // them with grad C_AF.  No block barrier inside the pipeline.
   using namespace umma;
-  constexpr int KS = Q2Shape<NP, TPC>::kS, KMP = Q2Shape<NP, TPC>::kMP, NB = Q2Shape<NP, TPC>::kNB;
+  constexpr int KS = Q2Shape<NP, TPC, DEEP>::kS, KMP = Q2Shape<NP, TPC, DEEP>::kMP, NB = Q2Shape<NP, TPC, DEEP>::kNB;
+  constexpr int TCOLS = Q2Shape<NP, TPC, DEEP>::kCols;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   uint16_t* stA = reinterpret_cast<uint16_t*>(smem_raw);                  // [KS][TPC][NP][kTileElems]
   uint16_t* stB = stA + (size_t)KS * TPC * NP * kTileElems;               // [KS][NP][kTileElems]
@@ -855,7 +860,7 @@ __global__ void __launch_bounds__(192) k_q2_umma(DevPlan P, MixPlan X, const int
   }
   if (warp == 1) {
     const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&tmem_base);
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(dst), "r"(256));   // NB * TPC * 128
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(dst), "r"(TCOLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -1012,7 +1017,7 @@ __global__ void __launch_bounds__(192) k_q2_umma(DevPlan P, MixPlan X, const int
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(256));
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(TCOLS));
   if (tid < 24) {
     const int i = tid / 3, c = tid % 3;
     if (qf[i] >= 0 && sg[i][c] != 0.0) dev::add_gC(P, 3 * qf[i] + c, -2.0 * sg[i][c]);
@@ -1428,8 +1433,9 @@ size_t ybuild_umma_smem(int np, int tpc) {
 }
 
 size_t q2_umma_smem(int np, int tpc) {
-  if (tpc == 2) {
-    const int ks = np == 2 ? Q2Shape<2, 2>::kS : Q2Shape<3, 2>::kS;
+  if (tpc >= 2) {   // 3: two tiles, the deep pipeline
+    const int ks = tpc == 3 ? (np == 2 ? Q2Shape<2, 2, 1>::kS : Q2Shape<3, 2, 1>::kS)
+                            : (np == 2 ? Q2Shape<2, 2>::kS : Q2Shape<3, 2>::kS);
     return (size_t)ks * 3 * np * umma::kTileElems * sizeof(uint16_t) + (size_t)Q2Shape<2, 2>::kMP * 8 * sizeof(int);
   }
   return (size_t)2 * Q2Shape<2, 1>::kS * np * umma::kTileElems * sizeof(uint16_t) +
@@ -1449,7 +1455,7 @@ long long ytab_size(int ngroups, int maxC) { return (long long)ngroups * 8 * max
 long long q2tab_size(int n_slots, int FC) { return (long long)n_slots * ((FC * 4 + 7) / 8) * 8; }
 
 int q2_umma_segments(int max_pairs_per_atom, int np, int tpc) {
-  const int kmp = tpc == 2 ? Q2Shape<2, 2>::kMP : Q2Shape<2, 1>::kMP;
+  const int kmp = tpc >= 2 ? Q2Shape<2, 2>::kMP : Q2Shape<2, 1>::kMP;
   return (max_pairs_per_atom + kmp - 1) / kmp;
 }
 
@@ -1518,11 +1524,12 @@ size_t term2_mma_smem(int np, int MAmax, int KZmax) {
 }
 
 cudaError_t set_mixed_smem_limits(int np) {
-  const void* f[6] = {
+  const void* f[7] = {
       np == 2 ? (const void*)k_ybuild_umma<2, 2> : (const void*)k_ybuild_umma<3, 2>,
       np == 2 ? (const void*)k_ybuild_umma<2, 1> : (const void*)k_ybuild_umma<3, 1>,
-      np == 2 ? (const void*)k_q2_umma<2, 2> : (const void*)k_q2_umma<3, 2>,
-      np == 2 ? (const void*)k_q2_umma<2, 1> : (const void*)k_q2_umma<3, 1>,
+      np == 2 ? (const void*)k_q2_umma<2, 2, 0> : (const void*)k_q2_umma<3, 2, 0>,
+      np == 2 ? (const void*)k_q2_umma<2, 2, 1> : (const void*)k_q2_umma<3, 2, 1>,
+      np == 2 ? (const void*)k_q2_umma<2, 1, 0> : (const void*)k_q2_umma<3, 1, 0>,
       np == 2 ? (const void*)k_term1_mma<2> : (const void*)k_term1_mma<3>,
       np == 2 ? (const void*)k_term2_pairs<2> : (const void*)k_term2_pairs<3>};
   for (const void* k : f) {
@@ -1551,27 +1558,24 @@ cudaError_t launch_term2_mma(const DevPlan& P, const MixPlan& X, int np, const i
   g_mix_launches += pairs_done ? 2 : 3;
   const int FC8 = (FC * 4 + 7) / 8;     // groups of 8 C slots for the tcgen05 kernel
   k_q2tab<<<grid_for(((long long)n * FC8 * 8 + 255) / 256, 152 * 16), 256, 0, s>>>(P, X, list, n, FC8);
-  const int tpc = X.q2tpc == 1 ? 1 : 2;
-  const size_t sq = q2_umma_smem(np, tpc);
+  const int tpc = X.q2tpc == 1 ? 1 : 2, deep = X.q2tpc == 3 ? 1 : 0;   // row tiles per CTA; the deep pipeline
+  const size_t sq = q2_umma_smem(np, X.q2tpc == 1 ? 1 : (deep ? 3 : 2));
   const long long grid = (long long)(a1 - a0) * FC8 * ((MC + tpc - 1) / tpc) * nseg;
+  auto q2 = [&](auto kern) {
+    kern<<<(unsigned)grid, 192, sq, s>>>(P, X, list, slot0, n, a0, a1, FC8, MC, nseg, zblk, flush, drows, err);
+  };
   if (np == 2) {
     if (!pairs_done)
       k_term2_pairs<2><<<grid_for(n, 152 * 32), kWarps * 32, smem, s>>>(P, X, list, n, MAmax, KZmax, zblk, zrows);
-    if (tpc == 2)
-      k_q2_umma<2, 2><<<(unsigned)grid, 192, sq, s>>>(P, X, list, slot0, n, a0, a1, FC8, MC, nseg, zblk, flush, drows,
-                                                      err);
-    else
-      k_q2_umma<2, 1><<<(unsigned)grid, 192, sq, s>>>(P, X, list, slot0, n, a0, a1, FC8, MC, nseg, zblk, flush, drows,
-                                                      err);
+    if (tpc == 1) q2(k_q2_umma<2, 1, 0>);
+    else if (deep) q2(k_q2_umma<2, 2, 1>);
+    else q2(k_q2_umma<2, 2, 0>);
   } else {
     if (!pairs_done)
       k_term2_pairs<3><<<grid_for(n, 152 * 32), kWarps * 32, smem, s>>>(P, X, list, n, MAmax, KZmax, zblk, zrows);
-    if (tpc == 2)
-      k_q2_umma<3, 2><<<(unsigned)grid, 192, sq, s>>>(P, X, list, slot0, n, a0, a1, FC8, MC, nseg, zblk, flush, drows,
-                                                      err);
-    else
-      k_q2_umma<3, 1><<<(unsigned)grid, 192, sq, s>>>(P, X, list, slot0, n, a0, a1, FC8, MC, nseg, zblk, flush, drows,
-                                                      err);
+    if (tpc == 1) q2(k_q2_umma<3, 1, 0>);
+    else if (deep) q2(k_q2_umma<3, 2, 1>);
+    else q2(k_q2_umma<3, 2, 0>);
   }
   return cudaGetLastError();
 }

@@ -35,7 +35,7 @@ def test_autotune_keeps_results_and_picks_the_fastest(case, prec):
         assert 0 < rep["best_ms"] <= rep["default_ms"]
         assert rep["t1_rows_per_slot"] >= 1 and rep["t1_slots"] >= 2
         assert rep["t1_home_order"] in (0, 1)
-        assert rep["y_tiles_per_cta"] in (1, 2) and rep["q2_tiles_per_cta"] in (1, 2)
+        assert rep["y_tiles_per_cta"] in (1, 2) and rep["q2_tiles_per_cta"] in (1, 2, 3)
         assert rep["candidates"] >= 4   # ring shapes, item order, two tile counts
         E1, F1, S1 = p.evaluate(w.lattice, w.positions)
     assert abs(E1 - E0) <= 1e-12 * abs(E0) and rel(F1, F0) <= 1e-12 and rel(S1, S0) <= 1e-12
@@ -43,19 +43,21 @@ def test_autotune_keeps_results_and_picks_the_fastest(case, prec):
 
 @pytest.mark.parametrize("prec", [hfx.HFX_BF16X6, hfx.HFX_BF16X3])
 @pytest.mark.parametrize("case", ["si8", "two_species"])
-def test_one_row_tile_per_cta_equals_two(case, prec, monkeypatch):
+@pytest.mark.parametrize("shape", ["1", "3"])
+def test_one_row_tile_per_cta_equals_two(case, prec, shape, monkeypatch):
     """The Y build and the Q2 GEMM with one 128-row tile per CTA (more stages,
-    two accumulators) give the results of two tiles per CTA: each tile runs
+    two accumulators), and the Q2 GEMM with two tiles in one CTA per SM and
+    a deeper pipeline (shape 3), give the results of two tiles per CTA: each tile runs
     the same K steps in the same order."""
     w = inputs.si_supercell(1) if case == "si8" else two_species()
     with hfx.Plan(w, precision=prec) as p:
         ref = p.evaluate(w.lattice, w.positions)
     monkeypatch.setenv("HFX_Y_TILES", "1")
-    monkeypatch.setenv("HFX_Q2_TILES", "1")
+    monkeypatch.setenv("HFX_Q2_TILES", shape)
     with hfx.Plan(w, precision=prec) as p:
         got = p.evaluate(w.lattice, w.positions)
         rep = p.autotune(w.lattice, w.positions, reps=1)
-        assert rep["y_tiles_per_cta"] in (1, 2) and rep["q2_tiles_per_cta"] in (1, 2)
+        assert rep["y_tiles_per_cta"] in (1, 2) and rep["q2_tiles_per_cta"] in (1, 2, 3)
     assert abs(got[0] - ref[0]) <= 1e-12 * abs(ref[0])
     assert rel(got[1], ref[1]) <= 1e-12 and rel(got[2], ref[2]) <= 1e-12
 
