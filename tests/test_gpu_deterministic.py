@@ -27,14 +27,20 @@ def same_bits(x, y):
 
 
 CASES = [
-    ("diamond8 fp64", inputs.diamond8, hfx.HFX_FP64),
-    ("si8 bf16x6", lambda: inputs.si_supercell(1), hfx.HFX_BF16X6),
-    ("perovskite bf16x6 wide", lambda: inputs.perovskite_supercell(1), hfx.HFX_BF16X6),
+    ("diamond8 fp64", inputs.diamond8, hfx.HFX_FP64, {}),
+    ("si8 bf16x6", lambda: inputs.si_supercell(1), hfx.HFX_BF16X6, {}),
+    # the warp-level first product and R2 / Z kernels (their shared-memory
+    # partial sums go straight into the exact cells)
+    ("si8 bf16x6 warp-level", lambda: inputs.si_supercell(1), hfx.HFX_BF16X6,
+     {"HFX_T1_KERNEL": "mma", "HFX_T2_KERNEL": "mma"}),
+    ("perovskite bf16x6 wide", lambda: inputs.perovskite_supercell(1), hfx.HFX_BF16X6, {}),
 ]
 
 
-@pytest.mark.parametrize("name,make,prec", CASES, ids=[c[0] for c in CASES])
-def test_same_bits_for_any_split_or_order(name, make, prec):
+@pytest.mark.parametrize("name,make,prec,env", CASES, ids=[c[0] for c in CASES])
+def test_same_bits_for_any_split_or_order(name, make, prec, env, monkeypatch):
+    for k, v in env.items():
+        monkeypatch.setenv(k, v)
     w = make()
     pos = inputs.geometry_sequence(w, 2, seed=11)[1]
     with hfx.Plan(w, precision=prec) as p:
