@@ -295,7 +295,7 @@ typedef struct {
   double default_ms;       /* median evaluation time with the initial choice */
   double best_ms;          /* median evaluation time with the chosen one */
   int t1_home_order;       /* chosen order of the first product's items: 0 = longest
-                              first, 1 = by home atom */
+                              first, 1 = by home atom, 2 = by the atom F of the item (A,F) */
   int y_tiles_per_cta;     /* chosen 128-row tiles per CTA of the tcgen05 Y build (1 or 2) */
   int q2_tiles_per_cta;    /* chosen shape of the tcgen05 Q2 GEMM: 1 or 2 row tiles of 128 per CTA,
                               or 3 = two tiles, one CTA per SM with a deeper copy pipeline */

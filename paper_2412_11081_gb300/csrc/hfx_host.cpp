@@ -200,7 +200,7 @@ struct hfx_plan {
   long long *qoff = nullptr, *q_idx = nullptr;
   int* t1q_list = nullptr;
   int* t1q_lpt = nullptr;      // the same items, longest (most kept B) first
-  bool t1_home_order = false;  // first-product items in home-atom order instead of longest first
+  int t1_order = 0;            // first-product items: 0 longest first, 1 home-atom (list) order, 2 by F
   int ybtpc = 2, q2tpc = 2;    // 128-row tiles per CTA of the tcgen05 Y build and Q2 GEMM (autotuner);
                                // q2tpc = 3: two tiles, one CTA per SM with the deep pipeline
   int q2_flush = 32;           // pairs per FP32 run of the second product's Q2 accumulator (128 for BF16X6)
@@ -1276,7 +1276,8 @@ void evaluate_launches(hfx_plan* P, const double* L, hfx_stats* st, bool tail) {
         ck(hfx::scan_flags(P->qcnt + c0, nullptr, nullptr, nullptr, 0, nc, P->q_idx + c0, ct + CT_Q, P->scan_tmp, s),
            "scan");
         ck(hfx::scatter_list(P->qcnt + c0, nullptr, nullptr, 0, nc, P->q_idx + c0, P->t1q_list + c0, c0, s), "scatter");
-        ck(hfx::launch_lpt_order(P->qcnt, P->t1q_list + c0, nc, ct + CT_Q, P->lpt_hist, P->t1q_lpt + c0, s),
+        ck(hfx::launch_lpt_order(P->t1_order == 2 ? P->c_j : P->qcnt, P->t1_order == 2 ? 1 : 0, P->t1q_list + c0, nc,
+                                 ct + CT_Q, P->lpt_hist, P->t1q_lpt + c0, s),
            "item order");
       }
     }
@@ -1355,7 +1356,7 @@ void evaluate_launches(hfx_plan* P, const double* L, hfx_stats* st, bool tail) {
   // first-product items: longest first (the last ones handed out are short),
   // or in home-atom order (items running at the same time share their V_AB,
   // grad V_AB in L2); the autotuner picks
-  const int* t1items = P->t1_home_order ? P->t1q_list : P->t1q_lpt;
+  const int* t1items = P->t1_order == 1 ? P->t1q_list : P->t1q_lpt;
   for (int c = 0; c < nch; ++c) {
     const int a0 = P->chunks[c].first, a1 = P->chunks[c].second;
     const int v0 = P->v_ptr_h[a0], c0 = P->c_ptr_h[a0];
@@ -1722,7 +1723,7 @@ hfx_status hfx_plan_autotune(hfx_plan* P, const double* lattice, const double* p
   hfx_tune_report R{};
   R.t1_rows_per_slot = P->t1u_FS;
   R.t1_slots = P->t1u_NS;
-  R.t1_home_order = P->t1_home_order ? 1 : 0;
+  R.t1_home_order = P->t1_order;
   R.y_tiles_per_cta = P->ybtpc;
   R.q2_tiles_per_cta = P->q2tpc;
   if (!P->t1u) {
@@ -1777,21 +1778,23 @@ hfx_status hfx_plan_autotune(hfx_plan* P, const double* lattice, const double* p
     }
   }
   // the order of the items, with the best ring shape
-  const bool order0 = P->t1_home_order;
-  bool best_order = order0;
+  const int order0 = P->t1_order;
+  int best_order = order0;
   if (ok) {
     use(best_fs, best_ns);
-    P->t1_home_order = !order0;
-    double ms = 0.0;
-    ok = time_it(ms);
-    if (ok) {
+    for (int o = 0; o < 3 && ok; ++o) {
+      if (o == order0) continue;
+      P->t1_order = o;
+      double ms = 0.0;
+      ok = time_it(ms);
+      if (!ok) break;
       ++R.candidates;
       if (ms < R.best_ms) {
         R.best_ms = ms;
-        best_order = !order0;
+        best_order = o;
       }
     }
-    P->t1_home_order = best_order;
+    P->t1_order = best_order;
   }
   // then the row tiles per CTA of the Y build and of the Q2 GEMM, one at a time
   const int yb0 = P->ybtpc, q20 = P->q2tpc;
@@ -1828,7 +1831,7 @@ hfx_status hfx_plan_autotune(hfx_plan* P, const double* lattice, const double* p
   if (!ok) {   // keep the initial choice
     use(fs0, ns0);
     P->smem_t1u = smem0;
-    P->t1_home_order = order0;
+    P->t1_order = order0;
     P->ybtpc = yb0;
     P->q2tpc = q20;
     return status;
@@ -1836,7 +1839,7 @@ hfx_status hfx_plan_autotune(hfx_plan* P, const double* lattice, const double* p
   use(best_fs, best_ns);
   R.t1_rows_per_slot = best_fs;
   R.t1_slots = best_ns;
-  R.t1_home_order = best_order ? 1 : 0;
+  R.t1_home_order = best_order;
   R.y_tiles_per_cta = P->ybtpc;
   R.q2_tiles_per_cta = P->q2tpc;
   if (report) *report = R;

@@ -261,12 +261,14 @@ long long t1u_launch_count();
 size_t t1u_smem(int np, int KP, int NS, int FS);
 // Columns of one FP32 plane of C / grad C in the operand store (KP rounded up to 32).
 __host__ __device__ inline int t1u_kp32(int KP) { return (KP + 31) & ~31; }
-// Items of the first product in longest-first order: list[0..*n) (n read on
-// the device) sorted by decreasing qcnt[list[i]] (counting sort over
-// kLptBuckets buckets; keys at or above the last bucket share it).
+// Items of the first product in a chosen order: list[0..*n) (n read on the
+// device) sorted by decreasing key[list[i]] (asc = 0: key = qcnt, longest
+// first) or increasing key[list[i]] (asc = 1: key = the C pairs' atom F);
+// counting sort over kLptBuckets buckets, keys at or above the last bucket
+// share it.
 constexpr int kLptBuckets = 4096;
-cudaError_t launch_lpt_order(const int* qcnt, const int* list, int n_max, const long long* n_dev, int* hist, int* out,
-                             cudaStream_t s);
+cudaError_t launch_lpt_order(const int* key, int asc, const int* list, int n_max, const long long* n_dev, int* hist,
+                             int* out, cudaStream_t s);
 int t1u_max_slots();
 cudaError_t t1u_set_smem(int np);
 // Needed V pairs: the second product's V store (MixPlan::Vm) and, with U.Vu

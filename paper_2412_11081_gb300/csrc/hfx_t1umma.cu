@@ -238,12 +238,19 @@ __global__ void k_t1u_dstore(DevPlan P, float* Df) {
 // ------------------------------------------------- longest-first item order
 // Items run on a dynamic queue; handing out the ones with the most kept B
 // first keeps the last items short, so the SMs finish together.  Counting
-// sort on the key (kLptBuckets - 1 - min(qcnt, kLptBuckets - 1)); the order
-// of equal keys is not fixed (it does not change any item's result).
-__global__ void k_lpt_hist(const int* qcnt, const int* list, const long long* n_dev, int* hist) {
+// sort on the bucket (kLptBuckets - 1 - min(qcnt, kLptBuckets - 1)); the
+// order of equal keys is not fixed (it does not change any item's result).
+// With asc = 1 the same sort orders the items by key[q] ascending (the
+// order by F: items of one F, which share many Y^{BF} blocks, run together).
+__device__ __forceinline__ int lpt_bucket(const int* key, int q, int asc) {
+  const int k = min(key[q], kLptBuckets - 1);
+  return asc ? k : kLptBuckets - 1 - k;
+}
+
+__global__ void k_lpt_hist(const int* key, int asc, const int* list, const long long* n_dev, int* hist) {
   const int n = (int)*n_dev;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    atomicAdd(&hist[kLptBuckets - 1 - min(qcnt[list[i]], kLptBuckets - 1)], 1);
+    atomicAdd(&hist[lpt_bucket(key, list[i], asc)], 1);
 }
 
 // Exclusive scan of the histogram, one block of 1024 threads.
@@ -272,11 +279,11 @@ __global__ void __launch_bounds__(1024) k_lpt_scan(int* hist) {
   }
 }
 
-__global__ void k_lpt_scatter(const int* qcnt, const int* list, const long long* n_dev, int* hist, int* out) {
+__global__ void k_lpt_scatter(const int* key, int asc, const int* list, const long long* n_dev, int* hist, int* out) {
   const int n = (int)*n_dev;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const int q = list[i];
-    out[atomicAdd(&hist[kLptBuckets - 1 - min(qcnt[q], kLptBuckets - 1)], 1)] = q;
+    out[atomicAdd(&hist[lpt_bucket(key, q, asc)], 1)] = q;
   }
 }
 
@@ -1298,16 +1305,16 @@ cudaError_t launch_t1u_stores(const DevPlan& P, const T1UPlan& U, int np, const 
   return cudaGetLastError();
 }
 
-cudaError_t launch_lpt_order(const int* qcnt, const int* list, int n_max, const long long* n_dev, int* hist, int* out,
-                             cudaStream_t s) {
+cudaError_t launch_lpt_order(const int* key, int asc, const int* list, int n_max, const long long* n_dev, int* hist,
+                             int* out, cudaStream_t s) {
   if (n_max <= 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(hist, 0, kLptBuckets * sizeof(int), s);
   if (e != cudaSuccess) return e;
   g_t1u_launches += 3;
   const int g = std::min((n_max + 255) / 256, 152 * 8);
-  k_lpt_hist<<<g, 256, 0, s>>>(qcnt, list, n_dev, hist);
+  k_lpt_hist<<<g, 256, 0, s>>>(key, asc, list, n_dev, hist);
   k_lpt_scan<<<1, 1024, 0, s>>>(hist);
-  k_lpt_scatter<<<g, 256, 0, s>>>(qcnt, list, n_dev, hist, out);
+  k_lpt_scatter<<<g, 256, 0, s>>>(key, asc, list, n_dev, hist, out);
   return cudaGetLastError();
 }
 
