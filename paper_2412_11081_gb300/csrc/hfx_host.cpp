@@ -243,6 +243,7 @@ struct hfx_plan {
   int wide_RB = 0;             // 64-row blocks of the largest Y block
   int wide_maxrows = 0;        // most rows (alpha, a) of a C block
   uint16_t* Cw = nullptr;      // C pieces of every C pair (written per call)
+  float* dCf = nullptr;        // grad C of every C pair in FP32, the layout of dCst (written per call)
   long long* cw_off = nullptr;
   uint16_t* Zw = nullptr;      // Z^{AB} of one pass's second-product pairs (bf16 pieces)
   long long Zwcap = 0;
@@ -825,6 +826,7 @@ void build_lists(hfx_plan* P, const double* L, const double* pos) {
     }
     P->cw_off = P->lalloc<long long>(nC + 1);
     P->Cw = P->lalloc<uint16_t>(std::max(1LL, cw_off[nC]));
+    P->dCf = P->lalloc<float>(std::max(1LL, 3 * c_off[nC]));
     upload(P->cw_off, cw_off, s);
   }
   if (P->np) {   // key groups of the Y build
@@ -1304,7 +1306,7 @@ void evaluate_launches(hfx_plan* P, const double* L, hfx_stats* st, bool tail) {
     ck(hfx::launch_ybuild(D, P->y_list, (int)P->tot[1], s), "ybuild");
   } else if (P->wide) {
     ensure_buf(P, P->Ysp, P->Yspcap, std::max(1LL, P->tot[0]));
-    ck(hfx::launch_cpieces_w(D, P->np, P->Cw, P->cw_off, s), "C pieces");
+    ck(hfx::launch_cpieces_w(D, P->np, P->Cw, P->cw_off, P->dCf, s), "C pieces");
     ck(hfx::launch_ybuild_w(D, P->np, P->Ysp, P->Cw, P->cw_off, P->Dw, P->dw_off, P->y_list, P->gX, P->gS, P->gN,
                             (int)P->tot[9], P->wide_RB, s),
        "ybuild");
@@ -1368,7 +1370,7 @@ void evaluate_launches(hfx_plan* P, const double* L, hfx_stats* st, bool tail) {
       ck(hfx::launch_vblocks(D, P->v_list + v0, (int)ct[CT_VN], s), "vblocks");
       k1a.push_back(tm.mark());
       if (P->wide)
-        ck(hfx::launch_term1_w(D, P->np, P->Ysp, P->Cw, P->cw_off, P->Dw, P->dw_off, P->t1_list + v0,
+        ck(hfx::launch_term1_w(D, P->np, P->Ysp, P->Cw, P->cw_off, P->Dw, P->dw_off, P->dCf, P->t1_list + v0,
                                (int)ct[CT_T1], P->ws, s),
            "term1");
       else

@@ -298,13 +298,14 @@ int wide_ybuild_row_blocks(int max_rows);
 cudaError_t set_wide_smem_limits(int np);
 // C pieces: per kept C pair, NP planes [alpha][rup8(n_ao(A) n_ao(F))] at Cw + cw_off[q]
 long long wide_cpieces_size(int np, int n_abf, int n_ao_a, int n_ao_f);
-cudaError_t launch_cpieces_w(const DevPlan& P, int np, uint16_t* Cw, const long long* cw_off, cudaStream_t s);
+cudaError_t launch_cpieces_w(const DevPlan& P, int np, uint16_t* Cw, const long long* cw_off, float* dCf,
+                             cudaStream_t s);
 cudaError_t launch_ybuild_w(const DevPlan& P, int np, uint16_t* Yp, const uint16_t* Cw, const long long* cw_off,
                             const uint16_t* Dw, const long long* dw_off, const int* ylist, const int* gX,
                             const int* gS, const int* gN, int ngroups, int RB, cudaStream_t s);
 cudaError_t launch_term1_w(const DevPlan& P, int np, const uint16_t* Yp, const uint16_t* Cw, const long long* cw_off,
-                           const uint16_t* Dw, const long long* dw_off, const int* list, int n, const WideShapes& w,
-                           cudaStream_t s);
+                           const uint16_t* Dw, const long long* dw_off, const float* dCf, const int* list, int n,
+                           const WideShapes& w, cudaStream_t s);
 // elements per bf16 piece plane of one pair slot of the Z store (rows (alpha, a), row stride KZ)
 long long wide_zplane(int max_rows, int KZ);
 // bf16 pieces of every D block (fixed for the plan): NP planes of

@@ -174,8 +174,11 @@ __global__ void k_dsplit_w(DevPlan P, uint16_t* Dw, const long long* dw_off) {
 // a 16-byte boundary).
 __host__ __device__ inline int cw_cols(int nA, int nF) { return (nA * nF + 7) & ~7; }
 
+// ... and grad C in FP32 (dCf, the layout of P.dCst), which the first
+// product's Q epilogue reads in MMA-fragment order: half the bytes of the
+// FP64 blocks, and the same values (the epilogue rounds to FP32 anyway).
 template <int NP>
-__global__ void k_cpieces_w(DevPlan P, uint16_t* Cw, const long long* cw_off) {
+__global__ void k_cpieces_w(DevPlan P, uint16_t* Cw, const long long* cw_off, float* dCf) {
   for (int q = blockIdx.x; q < P.nC; q += gridDim.x) {
     if (!P.c_keep[q]) continue;
     const int sA = P.species[P.c_home[q]], sF = P.species[P.c_j[q]];
@@ -192,6 +195,9 @@ __global__ void k_cpieces_w(DevPlan P, uint16_t* Cw, const long long* cw_off) {
       const int r = e / KW, c = e - r * KW;
       put_pieces<NP>(cy, (long long)mA * nA * KW, e, c < nF ? (float)src[(long long)r * nF + c] : 0.f);
     }
+    const double* dsrc = P.dCst + 3 * P.c_off[q];
+    float* dst = dCf + 3 * P.c_off[q];
+    for (int e = threadIdx.x; e < 3 * mA * naf; e += blockDim.x) dst[e] = (float)dsrc[e];
   }
 }
 
@@ -386,7 +392,8 @@ template <int NP>
 __global__ void __launch_bounds__(kPW * 32, 1) k_term1_w(DevPlan P, const uint16_t* __restrict__ Yp,
                                                        const uint16_t* __restrict__ Cw, const long long* cw_off,
                                                        const uint16_t* __restrict__ Dw, const long long* dw_off,
-                                                       const int* list, int n_list, T1W S) {
+                                                       const float* __restrict__ dCf, const int* list, int n_list,
+                                                       T1W S) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[4 * kPW];
   __shared__ double s_g[3];
@@ -484,7 +491,7 @@ __global__ void __launch_bounds__(kPW * 32, 1) k_term1_w(DevPlan P, const uint16
         const int CW = cw_cols(nA, nF);
         const uint16_t* C = Cw + cw_off[q];             // NP planes [alpha][(a, f)] (row length CW)
         const long long cplane = (long long)mA * CW;
-        const double* dC = P.dCst + 3 * P.c_off[q];
+        const float* dC = dCf + 3 * P.c_off[q];   // grad C_AF in FP32 (k_cpieces_w)
         const long long nc = (long long)mA * nA * nF;
         const int rowsU = mB * nF;
         float gq[3] = {0.f, 0.f, 0.f};
@@ -1095,11 +1102,12 @@ cudaError_t set_wide_smem_limits(int np) {
   return e;
 }
 
-cudaError_t launch_cpieces_w(const DevPlan& P, int np, uint16_t* Cw, const long long* cw_off, cudaStream_t s) {
+cudaError_t launch_cpieces_w(const DevPlan& P, int np, uint16_t* Cw, const long long* cw_off, float* dCf,
+                             cudaStream_t s) {
   if (P.nC <= 0) return cudaSuccess;
   const int grid = grid_cap(P.nC, 1 << 16);
-  if (np == 2) k_cpieces_w<2><<<grid, 256, 0, s>>>(P, Cw, cw_off);
-  else k_cpieces_w<3><<<grid, 256, 0, s>>>(P, Cw, cw_off);
+  if (np == 2) k_cpieces_w<2><<<grid, 256, 0, s>>>(P, Cw, cw_off, dCf);
+  else k_cpieces_w<3><<<grid, 256, 0, s>>>(P, Cw, cw_off, dCf);
   ++g_wide_launches;
   return cudaGetLastError();
 }
@@ -1123,13 +1131,13 @@ cudaError_t launch_ybuild_w(const DevPlan& P, int np, uint16_t* Yp, const uint16
 }
 
 cudaError_t launch_term1_w(const DevPlan& P, int np, const uint16_t* Yp, const uint16_t* Cw, const long long* cw_off,
-                           const uint16_t* Dw, const long long* dw_off, const int* list, int n, const WideShapes& w,
-                           cudaStream_t s) {
+                           const uint16_t* Dw, const long long* dw_off, const float* dCf, const int* list, int n,
+                           const WideShapes& w, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   const T1W S{w.MA, w.MB, w.t1_KC, w.t1_da};
   const int grid = grid_cap(n, 1 << 20);
-  if (np == 2) k_term1_w<2><<<grid, kPW * 32, w.smem_t1, s>>>(P, Yp, Cw, cw_off, Dw, dw_off, list, n, S);
-  else k_term1_w<3><<<grid, kPW * 32, w.smem_t1, s>>>(P, Yp, Cw, cw_off, Dw, dw_off, list, n, S);
+  if (np == 2) k_term1_w<2><<<grid, kPW * 32, w.smem_t1, s>>>(P, Yp, Cw, cw_off, Dw, dw_off, dCf, list, n, S);
+  else k_term1_w<3><<<grid, kPW * 32, w.smem_t1, s>>>(P, Yp, Cw, cw_off, Dw, dw_off, dCf, list, n, S);
   ++g_wide_launches;
   return cudaGetLastError();
 }
