@@ -1381,7 +1381,7 @@ void evaluate_launches(hfx_plan* P, const double* L, hfx_stats* st, bool tail) {
       if (P->wide) {
         ensure_buf(P, P->Zw, P->Zwcap,
                    std::max(1LL, ct[CT_T2]) * P->np * hfx::wide_zplane(P->wide_maxrows, P->ws.KZ));
-        ck(hfx::launch_term2_w(D, P->np, P->Ysp, P->Zw, P->Dw, P->dw_off, P->t2_list + v0, P->t2_idx, (int)ct[CT_T2],
+        ck(hfx::launch_term2_w(D, P->np, P->Ysp, P->Zw, P->Dw, P->dw_off, P->dCf, P->t2_list + v0, P->t2_idx, (int)ct[CT_T2],
                                a0, a1, P->wide_maxrows, P->maxC, P->ws, s),
            "term2");
       } else

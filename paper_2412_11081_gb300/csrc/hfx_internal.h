@@ -314,8 +314,8 @@ cudaError_t launch_dsplit_w(const DevPlan& P, int np, uint16_t* Dw, const long l
 // Second product of the home atoms [a0, a1): k_term2_w over the pass's pair
 // list (E, g^V and the Z piece store), then k_q2_w (grad C); slot0 as launch_term2_mma.
 cudaError_t launch_term2_w(const DevPlan& P, int np, const uint16_t* Yp, uint16_t* Zw, const uint16_t* Dw,
-                           const long long* dw_off, const int* list, const long long* slot0, int n, int a0, int a1,
-                           int max_rows, int max_c, const WideShapes& w, cudaStream_t s);
+                           const long long* dw_off, const float* dCf, const int* list, const long long* slot0, int n,
+                           int a0, int a1, int max_rows, int max_c, const WideShapes& w, cudaStream_t s);
 
 // Exclusive scan helpers.  `mode` selects what is summed per element i:
 //   0: flag[i] != 0 (int32 flags)

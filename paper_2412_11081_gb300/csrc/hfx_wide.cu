@@ -848,7 +848,7 @@ __global__ void __launch_bounds__(kQ2Threads, 1) k_q2_w(DevPlan P, const uint16_
                                                         int KZ, const uint16_t* __restrict__ Dw,
                                                         const long long* __restrict__ dw_off, const int* list,
                                                         const long long* slot0, int n_slots, int a0, int a1, int RBQ,
-                                                        int SG) {
+                                                        int SG, const float* __restrict__ dCf) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int m_dw[kQ2Seg][kQ2Slots];   // D piece block of (pair, slot) in 256-element units, or -1
   __shared__ int m_step[kQ2Seg];
@@ -903,7 +903,7 @@ __global__ void __launch_bounds__(kQ2Threads, 1) k_q2_w(DevPlan P, const uint16_
     for (int i = 0; i < 4; ++i) {
       if (!live4[i]) continue;
       const int nF = nf4[i];
-      const double* dC = P.dCst + 3 * P.c_off[s_q[4 * sh + i]];
+      const float* dC = dCf + 3 * P.c_off[s_q[4 * sh + i]];   // grad C_AF in FP32 (k_cpieces_w)
       const long long nc = (long long)rows * nF;
       float g[3] = {0.f, 0.f, 0.f};
 #pragma unroll
@@ -1154,8 +1154,8 @@ cudaError_t launch_dsplit_w(const DevPlan& P, int np, uint16_t* Dw, const long l
 }
 
 cudaError_t launch_term2_w(const DevPlan& P, int np, const uint16_t* Yp, uint16_t* Zw, const uint16_t* Dw,
-                           const long long* dw_off, const int* list, const long long* slot0, int n, int a0, int a1,
-                           int max_rows, int max_c, const WideShapes& w, cudaStream_t s) {
+                           const long long* dw_off, const float* dCf, const int* list, const long long* slot0, int n,
+                           int a0, int a1, int max_rows, int max_c, const WideShapes& w, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   const T2W S{w.MA, w.MB, w.t2_KC, w.t2_da, w.KZ, wide_zplane(max_rows, w.KZ)};
   const int grid = grid_cap(n, 1 << 20);
@@ -1169,10 +1169,10 @@ cudaError_t launch_term2_w(const DevPlan& P, int np, const uint16_t* Yp, uint16_
   if (qgrid <= 0) return cudaSuccess;
   if (np == 2)
     k_q2_w<2><<<(unsigned)qgrid, kQ2Threads, w.smem_q2, s>>>(P, Zw, S.zplane, w.KZ, Dw, dw_off, list, slot0, n, a0, a1,
-                                                             RBQ, SG);
+                                                             RBQ, SG, dCf);
   else
     k_q2_w<3><<<(unsigned)qgrid, kQ2Threads, w.smem_q2, s>>>(P, Zw, S.zplane, w.KZ, Dw, dw_off, list, slot0, n, a0, a1,
-                                                             RBQ, SG);
+                                                             RBQ, SG, dCf);
   ++g_wide_launches;
   return cudaGetLastError();
 }
