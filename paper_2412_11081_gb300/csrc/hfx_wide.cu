@@ -44,7 +44,7 @@ using namespace dev;
 
 constexpr int kWThreads = 256;   // 8 warps per CTA
 constexpr int kWarpsW = kWThreads / 32;
-constexpr int kFlushF = 4;       // F per FP32 run of R in the first product
+constexpr int kFlushF = 8;       // F per FP32 run of R in the first product
 std::atomic<long long> g_wide_launches{0};
 
 __device__ __forceinline__ int rup8(int x) { return (x + 7) & ~7; }
