@@ -49,6 +49,17 @@ def test_default_options(lib):
     o = hfx.default_options()
     assert o.theta_CS == 1e-10 and o.precision == hfx.HFX_FP64 and o.terms == 3 and o.skin == 0.5
     assert o.home_begin == 0 and o.home_end == 0 and o.home_chunk == 0
+    assert o.graph == 0 and o.deterministic == 0
+    # the binding's copy of hfx_options ends where the C struct does: a
+    # default-filled struct with a canary after it keeps the canary
+    import ctypes as ct
+
+    class Guarded(ct.Structure):
+        _fields_ = [("o", hfx.HfxOptions), ("canary", ct.c_uint64)]
+
+    g = Guarded()
+    g.canary = 0x5A5A5A5A5A5A5A5A
+    assert lib.hfx_default_options(ct.byref(g.o)) == 0 and g.canary == 0x5A5A5A5A5A5A5A5A
     assert lib.hfx_default_options(None) == 1
 
 
