@@ -279,11 +279,14 @@ hfx_status hfx_set_reference(hfx_plan* plan, const double* E, const double* F, c
  * memory): the shapes of the block pairs decide which run length balances
  * the copy of Y rows against the U build; then, with the best shape, the
  * order in which its items are handed out (longest first, so that the SMs
- * finish together, or by home atom, so that items running at the same time
- * share their V_AB and grad V_AB blocks in L2); then the 128-row tiles per
- * CTA of the tcgen05 Y build and of the Q2 GEMM (two tiles share each K
- * step's D blocks; one tile runs more pipeline stages and two accumulators),
- * each kept if it is faster.  Each candidate is timed as the
+ * finish together; by home atom, so that items running at the same time
+ * share their V_AB and grad V_AB blocks in L2; or by the atom F of the item
+ * (A,F), so that they share Y^{BF} blocks); then the 128-row tiles per CTA
+ * of the tcgen05 Y build (two tiles share each K step's D blocks; one tile
+ * runs more pipeline stages and two accumulators) and the shape of the Q2
+ * GEMM (one or two tiles per CTA, or two tiles in one CTA per SM with a
+ * deeper copy pipeline and two accumulators per tile), each kept if it is
+ * faster.  Each candidate is timed as the
  * median of `reps` >= 1 evaluations (CUDA events) after one warm-up.
  * `report` (nullable) receives the choice and both times.  Plans without a
  * tunable kernel (FP64, or the warp-level first product) return HFX_OK
